@@ -1,0 +1,460 @@
+"""Benchmark: batched OPMM estimation on GB300.
+
+One step = one complete fit of the workload's batch (trace gather, box centres,
+persistent parallel Nelder-Mead search, FP64 check), every row of the hot path.
+Default workload: 1,024 synthetic saccades, 65,536 candidates x 30 iterations
+each (the plain batched-search configuration).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batch1024|uneven10k|single10]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  value = candidate OPC simulations per second
+over the whole job (all ranks), inputs resident in HBM; e2e = the same metric
+through the C ABI with host buffers (H2D of traces and D2H of results inside
+the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "OPC candidate sims/s (% FP32 peak); saccades fitted/s at <=0.1 deg RMS; p99 latency"
+FP32_LANES_PER_SM = 128
+RESULT_BYTES = 112
+
+
+# ------------------------------------------------------------------ algorithmic work
+def pow_products(n: int) -> int:
+    """Matrix products of the binary powering of the RK4 step matrix."""
+    if n <= 1:
+        return 0
+    return (n.bit_length() - 1) + (bin(n).count("1") - 1)
+
+
+def flops_per_sim(L: int, onset: int, nsub: int) -> int:
+    """Algorithmic FP32 FLOPs of one candidate simulation + score in the
+    propagator formulation (FMA = 2): parameter map and stiffness guard (46),
+    plant coefficients (24), single-step RK4 increment matrices of both phases
+    (560), binary powering to one sample interval (332 per product),
+    equilibria (68), finish (2), and per integrated sample a 6x6 block update
+    plus the residual term (55).  The pulse-end interval (re-built step matrix,
+    nsub - 1 single-step updates, two split RK4 steps) is not counted."""
+    n_int = max(0, L - 1 - onset)
+    return 46 + 24 + 560 + 332 * pow_products(nsub) + 68 + 2 + 55 * n_int
+
+
+def rk4_stage_flops_per_sim(L: int, nsub: int) -> int:
+    """Same trajectory integrated stage by stage (168 FLOP per RK4 substep)."""
+    return 168 * max(0, L - 1) * nsub
+
+
+def nsub_for(fs: float) -> int:
+    return max(1, int(math.floor(1.0e4 / fs + 0.5)))
+
+
+# ------------------------------------------------------------------ peaks / clocks
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(n_gpus: int):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def dist_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str, rank: int, quick: bool):
+    if name == "batch1024":
+        w = W.batch1024(B=64 if quick else 1024)
+    elif name == "uneven10k":
+        w = W.uneven10k(B=256 if quick else 10000)
+    elif name == "single10":
+        w = W.single10()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if rank > 0 and name != "single10":
+        # weak scaling: every rank fits its own batch of the same size
+        g = W.batch1024 if name == "batch1024" else W.uneven10k
+        full = g(B=w.B * (rank + 1))
+        w = full.subset(np.arange(w.B * rank, w.B * (rank + 1)))
+    return w
+
+
+def workload_config(w, scaling_note: str):
+    return {"workload": w.name, "saccades": int(w.B), "candidates_per_iteration": int(w.candidates),
+            "iterations": int(w.iterations), "simplices_per_saccade": int(w.simplices),
+            "sample_rates_hz": sorted({float(x) for x in w.fs}),
+            "window_samples": [int(w.L.min()), int(w.L.max())],
+            "pulse_init": "calibrated" if w.calibrated_pulse else "table1",
+            "l2": scaling_note}
+
+
+# ------------------------------------------------------------------ our arm
+def gpu_inputs(G, ctx, w):
+    """Traces synthesised on the GPU by the library itself: hidden OPC =
+    centre x multiplier, trajectory by opmm_simulate, plus the seeded noise."""
+    n = w.B
+    descs = G.make_batch([np.zeros(int(L), np.float32) for L in w.L], w.fs, w.onset, w.theta0,
+                         w.thetaf, w.dur_ms)
+    pulse = G.OPMM_PULSE_CALIBRATED if w.calibrated_pulse else G.OPMM_PULSE_TABLE1
+    centre = G.opmm_nominal_opc(ctx, descs, pulse)
+    hidden = (centre.astype(np.float64) * w.mult).astype(np.float32)
+    traj, offs = G.opmm_simulate(ctx, hidden, descs)
+    traces = []
+    for i in range(n):
+        L = int(w.L[i])
+        traces.append((traj[offs[i]:offs[i] + L].astype(np.float64) + w.noise[i]).astype(np.float32))
+    return traces, pulse
+
+
+def packed(traces):
+    offs, o = [], 0
+    for t in traces:
+        offs.append(o)
+        o += (len(t) + 3) // 4 * 4
+    buf = np.zeros(o, np.float32)
+    for t, of in zip(traces, offs):
+        buf[of:of + len(t)] = t
+    return buf, np.array(offs, np.int64)
+
+
+def profile_traffic(kernel_src_hash: str):
+    """DRAM bytes per search launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "search_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha256") == kernel_src_hash:
+            return d
+    except Exception:
+        pass
+    return None
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "plant.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2007_09884_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2007_09884_gb300 as G
+
+    torch.cuda.set_device(local)
+    w = make_workload(args.workload, rank, args.quick)
+    ctx = G.opmm_create(local)
+    stream = torch.cuda.current_stream()
+    G.opmm_set_stream(ctx, stream.cuda_stream)
+    traces, pulse = gpu_inputs(G, ctx, w)
+    buf, offs = packed(traces)
+    dev = torch.from_numpy(buf).cuda()
+    batch_dev = G.make_batch(dev, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms, n_samples=w.L, offsets=offs)
+    opts = dict(candidates=w.candidates, iterations=w.iterations, seed=w.seed, pulse_init=pulse)
+    plan = G.Plan(ctx, batch_dev, **opts)
+    info = plan.info()
+    for _ in range(args.warmup):
+        plan.execute_raw()
+    torch.cuda.synchronize()
+
+    l2_bytes = 256 << 20
+    flush = torch.empty(l2_bytes // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(torch.cuda.current_device())
+    step_ms, search_ms = [], []
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    res = None
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = plan.execute_raw()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        search_ms.append(plan.last_search_ms())
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    barrier(ws)
+    r = G.results_to_numpy(res)
+    evals_rank = float(np.sum(r["evaluations"].astype(np.float64)))
+    fitted_rank = float(np.sum((r["rms_deg"] <= 0.1) & (r["status"] == 0)))
+    total_ms = sum(step_ms)
+    t_max = dist_max(total_ms, ws)
+    evals_all = dist_sum(evals_rank, ws) * args.steps
+    fitted_all = dist_sum(fitted_rank, ws) * args.steps
+    value = evals_all / (t_max * 1e-3)
+
+    # algorithmic FLOPs of this rank's search launch
+    flops = 0.0
+    rk4_eq = 0.0
+    for i in range(w.B):
+        nsub = nsub_for(float(w.fs[i]))
+        e = float(r["evaluations"][i])
+        flops += e * flops_per_sim(int(w.L[i]), int(w.onset[i]), nsub)
+        rk4_eq += e * rk4_stage_flops_per_sim(int(w.L[i]), nsub)
+    mean_search_ms = statistics.mean(search_ms)
+    achieved = flops / (mean_search_ms * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    mp = measured_peaks()
+    sm_max = (mp or {}).get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * float(sm_max) * 1e6 / 1e12
+    prof = profile_traffic(kernel_hash())
+
+    # end to end through the C ABI with host buffers
+    batch_host = G.make_batch(traces, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms)
+    plan_h = G.Plan(ctx, batch_host, **opts)
+    for _ in range(max(1, min(args.warmup, 2))):
+        plan_h.execute_raw()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rh = plan_h.execute_raw()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = dist_max(e2e_s, ws)
+    rh = G.results_to_numpy(rh)
+    e2e_value = dist_sum(float(np.sum(rh["evaluations"].astype(np.float64))), ws) * args.steps / e2e_s
+    h2d = int(buf.nbytes)
+    d2h = int(w.B * RESULT_BYTES + 4)
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "candidate sims/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded OPMM-simulated saccades + Gaussian noise; no dataset)",
+        "config": workload_config(w, "L2 flushed (256 MB write) before every timed step"),
+        "impl": "ours",
+        "saccades_fitted_per_s_at_0p1deg": fitted_all / (t_max * 1e-3),
+        "fraction_fitted_at_0p1deg": fitted_rank / w.B,
+        "median_rms_deg": float(np.median(r["rms_deg"])),
+        "step_ms_p50": statistics.median(step_ms),
+        "step_ms_p99": float(np.percentile(step_ms, 99)),
+        "search_ms_mean": mean_search_ms,
+        "rk4_stage_equivalent_tflops": rk4_eq / (mean_search_ms * 1e-3) / 1e12,
+        "launch_shape": info,
+        "roofline": {"bound": "alu", "kernel": "k_search (persistent Nelder-Mead + plant)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (of nominal max clock)",
+                     "traffic": (prof["dram_bytes_per_launch"] if prof else None),
+                     "traffic_basis": (prof.get("basis") if prof else "no ncu capture of the current kernel")},
+        "e2e": {"value": e2e_value, "unit": "candidate sims/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(info["kernels_per_execute"]) * args.steps,
+        "clocks": clk,
+    }
+    plan.destroy()
+    plan_h.destroy()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+    G.opmm_destroy(ctx)
+    return out
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample(w, budget_s: float, nthreads: int):
+    """Oracle fit of saccade 0 at the workload's full iteration cap on a
+    bounded number of simplices, sized to about budget_s of host time."""
+    import oracle as O
+    i = 0
+    A, D = float(w.amplitude[i]), float(w.dur_ms[i])
+    pn = np.float32(O.nominal_opc(A, D, calibrated=w.calibrated_pulse)).astype(np.float64)
+    ph = np.float32(pn * w.mult[i]).astype(np.float64)
+    L, fs, on = int(w.L[i]), float(w.fs[i]), int(w.onset[i])
+    th0, thf = float(w.theta0[i]), float(w.thetaf[i])
+    y = np.float32(O.simulate_rk4(ph, L, fs, on, th0, thf) + w.noise[i]).astype(np.float64)
+    # probe: one simplex per thread, 2 iterations
+    t0 = time.perf_counter()
+    O.fit(pn, L, fs, on, th0, thf, y, nthreads, 2, seed=w.seed, nthreads=nthreads)
+    probe = time.perf_counter() - t0
+    per_sim = probe / (nthreads * (19 + 2 * 22)) * nthreads      # wall seconds per sim per thread
+    sims_per_simplex = 19 + 22 * w.iterations
+    S = int(max(nthreads, min(w.simplices, budget_s / (per_sim / nthreads * sims_per_simplex))))
+    S = max(nthreads, (S // nthreads) * nthreads)
+    t0 = time.perf_counter()
+    r = O.fit(pn, L, fs, on, th0, thf, y, S, w.iterations, seed=w.seed, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    sims = S * 19 + 22 * float(np.sum(r["iters"]))
+    return sims, dt, S
+
+
+def cpu_baseline(w, budget_s=12.0):
+    nthreads = os.cpu_count() or 1
+    sims, dt, S = oracle_sample(w, budget_s, nthreads)
+    return {"value": sims / dt, "unit": "candidate sims/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"saccade 0 of {w.name}: {S} of {w.simplices} simplices x {w.iterations} "
+                      f"iterations ({int(sims)} simulations, {dt:.1f} s, FP64 RK4 stages)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    w = make_workload(args.workload, 0, args.quick)
+    nthreads = os.cpu_count() or 1
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(w, budget / 2, nthreads)
+    tot_sims, tot_t, S = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        sims, dt, S = oracle_sample(w, budget, nthreads)
+        tot_sims += sims
+        tot_t += dt
+    v = tot_sims / tot_t
+    return {
+        "metric": METRIC, "value": v, "unit": "candidate sims/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded OPMM-simulated saccades + Gaussian noise; no dataset)",
+        "config": workload_config(w, "CPU run"), "impl": "reference",
+        "cpu_baseline": {"value": v, "unit": "candidate sims/s", "cores": nthreads, "kind": "oracle",
+                         "sample": f"per step: saccade 0 of {w.name}, {S} simplices x {w.iterations} iterations"},
+        "e2e": {"value": v, "unit": "candidate sims/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch1024", choices=["batch1024", "uneven10k", "single10"])
+    ap.add_argument("--quick", action="store_true", help="small batch (smoke of the bench itself)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.quick:
+        args.warmup = 3
+    ws, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * opmm.h -- C ABI of the GB300 OPMM estimation library.
+ *
+ * The library fits oculomotor plant characteristic (OPC) vectors to recorded
+ * saccades: "recorded eye movement data as input ... an OPC vector as output"
+ * (paper Sec. 2, "Oculomotor plant mathematical model").  The model is the
+ * 18-parameter oculomotor plant (Sec. 2.2.1, Table 1), the estimator the
+ * parallel Nelder-Mead search of Sec. 2.3 / Algorithm 1.  All numerical work
+ * runs in the library's CUDA kernels on one GPU (sm_103a); there is no CPU
+ * fallback: a call on a machine without a usable device fails with
+ * OPMM_ECUDA.
+ *
+ * Conventions
+ *  - Every function returns an int status: OPMM_OK (0), OPMM_NOT_READY (1), or
+ *    a negative error.  No exception or abort crosses the ABI.  The text of
+ *    the last error of a context is returned by opmm_last_error.
+ *  - Inputs are owned by the caller and only read during the call; outputs
+ *    are caller-owned buffers.  Pointers documented as "host or device" may
+ *    point to either (the library asks the CUDA runtime which); all pointers
+ *    of one kind in one call must be of the same kind.
+ *  - OPC vectors are 18 floats in the column order of the paper's example
+ *    output (Fig. 4): SE_ag SE_ant LT_ag LT_ant PE_ag PE_ant Vis FV_ag FV_ant
+ *    Inert Act_ag Act_ant Deact_ag Deact_ant Step H_ag H_ant W.  Units:
+ *    elasticities g/deg, viscosities g*s/deg, inertia g*s^2/deg, the four
+ *    activation/deactivation times and the pulse width W in ms, tensions in g
+ *    (Table 1's values; the paper states no units, these follow Bahill).
+ *  - Positions are in degrees.  A saccade with theta_end < theta_start is
+ *    simulated in the mirrored frame and its output mirrored back (Fig. 1
+ *    shows the plant for positive saccades).
+ *  - A context is not thread-safe except for the serving calls, which may be
+ *    made from any thread.
+ */
+#ifndef OPMM_H
+#define OPMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define OPMM_OK 0
+#define OPMM_NOT_READY 1     /* serving: result not available yet */
+#define OPMM_EINVAL (-1)     /* malformed argument or descriptor */
+#define OPMM_ENOMEM (-2)     /* device or pinned host allocation failed */
+#define OPMM_ECUDA (-3)      /* CUDA runtime error, or no usable device */
+#define OPMM_ETIMEDOUT (-4)  /* a host deadline or a kernel's bounded wait expired */
+#define OPMM_EBUSY (-5)      /* serving: admission refused (queue or memory full) */
+
+#define OPMM_NPARAM 18
+#define OPMM_MODEL_18 18     /* the 18-parameter OPMM (Sec. 2.2.1) */
+
+/* How the box centre (initial OPC vector) is chosen when the caller gives none
+ * (Sec. 2.3: the estimator starts from model defaults culled from literature). */
+#define OPMM_PULSE_TABLE1 0      /* Table 1 verbatim; W = duration - 6 ms */
+#define OPMM_PULSE_CALIBRATED 1  /* Table 1, W = duration - 6 ms, agonist pulse
+                                    height set so that the default plant's
+                                    saccade from 0 to the amplitude peaks at the
+                                    amplitude (Table 1's single 55 g pulse cannot
+                                    reach every amplitude) */
+
+typedef struct opmm_ctx opmm_ctx;     /* opaque, library-owned */
+typedef struct opmm_plan opmm_plan;   /* opaque, library-owned */
+
+/* One recorded saccade (Sec. 2.3 "OPMM input": an extracted saccade, 1-D
+ * horizontal or vertical position).  The window holds fixation, saccade and
+ * fixation; the pulse of the neural control signal starts at
+ * onset_index / sample_rate_hz. */
+typedef struct {
+  const float* trace_deg;    /* [n_samples] positions, host or device memory */
+  int32_t n_samples;         /* >= 1 */
+  float sample_rate_hz;      /* > 0; RK4 uses round(1e4 / rate) substeps per sample */
+  int32_t onset_index;       /* 0 <= onset_index < n_samples */
+  float theta_start_deg;     /* fixation before the saccade */
+  float theta_end_deg;       /* fixation after the saccade */
+  float duration_ms;         /* detected duration; nominal W = duration - 6 ms */
+} opmm_saccade;
+
+/* Estimator settings (Sec. 2.3, Algorithm 1). */
+typedef struct {
+  int32_t model;             /* OPMM_MODEL_18 */
+  int32_t candidates;        /* trial points per iteration per saccade; the
+                                estimator runs candidates / 22 independent
+                                simplices (each iteration of one simplex
+                                evaluates its 18 + 4 trial points at once) */
+  int32_t iterations;        /* iteration cap per simplex (>= 0) */
+  float box_lo, box_hi;      /* search box: centre * [box_lo, box_hi], 0 < lo <= 1 <= hi */
+  float init_step;           /* initial simplex edge in ln-parameter units (e.g. 0.05) */
+  float tol_x, tol_f;        /* exit tolerances: max-norm vertex spread (ln units)
+                                and objective spread (deg^2) */
+  uint64_t seed;             /* Philox key for the simplex starting points */
+  int32_t pulse_init;        /* OPMM_PULSE_* when init_opc is NULL */
+  int32_t use_surrogate;     /* 1: centre the box on the surrogate's estimate
+                                (requires opmm_surrogate_load / _set) */
+  const float* init_opc;     /* nullable, host [n][18] box centres (all > 0) */
+} opmm_fit_opts;
+
+/* Result per saccade (Fig. 4: OPC vector and optimisation error). */
+typedef struct {
+  float opc[18];             /* best OPC vector found */
+  float f;                   /* its objective as the search computed it:
+                                mean squared error, deg^2, FP32 */
+  int32_t iterations_run;    /* iterations of the winning simplex */
+  double rms_deg;            /* FP64 recomputation: sqrt(mean squared error) */
+  double l1_deg;             /* FP64 recomputation: mean absolute error */
+  int32_t status;            /* 0 ok; 1 no finite candidate */
+  int32_t winner;            /* index of the winning simplex */
+  int32_t evaluations;       /* candidate OPC vectors simulated for this saccade */
+  int32_t reserved;
+} opmm_fit_result;
+
+/* ------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device_ordinal`.  Owns a stream, scratch
+ * buffers and the autotuner cache. */
+int opmm_create(int device_ordinal, opmm_ctx** out);
+void opmm_destroy(opmm_ctx* ctx);
+/* Message of the last failed call on this context (never NULL). */
+const char* opmm_last_error(const opmm_ctx* ctx);
+/* Use the caller's CUDA stream (cudaStream_t) for subsequent calls; NULL
+ * restores the context's own stream. */
+int opmm_set_stream(opmm_ctx* ctx, void* cuda_stream);
+
+/* ------------------------------------------------------------ plant */
+
+/* Simulate n trajectories (the plant of Sec. 2.2.1 integrated by RK4,
+ * h ~ 0.1 ms, pulse end split).  Trajectory i uses OPC vector opc[i] and the
+ * descriptor sacs[sac_index ? sac_index[i] : i] (its trace pointer is not
+ * read).  Output: out_deg[out_offset[i] + k], k < n_samples, positions at
+ * t_k = k / rate.
+ *   opc:        [n][18] host or device
+ *   sacs:       host array of descriptors
+ *   sac_index:  nullable host [n]
+ *   out_offset: host [n] element offsets into out_deg
+ *   out_deg:    host or device, caller-owned
+ * Synchronous with respect to the host. */
+int opmm_simulate(opmm_ctx* ctx, const float* opc, int32_t n, const opmm_saccade* sacs,
+                  int32_t n_sacs, const int32_t* sac_index, const int64_t* out_offset,
+                  float* out_deg);
+
+/* Objective of m candidate OPC vectors against one recorded saccade: mean
+ * squared error (deg^2) accumulated in FP32 with compensated summation,
+ * +inf for candidates outside RK4's stable step range.  opc: [m][18] host or
+ * device; out_f: [m] host or device. */
+int opmm_score(opmm_ctx* ctx, const float* opc, int32_t m, const opmm_saccade* sac,
+               float* out_f);
+
+/* Box centres the estimator would use: the caller's init_opc if given, else
+ * Table 1 with W = duration - 6 ms and the agonist pulse chosen by
+ * pulse_init.  out_opc: host [n][18]. */
+int opmm_nominal_opc(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, int32_t pulse_init,
+                     float* out_opc);
+
+/* ---------------------------------------------------------- estimation */
+
+/* Fit every saccade of the batch (Algorithm 1: one optimisation task per
+ * saccade, all on the device at once).  sacs: host array; traces host or
+ * device.  out: host [n], caller-owned.  Synchronous. */
+int opmm_fit_batch(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* opts,
+                   opmm_fit_result* out);
+
+/* Reusable plan for repeated fits of batches of one shape: validates and
+ * stages the descriptors, sizes the device buffers, picks the launch shape
+ * (autotuned on first use per device and shape class) and captures the whole
+ * fit (trace gather, box centres, persistent search, FP64 check) in one CUDA
+ * graph.  The descriptors' trace pointers are recorded: each execute re-reads
+ * the traces they point to.  opts->init_opc, if given, is copied. */
+int opmm_plan_create(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* opts,
+                     opmm_plan** out);
+/* Replay the plan's graph and copy the n results to `out` (host). */
+int opmm_plan_execute(opmm_plan* plan, opmm_fit_result* out);
+/* Launch-shape choice of the plan: simplices per block, threads per block,
+ * blocks per SM; and the number of kernels one execute launches. */
+int opmm_plan_info(const opmm_plan* plan, int32_t* simplices_per_block, int32_t* threads,
+                   int32_t* blocks_per_sm, int32_t* kernels_per_execute);
+/* Device time of the persistent search kernel in the last execute, from CUDA
+ * events recorded around it on the plan's stream (inside the graph). */
+int opmm_plan_last_search_ms(const opmm_plan* plan, float* ms);
+void opmm_plan_destroy(opmm_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPMM_H */

@@ -1,0 +1,350 @@
+"""Python binding of the GB300 OPMM library (include/opmm.h).
+
+Argument marshalling only: every step of the estimation path runs in the CUDA
+kernels of libopmm.so.  Functions keep the C names (opmm_create,
+opmm_simulate, opmm_score, opmm_nominal_opc, opmm_fit_batch, opmm_plan_*,
+...); arrays may be numpy (host) or torch CUDA tensors (device), passed to the
+library as plain pointers.  There is no CPU fallback: if the library cannot be
+loaded, or no CUDA device is usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libopmm.so")
+
+OPMM_OK = 0
+OPMM_NOT_READY = 1
+OPMM_EINVAL = -1
+OPMM_ENOMEM = -2
+OPMM_ECUDA = -3
+OPMM_ETIMEDOUT = -4
+OPMM_EBUSY = -5
+OPMM_NPARAM = 18
+OPMM_MODEL_18 = 18
+OPMM_PULSE_TABLE1 = 0
+OPMM_PULSE_CALIBRATED = 1
+
+PARAM_NAMES = ["SE_ag", "SE_ant", "LT_ag", "LT_ant", "PE_ag", "PE_ant", "Vis", "FV_ag", "FV_ant",
+               "Inert", "Act_ag", "Act_ant", "Deact_ag", "Deact_ant", "Step", "H_ag", "H_ant", "W"]
+
+# Every symbol include/opmm.h declares.
+EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", "opmm_simulate",
+           "opmm_score", "opmm_nominal_opc", "opmm_fit_batch", "opmm_plan_create",
+           "opmm_plan_execute", "opmm_plan_info", "opmm_plan_last_search_ms", "opmm_plan_destroy"]
+
+
+class OpmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"OPMM error {code}: {msg}")
+        self.code = code
+
+
+class opmm_saccade(ctypes.Structure):
+    _fields_ = [("trace_deg", ctypes.c_void_p), ("n_samples", ctypes.c_int32),
+                ("sample_rate_hz", ctypes.c_float), ("onset_index", ctypes.c_int32),
+                ("theta_start_deg", ctypes.c_float), ("theta_end_deg", ctypes.c_float),
+                ("duration_ms", ctypes.c_float)]
+
+
+class opmm_fit_opts(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("box_lo", ctypes.c_float),
+                ("box_hi", ctypes.c_float), ("init_step", ctypes.c_float),
+                ("tol_x", ctypes.c_float), ("tol_f", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("pulse_init", ctypes.c_int32), ("use_surrogate", ctypes.c_int32),
+                ("init_opc", ctypes.c_void_p)]
+
+
+class opmm_fit_result(ctypes.Structure):
+    _fields_ = [("opc", ctypes.c_float * 18), ("f", ctypes.c_float),
+                ("iterations_run", ctypes.c_int32), ("rms_deg", ctypes.c_double),
+                ("l1_deg", ctypes.c_double), ("status", ctypes.c_int32), ("winner", ctypes.c_int32),
+                ("evaluations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libopmm.so (building it first if missing).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, i64p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)
+    lib.opmm_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+    lib.opmm_destroy.argtypes = [vp]
+    lib.opmm_destroy.restype = None
+    lib.opmm_last_error.argtypes = [vp]
+    lib.opmm_last_error.restype = ctypes.c_char_p
+    lib.opmm_set_stream.argtypes = [vp, vp]
+    lib.opmm_simulate.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), i32, vp, i64p, vp]
+    lib.opmm_score.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), vp]
+    lib.opmm_nominal_opc.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
+    lib.opmm_fit_batch.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32,
+                                   ctypes.POINTER(opmm_fit_opts), ctypes.POINTER(opmm_fit_result)]
+    lib.opmm_plan_create.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32,
+                                     ctypes.POINTER(opmm_fit_opts), ctypes.POINTER(vp)]
+    lib.opmm_plan_execute.argtypes = [vp, ctypes.POINTER(opmm_fit_result)]
+    lib.opmm_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
+    lib.opmm_plan_last_search_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.opmm_plan_destroy.argtypes = [vp]
+    lib.opmm_plan_destroy.restype = None
+    for name in ["opmm_create", "opmm_set_stream", "opmm_simulate", "opmm_score", "opmm_nominal_opc",
+                 "opmm_fit_batch", "opmm_plan_create", "opmm_plan_execute", "opmm_plan_info",
+                 "opmm_plan_last_search_ms"]:
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ pointers
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=np.float32):
+    """(pointer, keepalive) of a host numpy array or a torch tensor."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+# ------------------------------------------------------------------ batches
+@dataclass
+class SaccadeBatch:
+    """Descriptors of n recorded saccades plus the storage their traces live in.
+
+    `traces` is either one packed array (numpy host array or torch CUDA tensor)
+    with `offsets[i]` the first sample of saccade i, or a list of per-saccade
+    arrays."""
+    traces: object
+    offsets: Optional[np.ndarray]
+    n_samples: np.ndarray
+    sample_rate_hz: np.ndarray
+    onset_index: np.ndarray
+    theta_start_deg: np.ndarray
+    theta_end_deg: np.ndarray
+    duration_ms: np.ndarray
+
+    def __len__(self):
+        return int(len(self.n_samples))
+
+    def descriptors(self):
+        n = len(self)
+        arr = (opmm_saccade * n)()
+        keep = []
+        if isinstance(self.traces, (list, tuple)):
+            bases = []
+            for t in self.traces:
+                p, k = _ptr(t)
+                keep.append(k)
+                bases.append(p.value)
+        else:
+            p, k = _ptr(self.traces)
+            keep.append(k)
+            esz = 4
+            bases = [p.value + int(o) * esz for o in self.offsets]
+        for i in range(n):
+            arr[i].trace_deg = bases[i]
+            arr[i].n_samples = int(self.n_samples[i])
+            arr[i].sample_rate_hz = float(self.sample_rate_hz[i])
+            arr[i].onset_index = int(self.onset_index[i])
+            arr[i].theta_start_deg = float(self.theta_start_deg[i])
+            arr[i].theta_end_deg = float(self.theta_end_deg[i])
+            arr[i].duration_ms = float(self.duration_ms[i])
+        return arr, keep
+
+
+def make_batch(traces, sample_rate_hz, onset_index, theta_start_deg, theta_end_deg, duration_ms,
+               n_samples=None, offsets=None) -> SaccadeBatch:
+    n = len(sample_rate_hz)
+    if n_samples is None:
+        n_samples = [len(t) for t in traces]
+    return SaccadeBatch(traces, None if offsets is None else np.asarray(offsets, np.int64),
+                        np.asarray(n_samples, np.int32), np.asarray(sample_rate_hz, np.float32),
+                        np.asarray(onset_index, np.int32), np.asarray(theta_start_deg, np.float32),
+                        np.asarray(theta_end_deg, np.float32),
+                        np.asarray(duration_ms if duration_ms is not None else [0.0] * n, np.float32))
+
+
+def fit_opts(candidates=4096, iterations=20, box_lo=0.5, box_hi=2.0, init_step=0.05, tol_x=1e-4,
+             tol_f=1e-4, seed=0, pulse_init=OPMM_PULSE_CALIBRATED, use_surrogate=False,
+             init_opc=None):
+    o = opmm_fit_opts()
+    o.model = OPMM_MODEL_18
+    o.candidates, o.iterations = int(candidates), int(iterations)
+    o.box_lo, o.box_hi, o.init_step = float(box_lo), float(box_hi), float(init_step)
+    o.tol_x, o.tol_f, o.seed = float(tol_x), float(tol_f), int(seed)
+    o.pulse_init, o.use_surrogate = int(pulse_init), int(bool(use_surrogate))
+    keep = None
+    if init_opc is not None:
+        keep = np.ascontiguousarray(init_opc, dtype=np.float32)
+        o.init_opc = keep.ctypes.data
+    return o, keep
+
+
+def results_to_numpy(res) -> dict:
+    n = len(res)
+    buf = np.frombuffer(bytes(res), dtype=np.dtype([("opc", "<f4", (18,)), ("f", "<f4"),
+                                                     ("iterations_run", "<i4"), ("rms_deg", "<f8"),
+                                                     ("l1_deg", "<f8"), ("status", "<i4"),
+                                                     ("winner", "<i4"), ("evaluations", "<i4"),
+                                                     ("reserved", "<i4")]), count=n)
+    return {k: buf[k].copy() for k in buf.dtype.names}
+
+
+# ------------------------------------------------------------------ C names
+def _check(ctx, rc):
+    if rc < 0:
+        lib = load_library()
+        msg = lib.opmm_last_error(ctx).decode(errors="replace") if ctx else "no context"
+        raise OpmmError(rc, msg)
+    return rc
+
+
+def opmm_create(device: int = 0):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rc = lib.opmm_create(int(device), ctypes.byref(h))
+    if rc != OPMM_OK:
+        raise OpmmError(rc, "opmm_create failed (no usable CUDA device?)")
+    return h
+
+
+def opmm_destroy(ctx):
+    load_library().opmm_destroy(ctx)
+
+
+def opmm_last_error(ctx) -> str:
+    return load_library().opmm_last_error(ctx).decode(errors="replace")
+
+
+def opmm_set_stream(ctx, stream_handle: int):
+    _check(ctx, load_library().opmm_set_stream(ctx, ctypes.c_void_p(int(stream_handle) or None)))
+
+
+def opmm_simulate(ctx, opc, batch: SaccadeBatch, sac_index=None, out=None):
+    """Trajectories [n][L_i] packed; returns (out, offsets)."""
+    lib = load_library()
+    n = int(opc.shape[0])
+    sidx = np.arange(n, dtype=np.int32) if sac_index is None else np.asarray(sac_index, np.int32)
+    L = np.asarray(batch.n_samples, np.int64)[sidx]
+    offs = np.concatenate([[0], np.cumsum(L)[:-1]]).astype(np.int64)
+    if out is None:
+        out = np.zeros(int(L.sum()), dtype=np.float32)
+    descs, keep = batch.descriptors()
+    po, ko = _ptr(opc)
+    pout, kout = _ptr(out)
+    rc = lib.opmm_simulate(ctx, po, n, descs, len(batch),
+                           None if sac_index is None else sidx.ctypes.data_as(ctypes.c_void_p),
+                           offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), pout)
+    _check(ctx, rc)
+    return out, offs
+
+
+def opmm_score(ctx, opc, batch: SaccadeBatch, index: int = 0, out=None):
+    lib = load_library()
+    m = int(opc.shape[0])
+    if out is None:
+        out = np.zeros(m, dtype=np.float32)
+    descs, keep = batch.descriptors()
+    po, ko = _ptr(opc)
+    pf, kf = _ptr(out)
+    _check(ctx, lib.opmm_score(ctx, po, m, ctypes.byref(descs[index]), pf))
+    return out
+
+
+def opmm_nominal_opc(ctx, batch: SaccadeBatch, pulse_init=OPMM_PULSE_CALIBRATED) -> np.ndarray:
+    lib = load_library()
+    out = np.zeros((len(batch), 18), dtype=np.float32)
+    descs, keep = batch.descriptors()
+    _check(ctx, lib.opmm_nominal_opc(ctx, descs, len(batch), int(pulse_init),
+                                     out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def opmm_fit_batch(ctx, batch: SaccadeBatch, **opts) -> dict:
+    lib = load_library()
+    o, keep_o = fit_opts(**opts)
+    descs, keep = batch.descriptors()
+    res = (opmm_fit_result * len(batch))()
+    _check(ctx, lib.opmm_fit_batch(ctx, descs, len(batch), ctypes.byref(o), res))
+    return results_to_numpy(res)
+
+
+class Plan:
+    """opmm_plan_*: a graph-captured fit of a fixed batch (traces re-read on
+    every execute)."""
+
+    def __init__(self, ctx, batch: SaccadeBatch, **opts):
+        self.lib = load_library()
+        self.ctx = ctx
+        o, self._keep_o = fit_opts(**opts)
+        self._descs, self._keep = batch.descriptors()
+        self.n = len(batch)
+        self.h = ctypes.c_void_p()
+        _check(ctx, self.lib.opmm_plan_create(ctx, self._descs, self.n, ctypes.byref(o),
+                                              ctypes.byref(self.h)))
+        self._res = (opmm_fit_result * self.n)()
+
+    def execute(self) -> dict:
+        _check(self.ctx, self.lib.opmm_plan_execute(self.h, self._res))
+        return results_to_numpy(self._res)
+
+    def execute_raw(self):
+        _check(self.ctx, self.lib.opmm_plan_execute(self.h, self._res))
+        return self._res
+
+    def info(self) -> dict:
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(self.ctx, self.lib.opmm_plan_info(self.h, *[ctypes.byref(x) for x in v]))
+        return {"simplices_per_block": v[0].value, "threads": v[1].value,
+                "blocks_per_sm": v[2].value, "kernels_per_execute": v[3].value}
+
+    def last_search_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(self.ctx, self.lib.opmm_plan_last_search_ms(self.h, ctypes.byref(ms)))
+        return float(ms.value)
+
+    def destroy(self):
+        if self.h:
+            self.lib.opmm_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def opmm_plan_create(ctx, batch: SaccadeBatch, **opts) -> Plan:
+    return Plan(ctx, batch, **opts)
+
+
+def opmm_plan_execute(plan: Plan) -> dict:
+    return plan.execute()
+
+
+def opmm_plan_info(plan: Plan) -> dict:
+    return plan.info()
+
+
+def opmm_plan_destroy(plan: Plan):
+    plan.destroy()

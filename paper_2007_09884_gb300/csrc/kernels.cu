@@ -1,0 +1,717 @@
+// kernels.cu -- CUDA kernels of the OPMM estimation path (sm_103a).
+//
+//   k_gather      copy caller traces into the packed, 16-byte aligned buffer
+//   k_nominal     box centres: Table 1, W = D - 6 ms, calibrated agonist pulse
+//   k_simulate    trajectories of (OPC, saccade) pairs
+//   k_score       objective of many OPC vectors against one saccade
+//   k_search      persistent multi-start parallel Nelder-Mead (Algorithm 1)
+//   k_finalize    per-saccade winner and FP64 re-computation of its error
+//
+// The hot loop is k_search's candidate evaluation: one thread integrates one
+// trial OPC vector's plant in registers (plant.cuh), scoring each sample against
+// the trace staged once per block in shared memory by a TMA bulk copy, with a
+// compensated FP32 sum.  Per block, G simplices of one saccade advance together:
+// all 22 trial points of every simplex are evaluated in one wave (Sec. 2.3:
+// "all of the simplex transformations are calculated simultaneously"), then a
+// warp per simplex takes the Lagarias decision and re-sorts its vertices.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/opmm.h"
+#include "common.cuh"
+#include "launch.h"
+#include "plant.cuh"
+
+namespace opmm {
+
+__device__ __forceinline__ SacConst sac_const(const DevSac& d) {
+  SacConst s;
+  s.L = d.L; s.onset = d.onset; s.nsub = d.nsub;
+  s.fs = d.fs; s.h = d.h; s.th0 = d.th0; s.thf = d.thf;
+  return s;
+}
+
+// ------------------------------------------------------------------ gather
+__global__ void k_gather(const float* const* src, const DevSac* sacs, float* dst, int n) {
+  const int b = blockIdx.x;
+  if (b >= n) return;
+  const DevSac d = sacs[b];
+  const float* s = src[b];
+  float* o = dst + d.off;
+  const int Lp = (d.L + 3) & ~3;
+  for (int k = threadIdx.x; k < Lp; k += blockDim.x) o[k] = k < d.L ? s[k] : 0.0f;
+}
+
+// ------------------------------------------------------------------ sinks
+struct KahanSink {
+  const float* z;   // trace minus end fixation, positive frame
+  float sum, c;
+  __device__ __forceinline__ void emit(int k, float dth) {
+    const float d = dth - z[k];
+    const float y = fmaf(d, d, -c);
+    const float t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+  }
+};
+
+struct WriteSink {
+  float* out;
+  float sign, thf;
+  __device__ __forceinline__ void emit(int k, float dth) { out[k] = sign * (thf + dth); }
+};
+
+struct PeakSink {
+  float m;
+  __device__ __forceinline__ void emit(int, float dth) { m = fmaxf(m, dth); }
+};
+
+// Objective of one OPC vector: mean squared error over the window; the
+// samples up to onset (the plant at rest) are folded into (sum0, c0).
+__device__ __forceinline__ float objective(const float* p, const SacConst& sc, const float* z,
+                                           float sum0, float c0) {
+  if (too_stiff(p, sc.h)) return INFINITY;
+  KahanSink s{z, sum0, c0};
+  walk(p, sc, s);
+  const float f = (s.sum - s.c) / (float)sc.L;
+  return isfinite(f) ? f : INFINITY;
+}
+
+// Stage one saccade for a block: TMA bulk copy of the raw trace, then the
+// positive-frame trace minus the end fixation and the compensated sum of the
+// rest samples.  All threads call it; returns false on a wait timeout.
+struct TraceStage {
+  float sum0, c0;
+};
+
+__device__ bool stage_trace(const DevSac& d, const float* traces, float* yraw, float* z, uint64_t* bar,
+                            uint32_t& phase, TraceStage* st) {
+  if (threadIdx.x == 0) {
+    fence_proxy_async_smem();
+    const uint32_t bytes = (uint32_t)(((d.L + 3) & ~3) * 4);
+    mbar_arrive_expect_tx(bar, bytes);
+    tma_load_1d(yraw, traces + d.off, bytes, bar);
+  }
+  const bool ok = mbar_wait(bar, phase, kMaxWaitTries);
+  phase ^= 1u;
+  if (__syncthreads_or(!ok)) return false;
+  for (int k = threadIdx.x; k < d.L; k += blockDim.x) z[k] = d.sign * yraw[k] - d.thf;
+  if (threadIdx.x == 0) {
+    float sum = 0.0f, c = 0.0f;
+    const int kend = min(d.onset, d.L - 1);
+    for (int k = 0; k <= kend; ++k) {
+      const float e = d.th0 - d.sign * yraw[k];
+      const float y = fmaf(e, e, -c);
+      const float t = sum + y;
+      c = (t - sum) - y;
+      sum = t;
+    }
+    st->sum0 = sum;
+    st->c0 = c;
+  }
+  __syncthreads();
+  return true;
+}
+
+// ------------------------------------------------------------------ nominal
+// Largest sample of the default plant's saccade from 0 to A with agonist
+// pulse nsac, 1 kHz grid, 250 ms after onset.
+__device__ float nominal_peak(float* p, float A, float nsac) {
+  p[kNsacAg] = nsac;
+  SacConst sc;
+  sc.L = 251; sc.onset = 0; sc.nsub = 10; sc.fs = 1000.0f; sc.h = 1.0e-4f; sc.th0 = 0.0f; sc.thf = A;
+  PeakSink pk{-A};
+  walk(p, sc, pk);
+  return A + pk.m;
+}
+
+// One warp per saccade.  Calibrated mode: the agonist pulse for which the
+// default plant's saccade peaks at its amplitude A; round 0 brackets the
+// crossing between lo 2^(i-1) and lo 2^i (lo = step level of A), six rounds of
+// a 32-point search narrow the bracket; if the step level already reaches A
+// it is used as is.
+__global__ void k_nominal(const DevSac* sacs, int n, int pulse_mode, const float* init_opc, float* pc) {
+  const int lane = threadIdx.x & 31;
+  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (b >= n) return;
+  float* out = pc + (size_t)b * kNumParams;
+  if (init_opc) {
+    if (lane < kNumParams) out[lane] = init_opc[(size_t)b * kNumParams + lane];
+    return;
+  }
+  const DevSac d = sacs[b];
+  float p[kNumParams];
+#pragma unroll
+  for (int j = 0; j < kNumParams; ++j) p[j] = kTable1[j];
+  p[kPw] = d.dur_ms - 6.0f;
+  float nsac = kTable1[kNsacAg];
+  if (pulse_mode == OPMM_PULSE_CALIBRATED) {
+    const float A = d.thf - d.th0;
+    float s[6];
+    rest_state(p, A, s);
+    const float lo = s[4];
+    float pk = nominal_peak(p, A, lo * ldexpf(1.0f, lane));
+    unsigned hit = __ballot_sync(0xffffffffu, pk >= A);
+    if (hit & 1u) {
+      nsac = lo;
+    } else if (hit == 0u) {
+      nsac = lo * ldexpf(1.0f, 31);
+    } else {
+      const int i0 = __ffs(hit) - 1;
+      float a = lo * ldexpf(1.0f, i0 - 1);
+      float bb = lo * ldexpf(1.0f, i0);
+      for (int round = 0; round < 6; ++round) {
+        const float x = a + (bb - a) * ((float)(lane + 1) * (1.0f / 33.0f));
+        pk = nominal_peak(p, A, x);
+        const unsigned h = __ballot_sync(0xffffffffu, pk >= A);
+        const int i = h ? __ffs(h) - 1 : 32;
+        const float xlo = __shfl_sync(0xffffffffu, x, i > 0 ? i - 1 : 0);
+        const float xhi = __shfl_sync(0xffffffffu, x, i < 32 ? i : 31);
+        const float na = i == 0 ? a : xlo;
+        const float nb = i == 32 ? bb : xhi;
+        a = na;
+        bb = nb;
+      }
+      nsac = 0.5f * (a + bb);
+    }
+  }
+  p[kNsacAg] = nsac;
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < kNumParams; ++j) out[j] = p[j];
+  }
+}
+
+// ------------------------------------------------------------------ simulate
+__global__ void k_simulate(const float* opc, int n, const DevSac* sacs, const int* sac_of,
+                           const long long* out_off, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float p[kNumParams];
+#pragma unroll
+  for (int j = 0; j < kNumParams; ++j) p[j] = opc[(size_t)i * kNumParams + j];
+  const DevSac d = sacs[sac_of ? sac_of[i] : i];
+  const SacConst sc = sac_const(d);
+  float* o = out + out_off[i];
+  const int kend = min(d.onset, d.L - 1);
+  for (int k = 0; k <= kend; ++k) o[k] = d.sign * d.th0;
+  WriteSink w{o, d.sign, d.thf};
+  walk(p, sc, w);
+}
+
+// ------------------------------------------------------------------ score
+__global__ void k_score(const float* opc, int m, const DevSac* sac, const float* traces, float* f,
+                        unsigned* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ TraceStage st;
+  const DevSac d = *sac;
+  const int lp = (d.L + 3) & ~3;
+  float* yraw = reinterpret_cast<float*>(smraw);
+  float* z = yraw + lp;
+  if (threadIdx.x == 0) { mbar_init(&bar, 1); fence_mbar_init(); }
+  __syncthreads();
+  uint32_t phase = 0;
+  if (!stage_trace(d, traces, yraw, z, &bar, phase, &st)) {
+    if (threadIdx.x == 0) raise_error(err, kErrWaitTimeout);
+    return;
+  }
+  const SacConst sc = sac_const(d);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    float p[kNumParams];
+#pragma unroll
+    for (int j = 0; j < kNumParams; ++j) p[j] = opc[(size_t)i * kNumParams + j];
+    f[i] = objective(p, sc, z, st.sum0, st.c0);
+  }
+}
+
+// ------------------------------------------------------------------ search
+// Unit record: [0] best f, [1] winning simplex (int), [2] its iterations (int),
+// [3] candidate evaluations of the unit (int), [4..21] best vertex (ln units).
+constexpr int kUnitRec = 24;
+constexpr int kNV = kNumParams + 1;      // vertices per simplex
+constexpr int kNT = kNumParams + 4;      // trial points per simplex and iteration
+
+template <int G>
+struct SearchSmem {
+  float U[G][kNV][kNumParams];   // vertices, by slot
+  float XT[G][4][kNumParams];    // reflection, expansion, outside/inside contraction
+  float XB[G][kNumParams];       // centroid of the best n vertices
+  float F[G][kNV];               // vertex values, by slot
+  float FT[G][kNT];              // trial values
+  float pc[kNumParams];          // box centre of the current saccade
+  unsigned char ord[G][kNV + 1]; // ord[r] = slot of rank r
+  int active[G];
+  int iters[G];
+  SacConst sc;
+  TraceStage st;
+  int cur_b;
+  int unit;
+  uint64_t bar;
+};
+
+template <int G>
+__host__ __device__ constexpr int search_threads() { return ((G * kNT + 31) / 32) * 32; }
+
+template <int G>
+size_t search_smem_bytes(int lcap) {
+  return ((sizeof(SearchSmem<G>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float);
+}
+
+// Trial point coordinate (Lagarias et al. coefficients rho 1, chi 2, gamma 1/2).
+__device__ __forceinline__ float trial_coord(int q, float xb, float w) {
+  const float xr = xb + (xb - w);
+  switch (q) {
+    case 0: return xr;
+    case 1: return xb + 2.0f * (xr - xb);
+    case 2: return xb + 0.5f * (xr - xb);
+    default: return xb - 0.5f * (xb - w);
+  }
+}
+
+__device__ __forceinline__ float shrink_coord(float x1, float xi) { return x1 + 0.5f * (xi - x1); }
+
+__device__ __forceinline__ float eval_u(const float (&u)[kNumParams], const float* pc, float lnlo,
+                                        float lnhi, const SacConst& sc, const float* z, float sum0,
+                                        float c0) {
+  float p[kNumParams];
+#pragma unroll
+  for (int j = 0; j < kNumParams; ++j) p[j] = pc[j] * __expf(fminf(fmaxf(u[j], lnlo), lnhi));
+  return objective(p, sc, z, sum0, c0);
+}
+
+template <int G>
+__global__ void __launch_bounds__(search_threads<G>()) k_search(SearchParams P) {
+  constexpr int NT = search_threads<G>();
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  SearchSmem<G>& S = *reinterpret_cast<SearchSmem<G>*>(smraw);
+  float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G>) + 127) / 128) * 128);
+  float* z = yraw + P.lcap;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) {
+    mbar_init(&S.bar, 1);
+    fence_mbar_init();
+    S.cur_b = -1;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  for (;;) {
+    if (tid == 0) S.unit = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int unit = S.unit;
+    if (unit >= P.n_units) break;
+    const int2 un = P.units[unit];
+    const int b = un.x, g0 = un.y;
+    if (b != S.cur_b) {
+      const DevSac d = P.sacs[b];
+      if (!stage_trace(d, P.traces, yraw, z, &S.bar, phase, &S.st)) {
+        if (tid == 0) raise_error(P.err, kErrWaitTimeout);
+        return;
+      }
+      if (tid < kNumParams) S.pc[tid] = P.pc[(size_t)b * kNumParams + tid];
+      if (tid == 0) {
+        S.sc = sac_const(d);
+        S.cur_b = b;
+      }
+      __syncthreads();
+    }
+    const int nsim = min(G, P.S - g0 * G);
+    const SacConst sc = S.sc;
+    const float sum0 = S.st.sum0, c0 = S.st.c0;
+    int evals = kNV * nsim;
+
+    // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
+    if (tid < kNV * nsim) {
+      const int gi = tid / kNV, v = tid - gi * kNV;
+      const int s = g0 * G + gi;
+      float u[kNumParams];
+      if (s == 0) {
+#pragma unroll
+        for (int j = 0; j < kNumParams; ++j) u[j] = 0.0f;
+      } else {
+#pragma unroll
+        for (int blk = 0; blk < 5; ++blk) {
+          uint32_t r[4];
+          philox4x32_10((uint32_t)P.sac_index[b], (uint32_t)s, (uint32_t)blk, 0u, P.seed_lo, P.seed_hi, r);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (4 * blk + q < kNumParams)
+              u[4 * blk + q] = P.lnlo + (P.lnhi - P.lnlo) * ((float)(r[q] >> 8) * (1.0f / 16777216.0f));
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kNumParams; ++j) {
+        if (v > 0 && j == v - 1) u[j] += P.step;
+        S.U[gi][v][j] = u[j];
+      }
+      S.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
+    }
+    __syncthreads();
+    for (int gi = warp; gi < nsim; gi += NW) {
+      if (lane == 0) {
+        unsigned char* o = S.ord[gi];
+        for (int i = 0; i < kNV; ++i) {
+          const float fi = S.F[gi][i];
+          int j = i - 1;
+          while (j >= 0 && S.F[gi][o[j]] > fi) { o[j + 1] = o[j]; --j; }
+          o[j + 1] = (unsigned char)i;
+        }
+        S.active[gi] = 1;
+        S.iters[gi] = 0;
+      }
+    }
+    __syncthreads();
+
+    for (int it = 0; it < P.T; ++it) {
+      // ---- exit test (Sec. 2.3): vertex spread <= tol_x and value spread <= tol_f
+      for (int gi = warp; gi < nsim; gi += NW) {
+        if (!S.active[gi]) continue;
+        const unsigned char* o = S.ord[gi];
+        bool ok = true;
+        if (lane < kNumParams) {
+          const float x1 = S.U[gi][o[0]][lane];
+          for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(S.U[gi][o[r]][lane] - x1) <= P.tolx);
+        }
+        if (lane >= 1 && lane < kNV) ok = ok && (fabsf(S.F[gi][o[lane]] - S.F[gi][o[0]]) <= P.tolf);
+        const bool conv = __all_sync(0xffffffffu, ok);
+        if (conv && lane == 0) S.active[gi] = 0;
+      }
+      __syncthreads();
+      int nact = 0;
+      for (int gi = 0; gi < nsim; ++gi) nact += S.active[gi];
+      if (!nact) break;
+      evals += kNT * nact;
+
+      // ---- centroid of the best n vertices
+      for (int idx = tid; idx < nsim * kNumParams; idx += NT) {
+        const int gi = idx / kNumParams, j = idx - gi * kNumParams;
+        if (!S.active[gi]) continue;
+        float acc = 0.0f;
+        for (int r = 0; r < kNumParams; ++r) acc += S.U[gi][S.ord[gi][r]][j];
+        S.XB[gi][j] = acc / (float)kNumParams;
+      }
+      __syncthreads();
+
+      // ---- one wave: all n + 4 trial points of every active simplex
+      if (tid < kNT * nsim) {
+        const int gi = tid / kNT, q = tid - gi * kNT;
+        if (S.active[gi]) {
+          const unsigned char* o = S.ord[gi];
+          float u[kNumParams];
+          if (q < 4) {
+            const int ws = o[kNumParams];
+#pragma unroll
+            for (int j = 0; j < kNumParams; ++j) {
+              u[j] = trial_coord(q, S.XB[gi][j], S.U[gi][ws][j]);
+              S.XT[gi][q][j] = u[j];
+            }
+          } else {
+            const int s1 = o[0], si = o[q - 3];
+#pragma unroll
+            for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(S.U[gi][s1][j], S.U[gi][si][j]);
+          }
+          S.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
+        }
+      }
+      __syncthreads();
+
+      // ---- Nelder-Mead decision and re-sort, one warp per simplex
+      for (int gi = warp; gi < nsim; gi += NW) {
+        if (!S.active[gi]) continue;
+        unsigned char* o = S.ord[gi];
+        const float f1 = S.F[gi][o[0]], fn = S.F[gi][o[kNumParams - 1]], fw = S.F[gi][o[kNumParams]];
+        const float fr = S.FT[gi][0], fe = S.FT[gi][1], fco = S.FT[gi][2], fci = S.FT[gi][3];
+        int kind;
+        float fnew = 0.0f;
+        if (fr < f1) {
+          if (fe < fr) { kind = 1; fnew = fe; } else { kind = 0; fnew = fr; }
+        } else if (fr < fn) {
+          kind = 0; fnew = fr;
+        } else if (fr < fw) {
+          if (fco <= fr) { kind = 2; fnew = fco; } else kind = -1;
+        } else {
+          if (fci < fw) { kind = 3; fnew = fci; } else kind = -1;
+        }
+        if (kind >= 0) {
+          const int ws = o[kNumParams];
+          if (lane < kNumParams) S.U[gi][ws][lane] = S.XT[gi][kind][lane];
+          __syncwarp();
+          if (lane == 0) {
+            S.F[gi][ws] = fnew;
+            int i = kNumParams;
+            while (i > 0 && S.F[gi][o[i - 1]] > fnew) { o[i] = o[i - 1]; --i; }
+            o[i] = (unsigned char)ws;
+          }
+        } else {
+          if (lane < kNumParams) {
+            const float x1 = S.U[gi][o[0]][lane];
+            for (int r = 1; r < kNV; ++r) S.U[gi][o[r]][lane] = shrink_coord(x1, S.U[gi][o[r]][lane]);
+          }
+          if (lane >= 1 && lane < kNV) S.F[gi][o[lane]] = S.FT[gi][4 + lane - 1];
+          __syncwarp();
+          if (lane == 0) {
+            for (int i = 1; i < kNV; ++i) {
+              const unsigned char si = o[i];
+              const float fi = S.F[gi][si];
+              int j = i - 1;
+              while (j >= 0 && S.F[gi][o[j]] > fi) { o[j + 1] = o[j]; --j; }
+              o[j + 1] = si;
+            }
+          }
+        }
+        if (lane == 0) S.iters[gi] += 1;
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+
+    // ---- unit result: lowest value, ties to the lowest simplex index
+    if (warp == 0) {
+      float f = INFINITY;
+      int best = 0x7fffffff;
+      if (lane < nsim) { f = S.F[lane][S.ord[lane][0]]; best = lane; }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float f2 = __shfl_xor_sync(0xffffffffu, f, o);
+        const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        if (f2 < f || (f2 == f && b2 < best)) { f = f2; best = b2; }
+      }
+      float* rec = P.unit_best + (size_t)unit * kUnitRec;
+      if (best < nsim) {
+        if (lane < kNumParams) rec[4 + lane] = S.U[best][S.ord[best][0]][lane];
+        if (lane == 0) {
+          rec[0] = f;
+          rec[1] = __int_as_float(g0 * G + best);
+          rec[2] = __int_as_float(S.iters[best]);
+          rec[3] = __int_as_float(evals);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ finalize
+// FP64 re-computation of the winner's error with the literal RK4 stages (the
+// serial check next to the parallel value, as Fig. 4's CPU_check column).
+struct Drive64 { double na, nn, ta, tn; };
+
+__device__ void deriv64(const double* p, const double* s, const Drive64& d, double* ds) {
+  const double ta = p[kSeAg] * (s[2] - s[0]);
+  const double tn = p[kSeAnt] * (s[3] + s[0]);
+  const double kp = p[kNcAg] + p[kNcAnt];
+  ds[0] = s[1];
+  ds[1] = (ta - tn - p[kBp] * s[1] - kp * s[0]) / p[kJ];
+  ds[2] = (s[4] - ta - p[kLtAg] * s[2]) / p[kBAg];
+  ds[3] = (s[5] - tn - p[kLtAnt] * s[3]) / p[kBAnt];
+  ds[4] = (d.na - s[4]) / d.ta;
+  ds[5] = (d.nn - s[5]) / d.tn;
+}
+
+__device__ void rk4_64(const double* p, double* s, const Drive64& d, double h) {
+  double k1[6], k2[6], k3[6], k4[6], t[6];
+  deriv64(p, s, d, k1);
+  for (int i = 0; i < 6; ++i) t[i] = s[i] + 0.5 * h * k1[i];
+  deriv64(p, t, d, k2);
+  for (int i = 0; i < 6; ++i) t[i] = s[i] + 0.5 * h * k2[i];
+  deriv64(p, t, d, k3);
+  for (int i = 0; i < 6; ++i) t[i] = s[i] + h * k3[i];
+  deriv64(p, t, d, k4);
+  for (int i = 0; i < 6; ++i) s[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+__device__ void rest64(const double* p, double th, double* s, double* fa, double* fn) {
+  const double ta = p[kNcFix] + p[kNcAg] * th, tn = p[kNcFix] - p[kNcAnt] * th;
+  s[0] = th; s[1] = 0.0;
+  s[2] = th + ta / p[kSeAg];
+  s[3] = tn / p[kSeAnt] - th;
+  *fa = ta * (1.0 + p[kLtAg] / p[kSeAg]) + p[kLtAg] * th;
+  *fn = tn * (1.0 + p[kLtAnt] / p[kSeAnt]) - p[kLtAnt] * th;
+  s[4] = *fa; s[5] = *fn;
+}
+
+__device__ void errors64(const float* pf, const DevSac& d, const float* y, double* mse, double* mae) {
+  double p[kNumParams];
+  for (int j = 0; j < kNumParams; ++j) p[j] = (double)pf[j];
+  const double th0 = d.th0, thf = d.thf, sg = d.sign;
+  const int nsub = d.nsub;
+  const double h = 1.0 / ((double)d.fs * nsub);
+  double tau = p[kPw] * (double)d.fs * (double)nsub / 1000.0;
+  if (!(tau >= 0.0)) tau = 0.0;
+  if (tau > 1.0e9) tau = 1.0e9;
+  const double fl = floor(tau);
+  const long long J = (long long)fl;
+  const double frac = tau - fl;
+  double s[6], fa0, fn0, faf, fnf, tmp[6];
+  rest64(p, th0, s, &fa0, &fn0);
+  rest64(p, thf, tmp, &faf, &fnf);
+  const Drive64 d0{fa0, fn0, p[kTdeAg] * 1e-3, p[kTacAnt] * 1e-3};
+  const Drive64 d1{p[kNsacAg], p[kNsacAnt], p[kTacAg] * 1e-3, p[kTdeAnt] * 1e-3};
+  const Drive64 d2{faf, fnf, p[kTdeAg] * 1e-3, p[kTacAnt] * 1e-3};
+  double s2 = 0.0, s1 = 0.0;
+  {
+    const double e = sg * s[0] - (double)y[0];
+    s2 += e * e; s1 += fabs(e);
+  }
+  const long long g_on = (long long)d.onset * nsub;
+  for (int k = 0; k + 1 < d.L; ++k) {
+    for (int j = 0; j < nsub; ++j) {
+      const long long rel = (long long)k * nsub + j - g_on;
+      if (rel < 0) rk4_64(p, s, d0, h);
+      else if (rel < J) rk4_64(p, s, d1, h);
+      else if (rel == J) { rk4_64(p, s, d1, frac * h); rk4_64(p, s, d2, h - frac * h); }
+      else rk4_64(p, s, d2, h);
+    }
+    const double e = sg * s[0] - (double)y[k + 1];
+    s2 += e * e; s1 += fabs(e);
+  }
+  *mse = s2 / d.L;
+  *mae = s1 / d.L;
+}
+
+__global__ void k_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
+                           int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
+                           opmm_fit_result* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  int w = -1, wsimp = 0x7fffffff, evals = 0;
+  float wf = INFINITY;
+  for (int u = ustart[b]; u < ustart[b] + ngroups; ++u) {
+    const float* rec = unit_best + (size_t)u * kUnitRec;
+    const float f = rec[0];
+    const int s = __float_as_int(rec[1]);
+    evals += __float_as_int(rec[3]);
+    if (w < 0 || f < wf || (f == wf && s < wsimp)) { w = u; wf = f; wsimp = s; }
+  }
+  opmm_fit_result r;
+  const DevSac d = sacs[b];
+  const float* rec = unit_best + (size_t)w * kUnitRec;
+  for (int j = 0; j < kNumParams; ++j)
+    r.opc[j] = pc[(size_t)b * kNumParams + j] * __expf(fminf(fmaxf(rec[4 + j], lnlo), lnhi));
+  r.f = wf;
+  r.iterations_run = __float_as_int(rec[2]);
+  r.winner = wsimp;
+  r.evaluations = evals;
+  r.reserved = 0;
+  if (isfinite(wf)) {
+    double mse, mae;
+    errors64(r.opc, d, traces + d.off, &mse, &mae);
+    r.rms_deg = sqrt(mse);
+    r.l1_deg = mae;
+    r.status = 0;
+  } else {
+    r.rms_deg = INFINITY;
+    r.l1_deg = INFINITY;
+    r.status = 1;
+  }
+  out[b] = r;
+}
+
+// ------------------------------------------------------------------ launch wrappers
+cudaError_t launch_gather(const float* const* src, const DevSac* sacs, float* dst, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_gather<<<n, 128, 0, st>>>(src, sacs, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nominal(const DevSac* sacs, int n, int pulse_mode, const float* init_opc, float* pc,
+                           cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 128;
+  const int blocks = (n * 32 + threads - 1) / threads;
+  k_nominal<<<blocks, threads, 0, st>>>(sacs, n, pulse_mode, init_opc, pc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simulate(const float* opc, int n, const DevSac* sacs, const int* sac_of,
+                            const long long* out_off, float* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_simulate<<<(n + 127) / 128, 128, 0, st>>>(opc, n, sacs, sac_of, out_off, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, const float* traces, float* f,
+                         unsigned* err, int num_sms, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const int threads = 256;
+  int blocks = (m + threads - 1) / threads;
+  if (blocks > 4 * num_sms) blocks = 4 * num_sms;
+  const size_t smem = 2 * (size_t)((L + 3) & ~3) * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_score<<<blocks, threads, smem, st>>>(opc, m, sac, traces, f, err);
+  return cudaGetLastError();
+}
+
+// The dynamic shared-memory attribute is set by search_occupancy(), which the
+// host calls for the same (G, lcap) before any launch or graph capture.
+template <int G>
+static cudaError_t launch_search_g(const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
+  const size_t smem = search_smem_bytes<G>(P.lcap);
+  k_search<G><<<blocks_per_sm * num_sms, search_threads<G>(), smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+int search_threads_for(int G) {
+  switch (G) {
+    case 8: return search_threads<8>();
+    case 16: return search_threads<16>();
+    case 32: return search_threads<32>();
+    default: return 0;
+  }
+}
+
+size_t search_smem_for(int G, int lcap) {
+  switch (G) {
+    case 8: return search_smem_bytes<8>(lcap);
+    case 16: return search_smem_bytes<16>(lcap);
+    case 32: return search_smem_bytes<32>(lcap);
+    default: return 0;
+  }
+}
+
+cudaError_t search_occupancy(int G, int lcap, int* blocks_per_sm) {
+  const size_t smem = search_smem_for(G, lcap);
+  cudaError_t e;
+  switch (G) {
+    case 8:
+      e = cudaFuncSetAttribute(k_search<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_search<8>, search_threads<8>(), smem);
+    case 16:
+      e = cudaFuncSetAttribute(k_search<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_search<16>, search_threads<16>(), smem);
+    case 32:
+      e = cudaFuncSetAttribute(k_search<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_search<32>, search_threads<32>(), smem);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_search(int G, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
+  switch (G) {
+    case 8: return launch_search_g<8>(P, blocks_per_sm, num_sms, st);
+    case 16: return launch_search_g<16>(P, blocks_per_sm, num_sms, st);
+    case 32: return launch_search_g<32>(P, blocks_per_sm, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
+                            int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
+                            opmm_fit_result* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_finalize<<<(n + 63) / 64, 64, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace opmm

@@ -1,0 +1,52 @@
+// launch.h -- host-side entry points of the CUDA kernels (internal to the
+// library; the public interface is include/opmm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/opmm.h"
+
+namespace opmm {
+
+struct DevSac;
+
+// Arguments of the persistent search kernel.
+struct SearchParams {
+  const DevSac* sacs;      // [B] staged saccades
+  const float* traces;     // packed traces
+  const float* pc;         // [B][18] box centres
+  const int* sac_index;    // [B] Philox counter word of each saccade
+  const int2* units;       // [n_units] (saccade, simplex group), most work first
+  int n_units;
+  int S;                   // simplices per saccade
+  int T;                   // iteration cap
+  int lcap;                // trace capacity of the shared-memory stage (floats, multiple of 4)
+  float lnlo, lnhi;        // ln of the box bounds
+  float step;              // initial simplex edge
+  float tolx, tolf;
+  uint32_t seed_lo, seed_hi;
+  int* counter;            // work-queue head, zeroed before each launch
+  float* unit_best;        // [n_units][24] results per unit
+  unsigned* err;           // error bits
+};
+
+cudaError_t launch_gather(const float* const* src, const DevSac* sacs, float* dst, int n, cudaStream_t st);
+cudaError_t launch_nominal(const DevSac* sacs, int n, int pulse_mode, const float* init_opc, float* pc,
+                           cudaStream_t st);
+cudaError_t launch_simulate(const float* opc, int n, const DevSac* sacs, const int* sac_of,
+                            const long long* out_off, float* out, cudaStream_t st);
+cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, const float* traces, float* f,
+                         unsigned* err, int num_sms, cudaStream_t st);
+int search_threads_for(int G);
+size_t search_smem_for(int G, int lcap);
+cudaError_t search_occupancy(int G, int lcap, int* blocks_per_sm);
+cudaError_t launch_search(int G, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st);
+cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
+                            int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
+                            opmm_fit_result* out, cudaStream_t st);
+
+constexpr int kUnitRecFloats = 24;
+
+}  // namespace opmm

@@ -1,0 +1,386 @@
+// plant.cuh -- device-side oculomotor plant for the 18-parameter OPMM.
+//
+// Model (paper Sec. 2.1 and Sec. 2.2.1, Table 1; the paper names the
+// components, this is the linear six-state reading used throughout):
+//   state (theta, omega, x, y, Fa, Fn) in the saccade's positive frame
+//   Ta = K_SE_AG (x - theta), Tn = K_SE_ANT (y + theta), K_P = N_C_AG + N_C_ANT
+//   theta' = omega
+//   J omega' = Ta - Tn - B_P omega - K_P theta
+//   B_AG x'  = Fa - Ta - K_LT_AG x
+//   B_ANT y' = Fn - Tn - K_LT_ANT y
+//   tau Fa' = Na - Fa,  tau Fn' = Nn - Fn   (pulse-step drive, Sec. 2.1)
+//
+// Integration: classical RK4 with h = 1 / (fs * nsub), nsub = round(1e4 / fs)
+// (h ~ 0.1 ms); the substep holding the pulse end is split into two RK4 steps.
+//
+// GB300 formulation.  Within one input phase the plant is linear and
+// time-invariant, so one RK4 step is exactly the affine map
+//     s <- s* + (I + Q)(s - s*),   Q = T4(hA) - I = hA(I + hA/2(I + hA/3(I + hA/4)))
+// around the phase equilibrium s*.  Q is built once per candidate in
+// "increment form" (no leading identity, so slow modes keep full relative
+// precision) and raised to the nsub-th power by squaring, giving one 6x6
+// update per recorded sample instead of nsub x 4 derivative evaluations.  The
+// matrix is block upper triangular: a 4x4 mechanical block shared by both
+// phases, a 4x2 coupling and a diagonal activation block per phase.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace opmm {
+
+// OPC vector layout: the column order of the paper's example output (Fig. 4).
+enum : int {
+  kSeAg = 0, kSeAnt, kLtAg, kLtAnt, kNcAg, kNcAnt, kBp, kBAg, kBAnt, kJ,
+  kTacAg, kTacAnt, kTdeAg, kTdeAnt, kNcFix, kNsacAg, kNsacAnt, kPw, kNumParams
+};
+
+// Per-saccade constants in the positive (mirrored) frame.
+struct SacConst {
+  int L;          // samples in the window
+  int onset;      // onset sample (pulse starts at onset / fs)
+  int nsub;       // RK4 substeps per sample
+  float fs;       // sample rate, Hz
+  float h;        // RK4 step, s
+  float th0;      // start fixation (th0 <= thf)
+  float thf;      // end fixation
+};
+
+// Continuous-time coefficients (A matrix entries) of one candidate.
+struct Coef {
+  float m10, m11, m12, m13;   // omega row: theta, omega, x, y
+  float m20, m22, cx;         // x row: theta, x, Fa
+  float m30, m33, cy;         // y row: theta, y, Fn
+  float da1, dn1;             // -1/tau of Fa, Fn during the pulse
+  float da2, dn2;             // -1/tau of Fa, Fn after the pulse
+};
+
+// Increment-form propagator of both phases: the 4x4 mechanical block m is
+// shared; c1/d1 (pulse) and c2/d2 (step) are the coupling and activation
+// blocks.  (I + P) acting on a phase-k deviation vector e:
+//   e_m <- e_m + m e_m + ck e_f,   e_f <- e_f + dk .* e_f
+struct Prop2 {
+  float m[4][4];
+  float c1[4][2], c2[4][2];
+  float d1[2], d2[2];
+};
+
+__device__ __forceinline__ void make_coef(const float* p, Coef& k) {
+  const float iJ = 1.0f / p[kJ];
+  const float iBa = 1.0f / p[kBAg];
+  const float iBn = 1.0f / p[kBAnt];
+  const float kp = p[kNcAg] + p[kNcAnt];
+  k.m10 = -(p[kSeAg] + p[kSeAnt] + kp) * iJ;
+  k.m11 = -p[kBp] * iJ;
+  k.m12 = p[kSeAg] * iJ;
+  k.m13 = -p[kSeAnt] * iJ;
+  k.m20 = p[kSeAg] * iBa;
+  k.m22 = -(p[kSeAg] + p[kLtAg]) * iBa;
+  k.cx = iBa;
+  k.m30 = -p[kSeAnt] * iBn;
+  k.m33 = -(p[kSeAnt] + p[kLtAnt]) * iBn;
+  k.cy = iBn;
+  // activation/deactivation times are in ms (Table 1)
+  k.da1 = -1000.0f / p[kTacAg];
+  k.dn1 = -1000.0f / p[kTdeAnt];
+  k.da2 = -1000.0f / p[kTdeAg];
+  k.dn2 = -1000.0f / p[kTacAnt];
+}
+
+// Tension held at fixation angle th (tension slope and intercept, Sec. 2.1).
+__device__ __forceinline__ float ta_eq(const float* p, float th) { return fmaf(p[kNcAg], th, p[kNcFix]); }
+__device__ __forceinline__ float tn_eq(const float* p, float th) { return fmaf(-p[kNcAnt], th, p[kNcFix]); }
+
+// Rest state at fixation angle th.
+__device__ __forceinline__ void rest_state(const float* p, float th, float* s) {
+  const float ta = ta_eq(p, th), tn = tn_eq(p, th);
+  s[0] = th;
+  s[1] = 0.0f;
+  s[2] = th + ta / p[kSeAg];
+  s[3] = tn / p[kSeAnt] - th;
+  s[4] = ta * (1.0f + p[kLtAg] / p[kSeAg]) + p[kLtAg] * th;
+  s[5] = tn * (1.0f + p[kLtAnt] / p[kSeAnt]) - p[kLtAnt] * th;
+}
+
+// Equilibrium under constant active-state tensions (fa, fn): from x' = y' = 0
+// the series tensions are Ta = a_g (fa - K_LT_AG th), Tn = a_n (fn + K_LT_ANT th)
+// with a = K_SE / (K_SE + K_LT); the globe balance Ta - Tn = K_P th fixes th.
+__device__ __forceinline__ void drive_equilibrium(const float* p, float fa, float fn, float* s) {
+  const float ag = p[kSeAg] / (p[kSeAg] + p[kLtAg]);
+  const float an = p[kSeAnt] / (p[kSeAnt] + p[kLtAnt]);
+  const float kp = p[kNcAg] + p[kNcAnt];
+  const float th = (ag * fa - an * fn) / (kp + ag * p[kLtAg] + an * p[kLtAnt]);
+  const float ta = ag * (fa - p[kLtAg] * th);
+  const float tn = an * (fn + p[kLtAnt] * th);
+  s[0] = th;
+  s[1] = 0.0f;
+  s[2] = th + ta / p[kSeAg];
+  s[3] = tn / p[kSeAnt] - th;
+  s[4] = fa;
+  s[5] = fn;
+}
+
+// out = Zm * w for the sparse mechanical block Zm = h * A_mech, w dense 4x4
+// (or 4x2 via ncol).  z: {h, h m10, h m11, h m12, h m13, h m20, h m22, h m30, h m33}
+struct ZMech {
+  float h, m10, m11, m12, m13, m20, m22, m30, m33;
+};
+
+template <int NC>
+__device__ __forceinline__ void zm_mul(const ZMech& z, const float (&w)[4][NC], float (&o)[4][NC]) {
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const float w0 = w[0][j], w1 = w[1][j], w2 = w[2][j], w3 = w[3][j];
+    o[0][j] = z.h * w1;
+    o[1][j] = fmaf(z.m13, w3, fmaf(z.m12, w2, fmaf(z.m11, w1, z.m10 * w0)));
+    o[2][j] = fmaf(z.m22, w2, z.m20 * w0);
+    o[3][j] = fmaf(z.m33, w3, z.m30 * w0);
+  }
+}
+
+// Single-substep increment propagator Q = T4(hA) - I of both phases by Horner:
+// W3 = I + Z/4, W2 = I + Z W3 / 3, W1 = I + Z W2 / 2, Q = Z W1, block by block.
+__device__ __forceinline__ void step_increment(const Coef& k, float h, Prop2& q) {
+  ZMech z;
+  z.h = h;
+  z.m10 = h * k.m10; z.m11 = h * k.m11; z.m12 = h * k.m12; z.m13 = h * k.m13;
+  z.m20 = h * k.m20; z.m22 = h * k.m22; z.m30 = h * k.m30; z.m33 = h * k.m33;
+  const float zcx = h * k.cx, zcy = h * k.cy;
+  // mechanical block
+  float w[4][4], t[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f);
+  // W3 = I + Zm / 4
+  zm_mul<4>(z, w, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f) + 0.25f * t[i][j];
+  // W2 = I + Zm W3 / 3
+  zm_mul<4>(z, w, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f) + t[i][j] * (1.0f / 3.0f);
+  // W1 = I + Zm W2 / 2
+  zm_mul<4>(z, w, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f) + 0.5f * t[i][j];
+  // Qm = Zm W1
+  zm_mul<4>(z, w, q.m);
+  // coupling and activation blocks, per phase
+#pragma unroll
+  for (int ph = 0; ph < 2; ++ph) {
+    const float zda = h * (ph == 0 ? k.da1 : k.da2);
+    const float zdn = h * (ph == 0 ? k.dn1 : k.dn2);
+    // level 3: Wc3 = Zc / 4, Wd3 = 1 + Zd / 4
+    float wc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.25f * zcx, 0.f}, {0.f, 0.25f * zcy}};
+    float wda = 1.0f + 0.25f * zda, wdn = 1.0f + 0.25f * zdn;
+    float tc[4][2];
+    // level 2: Wc2 = (Zm Wc3 + Zc Wd3) / 3, Wd2 = 1 + Zd Wd3 / 3
+    zm_mul<2>(z, wc, tc);
+    tc[2][0] = fmaf(zcx, wda, tc[2][0]);
+    tc[3][1] = fmaf(zcy, wdn, tc[3][1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { wc[i][0] = tc[i][0] * (1.0f / 3.0f); wc[i][1] = tc[i][1] * (1.0f / 3.0f); }
+    wda = 1.0f + zda * wda * (1.0f / 3.0f);
+    wdn = 1.0f + zdn * wdn * (1.0f / 3.0f);
+    // level 1: Wc1 = (Zm Wc2 + Zc Wd2) / 2, Wd1 = 1 + Zd Wd2 / 2
+    zm_mul<2>(z, wc, tc);
+    tc[2][0] = fmaf(zcx, wda, tc[2][0]);
+    tc[3][1] = fmaf(zcy, wdn, tc[3][1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { wc[i][0] = 0.5f * tc[i][0]; wc[i][1] = 0.5f * tc[i][1]; }
+    wda = 1.0f + 0.5f * zda * wda;
+    wdn = 1.0f + 0.5f * zdn * wdn;
+    // Q: Qc = Zm Wc1 + Zc Wd1, Qd = Zd Wd1
+    zm_mul<2>(z, wc, tc);
+    tc[2][0] = fmaf(zcx, wda, tc[2][0]);
+    tc[3][1] = fmaf(zcy, wdn, tc[3][1]);
+    if (ph == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { q.c1[i][0] = tc[i][0]; q.c1[i][1] = tc[i][1]; }
+      q.d1[0] = zda * wda; q.d1[1] = zdn * wdn;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { q.c2[i][0] = tc[i][0]; q.c2[i][1] = tc[i][1]; }
+      q.d2[0] = zda * wda; q.d2[1] = zdn * wdn;
+    }
+  }
+}
+
+// r = a + b + a b  (increment form of (I + a)(I + b)); r may alias neither.
+__device__ __forceinline__ void prop_mul(const Prop2& a, const Prop2& b, Prop2& r) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float acc = a.m[i][j] + b.m[i][j];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc = fmaf(a.m[i][kk], b.m[kk][j], acc);
+      r.m[i][j] = acc;
+    }
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      float acc1 = fmaf(a.c1[i][f], b.d1[f], a.c1[i][f] + b.c1[i][f]);
+      float acc2 = fmaf(a.c2[i][f], b.d2[f], a.c2[i][f] + b.c2[i][f]);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        acc1 = fmaf(a.m[i][kk], b.c1[kk][f], acc1);
+        acc2 = fmaf(a.m[i][kk], b.c2[kk][f], acc2);
+      }
+      r.c1[i][f] = acc1;
+      r.c2[i][f] = acc2;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    r.d1[f] = fmaf(a.d1[f], b.d1[f], a.d1[f] + b.d1[f]);
+    r.d2[f] = fmaf(a.d2[f], b.d2[f], a.d2[f] + b.d2[f]);
+  }
+}
+
+// out = (I + q)^n - I by binary powering (n >= 1).
+__device__ __forceinline__ void prop_pow(const Prop2& q, int n, Prop2& out) {
+  Prop2 base = q, tmp;
+  bool have = false;
+  while (true) {
+    if (n & 1) {
+      if (have) { prop_mul(out, base, tmp); out = tmp; }
+      else { out = base; have = true; }
+    }
+    n >>= 1;
+    if (!n) break;
+    prop_mul(base, base, tmp);
+    base = tmp;
+  }
+}
+
+// e <- (I + P_phase) e for a phase-1 (PH = 1) or phase-2 (PH = 2) deviation.
+template <int PH>
+__device__ __forceinline__ void prop_apply(const Prop2& q, float (&e)[6]) {
+  const float (&c)[4][2] = PH == 1 ? q.c1 : q.c2;
+  const float (&d)[2] = PH == 1 ? q.d1 : q.d2;
+  float n[6];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float acc = fmaf(q.m[i][0], e[0], e[i]);
+    acc = fmaf(q.m[i][1], e[1], acc);
+    acc = fmaf(q.m[i][2], e[2], acc);
+    acc = fmaf(q.m[i][3], e[3], acc);
+    acc = fmaf(c[i][0], e[4], acc);
+    acc = fmaf(c[i][1], e[5], acc);
+    n[i] = acc;
+  }
+  n[4] = fmaf(d[0], e[4], e[4]);
+  n[5] = fmaf(d[1], e[5], e[5]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) e[i] = n[i];
+}
+
+// v = A w for the homogeneous deviation system of one phase.
+__device__ __forceinline__ void a_apply(const Coef& k, float da, float dn, const float (&w)[6], float (&v)[6]) {
+  v[0] = w[1];
+  v[1] = fmaf(k.m13, w[3], fmaf(k.m12, w[2], fmaf(k.m11, w[1], k.m10 * w[0])));
+  v[2] = fmaf(k.cx, w[4], fmaf(k.m22, w[2], k.m20 * w[0]));
+  v[3] = fmaf(k.cy, w[5], fmaf(k.m33, w[3], k.m30 * w[0]));
+  v[4] = da * w[4];
+  v[5] = dn * w[5];
+}
+
+// One RK4 step of length hs on e' = A e (Horner form of T4(hs A) e).
+__device__ __forceinline__ void rk4_vec(const Coef& k, float da, float dn, float hs, float (&e)[6]) {
+  float w[6], v[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) w[i] = e[i];
+  const float c[4] = {0.25f * hs, hs * (1.0f / 3.0f), 0.5f * hs, hs};
+#pragma unroll
+  for (int lev = 0; lev < 4; ++lev) {
+    a_apply(k, da, dn, w, v);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) w[i] = fmaf(c[lev], v[i], e[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) e[i] = w[i];
+}
+
+// Stiffness guard shared with the oracle's rule: h * (B_P/J + (K_SE_AG +
+// K_LT_AG)/B_AG + (K_SE_ANT + K_LT_ANT)/B_ANT + 1/min tau) must stay <= 2.5.
+__device__ __forceinline__ bool too_stiff(const float* p, float h) {
+  float tmin = fminf(fminf(p[kTacAg], p[kTacAnt]), fminf(p[kTdeAg], p[kTdeAnt]));
+  float est = p[kBp] / p[kJ] + (p[kSeAg] + p[kLtAg]) / p[kBAg] +
+              (p[kSeAnt] + p[kLtAnt]) / p[kBAnt] + 1000.0f / tmin;
+  return !(h * est <= 2.5f);
+}
+
+// Walk one candidate's trajectory from the first sample after onset to the
+// end of the window.  The sink receives, for each sample k > onset, the value
+// dth = theta_k - thf (positive frame).  Samples k <= onset sit at th0 and are
+// handled by the caller.  Returns the number of samples emitted.
+template <class Sink>
+__device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& sink) {
+  const int ntot = sc.L - 1 - sc.onset;
+  if (ntot <= 0) return 0;
+  Coef k;
+  make_coef(p, k);
+  // pulse end, in substeps after onset
+  float tau = p[kPw] * sc.fs * (float)sc.nsub * 1e-3f;
+  tau = fminf(fmaxf(tau, 0.0f), 1.0e9f);
+  const float jf = floorf(tau);
+  const float frac = tau - jf;
+  const float span = (float)ntot * (float)sc.nsub;
+  int n1, jsw = 0;
+  bool sw;
+  if (jf >= span) { n1 = ntot; sw = false; }
+  else {
+    const int J = (int)jf;
+    n1 = J / sc.nsub;
+    jsw = J - n1 * sc.nsub;
+    sw = true;
+  }
+  float s0[6], s1[6], s2[6];
+  rest_state(p, sc.th0, s0);
+  drive_equilibrium(p, p[kNsacAg], p[kNsacAnt], s1);
+  rest_state(p, sc.thf, s2);
+  float e[6], dl[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) { e[i] = s0[i] - s1[i]; dl[i] = s1[i] - s2[i]; }
+  const float off1 = s1[0] - sc.thf;
+  Prop2 phi;
+  {
+    Prop2 q;
+    step_increment(k, sc.h, q);
+    prop_pow(q, sc.nsub, phi);
+  }
+  int kk = sc.onset + 1;
+  for (int i = 0; i < n1; ++i) {
+    prop_apply<1>(phi, e);
+    sink.emit(kk++, e[0] + off1);
+  }
+  if (sw) {
+    // pulse-end interval: jsw whole substeps of the pulse phase, the split
+    // substep (two RK4 steps around the switch), the rest of the step phase
+    Prop2 q;
+    step_increment(k, sc.h, q);
+    for (int s = 0; s < jsw; ++s) prop_apply<1>(q, e);
+    const float h1 = frac * sc.h;
+    rk4_vec(k, k.da1, k.dn1, h1, e);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) e[i] += dl[i];
+    rk4_vec(k, k.da2, k.dn2, sc.h - h1, e);
+    for (int s = jsw + 1; s < sc.nsub; ++s) prop_apply<2>(q, e);
+    sink.emit(kk++, e[0]);
+    const int n2 = ntot - n1 - 1;
+    for (int i = 0; i < n2; ++i) {
+      prop_apply<2>(phi, e);
+      sink.emit(kk++, e[0]);
+    }
+  }
+  return ntot;
+}
+
+}  // namespace opmm

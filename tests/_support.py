@@ -1,0 +1,53 @@
+"""Test helpers: turn seeded workloads into oracle-generated traces and into
+batches for the CUDA library (each side simulates with its own code; the GPU
+side only ever receives what the oracle generated here)."""
+import numpy as np
+
+import oracle as O
+import paper_2007_09884_gb300 as G
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def oracle_inputs(w, idx=None, noise=True):
+    """Per saccade: box centre pn (float32-exact), hidden OPC, clean and
+    recorded trace (float32-exact) for the oracle and the GPU alike."""
+    idx = range(w.B) if idx is None else idx
+    out = []
+    for i in idx:
+        A, D = float(w.amplitude[i]), float(w.dur_ms[i])
+        pn = f32(O.nominal_opc(A, D, calibrated=w.calibrated_pulse))
+        ph = f32(pn * w.mult[i])
+        L, fs, on = int(w.L[i]), float(w.fs[i]), int(w.onset[i])
+        th0, thf = float(w.theta0[i]), float(w.thetaf[i])
+        clean = O.simulate_rk4(ph, L, fs, on, th0, thf)
+        y = f32(clean + (w.noise[i] if noise else 0.0))
+        out.append(dict(i=i, pn=pn, ph=ph, clean=clean, y=y, L=L, fs=fs, onset=on, th0=th0,
+                        thf=thf, dur=D, A=A))
+    return out
+
+
+def to_batch(items, device=None):
+    traces = [np.asarray(it["y"], dtype=np.float32) for it in items]
+    if device is not None:
+        import torch
+        packed = np.zeros(sum((len(t) + 3) // 4 * 4 for t in traces), dtype=np.float32)
+        offs, o = [], 0
+        for t in traces:
+            packed[o:o + len(t)] = t
+            offs.append(o)
+            o += (len(t) + 3) // 4 * 4
+        tens = torch.from_numpy(packed).to(device)
+        return G.make_batch(tens, [it["fs"] for it in items], [it["onset"] for it in items],
+                            [it["th0"] for it in items], [it["thf"] for it in items],
+                            [it["dur"] for it in items], n_samples=[it["L"] for it in items],
+                            offsets=offs)
+    return G.make_batch(traces, [it["fs"] for it in items], [it["onset"] for it in items],
+                        [it["th0"] for it in items], [it["thf"] for it in items],
+                        [it["dur"] for it in items])
+
+
+def centres(items):
+    return np.stack([it["pn"] for it in items]).astype(np.float32)

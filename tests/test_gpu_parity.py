@@ -1,0 +1,293 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written here, derived in the design doc):
+  * trajectories: 1e-4 deg max abs per sample;
+  * objective f (mean squared error): the trajectory bound d gives
+    |f_gpu - f_ref| <= 2 sqrt(f) d + d^2, plus FP32 summation noise;
+  * fits: |RMS_gpu - RMS_oracle| <= 1e-3 deg (both runs of the same estimator
+    from the same seeded starts; FP32 and FP64 may take different branches on
+    near-ties, so the parameter vectors are not compared);
+  * the FP64 residual the GPU reports for its winner equals the oracle's
+    recomputation for that same OPC vector (the OptErr / CPU_check pattern of
+    Fig. 4, there ~1e-6 relative; here both are FP64 RK4 of the same vector).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2007_09884_gb300 as G
+import workloads as W
+from _support import centres, f32, oracle_inputs, to_batch
+
+pytestmark = pytest.mark.gpu
+
+TRAJ_TOL = 1e-4
+RMS_TOL = 1e-3
+
+
+def f_tol(f):
+    return 2.0 * math.sqrt(max(f, 0.0)) * TRAJ_TOL + TRAJ_TOL**2 + 1e-6 * f
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    h = G.opmm_create(0)
+    yield h
+    G.opmm_destroy(h)
+
+
+def _random_cases(n, seed):
+    rng = np.random.default_rng(seed)
+    cases = []
+    for i in range(n):
+        fs = float(rng.choice([250.0, 500.0, 1000.0, 600.0, 120.0]))
+        A = float(np.exp(rng.uniform(np.log(0.5), np.log(40.0))))
+        D = 2.2 * A + 21.0
+        L = int(rng.integers(1, 401))
+        if i % 7 == 0:
+            on = L - 1
+        else:
+            on = int(min(L - 1, math.ceil(0.01 * fs)))
+        th0 = float(np.float32(rng.uniform(-15, 15)))
+        sgn = 1.0 if rng.integers(2) else -1.0
+        thf = float(np.float32(th0 + sgn * A))
+        box = rng.uniform(0.5, 2.0, 18)
+        if i % 11 == 0:
+            box[17] = 40.0     # pulse outlasting the window
+        p = f32(O.nominal_opc(A, D) * box)
+        cases.append(dict(p=p, L=L, fs=fs, onset=on, th0=th0, thf=thf, dur=D))
+    return cases
+
+
+def test_simulate_matches_oracle_10k(ctx):
+    """T5: 10^4 random OPC vectors in the [0.5x, 2x] box, rates 120-1000 Hz,
+    windows 1-400 samples, both directions, onset at the window edge, pulses
+    longer than the window: max abs error <= 1e-4 deg per sample."""
+    cases = _random_cases(10000, 11)
+    batch = G.make_batch([np.zeros(c["L"], np.float32) for c in cases], [c["fs"] for c in cases],
+                         [c["onset"] for c in cases], [c["th0"] for c in cases],
+                         [c["thf"] for c in cases], [c["dur"] for c in cases])
+    opc = np.stack([c["p"] for c in cases]).astype(np.float32)
+    out, offs = G.opmm_simulate(ctx, opc, batch)
+    worst = 0.0
+    for c, o in zip(cases, offs):
+        ref = O.simulate_rk4(c["p"], c["L"], c["fs"], c["onset"], c["th0"], c["thf"])
+        got = out[o:o + c["L"]].astype(np.float64)
+        worst = max(worst, float(np.max(np.abs(got - ref))))
+    assert worst <= TRAJ_TOL, worst
+
+
+def test_simulate_device_buffers_and_sac_index(ctx):
+    torch = pytest.importorskip("torch")
+    cases = _random_cases(64, 12)
+    batch = G.make_batch([np.zeros(c["L"], np.float32) for c in cases[:4]], [c["fs"] for c in cases[:4]],
+                         [c["onset"] for c in cases[:4]], [c["th0"] for c in cases[:4]],
+                         [c["thf"] for c in cases[:4]], [c["dur"] for c in cases[:4]])
+    idx = np.arange(64, dtype=np.int32) % 4
+    opc = np.stack([c["p"] for c in cases]).astype(np.float32)
+    host, offs = G.opmm_simulate(ctx, opc, batch, sac_index=idx)
+    dev_out = torch.zeros(len(host), dtype=torch.float32, device="cuda")
+    dev, _ = G.opmm_simulate(ctx, torch.from_numpy(opc).cuda(), batch, sac_index=idx, out=dev_out)
+    np.testing.assert_array_equal(dev.cpu().numpy(), host)
+
+
+def test_nominal_opc_matches_oracle(ctx):
+    """Box centres: Table 1 with W = D - 6 ms; the calibrated agonist pulse
+    agrees with the oracle's bisection to 1e-4 relative."""
+    amps = np.concatenate([np.linspace(0.5, 45.0, 40), [1.0, 10.0, 20.0, 40.0]]).astype(np.float32)
+    n = len(amps)
+    D = (2.2 * amps.astype(np.float64) + 21.0).astype(np.float32)
+    sg = np.where(np.arange(n) % 2 == 0, 1.0, -1.0).astype(np.float32)
+    batch = G.make_batch([np.zeros(100, np.float32)] * n, [1000.0] * n, [10] * n, [0.0] * n,
+                         sg * amps, D)
+    cal = G.opmm_nominal_opc(ctx, batch, G.OPMM_PULSE_CALIBRATED)
+    tab = G.opmm_nominal_opc(ctx, batch, G.OPMM_PULSE_TABLE1)
+    for i in range(n):
+        ref_t = O.nominal_table1(float(D[i]))
+        np.testing.assert_allclose(tab[i], ref_t.astype(np.float32), rtol=0, atol=0)
+        ref_n = O.calibrate_pulse(float(amps[i]), float(D[i]))
+        assert abs(cal[i, 15] - ref_n) <= 1e-4 * ref_n, (amps[i], cal[i, 15], ref_n)
+
+
+def test_score_matches_oracle(ctx):
+    w = W.single10()
+    it = oracle_inputs(w)[0]
+    batch = to_batch([it])
+    rng = np.random.default_rng(3)
+    m = 3000
+    opc = (it["pn"] * rng.uniform(0.5, 2.0, (m, 18))).astype(np.float32)
+    opc[-1] = it["pn"].astype(np.float32) * np.array([1] * 6 + [10.0] + [1] * 2 + [0.1] + [1] * 8,
+                                                     dtype=np.float32)   # too stiff: +inf
+    got = G.opmm_score(ctx, opc, batch)
+    for i in range(m):
+        ref, _ = O.errors(opc[i].astype(np.float64), it["L"], it["fs"], it["onset"], it["th0"],
+                          it["thf"], it["y"])
+        if math.isinf(ref):
+            assert math.isinf(got[i])
+        else:
+            assert abs(got[i] - ref) <= f_tol(ref), (i, got[i], ref)
+
+
+def test_grid_argmin_matches_oracle(ctx):
+    """T7 on the GPU: a 41 x 41 grid over (passive viscosity, agonist pulse)
+    with the other OPCs at the hidden values; the GPU's best grid point is the
+    oracle's (or ties with it within the objective tolerance)."""
+    w = W.single10()
+    it = oracle_inputs(w)[0]
+    batch = to_batch([it])
+    g = np.linspace(np.log(0.5), np.log(2.0), 41)
+    pts = np.array([(a, b) for a in g for b in g])
+    base = it["ph"].copy()
+    base[6], base[15] = it["pn"][6], it["pn"][15]
+    opc = np.repeat(base[None, :], len(pts), axis=0)
+    opc[:, 6] *= np.exp(pts[:, 0])
+    opc[:, 15] *= np.exp(pts[:, 1])
+    opc = opc.astype(np.float32)
+    got = G.opmm_score(ctx, opc, batch)
+    ref = np.array([O.errors(o.astype(np.float64), it["L"], it["fs"], it["onset"], it["th0"],
+                             it["thf"], it["y"])[0] for o in opc])
+    kg, kr = int(np.argmin(got)), int(np.argmin(ref))
+    assert kg == kr or ref[kg] - ref[kr] <= f_tol(ref[kr])
+
+
+def _fit_both(ctx, items, S, T, seed=0, nthreads=None, **kw):
+    batch = to_batch(items)
+    res = G.opmm_fit_batch(ctx, batch, candidates=22 * S, iterations=T, seed=seed,
+                           init_opc=centres(items), **kw)
+    refs = []
+    for j, it in enumerate(items):
+        refs.append(O.fit(it["pn"], it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"],
+                          S, T, seed=seed, sac_index=j, nthreads=nthreads,
+                          box_lo=kw.get("box_lo", 0.5), box_hi=kw.get("box_hi", 2.0),
+                          step=kw.get("init_step", 0.05)))
+    return res, refs
+
+
+def test_fit_single10_matches_oracle(ctx):
+    """T10/T11 on the single-saccade workload (10 deg, 1 kHz, 150 samples,
+    4,096 candidates x 20 iterations, seed 0)."""
+    w = W.single10()
+    items = oracle_inputs(w)
+    res, refs = _fit_both(ctx, items, w.simplices, w.iterations, seed=w.seed)
+    it, ref = items[0], refs[0]
+    assert res["status"][0] == 0
+    assert abs(res["rms_deg"][0] - ref["rms"]) <= RMS_TOL, (res["rms_deg"][0], ref["rms"])
+    assert res["rms_deg"][0] < 0.1
+    # CPU_check: the oracle's FP64 error of the GPU's own winner
+    p = res["opc"][0].astype(np.float64)
+    mse, mae = O.errors(p, it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"])
+    assert res["rms_deg"][0] == pytest.approx(math.sqrt(mse), rel=1e-9)
+    assert res["l1_deg"][0] == pytest.approx(mae, rel=1e-9)
+    assert abs(res["f"][0] - mse) <= f_tol(mse)
+
+
+def test_fit_uneven_batch_matches_oracle(ctx):
+    """Mixed rates, both directions, ragged windows, a partial simplex group."""
+    w = W.uneven10k(B=12)
+    items = oracle_inputs(w)
+    res, refs = _fit_both(ctx, items, 19, 8)
+    for j in range(len(items)):
+        assert res["status"][j] == 0
+        assert abs(res["rms_deg"][j] - refs[j]["rms"]) <= RMS_TOL, (j, res["rms_deg"][j], refs[j]["rms"])
+        p = res["opc"][j].astype(np.float64)
+        it = items[j]
+        mse, _ = O.errors(p, it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"])
+        assert res["rms_deg"][j] == pytest.approx(math.sqrt(mse), rel=1e-9)
+
+
+def test_fit_zero_iterations_is_best_initial_vertex(ctx):
+    w = W.uneven10k(B=3)
+    items = oracle_inputs(w)
+    res, refs = _fit_both(ctx, items, 5, 0)
+    for j in range(3):
+        assert abs(res["rms_deg"][j] - refs[j]["rms"]) <= RMS_TOL
+        assert res["iterations_run"][j] == 0
+
+
+def test_plan_graph_is_deterministic_and_equals_fit_batch(ctx):
+    w = W.uneven10k(B=6)
+    items = oracle_inputs(w)
+    batch = to_batch(items)
+    kw = dict(candidates=22 * 40, iterations=6, init_opc=centres(items))
+    a = G.opmm_fit_batch(ctx, batch, **kw)
+    plan = G.opmm_plan_create(ctx, batch, **kw)
+    b = plan.execute()
+    c = plan.execute()
+    for k in ("opc", "f", "rms_deg", "winner", "iterations_run"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(b[k], c[k])
+    info = plan.info()
+    assert info["simplices_per_block"] in (8, 16, 32)
+    plan.destroy()
+
+
+def test_device_traces_equal_host_traces(ctx):
+    w = W.uneven10k(B=5)
+    items = oracle_inputs(w)
+    kw = dict(candidates=22 * 20, iterations=5, init_opc=centres(items))
+    a = G.opmm_fit_batch(ctx, to_batch(items), **kw)
+    b = G.opmm_fit_batch(ctx, to_batch(items, device="cuda"), **kw)
+    for k in ("opc", "f", "rms_deg", "winner"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_calibrated_centres_used_when_none_given(ctx):
+    """Without init_opc the GPU computes the calibrated box centre itself; the
+    fit then matches an oracle fit centred on the oracle's calibration."""
+    w = W.batch1024(B=3)
+    items = oracle_inputs(w)
+    batch = to_batch(items)
+    res = G.opmm_fit_batch(ctx, batch, candidates=22 * 12, iterations=6,
+                           pulse_init=G.OPMM_PULSE_CALIBRATED)
+    for j, it in enumerate(items):
+        ref = O.fit(it["pn"], it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"], 12, 6,
+                    sac_index=j)
+        assert abs(res["rms_deg"][j] - ref["rms"]) <= RMS_TOL
+
+
+def test_edge_windows(ctx):
+    """A one-sample window, a window that ends at onset, zero amplitude."""
+    y1 = np.array([0.3], np.float32)
+    y2 = np.linspace(0, 1, 12).astype(np.float32)
+    y3 = (0.01 * np.sin(np.arange(80))).astype(np.float32)
+    batch = G.make_batch([y1, y2, y3], [1000.0] * 3, [0, 11, 10], [0.0, 0.0, 2.0], [5.0, 8.0, 2.0],
+                         [32.0, 38.6, 21.0])
+    pc = np.stack([O.nominal_table1(d) for d in (32.0, 38.6, 21.0)]).astype(np.float32)
+    res = G.opmm_fit_batch(ctx, batch, candidates=44, iterations=4, init_opc=pc)
+    for j, (y, on, t0, tf) in enumerate([(y1, 0, 0.0, 5.0), (y2, 11, 0.0, 8.0), (y3, 10, 2.0, 2.0)]):
+        ref = O.fit(pc[j].astype(np.float64), len(y), 1000.0, on, t0, tf, y.astype(np.float64), 2, 4,
+                    sac_index=j)
+        assert abs(res["rms_deg"][j] - ref["rms"]) <= RMS_TOL
+
+
+@pytest.mark.parametrize("bad", ["L0", "onset", "fs", "box", "cand", "opc", "dur"])
+def test_invalid_arguments_are_rejected(ctx, bad):
+    y = np.zeros(50, np.float32)
+    L, on, fs, lo, cand = 50, 5, 1000.0, 0.5, 44
+    pc = O.nominal_table1(30.0).astype(np.float32)[None, :]
+    dur = 30.0
+    if bad == "L0":
+        L = 0
+    elif bad == "onset":
+        on = 50
+    elif bad == "fs":
+        fs = -1.0
+    elif bad == "box":
+        lo = 1.5
+    elif bad == "cand":
+        cand = 21
+    elif bad == "opc":
+        pc = pc.copy()
+        pc[0, 9] = -1.0
+    elif bad == "dur":
+        dur = 4.0
+        pc = None
+    batch = G.make_batch([y], [fs], [on], [0.0], [5.0], [dur], n_samples=[L])
+    with pytest.raises(G.OpmmError) as e:
+        G.opmm_fit_batch(ctx, batch, candidates=cand, iterations=2, box_lo=lo, init_opc=pc)
+    assert e.value.code == G.OPMM_EINVAL
