@@ -305,6 +305,8 @@ def run_ours(args, ws, rank, local):
         flops += e * flops_per_sim(int(w.L[i]), int(w.onset[i]), nsub)
         rk4_eq += e * rk4_stage_flops_per_sim(int(w.L[i]), nsub)
     mean_search_ms = statistics.mean(search_ms)
+    if not mean_search_ms > 0.0:
+        raise SystemExit("search kernel events returned no time")
     achieved = flops / (mean_search_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(local)
     mp = measured_peaks()

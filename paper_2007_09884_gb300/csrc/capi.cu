@@ -399,13 +399,13 @@ Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
   if (!s.ok()) return s;
   SearchParams P = p->params;
   if (p->ev_search[0]) {
-    s = cuda_status(cudaEventRecord(p->ev_search[0], st), "record search start");
+    s = cuda_status(cudaEventRecordWithFlags(p->ev_search[0], st, cudaEventRecordExternal), "record search start");
     if (!s.ok()) return s;
   }
   s = cuda_status(launch_search(p->G, P, p->blocks_per_sm, ctx->num_sms, st), "launch search");
   if (!s.ok()) return s;
   if (p->ev_search[1]) {
-    s = cuda_status(cudaEventRecord(p->ev_search[1], st), "record search end");
+    s = cuda_status(cudaEventRecordWithFlags(p->ev_search[1], st, cudaEventRecordExternal), "record search end");
     if (!s.ok()) return s;
   }
   s = cuda_status(launch_finalize(p->d_sacs.as<DevSac>(), p->d_traces.as<float>(), p->d_pc.as<float>(),
