@@ -398,14 +398,20 @@ Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
   s = cuda_status(cudaMemsetAsync(p->d_counter.ptr, 0, sizeof(int), st), "clear work counter");
   if (!s.ok()) return s;
   SearchParams P = p->params;
+  // inside stream capture the events become external record nodes of the
+  // graph; outside capture they are plain records
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  s = cuda_status(cudaStreamIsCapturing(st, &cap), "query capture");
+  if (!s.ok()) return s;
+  const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (p->ev_search[0]) {
-    s = cuda_status(cudaEventRecordWithFlags(p->ev_search[0], st, cudaEventRecordExternal), "record search start");
+    s = cuda_status(cudaEventRecordWithFlags(p->ev_search[0], st, ev_flags), "record search start");
     if (!s.ok()) return s;
   }
   s = cuda_status(launch_search(p->G, P, p->blocks_per_sm, ctx->num_sms, st), "launch search");
   if (!s.ok()) return s;
   if (p->ev_search[1]) {
-    s = cuda_status(cudaEventRecordWithFlags(p->ev_search[1], st, cudaEventRecordExternal), "record search end");
+    s = cuda_status(cudaEventRecordWithFlags(p->ev_search[1], st, ev_flags), "record search end");
     if (!s.ok()) return s;
   }
   s = cuda_status(launch_finalize(p->d_sacs.as<DevSac>(), p->d_traces.as<float>(), p->d_pc.as<float>(),
