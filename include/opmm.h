@@ -179,6 +179,32 @@ int opmm_plan_info(const opmm_plan* plan, int32_t* simplices_per_block, int32_t*
 int opmm_plan_last_search_ms(const opmm_plan* plan, float* ms);
 void opmm_plan_destroy(opmm_plan* plan);
 
+/* ------------------------------------------------- allocation-free fit */
+
+/* Fit one saccade without allocating any memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a real-time loop that must not stall on an allocation
+ * (cudaMalloc/cudaFree may synchronise the device), or a program whose device
+ * memory belongs to another allocator or a fixed budget.  It needs no
+ * context.
+ *   sac:        host descriptor; sac->trace_deg must be DEVICE memory
+ *   opts:       as for opmm_fit_batch (init_opc, if given, is one host [18]
+ *               vector); use_surrogate must be 0
+ *   out_device: DEVICE memory for one opmm_fit_result, written by the GPU
+ *   cuda_stream: cudaStream_t to run on (NULL = legacy default stream)
+ * Limits: n_samples <= 4096 and candidates <= 65536; larger sizes, a host
+ * trace or result pointer, or any malformed argument return OPMM_EINVAL
+ * before anything runs.  The working memory is one fixed ~37 KB __device__
+ * array inside the library, held by every GPU that loads the library until the
+ * process exits.  The first call on a device (with that device current) looks
+ * up that array's address and sets kernel attributes; make it before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU race,
+ * so run them one at a time (the call returns only after the fit finished).
+ * Returns OPMM_ETIMEDOUT if a kernel's bounded wait expired, OPMM_ECUDA on a
+ * CUDA error. */
+int opmm_fit_saccade_static(const opmm_saccade* sac, const opmm_fit_opts* opts,
+                            opmm_fit_result* out_device, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,7 +37,8 @@ PARAM_NAMES = ["SE_ag", "SE_ant", "LT_ag", "LT_ant", "PE_ag", "PE_ant", "Vis", "
 # Every symbol include/opmm.h declares.
 EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", "opmm_simulate",
            "opmm_score", "opmm_nominal_opc", "opmm_fit_batch", "opmm_plan_create",
-           "opmm_plan_execute", "opmm_plan_info", "opmm_plan_last_search_ms", "opmm_plan_destroy"]
+           "opmm_plan_execute", "opmm_plan_info", "opmm_plan_last_search_ms", "opmm_plan_destroy",
+           "opmm_fit_saccade_static"]
 
 
 class OpmmError(RuntimeError):
@@ -100,9 +101,11 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_plan_last_search_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.opmm_plan_destroy.argtypes = [vp]
     lib.opmm_plan_destroy.restype = None
+    lib.opmm_fit_saccade_static.argtypes = [ctypes.POINTER(opmm_saccade), ctypes.POINTER(opmm_fit_opts),
+                                            vp, vp]
     for name in ["opmm_create", "opmm_set_stream", "opmm_simulate", "opmm_score", "opmm_nominal_opc",
                  "opmm_fit_batch", "opmm_plan_create", "opmm_plan_execute", "opmm_plan_info",
-                 "opmm_plan_last_search_ms"]:
+                 "opmm_plan_last_search_ms", "opmm_fit_saccade_static"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -348,3 +351,17 @@ def opmm_plan_info(plan: Plan) -> dict:
 
 def opmm_plan_destroy(plan: Plan):
     plan.destroy()
+
+
+def opmm_fit_saccade_static(batch: SaccadeBatch, out_device, stream_handle: int = 0, index: int = 0,
+                            **opts) -> int:
+    """Allocation-free fit of saccade `index` of a batch whose traces are in
+    device memory; writes one opmm_fit_result into `out_device` (a device
+    tensor of at least sizeof(opmm_fit_result) bytes).  Returns the status
+    code (no context, so no error text)."""
+    lib = load_library()
+    o, keep_o = fit_opts(**opts)
+    descs, keep = batch.descriptors()
+    po, ko = _ptr(out_device)
+    return int(lib.opmm_fit_saccade_static(ctypes.byref(descs[index]), ctypes.byref(o), po,
+                                           ctypes.c_void_p(int(stream_handle) or None)))
