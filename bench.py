@@ -261,6 +261,7 @@ def run_ours(args, ws, rank, local):
     opts = dict(candidates=w.candidates, iterations=w.iterations, seed=w.seed, pulse_init=pulse)
     plan = G.Plan(ctx, batch_dev, **opts)
     info = plan.info()
+    info["autotuner_probes"] = plan.tuning()
     for _ in range(args.warmup):
         plan.execute_raw()
     torch.cuda.synchronize()

@@ -122,6 +122,13 @@ const char* opmm_last_error(const opmm_ctx* ctx);
  * restores the context's own stream. */
 int opmm_set_stream(opmm_ctx* ctx, void* cuda_stream);
 
+/* Launch-shape override for the search kernel (tuning and testing): variant
+ * in [0, count) from opmm_search_variants, or -1 (default) to let plans pick
+ * by timing.  All variants compute the same estimator; they differ in
+ * simplices per block, register budget and register-lean scheduling. */
+int opmm_set_search_variant(opmm_ctx* ctx, int32_t variant);
+int opmm_search_variants(int32_t* count);
+
 /* ------------------------------------------------------------ plant */
 
 /* Simulate n trajectories (the plant of Sec. 2.2.1 integrated by RK4,
@@ -174,6 +181,14 @@ int opmm_plan_execute(opmm_plan* plan, opmm_fit_result* out);
  * blocks per SM; and the number of kernels one execute launches. */
 int opmm_plan_info(const opmm_plan* plan, int32_t* simplices_per_block, int32_t* threads,
                    int32_t* blocks_per_sm, int32_t* kernels_per_execute);
+/* The autotuner's probes for this plan: for each launch-shape variant tried,
+ * its id, simplices per block, register bound (minimum resident blocks), the
+ * blocks per SM launched, and the probe's device time in ms (iteration cap 2).
+ * Writes at most `cap` entries; *count = number of probes (0 when the shape
+ * came from the context's cache without a log, or was not tuned). */
+int opmm_plan_tuning(const opmm_plan* plan, int32_t* variant, int32_t* simplices_per_block,
+                     int32_t* min_blocks, int32_t* blocks_per_sm, float* probe_ms, int32_t cap,
+                     int32_t* count);
 /* Device time of the persistent search kernel in the last execute, from CUDA
  * events recorded around it on the plan's stream (inside the graph). */
 int opmm_plan_last_search_ms(const opmm_plan* plan, float* ms);

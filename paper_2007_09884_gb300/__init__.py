@@ -35,9 +35,11 @@ PARAM_NAMES = ["SE_ag", "SE_ant", "LT_ag", "LT_ant", "PE_ag", "PE_ant", "Vis", "
                "Inert", "Act_ag", "Act_ant", "Deact_ag", "Deact_ant", "Step", "H_ag", "H_ant", "W"]
 
 # Every symbol include/opmm.h declares.
-EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", "opmm_simulate",
+EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", "opmm_set_search_variant",
+           "opmm_search_variants", "opmm_simulate",
            "opmm_score", "opmm_nominal_opc", "opmm_fit_batch", "opmm_plan_create",
-           "opmm_plan_execute", "opmm_plan_info", "opmm_plan_last_search_ms", "opmm_plan_destroy",
+           "opmm_plan_execute", "opmm_plan_info", "opmm_plan_tuning", "opmm_plan_last_search_ms",
+           "opmm_plan_destroy",
            "opmm_fit_saccade_static"]
 
 
@@ -89,6 +91,8 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_last_error.argtypes = [vp]
     lib.opmm_last_error.restype = ctypes.c_char_p
     lib.opmm_set_stream.argtypes = [vp, vp]
+    lib.opmm_set_search_variant.argtypes = [vp, i32]
+    lib.opmm_search_variants.argtypes = [ctypes.POINTER(i32)]
     lib.opmm_simulate.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), i32, vp, i64p, vp]
     lib.opmm_score.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), vp]
     lib.opmm_nominal_opc.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
@@ -99,13 +103,14 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_plan_execute.argtypes = [vp, ctypes.POINTER(opmm_fit_result)]
     lib.opmm_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
     lib.opmm_plan_last_search_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.opmm_plan_tuning.argtypes = [vp] + [vp] * 5 + [i32, ctypes.POINTER(i32)]
     lib.opmm_plan_destroy.argtypes = [vp]
     lib.opmm_plan_destroy.restype = None
     lib.opmm_fit_saccade_static.argtypes = [ctypes.POINTER(opmm_saccade), ctypes.POINTER(opmm_fit_opts),
                                             vp, vp]
-    for name in ["opmm_create", "opmm_set_stream", "opmm_simulate", "opmm_score", "opmm_nominal_opc",
+    for name in ["opmm_create", "opmm_set_stream", "opmm_set_search_variant", "opmm_search_variants", "opmm_simulate", "opmm_score", "opmm_nominal_opc",
                  "opmm_fit_batch", "opmm_plan_create", "opmm_plan_execute", "opmm_plan_info",
-                 "opmm_plan_last_search_ms", "opmm_fit_saccade_static"]:
+                 "opmm_plan_last_search_ms", "opmm_fit_saccade_static", "opmm_plan_tuning"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -242,6 +247,16 @@ def opmm_set_stream(ctx, stream_handle: int):
     _check(ctx, load_library().opmm_set_stream(ctx, ctypes.c_void_p(int(stream_handle) or None)))
 
 
+def opmm_set_search_variant(ctx, variant: int):
+    _check(ctx, load_library().opmm_set_search_variant(ctx, int(variant)))
+
+
+def opmm_search_variants() -> int:
+    n = ctypes.c_int32()
+    load_library().opmm_search_variants(ctypes.byref(n))
+    return int(n.value)
+
+
 def opmm_simulate(ctx, opc, batch: SaccadeBatch, sac_index=None, out=None):
     """Trajectories [n][L_i] packed; returns (out, offsets)."""
     lib = load_library()
@@ -319,6 +334,18 @@ class Plan:
         _check(self.ctx, self.lib.opmm_plan_info(self.h, *[ctypes.byref(x) for x in v]))
         return {"simplices_per_block": v[0].value, "threads": v[1].value,
                 "blocks_per_sm": v[2].value, "kernels_per_execute": v[3].value}
+
+    def tuning(self) -> list:
+        cap = 32
+        arrs = [np.zeros(cap, np.int32) for _ in range(4)]
+        ms = np.zeros(cap, np.float32)
+        cnt = ctypes.c_int32()
+        _check(self.ctx, self.lib.opmm_plan_tuning(self.h, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                                   ms.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(cnt)))
+        n = min(cnt.value, cap)
+        return [{"variant": int(arrs[0][i]), "simplices_per_block": int(arrs[1][i]),
+                 "min_blocks": int(arrs[2][i]), "blocks_per_sm": int(arrs[3][i]),
+                 "probe_ms": float(ms[i])} for i in range(n)]
 
     def last_search_ms(self) -> float:
         ms = ctypes.c_float()

@@ -207,6 +207,20 @@ extern "C" const char* opmm_last_error(const opmm_ctx* ctx) {
   return ctx->err.c_str();
 }
 
+extern "C" int opmm_set_search_variant(opmm_ctx* ctx, int32_t variant) {
+  if (!ctx) return OPMM_EINVAL;
+  if (variant < -1 || variant >= search_variant_count())
+    return fail(ctx, Status(OPMM_EINVAL, "search variant out of range"));
+  ctx->forced_variant = variant;
+  return OPMM_OK;
+}
+
+extern "C" int opmm_search_variants(int32_t* count) {
+  if (!count) return OPMM_EINVAL;
+  *count = search_variant_count();
+  return OPMM_OK;
+}
+
 extern "C" int opmm_set_stream(opmm_ctx* ctx, void* stream) {
   if (!ctx) return OPMM_EINVAL;
   ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
@@ -408,7 +422,7 @@ Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
     s = cuda_status(cudaEventRecordWithFlags(p->ev_search[0], st, ev_flags), "record search start");
     if (!s.ok()) return s;
   }
-  s = cuda_status(launch_search(p->G, P, p->blocks_per_sm, ctx->num_sms, st), "launch search");
+  s = cuda_status(launch_search_v(p->variant, P, p->blocks_per_sm, ctx->num_sms, st), "launch search");
   if (!s.ok()) return s;
   if (p->ev_search[1]) {
     s = cuda_status(cudaEventRecordWithFlags(p->ev_search[1], st, ev_flags), "record search end");
@@ -426,17 +440,19 @@ Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
                      "D2H error word");
 }
 
-// Candidate launch shapes: simplices per block G (threads = 22 G rounded to
-// warps) at the occupancy the device allows for this trace capacity.
+// Candidate launch shapes: the search kernel's variants (simplices per block G,
+// threads = 22 G rounded to warps, register bound for MINB resident blocks) at
+// the occupancy the device allows for this trace capacity.  Returns (variant,
+// blocks per SM) pairs.
 static std::vector<std::pair<int, int>> shape_candidates(int lcap) {
   std::vector<std::pair<int, int>> out;
-  for (int G : {8, 16, 32}) {
+  for (int v = 0; v < search_variant_count(); ++v) {
     int bps = 0;
-    if (search_occupancy(G, lcap, &bps) != cudaSuccess) {
+    if (search_occupancy_v(v, lcap, &bps) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
-    if (bps >= 1) out.push_back({G, bps});
+    if (bps >= 1) out.push_back({v, bps});
   }
   return out;
 }
@@ -451,17 +467,24 @@ static Status autotune(opmm_plan* p) {
   auto it = ctx->tune_cache.find(key);
   auto cands = shape_candidates(p->lcap);
   if (cands.empty()) return Status(OPMM_ECUDA, "no launchable search shape (shared memory)");
+  if (ctx->forced_variant >= 0) {
+    for (auto& cd : cands)
+      if (cd.first == ctx->forced_variant) {
+        p->variant = cd.first;
+        p->blocks_per_sm = cd.second;
+        return Status();
+      }
+    return Status(OPMM_EINVAL, "forced search variant cannot be launched with this batch");
+  }
   if (it != ctx->tune_cache.end()) {
-    p->G = it->second.first;
+    p->variant = it->second.first;
     p->blocks_per_sm = it->second.second;
+    p->tune_log = ctx->tune_logs[key];
     return Status();
   }
   if (!p->autotune || cands.size() == 1) {
-    // heuristic: 16 simplices per block if available
-    auto pick = cands[0];
-    for (auto& c : cands) if (c.first == 16) pick = c;
-    p->G = pick.first;
-    p->blocks_per_sm = pick.second;
+    p->variant = cands[0].first;        // variant 0 (16 simplices per block) when launchable
+    p->blocks_per_sm = cands[0].second;
     return Status();
   }
   cudaStream_t st = ctx->stream;
@@ -473,13 +496,13 @@ static Status autotune(opmm_plan* p) {
   std::pair<int, int> best = cands[0];
   for (auto& c : cands) {
     // the unit list depends on G: rebuild it for the probe
-    s = build_units(p, c.first);
+    s = build_units(p, search_variant_g(c.first));
     if (!s.ok()) break;
     SearchParams P = p->params;
     P.T = std::min(p->opts.iterations, 2);
     cudaMemsetAsync(p->d_counter.ptr, 0, sizeof(int), st);
     cudaEventRecord(e0, st);
-    cudaError_t le = launch_search(c.first, P, c.second, ctx->num_sms, st);
+    cudaError_t le = launch_search_v(c.first, P, c.second, ctx->num_sms, st);
     cudaEventRecord(e1, st);
     cudaError_t se = cudaStreamSynchronize(st);
     if (le != cudaSuccess || se != cudaSuccess) {
@@ -488,14 +511,16 @@ static Status autotune(opmm_plan* p) {
     }
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
+    p->tune_log.push_back({c.first, c.second, ms});
     if (ms < best_ms) { best_ms = ms; best = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!s.ok()) return s;
-  p->G = best.first;
+  p->variant = best.first;
   p->blocks_per_sm = best.second;
   ctx->tune_cache[key] = best;
+  ctx->tune_logs[key] = p->tune_log;
   return Status();
 }
 
@@ -637,6 +662,7 @@ Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm
   if (!s.ok()) return s;
   s = autotune(p);
   if (!s.ok()) return s;
+  p->G = search_variant_g(p->variant);
   s = build_units(p, p->G);
   if (!s.ok()) return s;
   p->threads = search_threads_for(p->G);
@@ -729,6 +755,23 @@ extern "C" int opmm_plan_info(const opmm_plan* plan, int32_t* g, int32_t* thread
   if (threads) *threads = plan->threads;
   if (bps) *bps = plan->blocks_per_sm;
   if (kernels) *kernels = (plan->traces_on_device ? 1 : 0) + (plan->centres_given ? 0 : 1) + plan->pre_search_kernels + 2;
+  return OPMM_OK;
+}
+
+extern "C" int opmm_plan_tuning(const opmm_plan* plan, int32_t* variant, int32_t* simplices_per_block,
+                                int32_t* min_blocks, int32_t* blocks_per_sm, float* probe_ms, int32_t cap,
+                                int32_t* count) {
+  if (!plan || !count || cap < 0) return OPMM_EINVAL;
+  const int n = (int)plan->tune_log.size();
+  *count = n;
+  for (int i = 0; i < n && i < cap; ++i) {
+    const auto& t = plan->tune_log[(size_t)i];
+    if (variant) variant[i] = t.variant;
+    if (simplices_per_block) simplices_per_block[i] = search_variant_g(t.variant);
+    if (min_blocks) min_blocks[i] = search_variant_minb(t.variant);
+    if (blocks_per_sm) blocks_per_sm[i] = t.bps;
+    if (probe_ms) probe_ms[i] = t.ms;
+  }
   return OPMM_OK;
 }
 

@@ -44,15 +44,24 @@ __global__ void k_gather(const float* const* src, const DevSac* sacs, float* dst
 }
 
 // ------------------------------------------------------------------ sinks
+// Blocked compensated summation: the squared errors of each block of samples
+// (the sample loops run in blocks of 4) are summed plainly, and each block sum
+// is added to the running total with Kahan compensation, so the relative error
+// stays O(4 eps) per block instead of growing with the window length.
 struct KahanSink {
   const float* z;   // trace minus end fixation, positive frame
   float sum, c;
+  float part;
   __device__ __forceinline__ void emit(int k, float dth) {
     const float d = dth - z[k];
-    const float y = fmaf(d, d, -c);
+    part = fmaf(d, d, part);
+  }
+  __device__ __forceinline__ void block_end() {
+    const float y = part - c;
     const float t = sum + y;
     c = (t - sum) - y;
     sum = t;
+    part = 0.0f;
   }
 };
 
@@ -60,11 +69,13 @@ struct WriteSink {
   float* out;
   float sign, thf;
   __device__ __forceinline__ void emit(int k, float dth) { out[k] = sign * (thf + dth); }
+  __device__ __forceinline__ void block_end() {}
 };
 
 struct PeakSink {
   float m;
   __device__ __forceinline__ void emit(int, float dth) { m = fmaxf(m, dth); }
+  __device__ __forceinline__ void block_end() {}
 };
 
 // Objective of one OPC vector: mean squared error over the window; the
@@ -72,10 +83,38 @@ struct PeakSink {
 __device__ __forceinline__ float objective(const float* p, const SacConst& sc, const float* z,
                                            float sum0, float c0) {
   if (too_stiff(p, sc.h)) return INFINITY;
-  KahanSink s{z, sum0, c0};
+  KahanSink s{z, sum0, c0, 0.0f};
   walk(p, sc, s);
+  s.block_end();
   const float f = (s.sum - s.c) / (float)sc.L;
   return isfinite(f) ? f : INFINITY;
+}
+
+// Parameter sources of the register-lean walk: each load() re-derives the
+// candidate's OPC vector instead of keeping it live.
+struct PtrSrc {
+  const float* p;
+  __device__ __forceinline__ void load(float (&o)[kNumParams]) const {
+#pragma unroll
+    for (int j = 0; j < kNumParams; ++j) o[j] = p[j];
+  }
+};
+
+// Candidate in ln-parameter space: u_j = a_j + s (b_j - a_j), or a trial
+// point given by trial_coord/shrink_coord (see the search kernel).
+struct ULinSrc {
+  const float* a;   // base point (shared memory)
+  const float* b;   // second point (shared memory)
+  float s;          // coefficient: u = a + s (b - a); a trial point uses its own form
+  int mode;         // 0: u = a (vertex), 1: trial_coord(q, a = centroid, b = worst), 2: shrink (a = best, b = vertex)
+  int q;
+  const float* pc;
+  float lnlo, lnhi;
+  __device__ __forceinline__ void load(float (&o)[kNumParams]) const;
+};
+
+__device__ __forceinline__ float objective_lean_guard(const float (&p)[kNumParams], const SacConst& sc) {
+  return too_stiff(p, sc.h) ? INFINITY : 0.0f;
 }
 
 // Stage one saccade for a block: TMA bulk copy of the raw trace, then the
@@ -232,6 +271,10 @@ __global__ void k_score(const float* opc, int m, const DevSac* sac, const float*
 constexpr int kUnitRec = 24;
 constexpr int kNV = kNumParams + 1;      // vertices per simplex
 constexpr int kNT = kNumParams + 4;      // trial points per simplex and iteration
+constexpr int kSortBins = 1024;          // pulse-end time bins of the per-wave ordering
+
+template <int G>
+__host__ __device__ constexpr int search_threads() { return ((G * kNT + 31) / 32) * 32; }
 
 template <int G>
 struct SearchSmem {
@@ -241,6 +284,8 @@ struct SearchSmem {
   float F[G][kNV];               // vertex values, by slot
   float FT[G][kNT];              // trial values
   float pc[kNumParams];          // box centre of the current saccade
+  int hist[kSortBins + kSortBins / 32];  // counting sort by pulse-end time (padded: bin b at b + b/32)
+  unsigned short perm[search_threads<G>()];
   unsigned char ord[G][kNV + 1]; // ord[r] = slot of rank r
   int active[G];
   int iters[G];
@@ -248,11 +293,9 @@ struct SearchSmem {
   TraceStage st;
   int cur_b;
   int unit;
+  int nvalid;
   uint64_t bar;
 };
-
-template <int G>
-__host__ __device__ constexpr int search_threads() { return ((G * kNT + 31) / 32) * 32; }
 
 template <int G>
 size_t search_smem_bytes(int lcap) {
@@ -272,6 +315,29 @@ __device__ __forceinline__ float trial_coord(int q, float xb, float w) {
 
 __device__ __forceinline__ float shrink_coord(float x1, float xi) { return x1 + 0.5f * (xi - x1); }
 
+__device__ __forceinline__ void ULinSrc::load(float (&o)[kNumParams]) const {
+#pragma unroll
+  for (int j = 0; j < kNumParams; ++j) {
+    const float u = mode == 0 ? a[j] : (mode == 1 ? trial_coord(q, a[j], b[j]) : shrink_coord(a[j], b[j]));
+    o[j] = pc[j] * __expf(fminf(fmaxf(u, lnlo), lnhi));
+  }
+}
+
+// Objective through the register-lean walk.
+__device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacConst& sc, const float* z,
+                                                float sum0, float c0) {
+  {
+    float p[kNumParams];
+    src.load(p);
+    if (too_stiff(p, sc.h)) return INFINITY;
+  }
+  KahanSink s{z, sum0, c0, 0.0f};
+  walk_lean(src, sc, s);
+  s.block_end();
+  const float f = (s.sum - s.c) / (float)sc.L;
+  return isfinite(f) ? f : INFINITY;
+}
+
 __device__ __forceinline__ float eval_u(const float (&u)[kNumParams], const float* pc, float lnlo,
                                         float lnhi, const SacConst& sc, const float* z, float sum0,
                                         float c0) {
@@ -281,8 +347,73 @@ __device__ __forceinline__ float eval_u(const float (&u)[kNumParams], const floa
   return objective(p, sc, z, sum0, c0);
 }
 
+// Sort key of a candidate: its pulse-end time, binned over the window (the
+// last bin holds pulses that outlast the window).  Lanes of a warp then run
+// nearly the same number of pulse-phase and step-phase samples.
+__device__ __forceinline__ int switch_key(float u_pw, float pc_pw, float lnlo, float lnhi, const SacConst& sc) {
+  const int ntot = sc.L - 1 - sc.onset;
+  if (ntot <= 0) return 0;
+  const float w = pc_pw * __expf(fminf(fmaxf(u_pw, lnlo), lnhi));
+  const float tau = fmaxf(w * sc.fs * 1e-3f, 0.0f);       // in samples after onset
+  const float x = tau * ((float)(kSortBins - 1) / (float)ntot);
+  return x >= (float)(kSortBins - 1) ? kSortBins - 1 : (int)x;
+}
+
+// Block-wide counting sort of this wave's candidates by key (key < 0: not
+// evaluated).  Afterwards S.perm[0 .. S.nvalid) lists candidate ids in key
+// order; candidate id = the thread index that computed the key.
+__device__ __forceinline__ int hist_slot(int b) { return b + (b >> 5); }
+
 template <int G>
-__global__ void __launch_bounds__(search_threads<G>()) k_search(SearchParams P) {
+__device__ __forceinline__ void order_wave(SearchSmem<G>& S, int key) {
+  constexpr int NT = search_threads<G>();
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < kSortBins + kSortBins / 32; i += NT) S.hist[i] = 0;
+  __syncthreads();
+  int slot = -1;
+  if (key >= 0) slot = atomicAdd(&S.hist[hist_slot(key)], 1);
+  __syncthreads();
+  if (tid < 32) {
+    // lane l owns bins [32 l, 32 l + 32), stored at 33 l + i: conflict-free
+    constexpr int per = kSortBins / 32;
+    int* h = S.hist + lane * (per + 1);
+    int s = 0;
+#pragma unroll 8
+    for (int i = 0; i < per; ++i) s += h[i];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int run = incl - s;
+#pragma unroll 8
+    for (int i = 0; i < per; ++i) {
+      const int c = h[i];
+      h[i] = run;
+      run += c;
+    }
+    if (lane == 31) S.nvalid = incl;
+  }
+  __syncthreads();
+  if (slot >= 0) S.perm[S.hist[hist_slot(key)] + slot] = (unsigned short)tid;
+  __syncthreads();
+}
+
+// Stable ranks of the 19 vertex values held by lanes 0..18 (lane r holds the
+// value at position r): rank = #{s : f_s < f_r or (f_s == f_r and s < r)}.
+__device__ __forceinline__ int stable_rank19(float fr, int lane) {
+  int rank = 0;
+#pragma unroll
+  for (int s = 0; s < kNV; ++s) {
+    const float fs = __shfl_sync(0xffffffffu, fr, s);
+    rank += (fs < fr || (fs == fr && s < lane)) ? 1 : 0;
+  }
+  return rank;
+}
+
+template <int G, int MINB, bool LEAN>
+__global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchParams P) {
   constexpr int NT = search_threads<G>();
   constexpr int NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -325,42 +456,55 @@ __global__ void __launch_bounds__(search_threads<G>()) k_search(SearchParams P) 
     int evals = kNV * nsim;
 
     // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
-    if (tid < kNV * nsim) {
-      const int gi = tid / kNV, v = tid - gi * kNV;
+    if (tid < 5 * nsim) {
+      const int gi = tid / 5, blk = tid - gi * 5;
       const int s = g0 * G + gi;
-      float u[kNumParams];
-      if (s == 0) {
+      uint32_t r[4] = {0u, 0u, 0u, 0u};
+      if (s != 0) philox4x32_10((uint32_t)P.sac_index[b], (uint32_t)s, (uint32_t)blk, 0u, P.seed_lo, P.seed_hi, r);
 #pragma unroll
-        for (int j = 0; j < kNumParams; ++j) u[j] = 0.0f;
-      } else {
+      for (int q = 0; q < 4; ++q) {
+        const int j = 4 * blk + q;
+        if (j < kNumParams)
+          S.U[gi][0][j] = s == 0 ? 0.0f : P.lnlo + (P.lnhi - P.lnlo) * ((float)(r[q] >> 8) * (1.0f / 16777216.0f));
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nsim * kNumParams * kNumParams; idx += NT) {
+      const int gi = idx / (kNumParams * kNumParams);
+      const int rem = idx - gi * kNumParams * kNumParams;
+      const int v = rem / kNumParams + 1, j = rem - (v - 1) * kNumParams;
+      float x = S.U[gi][0][j];
+      if (j == v - 1) x += P.step;
+      S.U[gi][v][j] = x;
+    }
+    __syncthreads();
+    {
+      int key = -1;
+      if (tid < kNV * nsim) {
+        const int gi = tid / kNV, v = tid - gi * kNV;
+        key = switch_key(S.U[gi][v][kPw], S.pc[kPw], P.lnlo, P.lnhi, sc);
+      }
+      order_wave<G>(S, key);
+      if (tid < S.nvalid) {
+        const int c = S.perm[tid];
+        const int gi = c / kNV, v = c - gi * kNV;
+        if (LEAN) {
+          const ULinSrc src{S.U[gi][v], S.U[gi][v], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
+          S.F[gi][v] = objective_lean(src, sc, z, sum0, c0);
+        } else {
+          float u[kNumParams];
 #pragma unroll
-        for (int blk = 0; blk < 5; ++blk) {
-          uint32_t r[4];
-          philox4x32_10((uint32_t)P.sac_index[b], (uint32_t)s, (uint32_t)blk, 0u, P.seed_lo, P.seed_hi, r);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (4 * blk + q < kNumParams)
-              u[4 * blk + q] = P.lnlo + (P.lnhi - P.lnlo) * ((float)(r[q] >> 8) * (1.0f / 16777216.0f));
-          }
+          for (int j = 0; j < kNumParams; ++j) u[j] = S.U[gi][v][j];
+          S.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
         }
       }
-#pragma unroll
-      for (int j = 0; j < kNumParams; ++j) {
-        if (v > 0 && j == v - 1) u[j] += P.step;
-        S.U[gi][v][j] = u[j];
-      }
-      S.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
     }
     __syncthreads();
     for (int gi = warp; gi < nsim; gi += NW) {
+      const float fv = lane < kNV ? S.F[gi][lane] : INFINITY;
+      const int rank = stable_rank19(fv, lane);
+      if (lane < kNV) S.ord[gi][rank] = (unsigned char)lane;
       if (lane == 0) {
-        unsigned char* o = S.ord[gi];
-        for (int i = 0; i < kNV; ++i) {
-          const float fi = S.F[gi][i];
-          int j = i - 1;
-          while (j >= 0 && S.F[gi][o[j]] > fi) { o[j + 1] = o[j]; --j; }
-          o[j + 1] = (unsigned char)i;
-        }
         S.active[gi] = 1;
         S.iters[gi] = 0;
       }
@@ -397,25 +541,51 @@ __global__ void __launch_bounds__(search_threads<G>()) k_search(SearchParams P) 
       }
       __syncthreads();
 
-      // ---- one wave: all n + 4 trial points of every active simplex
-      if (tid < kNT * nsim) {
-        const int gi = tid / kNT, q = tid - gi * kNT;
-        if (S.active[gi]) {
-          const unsigned char* o = S.ord[gi];
-          float u[kNumParams];
-          if (q < 4) {
-            const int ws = o[kNumParams];
-#pragma unroll
-            for (int j = 0; j < kNumParams; ++j) {
-              u[j] = trial_coord(q, S.XB[gi][j], S.U[gi][ws][j]);
-              S.XT[gi][q][j] = u[j];
-            }
-          } else {
-            const int s1 = o[0], si = o[q - 3];
-#pragma unroll
-            for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(S.U[gi][s1][j], S.U[gi][si][j]);
+      // ---- one wave: all n + 4 trial points of every active simplex, ordered
+      // by pulse-end time
+      {
+        int key = -1;
+        if (tid < kNT * nsim) {
+          const int gi = tid / kNT, q = tid - gi * kNT;
+          if (S.active[gi]) {
+            const unsigned char* o = S.ord[gi];
+            const float up = q < 4 ? trial_coord(q, S.XB[gi][kPw], S.U[gi][o[kNumParams]][kPw])
+                                   : shrink_coord(S.U[gi][o[0]][kPw], S.U[gi][o[q - 3]][kPw]);
+            key = switch_key(up, S.pc[kPw], P.lnlo, P.lnhi, sc);
           }
-          S.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
+        }
+        order_wave<G>(S, key);
+        if (tid < S.nvalid) {
+          const int c = S.perm[tid];
+          const int gi = c / kNT, q = c - gi * kNT;
+          const unsigned char* o = S.ord[gi];
+          if (LEAN) {
+            ULinSrc src;
+            if (q < 4) {
+              const int ws = o[kNumParams];
+#pragma unroll
+              for (int j = 0; j < kNumParams; ++j) S.XT[gi][q][j] = trial_coord(q, S.XB[gi][j], S.U[gi][ws][j]);
+              src = ULinSrc{S.XT[gi][q], S.XT[gi][q], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
+            } else {
+              src = ULinSrc{S.U[gi][o[0]], S.U[gi][o[q - 3]], 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
+            }
+            S.FT[gi][q] = objective_lean(src, sc, z, sum0, c0);
+          } else {
+            float u[kNumParams];
+            if (q < 4) {
+              const int ws = o[kNumParams];
+#pragma unroll
+              for (int j = 0; j < kNumParams; ++j) {
+                u[j] = trial_coord(q, S.XB[gi][j], S.U[gi][ws][j]);
+                S.XT[gi][q][j] = u[j];
+              }
+            } else {
+              const int s1 = o[0], si = o[q - 3];
+#pragma unroll
+              for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(S.U[gi][s1][j], S.U[gi][si][j]);
+            }
+            S.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
+          }
         }
       }
       __syncthreads();
@@ -437,32 +607,36 @@ __global__ void __launch_bounds__(search_threads<G>()) k_search(SearchParams P) 
         } else {
           if (fci < fw) { kind = 3; fnew = fci; } else kind = -1;
         }
+        // current order in registers: lane r < 19 holds the slot of rank r
+        const int my_slot = lane < kNV ? (int)o[lane] : 0;
         if (kind >= 0) {
-          const int ws = o[kNumParams];
+          // replace the worst vertex; the new point goes after every vertex
+          // with a value <= its own (ties stay in front of it)
+          const int ws = __shfl_sync(0xffffffffu, my_slot, kNumParams);
           if (lane < kNumParams) S.U[gi][ws][lane] = S.XT[gi][kind][lane];
+          const float fr_l = lane < kNumParams ? S.F[gi][my_slot] : INFINITY;
+          const unsigned le = __ballot_sync(0xffffffffu, lane < kNumParams && fr_l <= fnew);
+          const int pos = __popc(le);                     // ranks 0..pos-1 keep their place
+          const int from = lane < pos ? lane : lane - 1;  // ranks above pos shift up by one
+          const int moved = __shfl_sync(0xffffffffu, my_slot, from < 0 ? 0 : from);
           __syncwarp();
-          if (lane == 0) {
-            S.F[gi][ws] = fnew;
-            int i = kNumParams;
-            while (i > 0 && S.F[gi][o[i - 1]] > fnew) { o[i] = o[i - 1]; --i; }
-            o[i] = (unsigned char)ws;
-          }
+          if (lane < kNV) o[lane] = (unsigned char)(lane < pos ? my_slot : (lane == pos ? ws : moved));
+          if (lane == 0) S.F[gi][ws] = fnew;
         } else {
           if (lane < kNumParams) {
             const float x1 = S.U[gi][o[0]][lane];
             for (int r = 1; r < kNV; ++r) S.U[gi][o[r]][lane] = shrink_coord(x1, S.U[gi][o[r]][lane]);
           }
-          if (lane >= 1 && lane < kNV) S.F[gi][o[lane]] = S.FT[gi][4 + lane - 1];
-          __syncwarp();
-          if (lane == 0) {
-            for (int i = 1; i < kNV; ++i) {
-              const unsigned char si = o[i];
-              const float fi = S.F[gi][si];
-              int j = i - 1;
-              while (j >= 0 && S.F[gi][o[j]] > fi) { o[j + 1] = o[j]; --j; }
-              o[j + 1] = si;
-            }
+          float fv = INFINITY;
+          if (lane == 0) fv = S.F[gi][my_slot];
+          if (lane >= 1 && lane < kNV) {
+            fv = S.FT[gi][4 + lane - 1];
+            S.F[gi][my_slot] = fv;
           }
+          // stable sort of [x1, xs2, ..., xs19] by value
+          const int rank = stable_rank19(fv, lane);
+          __syncwarp();
+          if (lane < kNV) o[rank] = (unsigned char)my_slot;
         }
         if (lane == 0) S.iters[gi] += 1;
         __syncwarp();
@@ -498,29 +672,32 @@ __global__ void __launch_bounds__(search_threads<G>()) k_search(SearchParams P) 
 // ------------------------------------------------------------------ finalize
 // FP64 re-computation of the winner's error with the literal RK4 stages (the
 // serial check next to the parallel value, as Fig. 4's CPU_check column).
-struct Drive64 { double na, nn, ta, tn; };
+struct Drive64 { double na, nn, ita, itn; };   // drives and reciprocal time constants
 
-__device__ void deriv64(const double* p, const double* s, const Drive64& d, double* ds) {
-  const double ta = p[kSeAg] * (s[2] - s[0]);
-  const double tn = p[kSeAnt] * (s[3] + s[0]);
-  const double kp = p[kNcAg] + p[kNcAnt];
+struct Plant64 {
+  double kse_ag, kse_ant, klt_ag, klt_ant, kp, bp, iJ, iBa, iBn;
+};
+
+__device__ void deriv64(const Plant64& c, const double* s, const Drive64& d, double* ds) {
+  const double ta = c.kse_ag * (s[2] - s[0]);
+  const double tn = c.kse_ant * (s[3] + s[0]);
   ds[0] = s[1];
-  ds[1] = (ta - tn - p[kBp] * s[1] - kp * s[0]) / p[kJ];
-  ds[2] = (s[4] - ta - p[kLtAg] * s[2]) / p[kBAg];
-  ds[3] = (s[5] - tn - p[kLtAnt] * s[3]) / p[kBAnt];
-  ds[4] = (d.na - s[4]) / d.ta;
-  ds[5] = (d.nn - s[5]) / d.tn;
+  ds[1] = (ta - tn - c.bp * s[1] - c.kp * s[0]) * c.iJ;
+  ds[2] = (s[4] - ta - c.klt_ag * s[2]) * c.iBa;
+  ds[3] = (s[5] - tn - c.klt_ant * s[3]) * c.iBn;
+  ds[4] = (d.na - s[4]) * d.ita;
+  ds[5] = (d.nn - s[5]) * d.itn;
 }
 
-__device__ void rk4_64(const double* p, double* s, const Drive64& d, double h) {
+__device__ void rk4_64(const Plant64& c, double* s, const Drive64& d, double h) {
   double k1[6], k2[6], k3[6], k4[6], t[6];
-  deriv64(p, s, d, k1);
+  deriv64(c, s, d, k1);
   for (int i = 0; i < 6; ++i) t[i] = s[i] + 0.5 * h * k1[i];
-  deriv64(p, t, d, k2);
+  deriv64(c, t, d, k2);
   for (int i = 0; i < 6; ++i) t[i] = s[i] + 0.5 * h * k2[i];
-  deriv64(p, t, d, k3);
+  deriv64(c, t, d, k3);
   for (int i = 0; i < 6; ++i) t[i] = s[i] + h * k3[i];
-  deriv64(p, t, d, k4);
+  deriv64(c, t, d, k4);
   for (int i = 0; i < 6; ++i) s[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
@@ -534,9 +711,15 @@ __device__ void rest64(const double* p, double th, double* s, double* fa, double
   s[4] = *fa; s[5] = *fn;
 }
 
+// Mean squared and mean absolute error of the winner's trajectory, FP64,
+// literal RK4 stages with the pulse-end substep split (the serial check).
 __device__ void errors64(const float* pf, const DevSac& d, const float* y, double* mse, double* mae) {
   double p[kNumParams];
   for (int j = 0; j < kNumParams; ++j) p[j] = (double)pf[j];
+  Plant64 c;
+  c.kse_ag = p[kSeAg]; c.kse_ant = p[kSeAnt]; c.klt_ag = p[kLtAg]; c.klt_ant = p[kLtAnt];
+  c.kp = p[kNcAg] + p[kNcAnt]; c.bp = p[kBp];
+  c.iJ = 1.0 / p[kJ]; c.iBa = 1.0 / p[kBAg]; c.iBn = 1.0 / p[kBAnt];
   const double th0 = d.th0, thf = d.thf, sg = d.sign;
   const int nsub = d.nsub;
   const double h = 1.0 / ((double)d.fs * nsub);
@@ -549,9 +732,10 @@ __device__ void errors64(const float* pf, const DevSac& d, const float* y, doubl
   double s[6], fa0, fn0, faf, fnf, tmp[6];
   rest64(p, th0, s, &fa0, &fn0);
   rest64(p, thf, tmp, &faf, &fnf);
-  const Drive64 d0{fa0, fn0, p[kTdeAg] * 1e-3, p[kTacAnt] * 1e-3};
-  const Drive64 d1{p[kNsacAg], p[kNsacAnt], p[kTacAg] * 1e-3, p[kTdeAnt] * 1e-3};
-  const Drive64 d2{faf, fnf, p[kTdeAg] * 1e-3, p[kTacAnt] * 1e-3};
+  const double ide_ag = 1000.0 / p[kTdeAg], iac_ant = 1000.0 / p[kTacAnt];
+  const Drive64 d0{fa0, fn0, ide_ag, iac_ant};
+  const Drive64 d1{p[kNsacAg], p[kNsacAnt], 1000.0 / p[kTacAg], 1000.0 / p[kTdeAnt]};
+  const Drive64 d2{faf, fnf, ide_ag, iac_ant};
   double s2 = 0.0, s1 = 0.0;
   {
     const double e = sg * s[0] - (double)y[0];
@@ -561,10 +745,10 @@ __device__ void errors64(const float* pf, const DevSac& d, const float* y, doubl
   for (int k = 0; k + 1 < d.L; ++k) {
     for (int j = 0; j < nsub; ++j) {
       const long long rel = (long long)k * nsub + j - g_on;
-      if (rel < 0) rk4_64(p, s, d0, h);
-      else if (rel < J) rk4_64(p, s, d1, h);
-      else if (rel == J) { rk4_64(p, s, d1, frac * h); rk4_64(p, s, d2, h - frac * h); }
-      else rk4_64(p, s, d2, h);
+      if (rel < 0) rk4_64(c, s, d0, h);
+      else if (rel < J) rk4_64(c, s, d1, h);
+      else if (rel == J) { rk4_64(c, s, d1, frac * h); rk4_64(c, s, d2, h - frac * h); }
+      else rk4_64(c, s, d2, h);
     }
     const double e = sg * s[0] - (double)y[k + 1];
     s2 += e * e; s1 += fabs(e);
@@ -649,13 +833,64 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
   return cudaGetLastError();
 }
 
-// The dynamic shared-memory attribute is set by search_occupancy(), which the
-// host calls for the same (G, lcap) before any launch or graph capture.
-template <int G>
-static cudaError_t launch_search_g(const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
+// Launch-shape variants of the search kernel: simplices per block G and the
+// minimum resident blocks per SM the register allocation is bounded for.
+struct SearchVariantDesc { int G, minb, lean; };
+static const SearchVariantDesc kVariants[] = {
+    {16, 1, 0}, {8, 2, 0}, {16, 1, 1}, {8, 2, 1}, {8, 3, 1}, {16, 2, 1}, {8, 4, 1}, {32, 1, 1}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int search_variant_count() { return kNumVariants; }
+int search_variant_g(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].G : 0; }
+int search_variant_minb(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].minb : 0; }
+int search_variant_lean(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].lean : 0; }
+int search_variant_for_g(int G) {
+  for (int v = 0; v < kNumVariants; ++v)
+    if (kVariants[v].G == G) return v;
+  return -1;
+}
+
+template <int G, int MINB, bool LEAN>
+static cudaError_t occ_v(int lcap, int* bps) {
+  const size_t smem = search_smem_bytes<G>(lcap);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_search<G, MINB, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, MINB, LEAN>, search_threads<G>(), smem);
+}
+
+// The dynamic shared-memory attribute is set by search_occupancy_v(), which the
+// host calls for the same variant and lcap before any launch or graph capture.
+template <int G, int MINB, bool LEAN>
+static cudaError_t launch_v(const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
   const size_t smem = search_smem_bytes<G>(P.lcap);
-  k_search<G><<<blocks_per_sm * num_sms, search_threads<G>(), smem, st>>>(P);
+  k_search<G, MINB, LEAN><<<blocks_per_sm * num_sms, search_threads<G>(), smem, st>>>(P);
   return cudaGetLastError();
+}
+
+#define OPMM_VARIANT_SWITCH(v, CALL)        \
+  switch (v) {                              \
+    case 0: return CALL(16, 1, false);      \
+    case 1: return CALL(8, 2, false);       \
+    case 2: return CALL(16, 1, true);       \
+    case 3: return CALL(8, 2, true);        \
+    case 4: return CALL(8, 3, true);        \
+    case 5: return CALL(16, 2, true);       \
+    case 6: return CALL(8, 4, true);        \
+    case 7: return CALL(32, 1, true);       \
+    default: return cudaErrorInvalidValue;  \
+  }
+
+cudaError_t search_occupancy_v(int v, int lcap, int* blocks_per_sm) {
+#define OCC_CALL(G, M, L) occ_v<G, M, L>(lcap, blocks_per_sm)
+  OPMM_VARIANT_SWITCH(v, OCC_CALL)
+#undef OCC_CALL
+}
+
+cudaError_t launch_search_v(int v, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
+#define LAUNCH_CALL(G, M, L) launch_v<G, M, L>(P, blocks_per_sm, num_sms, st)
+  OPMM_VARIANT_SWITCH(v, LAUNCH_CALL)
+#undef LAUNCH_CALL
 }
 
 int search_threads_for(int G) {
@@ -676,41 +911,22 @@ size_t search_smem_for(int G, int lcap) {
   }
 }
 
+// G-only entry points: the first variant with that G.
 cudaError_t search_occupancy(int G, int lcap, int* blocks_per_sm) {
-  const size_t smem = search_smem_for(G, lcap);
-  cudaError_t e;
-  switch (G) {
-    case 8:
-      e = cudaFuncSetAttribute(k_search<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_search<8>, search_threads<8>(), smem);
-    case 16:
-      e = cudaFuncSetAttribute(k_search<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_search<16>, search_threads<16>(), smem);
-    case 32:
-      e = cudaFuncSetAttribute(k_search<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_search<32>, search_threads<32>(), smem);
-    default:
-      return cudaErrorInvalidValue;
-  }
+  return search_occupancy_v(search_variant_for_g(G), lcap, blocks_per_sm);
 }
 
 cudaError_t launch_search(int G, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
-  switch (G) {
-    case 8: return launch_search_g<8>(P, blocks_per_sm, num_sms, st);
-    case 16: return launch_search_g<16>(P, blocks_per_sm, num_sms, st);
-    case 32: return launch_search_g<32>(P, blocks_per_sm, num_sms, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_search_v(search_variant_for_g(G), P, blocks_per_sm, num_sms, st);
 }
 
 cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
                             int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
                             opmm_fit_result* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_finalize<<<(n + 63) / 64, 64, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n, out);
+  // the FP64 recomputation is latency bound per thread and the FP64 pipe is
+  // narrow: spread the saccades over all SMs, a few threads per block
+  k_finalize<<<(n + 7) / 8, 8, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n, out);
   return cudaGetLastError();
 }
 

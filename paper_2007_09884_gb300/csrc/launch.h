@@ -39,6 +39,13 @@ cudaError_t launch_simulate(const float* opc, int n, const DevSac* sacs, const i
                             const long long* out_off, float* out, cudaStream_t st);
 cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, const float* traces, float* f,
                          unsigned* err, int num_sms, cudaStream_t st);
+int search_variant_count();
+int search_variant_g(int v);
+int search_variant_minb(int v);
+int search_variant_lean(int v);
+int search_variant_for_g(int G);
+cudaError_t search_occupancy_v(int v, int lcap, int* blocks_per_sm);
+cudaError_t launch_search_v(int v, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st);
 int search_threads_for(int G);
 size_t search_smem_for(int G, int lcap);
 cudaError_t search_occupancy(int G, int lcap, int* blocks_per_sm);

@@ -260,6 +260,119 @@ __device__ __forceinline__ void prop_pow(const Prop2& q, int n, Prop2& out) {
   }
 }
 
+// Single-phase increment propagator: the mechanical block plus one phase's
+// coupling and activation blocks (26 floats).
+struct Prop1 {
+  float m[4][4];
+  float c[4][2];
+  float d[2];
+};
+
+// Single-substep increment propagator of one phase (PH = 1 pulse, 2 step),
+// Horner form as step_increment.
+template <int PH>
+__device__ __forceinline__ void step_increment1(const Coef& k, float h, Prop1& q) {
+  ZMech z;
+  z.h = h;
+  z.m10 = h * k.m10; z.m11 = h * k.m11; z.m12 = h * k.m12; z.m13 = h * k.m13;
+  z.m20 = h * k.m20; z.m22 = h * k.m22; z.m30 = h * k.m30; z.m33 = h * k.m33;
+  const float zcx = h * k.cx, zcy = h * k.cy;
+  const float zda = h * (PH == 1 ? k.da1 : k.da2);
+  const float zdn = h * (PH == 1 ? k.dn1 : k.dn2);
+  float w[4][4], t[4][4];
+  float wc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.25f * zcx, 0.f}, {0.f, 0.25f * zcy}};
+  float tc[4][2];
+  float wda = 1.0f + 0.25f * zda, wdn = 1.0f + 0.25f * zdn;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f);
+  zm_mul<4>(z, w, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f) + 0.25f * t[i][j];
+#pragma unroll
+  for (int lev = 3; lev >= 2; --lev) {
+    const float inv = lev == 3 ? (1.0f / 3.0f) : 0.5f;
+    zm_mul<4>(z, w, t);
+    zm_mul<2>(z, wc, tc);
+    tc[2][0] = fmaf(zcx, wda, tc[2][0]);
+    tc[3][1] = fmaf(zcy, wdn, tc[3][1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f) + t[i][j] * inv;
+      wc[i][0] = tc[i][0] * inv;
+      wc[i][1] = tc[i][1] * inv;
+    }
+    wda = 1.0f + zda * wda * inv;
+    wdn = 1.0f + zdn * wdn * inv;
+  }
+  zm_mul<4>(z, w, q.m);
+  zm_mul<2>(z, wc, q.c);
+  q.c[2][0] = fmaf(zcx, wda, q.c[2][0]);
+  q.c[3][1] = fmaf(zcy, wdn, q.c[3][1]);
+  q.d[0] = zda * wda;
+  q.d[1] = zdn * wdn;
+}
+
+// r = a + b + a b for single-phase propagators.
+__device__ __forceinline__ void prop1_mul(const Prop1& a, const Prop1& b, Prop1& r) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float acc = a.m[i][j] + b.m[i][j];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc = fmaf(a.m[i][kk], b.m[kk][j], acc);
+      r.m[i][j] = acc;
+    }
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      float acc = fmaf(a.c[i][f], b.d[f], a.c[i][f] + b.c[i][f]);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc = fmaf(a.m[i][kk], b.c[kk][f], acc);
+      r.c[i][f] = acc;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 2; ++f) r.d[f] = fmaf(a.d[f], b.d[f], a.d[f] + b.d[f]);
+}
+
+__device__ __forceinline__ void prop1_pow(const Prop1& q, int n, Prop1& out) {
+  Prop1 base = q, tmp;
+  bool have = false;
+  while (true) {
+    if (n & 1) {
+      if (have) { prop1_mul(out, base, tmp); out = tmp; }
+      else { out = base; have = true; }
+    }
+    n >>= 1;
+    if (!n) break;
+    prop1_mul(base, base, tmp);
+    base = tmp;
+  }
+}
+
+__device__ __forceinline__ void prop1_apply(const Prop1& q, float (&e)[6]) {
+  float n[6];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float acc = fmaf(q.m[i][0], e[0], e[i]);
+    acc = fmaf(q.m[i][1], e[1], acc);
+    acc = fmaf(q.m[i][2], e[2], acc);
+    acc = fmaf(q.m[i][3], e[3], acc);
+    acc = fmaf(q.c[i][0], e[4], acc);
+    acc = fmaf(q.c[i][1], e[5], acc);
+    n[i] = acc;
+  }
+  n[4] = fmaf(q.d[0], e[4], e[4]);
+  n[5] = fmaf(q.d[1], e[5], e[5]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) e[i] = n[i];
+}
+
 // e <- (I + P_phase) e for a phase-1 (PH = 1) or phase-2 (PH = 2) deviation.
 template <int PH>
 __device__ __forceinline__ void prop_apply(const Prop2& q, float (&e)[6]) {
@@ -317,10 +430,32 @@ __device__ __forceinline__ bool too_stiff(const float* p, float h) {
   return !(h * est <= 2.5f);
 }
 
+// n sample intervals of one phase with the one-sample propagator, emitting
+// theta_k - thf (+ off) after each; the sink is told where each block of 4
+// samples ends (the residual sink compensates per block).
+template <int PH, class Sink>
+__device__ __forceinline__ void run_samples(const Prop2& phi, float (&e)[6], float off, int& kk, int n,
+                                            Sink& sink) {
+  int i = 0;
+  for (; i + 4 <= n; i += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      prop_apply<PH>(phi, e);
+      sink.emit(kk++, e[0] + off);
+    }
+    sink.block_end();
+  }
+  for (; i < n; ++i) {
+    prop_apply<PH>(phi, e);
+    sink.emit(kk++, e[0] + off);
+  }
+}
+
 // Walk one candidate's trajectory from the first sample after onset to the
 // end of the window.  The sink receives, for each sample k > onset, the value
-// dth = theta_k - thf (positive frame).  Samples k <= onset sit at th0 and are
-// handled by the caller.  Returns the number of samples emitted.
+// dth = theta_k - thf (positive frame), and block_end() after blocks of
+// samples.  Samples k <= onset sit at th0 and are handled by the caller.
+// Returns the number of samples emitted.
 template <class Sink>
 __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& sink) {
   const int ntot = sc.L - 1 - sc.onset;
@@ -357,10 +492,7 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
     prop_pow(q, sc.nsub, phi);
   }
   int kk = sc.onset + 1;
-  for (int i = 0; i < n1; ++i) {
-    prop_apply<1>(phi, e);
-    sink.emit(kk++, e[0] + off1);
-  }
+  run_samples<1>(phi, e, off1, kk, n1, sink);
   if (sw) {
     // pulse-end interval: jsw whole substeps of the pulse phase, the split
     // substep (two RK4 steps around the switch), the rest of the step phase
@@ -375,10 +507,103 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
     for (int s = jsw + 1; s < sc.nsub; ++s) prop_apply<2>(q, e);
     sink.emit(kk++, e[0]);
     const int n2 = ntot - n1 - 1;
-    for (int i = 0; i < n2; ++i) {
-      prop_apply<2>(phi, e);
-      sink.emit(kk++, e[0]);
+    run_samples<2>(phi, e, 0.0f, kk, n2, sink);
+  }
+  return ntot;
+}
+
+// Single-phase version of run_samples.
+template <class Sink>
+__device__ __forceinline__ void run_samples1(const Prop1& phi, float (&e)[6], float off, int& kk, int n,
+                                             Sink& sink) {
+  int i = 0;
+  for (; i + 4 <= n; i += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      prop1_apply(phi, e);
+      sink.emit(kk++, e[0] + off);
     }
+    sink.block_end();
+  }
+  for (; i < n; ++i) {
+    prop1_apply(phi, e);
+    sink.emit(kk++, e[0] + off);
+  }
+}
+
+// Register-lean walk: the same RK4 trajectory as walk(), scheduled so that
+// only one phase's propagator is live at a time.  The parameters come from
+// `src.load(p)`, called whenever they are needed again instead of being kept:
+// the pulse phase's one-sample propagator is built first, then the
+// equilibria, the pulse-phase samples, the pulse-end interval (single-substep
+// matrices of both phases, the split step) and the step phase's one-sample
+// propagator, built only once the pulse phase is done.
+template <class PSrc, class Sink>
+__device__ __forceinline__ int walk_lean(const PSrc& src, const SacConst& sc, Sink& sink) {
+  const int ntot = sc.L - 1 - sc.onset;
+  if (ntot <= 0) return 0;
+  Prop1 phi;
+  {
+    float p[kNumParams];
+    src.load(p);
+    Coef k;
+    make_coef(p, k);
+    Prop1 q;
+    step_increment1<1>(k, sc.h, q);
+    prop1_pow(q, sc.nsub, phi);
+  }
+  float e[6], dl[6], off1, frac;
+  int n1, jsw = 0;
+  bool sw;
+  {
+    float p[kNumParams];
+    src.load(p);
+    float tau = p[kPw] * sc.fs * (float)sc.nsub * 1e-3f;
+    tau = fminf(fmaxf(tau, 0.0f), 1.0e9f);
+    const float jf = floorf(tau);
+    frac = tau - jf;
+    const float span = (float)ntot * (float)sc.nsub;
+    if (jf >= span) { n1 = ntot; sw = false; }
+    else {
+      const int J = (int)jf;
+      n1 = J / sc.nsub;
+      jsw = J - n1 * sc.nsub;
+      sw = true;
+    }
+    float s0[6], s1[6], s2[6];
+    rest_state(p, sc.th0, s0);
+    drive_equilibrium(p, p[kNsacAg], p[kNsacAnt], s1);
+    rest_state(p, sc.thf, s2);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { e[i] = s0[i] - s1[i]; dl[i] = s1[i] - s2[i]; }
+    off1 = s1[0] - sc.thf;
+  }
+  int kk = sc.onset + 1;
+  run_samples1(phi, e, off1, kk, n1, sink);
+  if (sw) {
+    {
+      float p[kNumParams];
+      src.load(p);
+      Coef k;
+      make_coef(p, k);
+      {
+        Prop1 q;
+        step_increment1<1>(k, sc.h, q);
+        for (int s = 0; s < jsw; ++s) prop1_apply(q, e);
+      }
+      const float h1 = frac * sc.h;
+      rk4_vec(k, k.da1, k.dn1, h1, e);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) e[i] += dl[i];
+      rk4_vec(k, k.da2, k.dn2, sc.h - h1, e);
+      Prop1 q;
+      step_increment1<2>(k, sc.h, q);
+      for (int s = jsw + 1; s < sc.nsub; ++s) prop1_apply(q, e);
+      prop1_pow(q, sc.nsub, phi);
+    }
+    sink.emit(kk++, e[0]);
+    const int n2 = ntot - n1 - 1;
+    run_samples1(phi, e, 0.0f, kk, n2, sink);
   }
   return ntot;
 }

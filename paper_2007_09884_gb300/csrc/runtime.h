@@ -62,6 +62,12 @@ struct HostBuf {
 struct SurrogateState;
 struct ServeState;
 
+struct TuneProbe {
+  int variant;
+  int bps;
+  float ms;
+};
+
 }  // namespace opmm
 
 struct opmm_ctx {
@@ -70,9 +76,11 @@ struct opmm_ctx {
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   std::string err;
+  int forced_variant = -1;            // -1: autotune; else a search kernel variant
   opmm::DevBuf d_err;                 // device error word of the kernels
   opmm::DevBuf scratch[16];           // per-call scratch of the synchronous entry points
   std::map<std::tuple<int, int, int, int>, std::pair<int, int>> tune_cache;
+  std::map<std::tuple<int, int, int, int>, std::vector<opmm::TuneProbe>> tune_logs;
   opmm::SurrogateState* surrogate = nullptr;   // owned, released by surrogate_release
   opmm::ServeState* serve = nullptr;           // owned, released by serve_shutdown
   opmm_ctx();
@@ -84,6 +92,7 @@ struct opmm_plan {
   int n = 0;
   opmm_fit_opts opts{};
   int S = 0;                          // simplices per saccade
+  int variant = 0;                    // search kernel variant (see kernels.cu)
   int G = 16;                         // simplices per block
   int threads = 0;
   int blocks_per_sm = 1;
@@ -95,6 +104,7 @@ struct opmm_plan {
   bool traces_on_device = false;
   bool centres_given = false;
   int pre_search_kernels = 0;
+  std::vector<opmm::TuneProbe> tune_log;  // autotuner probes (variant, blocks/SM, ms)
   std::function<opmm::Status(opmm_plan*, cudaStream_t)> pre_search;   // e.g. surrogate centres
   std::vector<opmm::DevSac> hsacs;
   std::vector<const float*> src;

@@ -291,3 +291,27 @@ def test_invalid_arguments_are_rejected(ctx, bad):
     with pytest.raises(G.OpmmError) as e:
         G.opmm_fit_batch(ctx, batch, candidates=cand, iterations=2, box_lo=lo, init_opc=pc)
     assert e.value.code == G.OPMM_EINVAL
+
+
+def test_every_search_variant_matches_oracle(ctx):
+    """All launch-shape variants of the search kernel (simplices per block,
+    register budget, register-lean schedule) run the same estimator."""
+    w = W.uneven10k(B=4)
+    items = oracle_inputs(w)
+    S, T = 19, 5
+    refs = [O.fit(it["pn"], it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"], S, T,
+                  sac_index=j) for j, it in enumerate(items)]
+    base = None
+    try:
+        for v in range(G.opmm_search_variants()):
+            G.opmm_set_search_variant(ctx, v)
+            res = G.opmm_fit_batch(ctx, to_batch(items), candidates=22 * S, iterations=T,
+                                   init_opc=centres(items))
+            for j in range(len(items)):
+                assert abs(res["rms_deg"][j] - refs[j]["rms"]) <= RMS_TOL, (v, j)
+            if base is None:
+                base = res
+            else:
+                np.testing.assert_allclose(res["f"], base["f"], rtol=1e-4, atol=1e-7)
+    finally:
+        G.opmm_set_search_variant(ctx, -1)
