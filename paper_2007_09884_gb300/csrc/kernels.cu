@@ -81,10 +81,9 @@ struct PeakSink {
 // Objective of one OPC vector: mean squared error over the window; the
 // samples up to onset (the plant at rest) are folded into (sum0, c0).
 __device__ __forceinline__ float objective(const float* p, const SacConst& sc, const float* z,
-                                           float sum0, float c0) {
-  if (too_stiff(p, sc.h)) return INFINITY;
+                                           float sum0, float c0, float* qs = nullptr, int qstride = 0) {
   KahanSink s{z, sum0, c0, 0.0f};
-  walk(p, sc, s);
+  if (walk(p, sc, s, qs, qstride, true) < 0) return INFINITY;
   s.block_end();
   const float f = (s.sum - s.c) / (float)sc.L;
   return isfinite(f) ? f : INFINITY;
@@ -272,6 +271,7 @@ constexpr int kUnitRec = 24;
 constexpr int kNV = kNumParams + 1;      // vertices per simplex
 constexpr int kNT = kNumParams + 4;      // trial points per simplex and iteration
 constexpr int kSortBins = 1024;          // pulse-end time bins of the per-wave ordering
+constexpr int kHistLen = kSortBins + kSortBins / 32;   // bin b stored at b + b/32
 
 template <int G>
 __host__ __device__ constexpr int search_threads() { return ((G * kNT + 31) / 32) * 32; }
@@ -284,7 +284,7 @@ struct SearchSmem {
   float F[G][kNV];               // vertex values, by slot
   float FT[G][kNT];              // trial values
   float pc[kNumParams];          // box centre of the current saccade
-  int hist[kSortBins + kSortBins / 32];  // counting sort by pulse-end time (padded: bin b at b + b/32)
+  int hist[2][kHistLen];          // counting sort by pulse-end time, double-buffered (padded)
   unsigned short perm[search_threads<G>()];
   unsigned char ord[G][kNV + 1]; // ord[r] = slot of rank r
   int active[G];
@@ -297,9 +297,14 @@ struct SearchSmem {
   uint64_t bar;
 };
 
+constexpr int kQSlotFloats = (int)(sizeof(Prop2) / sizeof(float));
+
+// Dynamic shared memory: the block state, the raw and shifted traces (lcap
+// floats each) and one single-substep propagator slot per thread.
 template <int G>
 size_t search_smem_bytes(int lcap) {
-  return ((sizeof(SearchSmem<G>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float);
+  return ((sizeof(SearchSmem<G>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float) +
+         (size_t)kQSlotFloats * search_threads<G>() * sizeof(float);
 }
 
 // Trial point coordinate (Lagarias et al. coefficients rho 1, chi 2, gamma 1/2).
@@ -329,7 +334,9 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
   {
     float p[kNumParams];
     src.load(p);
-    if (too_stiff(p, sc.h)) return INFINITY;
+    Coef k;
+    make_coef(p, k);
+    if (too_stiff_coef(k, sc.h)) return INFINITY;
   }
   KahanSink s{z, sum0, c0, 0.0f};
   walk_lean(src, sc, s);
@@ -340,11 +347,11 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
 
 __device__ __forceinline__ float eval_u(const float (&u)[kNumParams], const float* pc, float lnlo,
                                         float lnhi, const SacConst& sc, const float* z, float sum0,
-                                        float c0) {
+                                        float c0, float* qs, int qstride) {
   float p[kNumParams];
 #pragma unroll
   for (int j = 0; j < kNumParams; ++j) p[j] = pc[j] * __expf(fminf(fmaxf(u[j], lnlo), lnhi));
-  return objective(p, sc, z, sum0, c0);
+  return objective(p, sc, z, sum0, c0, qs, qstride);
 }
 
 // Sort key of a candidate: its pulse-end time, binned over the window (the
@@ -364,19 +371,20 @@ __device__ __forceinline__ int switch_key(float u_pw, float pc_pw, float lnlo, f
 // order; candidate id = the thread index that computed the key.
 __device__ __forceinline__ int hist_slot(int b) { return b + (b >> 5); }
 
+// Two histogram buffers alternate between waves: the one not in use is
+// cleared during this wave's scatter, so a wave costs three block barriers.
 template <int G>
-__device__ __forceinline__ void order_wave(SearchSmem<G>& S, int key) {
+__device__ __forceinline__ void order_wave(SearchSmem<G>& S, int key, int wave) {
   constexpr int NT = search_threads<G>();
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int i = tid; i < kSortBins + kSortBins / 32; i += NT) S.hist[i] = 0;
-  __syncthreads();
+  int* h0 = S.hist[wave & 1];
   int slot = -1;
-  if (key >= 0) slot = atomicAdd(&S.hist[hist_slot(key)], 1);
+  if (key >= 0) slot = atomicAdd(&h0[hist_slot(key)], 1);
   __syncthreads();
   if (tid < 32) {
     // lane l owns bins [32 l, 32 l + 32), stored at 33 l + i: conflict-free
     constexpr int per = kSortBins / 32;
-    int* h = S.hist + lane * (per + 1);
+    int* h = h0 + lane * (per + 1);
     int s = 0;
 #pragma unroll 8
     for (int i = 0; i < per; ++i) s += h[i];
@@ -396,7 +404,9 @@ __device__ __forceinline__ void order_wave(SearchSmem<G>& S, int key) {
     if (lane == 31) S.nvalid = incl;
   }
   __syncthreads();
-  if (slot >= 0) S.perm[S.hist[hist_slot(key)] + slot] = (unsigned short)tid;
+  if (slot >= 0) S.perm[h0[hist_slot(key)] + slot] = (unsigned short)tid;
+  int* h1 = S.hist[(wave + 1) & 1];
+  for (int i = tid; i < kHistLen; i += NT) h1[i] = 0;
   __syncthreads();
 }
 
@@ -412,6 +422,29 @@ __device__ __forceinline__ int stable_rank19(float fr, int lane) {
   return rank;
 }
 
+// Exit test (Sec. 2.3: every vertex within tol_x of the best in max-norm and
+// every value within tol_f of the best value) and the centroid of the best n
+// vertices for the next wave, for simplex gi, by one warp.
+template <int G>
+__device__ __forceinline__ void test_and_centroid(SearchSmem<G>& S, int gi, int lane, float tolx, float tolf) {
+  const unsigned char* o = S.ord[gi];
+  bool ok = true;
+  if (lane < kNumParams) {
+    const float x1 = S.U[gi][o[0]][lane];
+    float acc = 0.0f;
+    for (int r = 0; r < kNumParams; ++r) {
+      const float x = S.U[gi][o[r]][lane];
+      acc += x;
+      if (r > 0) ok = ok && (fabsf(x - x1) <= tolx);
+    }
+    ok = ok && (fabsf(S.U[gi][o[kNumParams]][lane] - x1) <= tolx);
+    S.XB[gi][lane] = acc / (float)kNumParams;
+  }
+  if (lane >= 1 && lane < kNV) ok = ok && (fabsf(S.F[gi][o[lane]] - S.F[gi][o[0]]) <= tolf);
+  const bool conv = __all_sync(0xffffffffu, ok);
+  if (conv && lane == 0) S.active[gi] = 0;
+}
+
 template <int G, int MINB, bool LEAN>
 __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchParams P) {
   constexpr int NT = search_threads<G>();
@@ -420,6 +453,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
   SearchSmem<G>& S = *reinterpret_cast<SearchSmem<G>*>(smraw);
   float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G>) + 127) / 128) * 128);
   float* z = yraw + P.lcap;
+  float* qslot = z + P.lcap;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
@@ -427,8 +461,10 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     fence_mbar_init();
     S.cur_b = -1;
   }
+  for (int i = tid; i < 2 * kHistLen; i += NT) (&S.hist[0][0])[i] = 0;
   __syncthreads();
   uint32_t phase = 0;
+  int wave = 0;
 
   for (;;) {
     if (tid == 0) S.unit = atomicAdd(P.counter, 1);
@@ -484,7 +520,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         const int gi = tid / kNV, v = tid - gi * kNV;
         key = switch_key(S.U[gi][v][kPw], S.pc[kPw], P.lnlo, P.lnhi, sc);
       }
-      order_wave<G>(S, key);
+      order_wave<G>(S, key, wave++);
       if (tid < S.nvalid) {
         const int c = S.perm[tid];
         const int gi = c / kNV, v = c - gi * kNV;
@@ -495,7 +531,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
           float u[kNumParams];
 #pragma unroll
           for (int j = 0; j < kNumParams; ++j) u[j] = S.U[gi][v][j];
-          S.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
+          S.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qslot + tid, NT);
         }
       }
     }
@@ -508,38 +544,16 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         S.active[gi] = 1;
         S.iters[gi] = 0;
       }
+      __syncwarp();
+      test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf);
     }
     __syncthreads();
 
     for (int it = 0; it < P.T; ++it) {
-      // ---- exit test (Sec. 2.3): vertex spread <= tol_x and value spread <= tol_f
-      for (int gi = warp; gi < nsim; gi += NW) {
-        if (!S.active[gi]) continue;
-        const unsigned char* o = S.ord[gi];
-        bool ok = true;
-        if (lane < kNumParams) {
-          const float x1 = S.U[gi][o[0]][lane];
-          for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(S.U[gi][o[r]][lane] - x1) <= P.tolx);
-        }
-        if (lane >= 1 && lane < kNV) ok = ok && (fabsf(S.F[gi][o[lane]] - S.F[gi][o[0]]) <= P.tolf);
-        const bool conv = __all_sync(0xffffffffu, ok);
-        if (conv && lane == 0) S.active[gi] = 0;
-      }
-      __syncthreads();
       int nact = 0;
       for (int gi = 0; gi < nsim; ++gi) nact += S.active[gi];
       if (!nact) break;
       evals += kNT * nact;
-
-      // ---- centroid of the best n vertices
-      for (int idx = tid; idx < nsim * kNumParams; idx += NT) {
-        const int gi = idx / kNumParams, j = idx - gi * kNumParams;
-        if (!S.active[gi]) continue;
-        float acc = 0.0f;
-        for (int r = 0; r < kNumParams; ++r) acc += S.U[gi][S.ord[gi][r]][j];
-        S.XB[gi][j] = acc / (float)kNumParams;
-      }
-      __syncthreads();
 
       // ---- one wave: all n + 4 trial points of every active simplex, ordered
       // by pulse-end time
@@ -554,7 +568,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
             key = switch_key(up, S.pc[kPw], P.lnlo, P.lnhi, sc);
           }
         }
-        order_wave<G>(S, key);
+        order_wave<G>(S, key, wave++);
         if (tid < S.nvalid) {
           const int c = S.perm[tid];
           const int gi = c / kNT, q = c - gi * kNT;
@@ -584,7 +598,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
 #pragma unroll
               for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(S.U[gi][s1][j], S.U[gi][si][j]);
             }
-            S.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0);
+            S.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qslot + tid, NT);
           }
         }
       }
@@ -640,6 +654,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         }
         if (lane == 0) S.iters[gi] += 1;
         __syncwarp();
+        test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf);
       }
       __syncthreads();
     }

@@ -53,6 +53,7 @@ struct Coef {
   float m30, m33, cy;         // y row: theta, y, Fn
   float da1, dn1;             // -1/tau of Fa, Fn during the pulse
   float da2, dn2;             // -1/tau of Fa, Fn after the pulse
+  float iKa, iKn;             // 1/K_SE_AG, 1/K_SE_ANT (equilibria)
 };
 
 // Increment-form propagator of both phases: the 4x4 mechanical block m is
@@ -85,6 +86,43 @@ __device__ __forceinline__ void make_coef(const float* p, Coef& k) {
   k.dn1 = -1000.0f / p[kTdeAnt];
   k.da2 = -1000.0f / p[kTdeAg];
   k.dn2 = -1000.0f / p[kTacAnt];
+  k.iKa = 1.0f / p[kSeAg];
+  k.iKn = 1.0f / p[kSeAnt];
+}
+
+// Stiffness guard from the coefficients (no divisions): h (B_P/J +
+// (K_SE_AG + K_LT_AG)/B_AG + (K_SE_ANT + K_LT_ANT)/B_ANT + 1/tau_min) <= 2.5.
+__device__ __forceinline__ bool too_stiff_coef(const Coef& k, float h) {
+  const float rate = fmaxf(fmaxf(-k.da1, -k.dn1), fmaxf(-k.da2, -k.dn2));
+  const float est = -(k.m11 + k.m22 + k.m33) + rate;
+  return !(h * est <= 2.5f);
+}
+
+// Rest state at fixation th with precomputed 1/K_SE.
+__device__ __forceinline__ void rest_state_k(const float* p, const Coef& k, float th, float* s) {
+  const float ta = fmaf(p[kNcAg], th, p[kNcFix]), tn = fmaf(-p[kNcAnt], th, p[kNcFix]);
+  s[0] = th;
+  s[1] = 0.0f;
+  s[2] = fmaf(ta, k.iKa, th);
+  s[3] = fmaf(tn, k.iKn, -th);
+  s[4] = fmaf(ta, fmaf(p[kLtAg], k.iKa, 1.0f), p[kLtAg] * th);
+  s[5] = fmaf(tn, fmaf(p[kLtAnt], k.iKn, 1.0f), -p[kLtAnt] * th);
+}
+
+// Equilibrium under constant active-state tensions, precomputed 1/K_SE.
+__device__ __forceinline__ void drive_equilibrium_k(const float* p, const Coef& k, float fa, float fn, float* s) {
+  const float ag = 1.0f / fmaf(p[kLtAg], k.iKa, 1.0f);     // K_SE / (K_SE + K_LT)
+  const float an = 1.0f / fmaf(p[kLtAnt], k.iKn, 1.0f);
+  const float kp = p[kNcAg] + p[kNcAnt];
+  const float th = (ag * fa - an * fn) / (kp + ag * p[kLtAg] + an * p[kLtAnt]);
+  const float ta = ag * (fa - p[kLtAg] * th);
+  const float tn = an * (fn + p[kLtAnt] * th);
+  s[0] = th;
+  s[1] = 0.0f;
+  s[2] = fmaf(ta, k.iKa, th);
+  s[3] = fmaf(tn, k.iKn, -th);
+  s[4] = fa;
+  s[5] = fn;
 }
 
 // Tension held at fixation angle th (tension slope and intercept, Sec. 2.1).
@@ -359,13 +397,13 @@ __device__ __forceinline__ void prop1_apply(const Prop1& q, float (&e)[6]) {
   float n[6];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float acc = fmaf(q.m[i][0], e[0], e[i]);
-    acc = fmaf(q.m[i][1], e[1], acc);
-    acc = fmaf(q.m[i][2], e[2], acc);
-    acc = fmaf(q.m[i][3], e[3], acc);
-    acc = fmaf(q.c[i][0], e[4], acc);
-    acc = fmaf(q.c[i][1], e[5], acc);
-    n[i] = acc;
+    float a = fmaf(q.m[i][0], e[0], e[i]);
+    a = fmaf(q.m[i][1], e[1], a);
+    a = fmaf(q.m[i][2], e[2], a);
+    float b = q.m[i][3] * e[3];
+    b = fmaf(q.c[i][0], e[4], b);
+    b = fmaf(q.c[i][1], e[5], b);
+    n[i] = a + b;
   }
   n[4] = fmaf(q.d[0], e[4], e[4]);
   n[5] = fmaf(q.d[1], e[5], e[5]);
@@ -374,6 +412,8 @@ __device__ __forceinline__ void prop1_apply(const Prop1& q, float (&e)[6]) {
 }
 
 // e <- (I + P_phase) e for a phase-1 (PH = 1) or phase-2 (PH = 2) deviation.
+// Each row is summed as two three-term chains joined by one add: the
+// sample-to-sample dependency is four operations deep instead of six.
 template <int PH>
 __device__ __forceinline__ void prop_apply(const Prop2& q, float (&e)[6]) {
   const float (&c)[4][2] = PH == 1 ? q.c1 : q.c2;
@@ -381,13 +421,13 @@ __device__ __forceinline__ void prop_apply(const Prop2& q, float (&e)[6]) {
   float n[6];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float acc = fmaf(q.m[i][0], e[0], e[i]);
-    acc = fmaf(q.m[i][1], e[1], acc);
-    acc = fmaf(q.m[i][2], e[2], acc);
-    acc = fmaf(q.m[i][3], e[3], acc);
-    acc = fmaf(c[i][0], e[4], acc);
-    acc = fmaf(c[i][1], e[5], acc);
-    n[i] = acc;
+    float a = fmaf(q.m[i][0], e[0], e[i]);
+    a = fmaf(q.m[i][1], e[1], a);
+    a = fmaf(q.m[i][2], e[2], a);
+    float b = q.m[i][3] * e[3];
+    b = fmaf(c[i][0], e[4], b);
+    b = fmaf(c[i][1], e[5], b);
+    n[i] = a + b;
   }
   n[4] = fmaf(d[0], e[4], e[4]);
   n[5] = fmaf(d[1], e[5], e[5]);
@@ -451,17 +491,35 @@ __device__ __forceinline__ void run_samples(const Prop2& phi, float (&e)[6], flo
   }
 }
 
+// Copy a Prop2 to / from a per-thread shared-memory slot (element i of the
+// thread's copy at qs[i * stride]: consecutive threads hit consecutive banks).
+__device__ __forceinline__ void prop_store(const Prop2& q, float* qs, int stride) {
+  const float* f = reinterpret_cast<const float*>(&q);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(Prop2) / sizeof(float)); ++i) qs[i * stride] = f[i];
+}
+__device__ __forceinline__ void prop_load(Prop2& q, const float* qs, int stride) {
+  float* f = reinterpret_cast<float*>(&q);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(Prop2) / sizeof(float)); ++i) f[i] = qs[i * stride];
+}
+
 // Walk one candidate's trajectory from the first sample after onset to the
 // end of the window.  The sink receives, for each sample k > onset, the value
 // dth = theta_k - thf (positive frame), and block_end() after blocks of
 // samples.  Samples k <= onset sit at th0 and are handled by the caller.
-// Returns the number of samples emitted.
+// Returns the number of samples emitted; with `guard` set, -1 (nothing
+// emitted) for a candidate outside RK4's stable step range (too_stiff_coef).
+// qs (optional): a shared-memory slot that keeps the single-substep
+// propagator from the set-up to the pulse-end interval instead of rebuilding it.
 template <class Sink>
-__device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& sink) {
-  const int ntot = sc.L - 1 - sc.onset;
-  if (ntot <= 0) return 0;
+__device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& sink, float* qs = nullptr,
+                                    int qstride = 0, bool guard = false) {
   Coef k;
   make_coef(p, k);
+  if (guard && too_stiff_coef(k, sc.h)) return -1;
+  const int ntot = sc.L - 1 - sc.onset;
+  if (ntot <= 0) return 0;
   // pulse end, in substeps after onset
   float tau = p[kPw] * sc.fs * (float)sc.nsub * 1e-3f;
   tau = fminf(fmaxf(tau, 0.0f), 1.0e9f);
@@ -478,9 +536,9 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
     sw = true;
   }
   float s0[6], s1[6], s2[6];
-  rest_state(p, sc.th0, s0);
-  drive_equilibrium(p, p[kNsacAg], p[kNsacAnt], s1);
-  rest_state(p, sc.thf, s2);
+  rest_state_k(p, k, sc.th0, s0);
+  drive_equilibrium_k(p, k, p[kNsacAg], p[kNsacAnt], s1);
+  rest_state_k(p, k, sc.thf, s2);
   float e[6], dl[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) { e[i] = s0[i] - s1[i]; dl[i] = s1[i] - s2[i]; }
@@ -489,6 +547,7 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
   {
     Prop2 q;
     step_increment(k, sc.h, q);
+    if (qs) prop_store(q, qs, qstride);
     prop_pow(q, sc.nsub, phi);
   }
   int kk = sc.onset + 1;
@@ -497,7 +556,8 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
     // pulse-end interval: jsw whole substeps of the pulse phase, the split
     // substep (two RK4 steps around the switch), the rest of the step phase
     Prop2 q;
-    step_increment(k, sc.h, q);
+    if (qs) prop_load(q, qs, qstride);
+    else step_increment(k, sc.h, q);
     for (int s = 0; s < jsw; ++s) prop_apply<1>(q, e);
     const float h1 = frac * sc.h;
     rk4_vec(k, k.da1, k.dn1, h1, e);
@@ -570,10 +630,12 @@ __device__ __forceinline__ int walk_lean(const PSrc& src, const SacConst& sc, Si
       jsw = J - n1 * sc.nsub;
       sw = true;
     }
+    Coef k;
+    make_coef(p, k);
     float s0[6], s1[6], s2[6];
-    rest_state(p, sc.th0, s0);
-    drive_equilibrium(p, p[kNsacAg], p[kNsacAnt], s1);
-    rest_state(p, sc.thf, s2);
+    rest_state_k(p, k, sc.th0, s0);
+    drive_equilibrium_k(p, k, p[kNsacAg], p[kNsacAnt], s1);
+    rest_state_k(p, k, sc.thf, s2);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { e[i] = s0[i] - s1[i]; dl[i] = s1[i] - s2[i]; }
     off1 = s1[0] - sc.thf;

@@ -210,20 +210,30 @@ def test_fit_zero_iterations_is_best_initial_vertex(ctx):
 
 
 def test_plan_graph_is_deterministic_and_equals_fit_batch(ctx):
+    """A captured plan replays bit-identically and equals the one-shot fit on
+    the same launch variant; an autotuned plan agrees within tolerance."""
     w = W.uneven10k(B=6)
     items = oracle_inputs(w)
     batch = to_batch(items)
     kw = dict(candidates=22 * 40, iterations=6, init_opc=centres(items))
-    a = G.opmm_fit_batch(ctx, batch, **kw)
-    plan = G.opmm_plan_create(ctx, batch, **kw)
-    b = plan.execute()
-    c = plan.execute()
-    for k in ("opc", "f", "rms_deg", "winner", "iterations_run"):
-        np.testing.assert_array_equal(a[k], b[k])
-        np.testing.assert_array_equal(b[k], c[k])
-    info = plan.info()
+    G.opmm_set_search_variant(ctx, 0)
+    try:
+        a = G.opmm_fit_batch(ctx, batch, **kw)
+        plan = G.opmm_plan_create(ctx, batch, **kw)
+        b = plan.execute()
+        c = plan.execute()
+        for k in ("opc", "f", "rms_deg", "winner", "iterations_run", "evaluations"):
+            np.testing.assert_array_equal(a[k], b[k])
+            np.testing.assert_array_equal(b[k], c[k])
+        plan.destroy()
+    finally:
+        G.opmm_set_search_variant(ctx, -1)
+    tuned = G.opmm_plan_create(ctx, batch, **kw)
+    d = tuned.execute()
+    info = tuned.info()
     assert info["simplices_per_block"] in (8, 16, 32)
-    plan.destroy()
+    assert np.all(np.abs(d["rms_deg"] - a["rms_deg"]) <= RMS_TOL)
+    tuned.destroy()
 
 
 def test_device_traces_equal_host_traces(ctx):
