@@ -92,7 +92,7 @@ typedef struct {
   uint64_t seed;             /* Philox key for the simplex starting points */
   int32_t pulse_init;        /* OPMM_PULSE_* when init_opc is NULL */
   int32_t use_surrogate;     /* 1: centre the box on the surrogate's estimate
-                                (requires opmm_surrogate_load / _set) */
+                                (requires opmm_surrogate_init or _load) */
   const float* init_opc;     /* nullable, host [n][18] box centres (all > 0) */
 } opmm_fit_opts;
 
@@ -193,6 +193,55 @@ int opmm_plan_tuning(const opmm_plan* plan, int32_t* variant, int32_t* simplices
  * events recorded around it on the plan's stream (inside the graph). */
 int opmm_plan_last_search_ms(const opmm_plan* plan, float* ms);
 void opmm_plan_destroy(opmm_plan* plan);
+
+/* ------------------------------------------------------------ surrogate */
+/* A learned amortised inverse (not in the paper): a multilayer perceptron
+ * 512 -> 4 x 512 (GELU) -> 18, BF16 weights with FP32 accumulation on the
+ * tensor cores, maps a saccade resampled to 256 points of position and
+ * velocity (1 ms apart from onset, position normalised so that the start
+ * fixation is 0 and the end fixation 1, velocity = 10 x the per-ms
+ * difference) to y with OPC centre = nominal centre * exp(0.2 y).  It only
+ * seeds a fit (opmm_fit_opts.use_surrogate) whose box is then narrowed; the
+ * plain search is the fallback. */
+
+/* Fresh weights (uniform +-1/sqrt(512), seeded) and zeroed AdamW state; builds
+ * the amplitude -> agonist-pulse table the training data uses. */
+int opmm_surrogate_init(opmm_ctx* ctx, uint64_t seed);
+/* Number of parameters of the flat FP32 parameter vector: for each hidden
+ * layer W [512 out][512 in] then b [512]; then W_out [18][512] and b_out [18]. */
+int opmm_surrogate_num_params(int64_t* n);
+int opmm_surrogate_get_params(opmm_ctx* ctx, float* out /* host [n] */);
+int opmm_surrogate_set_params(opmm_ctx* ctx, const float* in /* host [n] */);
+/* Loss (mean over rows and the 18 outputs of (y - t)^2) and its gradient with
+ * respect to the flat parameter vector, for m rows of features x [m][512]
+ * (rounded to BF16) and targets t [m][18]; m a multiple of 128.  y_out
+ * (nullable) receives the network outputs [m][18].  All host memory. */
+int opmm_surrogate_grad(opmm_ctx* ctx, const float* x, const float* t, int32_t m, float* loss, float* grad,
+                        float* y_out);
+/* `steps` AdamW steps (betas 0.9, 0.999, eps 1e-8, decoupled weight decay on
+ * weight matrices) on fresh batches of `batch` saccades (multiple of 128)
+ * generated on the device by the plant itself: rates 250/500/1000 Hz, windows
+ * of 40-400 samples, amplitudes log-uniform in 1-40 deg, both directions,
+ * hidden OPC = calibrated nominal x U(0.8, 1.2) per entry, N(0, 0.05^2) deg
+ * noise; sample i of step s is drawn from Philox4x32-10 (key data_seed,
+ * counter sample_base + s * batch + i).  losses (nullable, host [steps]). */
+int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch, float lr, float weight_decay,
+                         uint64_t data_seed, int64_t sample_base, float* losses);
+/* Box centres the surrogate proposes for n saccades (host descriptors, traces
+ * host or device): out_opc host [n][18]. */
+int opmm_surrogate_predict(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, int32_t pulse_init,
+                           float* out_opc);
+/* The surrogate's input features of n saccades (host descriptors, traces host
+ * or device), as BF16 values widened to float: out host [n][512] (positions
+ * 0..255, velocities 256..511). */
+int opmm_featurize(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, float* out);
+/* D[M][N] = A[M][K] . B[N][K]^T on the tensor cores (tcgen05): A, B BF16
+ * row-major, D FP32 row-major, all DEVICE pointers (16-byte aligned); M and N
+ * multiples of 128, K a multiple of 64.  The surrogate's layer primitive. */
+int opmm_gemm_bf16(opmm_ctx* ctx, const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* D);
+/* Weights file: 8-byte magic "OPMMSG1", int64 count, float32 parameters. */
+int opmm_surrogate_save(opmm_ctx* ctx, const char* path);
+int opmm_surrogate_load(opmm_ctx* ctx, const char* path);
 
 /* ------------------------------------------------- allocation-free fit */
 

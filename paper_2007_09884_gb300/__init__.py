@@ -40,7 +40,10 @@ EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", 
            "opmm_score", "opmm_nominal_opc", "opmm_fit_batch", "opmm_plan_create",
            "opmm_plan_execute", "opmm_plan_info", "opmm_plan_tuning", "opmm_plan_last_search_ms",
            "opmm_plan_destroy",
-           "opmm_fit_saccade_static"]
+           "opmm_fit_saccade_static", "opmm_surrogate_init", "opmm_surrogate_num_params",
+           "opmm_surrogate_get_params", "opmm_surrogate_set_params", "opmm_surrogate_grad",
+           "opmm_surrogate_train", "opmm_surrogate_predict", "opmm_surrogate_save", "opmm_surrogate_load", "opmm_featurize",
+           "opmm_gemm_bf16"]
 
 
 class OpmmError(RuntimeError):
@@ -108,9 +111,25 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_plan_destroy.restype = None
     lib.opmm_fit_saccade_static.argtypes = [ctypes.POINTER(opmm_saccade), ctypes.POINTER(opmm_fit_opts),
                                             vp, vp]
+    lib.opmm_surrogate_init.argtypes = [vp, ctypes.c_uint64]
+    lib.opmm_surrogate_num_params.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    lib.opmm_surrogate_get_params.argtypes = [vp, vp]
+    lib.opmm_surrogate_set_params.argtypes = [vp, vp]
+    lib.opmm_surrogate_grad.argtypes = [vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp, vp]
+    lib.opmm_surrogate_train.argtypes = [vp, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                         ctypes.c_int64, vp]
+    lib.opmm_surrogate_predict.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
+    lib.opmm_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+    lib.opmm_surrogate_load.argtypes = [vp, ctypes.c_char_p]
+    lib.opmm_featurize.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, vp]
+    lib.opmm_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     for name in ["opmm_create", "opmm_set_stream", "opmm_set_search_variant", "opmm_search_variants", "opmm_simulate", "opmm_score", "opmm_nominal_opc",
                  "opmm_fit_batch", "opmm_plan_create", "opmm_plan_execute", "opmm_plan_info",
-                 "opmm_plan_last_search_ms", "opmm_fit_saccade_static", "opmm_plan_tuning"]:
+                 "opmm_plan_last_search_ms", "opmm_fit_saccade_static", "opmm_plan_tuning",
+                 "opmm_surrogate_init", "opmm_surrogate_num_params", "opmm_surrogate_get_params",
+                 "opmm_surrogate_set_params", "opmm_surrogate_grad", "opmm_surrogate_train",
+                 "opmm_surrogate_predict", "opmm_surrogate_save", "opmm_surrogate_load",
+                 "opmm_featurize", "opmm_gemm_bf16"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -392,3 +411,83 @@ def opmm_fit_saccade_static(batch: SaccadeBatch, out_device, stream_handle: int 
     po, ko = _ptr(out_device)
     return int(lib.opmm_fit_saccade_static(ctypes.byref(descs[index]), ctypes.byref(o), po,
                                            ctypes.c_void_p(int(stream_handle) or None)))
+
+
+# ------------------------------------------------------------------ surrogate
+def _vp(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def opmm_surrogate_init(ctx, seed: int = 0):
+    _check(ctx, load_library().opmm_surrogate_init(ctx, int(seed)))
+
+
+def opmm_surrogate_num_params() -> int:
+    n = ctypes.c_int64()
+    load_library().opmm_surrogate_num_params(ctypes.byref(n))
+    return int(n.value)
+
+
+def opmm_surrogate_get_params(ctx) -> np.ndarray:
+    out = np.zeros(opmm_surrogate_num_params(), np.float32)
+    _check(ctx, load_library().opmm_surrogate_get_params(ctx, _vp(out)))
+    return out
+
+
+def opmm_surrogate_set_params(ctx, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, load_library().opmm_surrogate_set_params(ctx, _vp(p)))
+
+
+def opmm_surrogate_grad(ctx, x, t):
+    """(loss, grad[n_params], y[m][18]) for features x [m][512], targets t [m][18]."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    m = x.shape[0]
+    g = np.zeros(opmm_surrogate_num_params(), np.float32)
+    y = np.zeros((m, 18), np.float32)
+    loss = ctypes.c_float()
+    _check(ctx, load_library().opmm_surrogate_grad(ctx, _vp(x), _vp(t), m, ctypes.byref(loss), _vp(g), _vp(y)))
+    return float(loss.value), g, y
+
+
+def opmm_surrogate_train(ctx, steps, batch=4096, lr=1e-3, weight_decay=1e-4, data_seed=1, sample_base=0):
+    losses = np.zeros(max(1, steps), np.float32)
+    _check(ctx, load_library().opmm_surrogate_train(ctx, int(steps), int(batch), float(lr),
+                                                     float(weight_decay), int(data_seed),
+                                                     int(sample_base), _vp(losses)))
+    return losses[:steps]
+
+
+def opmm_surrogate_predict(ctx, batch: SaccadeBatch, pulse_init=OPMM_PULSE_CALIBRATED) -> np.ndarray:
+    out = np.zeros((len(batch), 18), np.float32)
+    descs, keep = batch.descriptors()
+    _check(ctx, load_library().opmm_surrogate_predict(ctx, descs, len(batch), int(pulse_init), _vp(out)))
+    return out
+
+
+def opmm_surrogate_save(ctx, path: str):
+    _check(ctx, load_library().opmm_surrogate_save(ctx, path.encode()))
+
+
+def opmm_surrogate_load(ctx, path: str):
+    _check(ctx, load_library().opmm_surrogate_load(ctx, path.encode()))
+
+
+def opmm_featurize(ctx, batch: SaccadeBatch) -> np.ndarray:
+    out = np.zeros((len(batch), 512), np.float32)
+    descs, keep = batch.descriptors()
+    _check(ctx, load_library().opmm_featurize(ctx, descs, len(batch), _vp(out)))
+    return out
+
+
+def opmm_gemm_bf16(ctx, A, B, out=None):
+    """D = A . B^T for torch bfloat16 CUDA tensors A [M][K], B [N][K]; returns D (float32)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(ctx, load_library().opmm_gemm_bf16(ctx, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                               int(M), int(N), int(K), ctypes.c_void_p(out.data_ptr())))
+    return out

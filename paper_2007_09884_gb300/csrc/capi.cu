@@ -386,12 +386,11 @@ opmm_plan::~opmm_plan() {
 
 namespace opmm {
 
-// Everything one fit launches, in stream order (graph-captured by plans).
-Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
-  opmm_ctx* ctx = p->ctx;
+// Trace staging and box centres, in stream order: device gather or one H2D
+// copy of the packed traces, nominal centres (unless given), then any
+// pre-search stage (the surrogate's re-centring).
+Status enqueue_centres(opmm_plan* p, cudaStream_t st) {
   Status s;
-  s = cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, sizeof(unsigned), st), "clear error word");
-  if (!s.ok()) return s;
   if (p->traces_on_device) {
     s = cuda_status(launch_gather(p->d_src.as<const float*>(), p->d_sacs.as<DevSac>(), p->d_traces.as<float>(), p->n, st),
                     "launch gather");
@@ -404,11 +403,27 @@ Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
     s = cuda_status(launch_nominal(p->d_sacs.as<DevSac>(), p->n, p->opts.pulse_init, nullptr, p->d_pc.as<float>(), st),
                     "launch nominal");
     if (!s.ok()) return s;
+  } else if (p->pre_search) {
+    // the surrogate scales the caller's centres: restore them first
+    s = cuda_status(cudaMemcpyAsync(p->d_pc.ptr, p->d_pc_given.ptr, sizeof(float) * OPMM_NPARAM * (size_t)p->n,
+                                    cudaMemcpyDeviceToDevice, st), "restore centres");
+    if (!s.ok()) return s;
   }
   if (p->pre_search) {
     s = p->pre_search(p, st);
     if (!s.ok()) return s;
   }
+  return Status();
+}
+
+// Everything one fit launches, in stream order (graph-captured by plans).
+Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
+  opmm_ctx* ctx = p->ctx;
+  Status s;
+  s = cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, sizeof(unsigned), st), "clear error word");
+  if (!s.ok()) return s;
+  s = enqueue_centres(p, st);
+  if (!s.ok()) return s;
   s = cuda_status(cudaMemsetAsync(p->d_counter.ptr, 0, sizeof(int), st), "clear work counter");
   if (!s.ok()) return s;
   SearchParams P = p->params;
@@ -561,9 +576,8 @@ Status build_units(opmm_plan* p, int G) {
   return s;
 }
 
-// Validate, stage descriptors, allocate, choose the shape and capture.
-Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o, bool capture,
-                  bool tune, opmm_plan* p) {
+// Validate, stage descriptors and traces, allocate, compute the box centres.
+Status plan_stage(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o, opmm_plan* p) {
   Status s = check_opts(o);
   if (!s.ok()) return s;
   if (n < 1 || !sacs) return Status(OPMM_EINVAL, "empty batch");
@@ -572,14 +586,13 @@ Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm
   p->opts = o;
   p->opts.init_opc = nullptr;
   p->S = o.candidates / (OPMM_NPARAM + 4);
-  p->autotune = tune;
-  p->centres_given = o.init_opc != nullptr || o.use_surrogate;
+  p->centres_given = o.init_opc != nullptr;
   p->hsacs.resize((size_t)n);
   p->src.resize((size_t)n);
   int lmax = 0;
   long long off = 0;
   for (int i = 0; i < n; ++i) {
-    s = check_saccade(sacs[i], i, o.init_opc == nullptr && !o.use_surrogate);
+    s = check_saccade(sacs[i], i, o.init_opc == nullptr);
     if (!s.ok()) return s;
     if (!sacs[i].trace_deg) return Status(OPMM_EINVAL, "saccade " + std::to_string(i) + ": null trace");
     DevSac d = make_devsac(sacs[i]);
@@ -625,6 +638,12 @@ Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm
   if (s.ok() && o.init_opc)
     s = cuda_status(cudaMemcpyAsync(p->d_pc.ptr, o.init_opc, sizeof(float) * OPMM_NPARAM * (size_t)n,
                                     cudaMemcpyHostToDevice, st), "H2D box centres");
+  if (s.ok() && o.init_opc && o.use_surrogate) {
+    s = p->d_pc_given.ensure(sizeof(float) * OPMM_NPARAM * (size_t)n);
+    if (s.ok())
+      s = cuda_status(cudaMemcpyAsync(p->d_pc_given.ptr, o.init_opc, sizeof(float) * OPMM_NPARAM * (size_t)n,
+                                      cudaMemcpyHostToDevice, st), "H2D box centres");
+  }
   if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "stage plan");
   if (!s.ok()) return s;
 
@@ -646,20 +665,20 @@ Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm
   P.counter = p->d_counter.as<int>();
   P.err = ctx->d_err.as<unsigned>();
 
-  if (!p->traces_on_device) {
-    // the tuner's probe runs need staged traces
-    pack_host_traces(p);
-    s = cuda_status(cudaMemcpyAsync(p->d_traces.ptr, p->h_traces.ptr, p->trace_floats * sizeof(float),
-                                    cudaMemcpyHostToDevice, st), "H2D traces");
-  } else {
-    s = cuda_status(launch_gather(p->d_src.as<const float*>(), p->d_sacs.as<DevSac>(), p->d_traces.as<float>(), n, st),
-                    "gather traces");
-  }
-  if (s.ok() && !p->centres_given)
-    s = cuda_status(launch_nominal(p->d_sacs.as<DevSac>(), n, o.pulse_init, nullptr, p->d_pc.as<float>(), st),
-                    "nominal");
+  // stage the traces and centres now (the tuner's probes and direct callers need them)
+  if (!p->traces_on_device) pack_host_traces(p);
+  s = enqueue_centres(p, st);
   if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "stage");
+  return s;
+}
+
+// plan_stage, then the search part: launch shape, work units, graph capture.
+Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o, bool capture,
+                  bool tune, opmm_plan* p) {
+  p->autotune = tune;
+  Status s = plan_stage(ctx, sacs, n, o, p);
   if (!s.ok()) return s;
+  cudaStream_t st = ctx->stream;
   s = autotune(p);
   if (!s.ok()) return s;
   p->G = search_variant_g(p->variant);

@@ -111,7 +111,7 @@ struct opmm_plan {
   size_t trace_floats = 0;
   opmm::SearchParams params{};
   opmm::DevBuf d_sacs, d_traces, d_pc, d_sac_index, d_units, d_ustart, d_unit_best, d_counter, d_results, d_src;
-  opmm::DevBuf d_aux[4];              // extra buffers of optional stages (surrogate features)
+  opmm::DevBuf d_pc_given;            // caller's centres when the surrogate rescales them
   opmm::HostBuf h_traces, h_results, h_err;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -122,8 +122,10 @@ struct opmm_plan {
 namespace opmm {
 
 Status build_units(opmm_plan* p, int G);
+Status plan_stage(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o, opmm_plan* p);
 Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o, bool capture,
                   bool tune, opmm_plan* p);
+Status enqueue_centres(opmm_plan* p, cudaStream_t st);
 Status plan_run(opmm_plan* p, opmm_fit_result* out);
 Status enqueue_fit(opmm_plan* p, cudaStream_t st);
 void pack_host_traces(opmm_plan* p);

@@ -1,19 +1,479 @@
-// surrogate.cu -- learned surrogate that seeds the search (placeholder until
-// the MLP kernels land).
+// surrogate.cu -- host side of the learned surrogate: parameters and AdamW
+// state, on-device training (data generated by the plant itself), inference
+// that re-centres a fit's search box, gradient access for checking, and
+// save / load.  The network maps a resampled saccade (512 features) through
+// four 512-wide GELU layers to 18 outputs y with centre = nominal * exp(0.2 y).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/opmm.h"
+#include "launch.h"
+#include "mlp.h"
 #include "runtime.h"
 
 namespace opmm {
 
-struct SurrogateState {};
+using namespace mlp;
+
+namespace {
+constexpr int kCal = 512;               // calibration table points
+constexpr float kCalLo = 0.5f, kCalHi = 45.0f;
+constexpr int kTrainLcap = 400;         // longest training window
+}  // namespace
+
+// Activations and gradients of one batch of M rows (M a multiple of 128).
+struct MlpBuffers {
+  int M = 0;
+  DevBuf X, Xt, H[kLayers], Ht[kLayers], Z[kLayers], Y, dY, rowloss, dH, dZ, dZt, colpart, dWpart, dbpart;
+  Status ensure(int m) {
+    if (m <= M) return Status();
+    Status s;
+    const size_t act = (size_t)m * kHidden;
+    s = X.ensure(act * 2);
+    if (s.ok()) s = Xt.ensure(act * 2);
+    for (int l = 0; l < kLayers && s.ok(); ++l) {
+      s = H[l].ensure(act * 2);
+      if (s.ok()) s = Ht[l].ensure(act * 2);
+      if (s.ok()) s = Z[l].ensure(act * 4);
+    }
+    if (s.ok()) s = Y.ensure((size_t)m * kOut * 4);
+    if (s.ok()) s = dY.ensure((size_t)m * kOut * 4);
+    if (s.ok()) s = rowloss.ensure((size_t)m * 4);
+    if (s.ok()) s = dH.ensure(act * 4);
+    if (s.ok()) s = dZ.ensure(act * 2);
+    if (s.ok()) s = dZt.ensure(act * 2);
+    if (s.ok()) s = colpart.ensure((size_t)(m / 32) * kHidden * 4);
+    if (s.ok()) s = dWpart.ensure((size_t)(m / 32) * kOut * kHidden * 4);
+    if (s.ok()) s = dbpart.ensure((size_t)(m / 32) * kOut * 4);
+    if (s.ok()) M = m;
+    return s;
+  }
+};
+
+struct SurrogateState {
+  DevBuf w, g, m1, m2, wb, wt;           // FP32 master, gradient, Adam moments; BF16 copies
+  DevBuf cal_amp, cal_pulse;             // agonist pulse by amplitude (calibrated nominal)
+  MlpBuffers buf;
+  // training data of one batch
+  DevBuf sacs, traces, hidden, target, outoff, losses;
+  int train_M = 0;
+  int step = 0;
+  bool ready = false;
+};
+
+static __nv_bfloat16* bf(const DevBuf& b, size_t off = 0) { return b.as<__nv_bfloat16>() + off; }
+static float* f32(const DevBuf& b, size_t off = 0) { return b.as<float>() + off; }
+
+static Status ensure_state(opmm_ctx* ctx) {
+  if (!ctx->surrogate) ctx->surrogate = new SurrogateState();
+  SurrogateState& S = *ctx->surrogate;
+  Status s = S.w.ensure(sizeof(float) * kNumParams);
+  if (s.ok()) s = S.g.ensure(sizeof(float) * kNumParams);
+  if (s.ok()) s = S.m1.ensure(sizeof(float) * kNumParams);
+  if (s.ok()) s = S.m2.ensure(sizeof(float) * kNumParams);
+  if (s.ok()) s = S.wb.ensure(sizeof(__nv_bfloat16) * kWbElems);
+  if (s.ok()) s = S.wt.ensure(sizeof(__nv_bfloat16) * kWtElems);
+  if (s.ok()) s = S.cal_amp.ensure(sizeof(float) * kCal);
+  if (s.ok()) s = S.cal_pulse.ensure(sizeof(float) * kCal);
+  if (s.ok()) s = cuda_status(gemm_prepare(), "GEMM attributes");
+  return s;
+}
+
+// Agonist pulse of the calibrated nominal plant on an amplitude grid, by the
+// same device calibration the fits use (k_nominal).
+static Status build_calibration(opmm_ctx* ctx) {
+  SurrogateState& S = *ctx->surrogate;
+  std::vector<DevSac> hs(kCal);
+  std::vector<float> amp(kCal);
+  for (int i = 0; i < kCal; ++i) {
+    const float A = kCalLo + (kCalHi - kCalLo) * (float)i / (float)(kCal - 1);
+    amp[(size_t)i] = A;
+    DevSac d{};
+    d.L = 2; d.onset = 0; d.nsub = 10; d.fs = 1000.0f; d.h = 1e-4f;
+    d.th0 = 0.0f; d.thf = A; d.sign = 1.0f; d.dur_ms = 2.2f * A + 21.0f;
+    hs[(size_t)i] = d;
+  }
+  DevBuf dsac, dpc;
+  Status s = dsac.ensure(sizeof(DevSac) * kCal);
+  if (s.ok()) s = dpc.ensure(sizeof(float) * kCal * OPMM_NPARAM);
+  if (!s.ok()) return s;
+  cudaStream_t st = ctx->stream;
+  s = cuda_status(cudaMemcpyAsync(dsac.ptr, hs.data(), sizeof(DevSac) * kCal, cudaMemcpyHostToDevice, st), "H2D cal");
+  if (s.ok()) s = cuda_status(launch_nominal(dsac.as<DevSac>(), kCal, OPMM_PULSE_CALIBRATED, nullptr, f32(dpc), st), "calibrate");
+  std::vector<float> pc((size_t)kCal * OPMM_NPARAM), pulse(kCal);
+  if (s.ok()) s = cuda_status(cudaMemcpyAsync(pc.data(), dpc.ptr, pc.size() * 4, cudaMemcpyDeviceToHost, st), "D2H cal");
+  if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "calibration");
+  if (!s.ok()) return s;
+  for (int i = 0; i < kCal; ++i) pulse[(size_t)i] = pc[(size_t)i * OPMM_NPARAM + 15]  /* agonist pulse (H_ag) */;
+  s = cuda_status(cudaMemcpy(S.cal_amp.ptr, amp.data(), kCal * 4, cudaMemcpyHostToDevice), "H2D amp");
+  if (s.ok()) s = cuda_status(cudaMemcpy(S.cal_pulse.ptr, pulse.data(), kCal * 4, cudaMemcpyHostToDevice), "H2D pulse");
+  return s;
+}
+
+static Status refresh_copies(opmm_ctx* ctx) {
+  SurrogateState& S = *ctx->surrogate;
+  return cuda_status(pack_params(f32(S.w), (int)kNumParams, AdamLayout{}, bf(S.wb), bf(S.wt), ctx->stream), "pack");
+}
+
+// Forward pass of M rows from B.X (and B.Xt): hidden layers on the tensor
+// cores, output layer (and, with T, loss and its gradient) on CUDA cores.
+static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, const float* T, bool keep_transposes) {
+  SurrogateState& S = *ctx->surrogate;
+  cudaStream_t st = ctx->stream;
+  for (int l = 0; l < kLayers; ++l) {
+    GemmArgs a{};
+    a.epi = kEpiBiasGelu;
+    a.bias = f32(S.w, (size_t)l * kLayerParams + (size_t)kHidden * kHidden);
+    a.out_bf16 = bf(B.H[l]);
+    a.out_f32 = f32(B.Z[l]);
+    a.out_t = keep_transposes ? bf(B.Ht[l]) : nullptr;
+    a.ldo = kHidden;
+    a.ldt = M;
+    a.err = ctx->d_err.as<unsigned>();
+    const __nv_bfloat16* in = l == 0 ? bf(B.X) : bf(B.H[l - 1]);
+    Status s = cuda_status(gemm_tn(in, bf(S.wb, (size_t)l * kHidden * kHidden), M, kHidden, kHidden, a, st), "GEMM fwd");
+    if (!s.ok()) return s;
+  }
+  return cuda_status(head_fwd_loss(bf(B.H[kLayers - 1]), bf(S.wb, (size_t)kLayers * kHidden * kHidden),
+                                   f32(S.w, kHeadB), T, M, f32(B.Y), f32(B.dY), T ? f32(B.rowloss) : nullptr, st),
+                     "head");
+}
+
+// Backward pass into S.g (after forward with T and transposes kept).
+static Status backward(opmm_ctx* ctx, MlpBuffers& B, int M) {
+  SurrogateState& S = *ctx->surrogate;
+  cudaStream_t st = ctx->stream;
+  Status s = cuda_status(head_bwd(f32(B.dY), bf(B.H[kLayers - 1]), bf(S.wb, (size_t)kLayers * kHidden * kHidden), M,
+                                  f32(B.dH), f32(B.dWpart), f32(B.dbpart), f32(S.g, kHeadW), f32(S.g, kHeadB), st),
+                         "head backward");
+  for (int l = kLayers - 1; l >= 0 && s.ok(); --l) {
+    const size_t wo = (size_t)l * kLayerParams;
+    s = cuda_status(gelu_bwd(f32(B.dH), f32(B.Z[l]), M, kHidden, bf(B.dZ), bf(B.dZt), f32(B.colpart),
+                             f32(S.g, wo + (size_t)kHidden * kHidden), st),
+                    "GELU backward");
+    if (!s.ok()) break;
+    // dW[n][k] = sum_m dZ[m][n] H_{l-1}[m][k]
+    GemmArgs a{};
+    a.epi = kEpiF32;
+    a.out_f32 = f32(S.g, wo);
+    a.ldo = kHidden;
+    a.err = ctx->d_err.as<unsigned>();
+    const __nv_bfloat16* ht = l == 0 ? bf(B.Xt) : bf(B.Ht[l - 1]);
+    s = cuda_status(gemm_tn(bf(B.dZt), ht, kHidden, kHidden, M, a, st), "GEMM wgrad");
+    if (!s.ok() || l == 0) break;
+    // dH_{l-1}[m][k] = sum_n dZ[m][n] W_l[n][k]
+    GemmArgs d{};
+    d.epi = kEpiF32;
+    d.out_f32 = f32(B.dH);
+    d.ldo = kHidden;
+    d.err = ctx->d_err.as<unsigned>();
+    s = cuda_status(gemm_tn(bf(B.dZ), bf(S.wt, (size_t)l * kHidden * kHidden), M, kHidden, kHidden, d, st), "GEMM dgrad");
+  }
+  return s;
+}
 
 void surrogate_release(opmm_ctx* ctx) {
   delete ctx->surrogate;
   ctx->surrogate = nullptr;
 }
 
-Status surrogate_prepare_plan(opmm_ctx* ctx, opmm_plan*, const opmm_saccade*, int32_t) {
-  if (!ctx->surrogate) return Status(OPMM_EINVAL, "use_surrogate set but no surrogate is loaded");
-  return Status(OPMM_EINVAL, "surrogate not available");
+// Box centres of a plan from the network: featurize the staged traces, run the
+// forward pass, centre = nominal centre * exp(0.2 y).
+Status surrogate_prepare_plan(opmm_ctx* ctx, opmm_plan* p, const opmm_saccade*, int32_t n) {
+  if (!ctx->surrogate || !ctx->surrogate->ready)
+    return Status(OPMM_EINVAL, "use_surrogate set but no surrogate is initialised or loaded");
+  const int M = (n + kBM - 1) / kBM * kBM;
+  auto* bufs = new MlpBuffers();
+  Status s = bufs->ensure(M);
+  if (!s.ok()) {
+    delete bufs;
+    return s;
+  }
+  s = cuda_status(cudaMemset(bufs->X.ptr, 0, (size_t)M * kIn * 2), "clear features");
+  if (!s.ok()) {
+    delete bufs;
+    return s;
+  }
+  std::shared_ptr<MlpBuffers> keep(bufs);
+  p->pre_search_kernels = 1 + kLayers + 2;
+  p->pre_search = [keep, M](opmm_plan* pl, cudaStream_t st) -> Status {
+    opmm_ctx* c = pl->ctx;
+    cudaStream_t saved = c->stream;
+    c->stream = st;
+    Status r = cuda_status(featurize(pl->d_sacs.as<DevSac>(), pl->d_traces.as<float>(), pl->n, bf(keep->X), nullptr, M, st),
+                           "featurize");
+    if (r.ok()) r = forward(c, *keep, M, nullptr, false);
+    if (r.ok()) r = cuda_status(apply_centres(f32(keep->Y), pl->n, pl->d_pc.as<float>(), st), "centres");
+    c->stream = saved;
+    return r;
+  };
+  return Status();
 }
 
 }  // namespace opmm
+
+using namespace opmm;
+
+static int sfail(opmm_ctx* ctx, const Status& s) {
+  ctx->err = s.msg;
+  return s.code;
+}
+
+#define STRY(expr)                                 \
+  do {                                             \
+    Status _s = (expr);                            \
+    if (!_s.ok()) return sfail(ctx, _s);           \
+  } while (0)
+
+extern "C" int opmm_surrogate_init(opmm_ctx* ctx, uint64_t seed) {
+  if (!ctx) return OPMM_EINVAL;
+  STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
+  STRY(ensure_state(ctx));
+  SurrogateState& S = *ctx->surrogate;
+  // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for weights and biases (splitmix64)
+  std::vector<float> w((size_t)kNumParams);
+  uint64_t x = seed;
+  auto next = [&]() {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  const double bound = 1.0 / std::sqrt((double)kHidden);
+  for (size_t i = 0; i < w.size(); ++i) w[i] = (float)((2.0 * next() - 1.0) * bound);
+  STRY(cuda_status(cudaMemcpy(S.w.ptr, w.data(), w.size() * 4, cudaMemcpyHostToDevice), "H2D params"));
+  STRY(cuda_status(cudaMemset(S.m1.ptr, 0, (size_t)kNumParams * 4), "clear m1"));
+  STRY(cuda_status(cudaMemset(S.m2.ptr, 0, (size_t)kNumParams * 4), "clear m2"));
+  STRY(build_calibration(ctx));
+  STRY(refresh_copies(ctx));
+  STRY(cuda_status(cudaStreamSynchronize(ctx->stream), "init"));
+  S.step = 0;
+  S.ready = true;
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_num_params(int64_t* n) {
+  if (!n) return OPMM_EINVAL;
+  *n = kNumParams;
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_get_params(opmm_ctx* ctx, float* out) {
+  if (!ctx || !out) return OPMM_EINVAL;
+  if (!ctx->surrogate || !ctx->surrogate->ready) return sfail(ctx, Status(OPMM_EINVAL, "no surrogate"));
+  STRY(cuda_status(cudaMemcpy(out, ctx->surrogate->w.ptr, (size_t)kNumParams * 4, cudaMemcpyDeviceToHost), "D2H params"));
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_set_params(opmm_ctx* ctx, const float* in) {
+  if (!ctx || !in) return OPMM_EINVAL;
+  if (!ctx->surrogate || !ctx->surrogate->ready) return sfail(ctx, Status(OPMM_EINVAL, "no surrogate"));
+  STRY(cuda_status(cudaMemcpy(ctx->surrogate->w.ptr, in, (size_t)kNumParams * 4, cudaMemcpyHostToDevice), "H2D params"));
+  STRY(refresh_copies(ctx));
+  STRY(cuda_status(cudaStreamSynchronize(ctx->stream), "set params"));
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_grad(opmm_ctx* ctx, const float* x, const float* t, int32_t m, float* loss, float* grad,
+                                   float* y_out) {
+  if (!ctx || !x || !t || !loss || !grad || m <= 0 || m % kBM) return ctx ? sfail(ctx, Status(OPMM_EINVAL, "grad: rows must be a positive multiple of 128")) : OPMM_EINVAL;
+  if (!ctx->surrogate || !ctx->surrogate->ready) return sfail(ctx, Status(OPMM_EINVAL, "no surrogate"));
+  STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
+  SurrogateState& S = *ctx->surrogate;
+  MlpBuffers& B = S.buf;
+  STRY(B.ensure(m));
+  cudaStream_t st = ctx->stream;
+  // host features -> BF16 (round to nearest even) and the transpose
+  std::vector<__nv_bfloat16> xb((size_t)m * kIn), xt((size_t)m * kIn);
+  for (int i = 0; i < m; ++i)
+    for (int k = 0; k < kIn; ++k) {
+      const __nv_bfloat16 v = __float2bfloat16_rn(x[(size_t)i * kIn + k]);
+      xb[(size_t)i * kIn + k] = v;
+      xt[(size_t)k * m + i] = v;
+    }
+  DevBuf dt;
+  STRY(dt.ensure((size_t)m * kOut * 4));
+  STRY(cuda_status(cudaMemcpyAsync(B.X.ptr, xb.data(), xb.size() * 2, cudaMemcpyHostToDevice, st), "H2D X"));
+  STRY(cuda_status(cudaMemcpyAsync(B.Xt.ptr, xt.data(), xt.size() * 2, cudaMemcpyHostToDevice, st), "H2D Xt"));
+  STRY(cuda_status(cudaMemcpyAsync(dt.ptr, t, (size_t)m * kOut * 4, cudaMemcpyHostToDevice, st), "H2D T"));
+  STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, st), "clear error"));
+  STRY(forward(ctx, B, m, f32(dt), true));
+  STRY(backward(ctx, B, m));
+  std::vector<float> rl((size_t)m);
+  STRY(cuda_status(cudaMemcpyAsync(rl.data(), B.rowloss.ptr, (size_t)m * 4, cudaMemcpyDeviceToHost, st), "D2H loss"));
+  STRY(cuda_status(cudaMemcpyAsync(grad, S.g.ptr, (size_t)kNumParams * 4, cudaMemcpyDeviceToHost, st), "D2H grad"));
+  if (y_out) STRY(cuda_status(cudaMemcpyAsync(y_out, B.Y.ptr, (size_t)m * kOut * 4, cudaMemcpyDeviceToHost, st), "D2H Y"));
+  unsigned e = 0;
+  STRY(cuda_status(cudaMemcpyAsync(&e, ctx->d_err.ptr, 4, cudaMemcpyDeviceToHost, st), "D2H error"));
+  STRY(cuda_status(cudaStreamSynchronize(st), "grad"));
+  if (e) return sfail(ctx, Status(OPMM_ETIMEDOUT, "GEMM pipeline wait expired"));
+  double l = 0.0;
+  for (float v : rl) l += v;
+  *loss = (float)l;
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch, float lr, float weight_decay,
+                                    uint64_t data_seed, int64_t sample_base, float* losses) {
+  if (!ctx) return OPMM_EINVAL;
+  if (steps < 0 || batch <= 0 || batch % kBM || !(lr > 0.0f))
+    return sfail(ctx, Status(OPMM_EINVAL, "train: batch must be a positive multiple of 128, lr > 0"));
+  if (!ctx->surrogate || !ctx->surrogate->ready) return sfail(ctx, Status(OPMM_EINVAL, "no surrogate"));
+  STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
+  SurrogateState& S = *ctx->surrogate;
+  MlpBuffers& B = S.buf;
+  STRY(B.ensure(batch));
+  if (S.train_M < batch) {
+    STRY(S.sacs.ensure(sizeof(DevSac) * (size_t)batch));
+    STRY(S.traces.ensure(sizeof(float) * (size_t)batch * kTrainLcap));
+    STRY(S.hidden.ensure(sizeof(float) * (size_t)batch * kOut));
+    STRY(S.target.ensure(sizeof(float) * (size_t)batch * kOut));
+    STRY(S.outoff.ensure(sizeof(long long) * (size_t)batch));
+    std::vector<long long> off((size_t)batch);
+    for (int i = 0; i < batch; ++i) off[(size_t)i] = (long long)i * kTrainLcap;
+    STRY(cuda_status(cudaMemcpy(S.outoff.ptr, off.data(), off.size() * 8, cudaMemcpyHostToDevice), "H2D offsets"));
+    S.train_M = batch;
+  }
+  STRY(S.losses.ensure(sizeof(float) * (size_t)(steps > 0 ? steps : 1)));
+  cudaStream_t st = ctx->stream;
+  STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, st), "clear error"));
+  for (int it = 0; it < steps; ++it) {
+    const long long base = (long long)sample_base + (long long)it * batch;
+    STRY(cuda_status(gen_desc(data_seed, base, batch, f32(S.cal_amp), f32(S.cal_pulse), kCal, S.sacs.as<DevSac>(),
+                              f32(S.hidden), f32(S.target), kTrainLcap, st), "generate"));
+    STRY(cuda_status(launch_simulate(f32(S.hidden), batch, S.sacs.as<DevSac>(), nullptr, S.outoff.as<long long>(),
+                                     f32(S.traces), st), "simulate"));
+    STRY(cuda_status(add_noise(data_seed, base, S.sacs.as<DevSac>(), batch, f32(S.traces), 0.05f, st), "noise"));
+    STRY(cuda_status(featurize(S.sacs.as<DevSac>(), f32(S.traces), batch, bf(B.X), bf(B.Xt), batch, st), "featurize"));
+    STRY(forward(ctx, B, batch, f32(S.target), true));
+    STRY(backward(ctx, B, batch));
+    S.step += 1;
+    STRY(cuda_status(adamw(f32(S.w), f32(S.g), f32(S.m1), f32(S.m2), (int)kNumParams, lr, 0.9f, 0.999f, 1e-8f,
+                           weight_decay, S.step, AdamLayout{}, bf(S.wb), bf(S.wt), st), "AdamW"));
+    // batch loss (sum of per-row contributions, fixed order)
+    STRY(cuda_status(sum_array(f32(B.rowloss), batch, f32(S.losses, (size_t)it), st), "loss"));
+  }
+  if (losses && steps > 0)
+    STRY(cuda_status(cudaMemcpyAsync(losses, S.losses.ptr, (size_t)steps * 4, cudaMemcpyDeviceToHost, st), "D2H losses"));
+  unsigned e = 0;
+  STRY(cuda_status(cudaMemcpyAsync(&e, ctx->d_err.ptr, 4, cudaMemcpyDeviceToHost, st), "D2H error"));
+  STRY(cuda_status(cudaStreamSynchronize(st), "train"));
+  if (e) return sfail(ctx, Status(OPMM_ETIMEDOUT, "GEMM pipeline wait expired"));
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_predict(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, int32_t pulse_init,
+                                      float* out_opc) {
+  if (!ctx) return OPMM_EINVAL;
+  if (!sacs || !out_opc || n <= 0) return sfail(ctx, Status(OPMM_EINVAL, "predict: bad arguments"));
+  opmm_fit_opts o{};
+  o.model = OPMM_MODEL_18;
+  o.candidates = 22;
+  o.iterations = 0;
+  o.box_lo = 1.0f;
+  o.box_hi = 1.0f;
+  o.init_step = 1e-3f;
+  o.pulse_init = pulse_init;
+  o.use_surrogate = 1;
+  opmm_plan p;
+  Status s = surrogate_prepare_plan(ctx, &p, sacs, n);
+  if (s.ok()) s = plan_stage(ctx, sacs, n, o, &p);   // stages traces and applies the surrogate
+  if (s.ok())
+    s = cuda_status(cudaMemcpyAsync(out_opc, p.d_pc.ptr, sizeof(float) * OPMM_NPARAM * (size_t)n, cudaMemcpyDeviceToHost,
+                                    ctx->stream), "D2H centres");
+  if (s.ok()) s = cuda_status(cudaStreamSynchronize(ctx->stream), "predict");
+  if (!s.ok()) return sfail(ctx, s);
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_save(opmm_ctx* ctx, const char* path) {
+  if (!ctx || !path) return OPMM_EINVAL;
+  if (!ctx->surrogate || !ctx->surrogate->ready) return sfail(ctx, Status(OPMM_EINVAL, "no surrogate"));
+  std::vector<float> w((size_t)kNumParams);
+  STRY(cuda_status(cudaMemcpy(w.data(), ctx->surrogate->w.ptr, w.size() * 4, cudaMemcpyDeviceToHost), "D2H params"));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return sfail(ctx, Status(OPMM_EINVAL, std::string("cannot open ") + path));
+  const char magic[8] = {'O', 'P', 'M', 'M', 'S', 'G', '1', 0};
+  const int64_t n = kNumParams;
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(&n, 8, 1, f) == 1 &&
+            std::fwrite(w.data(), 4, w.size(), f) == w.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return sfail(ctx, Status(OPMM_EINVAL, "write failed"));
+  return OPMM_OK;
+}
+
+extern "C" int opmm_surrogate_load(opmm_ctx* ctx, const char* path) {
+  if (!ctx || !path) return OPMM_EINVAL;
+  STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return sfail(ctx, Status(OPMM_EINVAL, std::string("cannot open ") + path));
+  char magic[8];
+  int64_t n = 0;
+  std::vector<float> w((size_t)kNumParams);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "OPMMSG1", 8) == 0 && std::fread(&n, 8, 1, f) == 1 &&
+            n == kNumParams && std::fread(w.data(), 4, w.size(), f) == w.size();
+  std::fclose(f);
+  if (!ok) return sfail(ctx, Status(OPMM_EINVAL, "not a surrogate weights file of this architecture"));
+  const bool fresh = !ctx->surrogate || !ctx->surrogate->ready;
+  if (fresh) {
+    const int rc = opmm_surrogate_init(ctx, 0);
+    if (rc != OPMM_OK) return rc;
+  }
+  return opmm_surrogate_set_params(ctx, w.data());
+}
+
+extern "C" int opmm_featurize(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, float* out) {
+  if (!ctx) return OPMM_EINVAL;
+  if (!sacs || !out || n <= 0) return sfail(ctx, Status(OPMM_EINVAL, "featurize: bad arguments"));
+  STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
+  opmm_fit_opts o{};
+  o.model = OPMM_MODEL_18;
+  o.candidates = 22;
+  o.box_lo = 1.0f;
+  o.box_hi = 1.0f;
+  o.init_step = 1e-3f;
+  o.pulse_init = OPMM_PULSE_TABLE1;
+  std::vector<float> zero_centres((size_t)n * OPMM_NPARAM, 1.0f);
+  o.init_opc = zero_centres.data();
+  opmm_plan p;
+  STRY(plan_stage(ctx, sacs, n, o, &p));
+  DevBuf X;
+  STRY(X.ensure((size_t)n * kIn * 2));
+  STRY(cuda_status(featurize(p.d_sacs.as<DevSac>(), p.d_traces.as<float>(), n, bf(X), nullptr, n, ctx->stream),
+                   "featurize"));
+  std::vector<__nv_bfloat16> h((size_t)n * kIn);
+  STRY(cuda_status(cudaMemcpyAsync(h.data(), X.ptr, h.size() * 2, cudaMemcpyDeviceToHost, ctx->stream), "D2H"));
+  STRY(cuda_status(cudaStreamSynchronize(ctx->stream), "featurize"));
+  for (size_t i = 0; i < h.size(); ++i) out[i] = __bfloat162float(h[i]);
+  return OPMM_OK;
+}
+
+extern "C" int opmm_gemm_bf16(opmm_ctx* ctx, const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* D) {
+  if (!ctx) return OPMM_EINVAL;
+  if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || M % kBM || N % kBN || K % kBK)
+    return sfail(ctx, Status(OPMM_EINVAL, "gemm: M, N multiples of 128 and K a multiple of 64 required"));
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(D))
+    return sfail(ctx, Status(OPMM_EINVAL, "gemm: device pointers required"));
+  STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
+  STRY(cuda_status(gemm_prepare(), "GEMM attributes"));
+  GemmArgs a{};
+  a.epi = kEpiF32;
+  a.out_f32 = D;
+  a.ldo = N;
+  a.err = ctx->d_err.as<unsigned>();
+  STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, ctx->stream), "clear error"));
+  STRY(cuda_status(gemm_tn(static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), M, N, K, a,
+                           ctx->stream), "GEMM"));
+  unsigned e = 0;
+  STRY(cuda_status(cudaMemcpyAsync(&e, ctx->d_err.ptr, 4, cudaMemcpyDeviceToHost, ctx->stream), "D2H error"));
+  STRY(cuda_status(cudaStreamSynchronize(ctx->stream), "gemm"));
+  if (e) return sfail(ctx, Status(OPMM_ETIMEDOUT, "GEMM pipeline wait expired"));
+  return OPMM_OK;
+}

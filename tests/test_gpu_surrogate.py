@@ -1,0 +1,138 @@
+"""The learned surrogate on the GPU: the tcgen05 GEMM against torch, the
+featurizer against a numpy restatement, forward/backward against the FP64
+oracle (on the same BF16-rounded weights and inputs), training, seeding.
+
+Tolerances: the GEMM accumulates BF16 products in FP32 exactly like the
+reference matmul up to summation order (1e-3 relative); the network rounds
+activations and back-propagated errors to BF16 between layers (relative
+precision 2^-8), so outputs and gradients are compared to the FP64 oracle at a
+few percent (cosine > 0.998)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2007_09884_gb300 as G
+import workloads as W
+from _support import centres, oracle_inputs, to_batch
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    h = G.opmm_create(0)
+    yield h
+    G.opmm_destroy(h)
+
+
+def bf16(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    r = ((b >> 16) & 1) + 0x7FFF
+    return ((b + r) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("M_,N_,K_", [(128, 128, 64), (256, 512, 512), (512, 512, 4096), (384, 256, 192)])
+def test_tcgen05_gemm_matches_torch(ctx, M_, N_, K_):
+    torch = pytest.importorskip("torch")
+    g = torch.Generator(device="cuda").manual_seed(M_ + N_ + K_)
+    A = torch.randn(M_, K_, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N_, K_, device="cuda", generator=g).to(torch.bfloat16)
+    D = G.opmm_gemm_bf16(ctx, A, B)
+    ref = A.double() @ B.double().T
+    err = (D.double() - ref).abs().max().item()
+    assert err <= 1e-3 * ref.abs().max().item() + 1e-3, err
+
+
+def _features_np(y, fs, onset, th0, thf):
+    sign = -1.0 if thf < th0 else 1.0
+    a0, af = sign * th0, sign * thf
+    amp = max(af - a0, 0.5)
+    L = len(y)
+    pos = np.zeros(257)
+    for i in range(257):
+        s = min(onset + i * fs * 1e-3, L - 1)
+        k0 = int(math.floor(s))
+        k1 = min(k0 + 1, L - 1)
+        w = s - k0
+        pos[i] = (sign * ((1 - w) * y[k0] + w * y[k1]) - a0) / amp
+    vel = 10.0 * (pos[1:257] - pos[0:256])
+    vel[255] = 0.0
+    return np.concatenate([pos[:256], vel])
+
+
+def test_featurizer_matches_numpy(ctx):
+    items = oracle_inputs(W.uneven10k(B=24))
+    got = G.opmm_featurize(ctx, to_batch(items))
+    for j, it in enumerate(items):
+        ref = _features_np(np.float32(it["y"]).astype(np.float64), it["fs"], it["onset"], it["th0"], it["thf"])
+        np.testing.assert_allclose(got[j], ref, rtol=8e-3, atol=2e-3 * max(1.0, np.abs(ref).max()))
+
+
+def test_forward_backward_match_fp64_oracle(ctx):
+    G.opmm_surrogate_init(ctx, 7)
+    p = G.opmm_surrogate_get_params(ctx).astype(np.float64)
+    layers_end = 4 * (512 * 512 + 512)
+    pb = p.copy()
+    for l in range(4):
+        o = l * (512 * 512 + 512)
+        pb[o:o + 512 * 512] = bf16(p[o:o + 512 * 512])
+    pb[layers_end:layers_end + 18 * 512] = bf16(p[layers_end:layers_end + 18 * 512])
+    rng = np.random.default_rng(1)
+    x = rng.normal(0, 1, (256, 512)).astype(np.float32)
+    t = rng.normal(0, 0.5, (256, 18)).astype(np.float32)
+    loss_g, grad_g, y_g = G.opmm_surrogate_grad(ctx, x, t)
+    loss_o, grad_o = M.loss_and_grad(pb, bf16(x).astype(np.float64), t.astype(np.float64))
+    y_o, _ = M.forward(pb, bf16(x).astype(np.float64))
+    assert np.linalg.norm(y_g - y_o) <= 2e-2 * np.linalg.norm(y_o)
+    assert abs(loss_g - loss_o) <= 2e-2 * loss_o
+    segs = []
+    for l in range(4):
+        o = l * (512 * 512 + 512)
+        segs += [(o, o + 512 * 512), (o + 512 * 512, o + 512 * 512 + 512)]
+    segs += [(layers_end, layers_end + 18 * 512), (layers_end + 18 * 512, layers_end + 18 * 512 + 18)]
+    for a, b in segs:
+        gg, go = grad_g[a:b].astype(np.float64), grad_o[a:b]
+        cos = gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go))
+        assert cos > 0.998, (a, b, cos)
+        assert np.linalg.norm(gg - go) <= 6e-2 * np.linalg.norm(go), (a, b)
+
+
+def test_training_reduces_loss_and_weights_round_trip(ctx, tmp_path):
+    # targets ln(U(0.8, 1.2)) / 0.2 have variance ~0.333 per output: an untrained
+    # network starts there; 600 steps of 2,048 generated saccades must cut it
+    G.opmm_surrogate_init(ctx, 3)
+    losses = G.opmm_surrogate_train(ctx, 600, batch=2048, lr=2e-3, data_seed=11)
+    assert np.all(np.isfinite(losses))
+    assert 0.30 < losses[:5].mean() < 0.37
+    assert losses[-50:].mean() < 0.93 * losses[:5].mean(), (losses[:5], losses[-50:])
+    path = str(tmp_path / "w.bin")
+    G.opmm_surrogate_save(ctx, path)
+    p1 = G.opmm_surrogate_get_params(ctx)
+    G.opmm_surrogate_init(ctx, 99)
+    G.opmm_surrogate_load(ctx, path)
+    np.testing.assert_array_equal(G.opmm_surrogate_get_params(ctx), p1)
+
+
+def test_seeded_fit_stays_in_the_narrowed_box(ctx):
+    G.opmm_surrogate_init(ctx, 5)
+    G.opmm_surrogate_train(ctx, 50, batch=1024, lr=1e-3, data_seed=12)
+    items = oracle_inputs(W.uneven10k(B=6))
+    batch = to_batch(items)
+    pred = G.opmm_surrogate_predict(ctx, batch)
+    nominal = G.opmm_nominal_opc(ctx, batch, G.OPMM_PULSE_CALIBRATED)
+    ratio = pred / nominal
+    assert np.all(np.isfinite(pred)) and np.all(pred > 0)
+    assert np.all(np.abs(np.log(ratio)) < 3.0)
+    res = G.opmm_fit_batch(ctx, batch, candidates=22 * 16, iterations=8, box_lo=0.95, box_hi=1.05,
+                           init_step=0.025, use_surrogate=True)
+    assert np.all(res["status"] == 0)
+    r = res["opc"] / pred
+    assert np.all(r >= 0.95 * (1 - 1e-5)) and np.all(r <= 1.05 * (1 + 1e-5))
