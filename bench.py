@@ -373,6 +373,114 @@ def run_ours(args, ws, rank, local):
     return out
 
 
+# ------------------------------------------------------------------ serving
+def serve_run(G, ctx, traces_desc, arrivals, fit, cfg):
+    """Submit saccades at the given arrival times (s), collect every result;
+    returns per-request latency (ms), RMS, and counts."""
+    import threading
+    G.opmm_serve_start(ctx, cfg, **fit)
+    descs, keep = traces_desc.descriptors()
+    n_desc = len(traces_desc)
+    tickets, rejected = [], 0
+    lock = threading.Lock()
+    done = {"lat": [], "rms": [], "status": []}
+    stop = {"flag": False}
+
+    def collector():
+        i = 0
+        while True:
+            with lock:
+                have = i < len(tickets)
+                t = tickets[i] if have else None
+            if not have:
+                if stop["flag"]:
+                    break
+                time.sleep(0.0005)
+                continue
+            rc, res, lat = G.opmm_serve_poll_raw(ctx, t, 2_000_000)
+            if rc == G.OPMM_OK:
+                done["lat"].append(lat / 1000.0)
+                done["rms"].append(res["rms_deg"])
+                done["status"].append(res["status"])
+                i += 1
+            elif rc == G.OPMM_ETIMEDOUT:
+                continue
+            else:
+                i += 1
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    k = 0
+    n = len(arrivals)
+    while k < n:
+        now = time.perf_counter() - t0
+        while k < n and arrivals[k] <= now:
+            rc, t = G.opmm_serve_submit_raw(ctx, descs[k % n_desc])
+            if rc == G.OPMM_OK:
+                with lock:
+                    tickets.append(t)
+            elif rc == G.OPMM_EBUSY:
+                rejected += 1
+            k += 1
+        time.sleep(0.0002)
+    t_submit_end = time.perf_counter() - t0
+    stop["flag"] = True
+    th.join()
+    t_all = time.perf_counter() - t0
+    stats = G.opmm_serve_stats_get(ctx)
+    G.opmm_serve_stop(ctx)
+    lat = np.array(done["lat"]) if done["lat"] else np.array([float("nan")])
+    rms = np.array(done["rms"]) if done["rms"] else np.array([float("nan")])
+    return {"offered": n, "completed": len(done["lat"]), "rejected": rejected,
+            "duration_s": t_all, "submit_window_s": t_submit_end,
+            "throughput_per_s": len(done["lat"]) / t_all,
+            "fitted_per_s_at_0p1deg": float(np.sum(rms <= 0.1)) / t_all,
+            "fraction_fitted_at_0p1deg": float(np.mean(rms <= 0.1)),
+            "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+            "slots": stats["slots"], "rounds": stats["rounds"]}
+
+
+def run_serve(args):
+    import torch
+    import paper_2007_09884_gb300 as G
+    ctx = G.opmm_create(0)
+    w = W.uneven10k(B=2048, config_index=4)
+    traces, pulse = gpu_inputs(G, ctx, w)
+    batch = G.make_batch(traces, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms)
+    t0 = time.perf_counter()
+    G.opmm_surrogate_init(ctx, 1)
+    base = 0
+    for steps, lr in [(800, 2e-3), (800, 1e-3), (500, 5e-4), (341, 2.5e-4)]:
+        G.opmm_surrogate_train(ctx, steps, batch=4096, lr=lr, weight_decay=1e-4, data_seed=7, sample_base=base)
+        base += steps * 4096
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    plain = dict(candidates=16384, iterations=30, seed=0, pulse_init=pulse)
+    seeded = dict(candidates=1024, iterations=20, seed=0, pulse_init=pulse, box_lo=0.95, box_hi=1.05,
+                  init_step=0.025, use_surrogate=True)
+    rows = []
+    for rate in args.rates:
+        arr = W.poisson_arrivals(rate, args.serve_seconds, seed=int(rate))
+        for name, fit, ri in (("plain", plain, 10), ("surrogate", seeded, 5)):
+            cfg = G.serve_opts(max_slots=args.serve_slots, max_queue=max(1000, int(rate * 2)), max_samples=400,
+                               round_iters=ri, max_admit_per_round=4096)
+            r = serve_run(G, ctx, batch, arr, fit, cfg)
+            r.update({"rate_per_s": rate, "search": name})
+            rows.append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+    G.opmm_destroy(ctx)
+    head = [r for r in rows if r["search"] == "surrogate"]
+    best = max(head, key=lambda r: r["fitted_per_s_at_0p1deg"])
+    return {"metric": "saccades fitted/s at <=0.1 deg RMS with p50/p99 fit latency (real-time serving)",
+            "value": best["fitted_per_s_at_0p1deg"], "unit": "saccades/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic (Poisson arrivals)",
+            "config": {"workload": "serve", "rates_per_s": args.rates, "seconds_per_rate": args.serve_seconds,
+                       "plain": plain, "surrogate": {k: v for k, v in seeded.items()},
+                       "surrogate_training_s": train_s, "surrogate_training_samples": base},
+            "rows": rows}
+
+
 # ------------------------------------------------------------------ oracle arm
 def oracle_sample(w, budget_s: float, nthreads: int):
     """Oracle fit of saccade 0 at the workload's full iteration cap on a
@@ -440,7 +548,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch1024", choices=["batch1024", "uneven10k", "single10"])
+    ap.add_argument("--workload", default="batch1024", choices=["batch1024", "uneven10k", "single10", "serve"])
+    ap.add_argument("--rates", type=float, nargs="+", default=[1000.0, 10000.0, 50000.0])
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-slots", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="small batch (smoke of the bench itself)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -450,6 +561,8 @@ def main():
     ws, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
+    elif args.workload == "serve":
+        out = run_serve(args) if rank == 0 else None
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:

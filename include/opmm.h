@@ -13,7 +13,7 @@
  * Conventions
  *  - Every function returns an int status: OPMM_OK (0), OPMM_NOT_READY (1), or
  *    a negative error.  No exception or abort crosses the ABI.  The text of
- *    the last error of a context is returned by opmm_last_error.
+ *    the calling thread's last error is returned by opmm_last_error.
  *  - Inputs are owned by the caller and only read during the call; outputs
  *    are caller-owned buffers.  Pointers documented as "host or device" may
  *    point to either (the library asks the CUDA runtime which); all pointers
@@ -116,7 +116,8 @@ typedef struct {
  * buffers and the autotuner cache. */
 int opmm_create(int device_ordinal, opmm_ctx** out);
 void opmm_destroy(opmm_ctx* ctx);
-/* Message of the last failed call on this context (never NULL). */
+/* Message of the last failed call made by the calling thread (never NULL;
+ * valid until that thread's next failing call). */
 const char* opmm_last_error(const opmm_ctx* ctx);
 /* Use the caller's CUDA stream (cudaStream_t) for subsequent calls; NULL
  * restores the context's own stream. */
@@ -193,6 +194,47 @@ int opmm_plan_tuning(const opmm_plan* plan, int32_t* variant, int32_t* simplices
  * events recorded around it on the plan's stream (inside the graph). */
 int opmm_plan_last_search_ms(const opmm_plan* plan, float* ms);
 void opmm_plan_destroy(opmm_plan* plan);
+
+/* ------------------------------------------------------------ serving */
+/* Real-time request loop with continuous batching (the paper's motivation:
+ * estimation as fast as the recording, Sec. 4).  Single saccades arrive
+ * with opmm_serve_submit; a scheduler thread admits them into device slots
+ * while earlier requests are still being searched, advances all resident
+ * requests together a few Nelder-Mead iterations per round (search state
+ * stays in HBM between rounds), and completes each one after
+ * opmm_fit_opts.iterations iterations.  A request's result does not depend
+ * on what else is running. */
+typedef struct {
+  int32_t max_slots;            /* upper bound on requests resident on the device */
+  uint64_t max_device_bytes;    /* admission budget for slot state; 0 = half the free HBM */
+  int32_t max_queue;            /* queued requests beyond which submit returns OPMM_EBUSY */
+  int32_t max_samples;          /* longest accepted trace (<= 16384) */
+  int32_t round_iters;          /* iterations per scheduling round (>= 1) */
+  int32_t max_admit_per_round;  /* admissions per round (>= 1) */
+} opmm_serve_opts;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, rejected, rounds;
+  int32_t queued, active, slots, reserved;
+} opmm_serve_stats;
+
+/* Start the loop with fixed fit options (fit->init_opc, if given, is one
+ * host [18] centre used for every request).  The number of slots is
+ * min(max_slots, budget / bytes per slot); OPMM_EBUSY if not even one fits. */
+int opmm_serve_start(opmm_ctx* ctx, const opmm_serve_opts* cfg, const opmm_fit_opts* fit);
+/* Queue one saccade (the trace, host or device, is copied before returning);
+ * OPMM_EBUSY when the queue is full (back-pressure), OPMM_EINVAL for a
+ * malformed descriptor.  Thread-safe. */
+int opmm_serve_submit(opmm_ctx* ctx, const opmm_saccade* sac, uint64_t* ticket);
+/* Result of a ticket: OPMM_OK (and the ticket is released), OPMM_NOT_READY
+ * (timeout_us == 0), OPMM_ETIMEDOUT (waited timeout_us), OPMM_EINVAL for an
+ * unknown ticket.  latency_us (nullable): submit-to-completion time.
+ * Thread-safe. */
+int opmm_serve_poll(opmm_ctx* ctx, uint64_t ticket, opmm_fit_result* out, int32_t timeout_us,
+                    double* latency_us);
+int opmm_serve_stats_get(opmm_ctx* ctx, opmm_serve_stats* out);
+/* Stop the loop; queued and running requests are dropped. */
+int opmm_serve_stop(opmm_ctx* ctx);
 
 /* ------------------------------------------------------------ surrogate */
 /* A learned amortised inverse (not in the paper): a multilayer perceptron

@@ -43,7 +43,8 @@ EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", 
            "opmm_fit_saccade_static", "opmm_surrogate_init", "opmm_surrogate_num_params",
            "opmm_surrogate_get_params", "opmm_surrogate_set_params", "opmm_surrogate_grad",
            "opmm_surrogate_train", "opmm_surrogate_predict", "opmm_surrogate_save", "opmm_surrogate_load", "opmm_featurize",
-           "opmm_gemm_bf16"]
+           "opmm_gemm_bf16", "opmm_serve_start", "opmm_serve_submit", "opmm_serve_poll",
+           "opmm_serve_stats_get", "opmm_serve_stop"]
 
 
 class OpmmError(RuntimeError):
@@ -66,6 +67,19 @@ class opmm_fit_opts(ctypes.Structure):
                 ("tol_x", ctypes.c_float), ("tol_f", ctypes.c_float), ("seed", ctypes.c_uint64),
                 ("pulse_init", ctypes.c_int32), ("use_surrogate", ctypes.c_int32),
                 ("init_opc", ctypes.c_void_p)]
+
+
+class opmm_serve_opts(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_device_bytes", ctypes.c_uint64),
+                ("max_queue", ctypes.c_int32), ("max_samples", ctypes.c_int32),
+                ("round_iters", ctypes.c_int32), ("max_admit_per_round", ctypes.c_int32)]
+
+
+class opmm_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("queued", ctypes.c_int32), ("active", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class opmm_fit_result(ctypes.Structure):
@@ -123,13 +137,20 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_surrogate_load.argtypes = [vp, ctypes.c_char_p]
     lib.opmm_featurize.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, vp]
     lib.opmm_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+    lib.opmm_serve_start.argtypes = [vp, ctypes.POINTER(opmm_serve_opts), ctypes.POINTER(opmm_fit_opts)]
+    lib.opmm_serve_submit.argtypes = [vp, ctypes.POINTER(opmm_saccade), ctypes.POINTER(ctypes.c_uint64)]
+    lib.opmm_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(opmm_fit_result), i32,
+                                    ctypes.POINTER(ctypes.c_double)]
+    lib.opmm_serve_stats_get.argtypes = [vp, ctypes.POINTER(opmm_serve_stats)]
+    lib.opmm_serve_stop.argtypes = [vp]
     for name in ["opmm_create", "opmm_set_stream", "opmm_set_search_variant", "opmm_search_variants", "opmm_simulate", "opmm_score", "opmm_nominal_opc",
                  "opmm_fit_batch", "opmm_plan_create", "opmm_plan_execute", "opmm_plan_info",
                  "opmm_plan_last_search_ms", "opmm_fit_saccade_static", "opmm_plan_tuning",
                  "opmm_surrogate_init", "opmm_surrogate_num_params", "opmm_surrogate_get_params",
                  "opmm_surrogate_set_params", "opmm_surrogate_grad", "opmm_surrogate_train",
                  "opmm_surrogate_predict", "opmm_surrogate_save", "opmm_surrogate_load",
-                 "opmm_featurize", "opmm_gemm_bf16"]:
+                 "opmm_featurize", "opmm_gemm_bf16", "opmm_serve_start", "opmm_serve_submit",
+                 "opmm_serve_poll", "opmm_serve_stats_get", "opmm_serve_stop"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -491,3 +512,60 @@ def opmm_gemm_bf16(ctx, A, B, out=None):
     _check(ctx, load_library().opmm_gemm_bf16(ctx, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                                int(M), int(N), int(K), ctypes.c_void_p(out.data_ptr())))
     return out
+
+
+# ------------------------------------------------------------------ serving
+def serve_opts(max_slots=4096, max_device_bytes=0, max_queue=100000, max_samples=400, round_iters=5,
+               max_admit_per_round=4096):
+    o = opmm_serve_opts()
+    o.max_slots, o.max_device_bytes, o.max_queue = int(max_slots), int(max_device_bytes), int(max_queue)
+    o.max_samples, o.round_iters, o.max_admit_per_round = int(max_samples), int(round_iters), int(max_admit_per_round)
+    return o
+
+
+def opmm_serve_start(ctx, cfg: opmm_serve_opts, **fit):
+    o, keep = fit_opts(**fit)
+    _check(ctx, load_library().opmm_serve_start(ctx, ctypes.byref(cfg), ctypes.byref(o)))
+
+
+def opmm_serve_submit_raw(ctx, desc) -> tuple:
+    """(status, ticket) for one opmm_saccade (no exception on EBUSY)."""
+    t = ctypes.c_uint64()
+    rc = load_library().opmm_serve_submit(ctx, ctypes.byref(desc), ctypes.byref(t))
+    return int(rc), int(t.value)
+
+
+def opmm_serve_submit(ctx, batch: SaccadeBatch, index: int = 0) -> int:
+    descs, keep = batch.descriptors()
+    rc, t = opmm_serve_submit_raw(ctx, descs[index])
+    _check(ctx, rc)
+    return t
+
+
+def opmm_serve_poll_raw(ctx, ticket: int, timeout_us: int = 0):
+    """(status, result-dict or None, latency_us)."""
+    r = opmm_fit_result()
+    lat = ctypes.c_double()
+    rc = load_library().opmm_serve_poll(ctx, ctypes.c_uint64(int(ticket)), ctypes.byref(r), int(timeout_us),
+                                        ctypes.byref(lat))
+    if rc != OPMM_OK:
+        return int(rc), None, None
+    return OPMM_OK, {k: v[0] for k, v in results_to_numpy((opmm_fit_result * 1)(r)).items()}, float(lat.value)
+
+
+def opmm_serve_poll(ctx, ticket: int, timeout_us: int = 10_000_000):
+    rc, res, lat = opmm_serve_poll_raw(ctx, ticket, timeout_us)
+    _check(ctx, rc)
+    if rc != OPMM_OK:
+        raise OpmmError(rc, "result not ready")
+    return res, lat
+
+
+def opmm_serve_stats_get(ctx) -> dict:
+    s = opmm_serve_stats()
+    _check(ctx, load_library().opmm_serve_stats_get(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def opmm_serve_stop(ctx):
+    _check(ctx, load_library().opmm_serve_stop(ctx))

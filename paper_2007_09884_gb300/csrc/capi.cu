@@ -140,8 +140,16 @@ opmm_ctx::~opmm_ctx() {
   if (own_stream) cudaStreamDestroy(own_stream);
 }
 
+namespace opmm {
+// Error text of the last failed call, per calling thread: the serving calls
+// run concurrently from several threads.
+static thread_local std::string tl_last_error;
+void set_last_error(const std::string& msg) { tl_last_error = msg; }
+}  // namespace opmm
+
 static int fail(opmm_ctx* ctx, const Status& s) {
-  if (ctx) ctx->err = s.msg;
+  (void)ctx;
+  set_last_error(s.msg);
   return s.code;
 }
 
@@ -203,8 +211,8 @@ extern "C" void opmm_destroy(opmm_ctx* ctx) {
 }
 
 extern "C" const char* opmm_last_error(const opmm_ctx* ctx) {
-  if (!ctx) return "null context";
-  return ctx->err.c_str();
+  (void)ctx;
+  return tl_last_error.c_str();
 }
 
 extern "C" int opmm_set_search_variant(opmm_ctx* ctx, int32_t variant) {

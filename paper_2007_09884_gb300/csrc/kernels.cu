@@ -271,6 +271,9 @@ constexpr int kUnitRec = 24;
 constexpr int kNV = kNumParams + 1;      // vertices per simplex
 constexpr int kNT = kNumParams + 4;      // trial points per simplex and iteration
 constexpr int kSortBins = 1024;          // pulse-end time bins of the per-wave ordering
+// Saved simplex (serving): vertices, values, centroid, order, active, iterations.
+constexpr int kStateFloats = kNV * kNumParams + kNV + kNumParams + kNV + 2;
+static_assert(kStateFloats == kSearchStateFloats, "saved simplex layout");
 constexpr int kHistLen = kSortBins + kSortBins / 32;   // bin b stored at b + b/32
 
 template <int G>
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     __syncthreads();
     const int unit = S.unit;
     if (unit >= P.n_units) break;
-    const int2 un = P.units[unit];
+    const int2 un = P.slot_list ? make_int2(P.slot_list[unit / P.ngroups], unit % P.ngroups) : P.units[unit];
     const int b = un.x, g0 = un.y;
     if (b != S.cur_b) {
       const DevSac d = P.sacs[b];
@@ -489,7 +492,27 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     const int nsim = min(G, P.S - g0 * G);
     const SacConst sc = S.sc;
     const float sum0 = S.st.sum0, c0 = S.st.c0;
-    int evals = kNV * nsim;
+    // resumable mode (serving): iterations already done by this saccade and
+    // this launch's share; the simplex state lives in HBM between launches
+    const int it0 = P.state ? P.progress[b] : 0;
+    const int t_run = P.state ? min(P.round_iters, P.T - it0) : P.T;
+    float* gstate = P.state ? P.state + ((size_t)b * P.S + (size_t)g0 * G) * kStateFloats : nullptr;
+    float* rec = P.unit_best + (size_t)(P.slot_list ? b * P.ngroups + g0 : unit) * kUnitRec;
+    int evals = it0 > 0 ? __float_as_int(rec[3]) : kNV * nsim;
+    if (it0 > 0) {
+      // restore the simplices: vertices, values, centroid, order, flags
+      for (int idx = tid; idx < nsim * kStateFloats; idx += NT) {
+        const int gi = idx / kStateFloats, r = idx - gi * kStateFloats;
+        const float v = gstate[idx];
+        if (r < kNV * kNumParams) (&S.U[gi][0][0])[r] = v;
+        else if (r < kNV * kNumParams + kNV) S.F[gi][r - kNV * kNumParams] = v;
+        else if (r < kNV * kNumParams + kNV + kNumParams) S.XB[gi][r - kNV * kNumParams - kNV] = v;
+        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) S.ord[gi][r - kNV * kNumParams - kNV - kNumParams] = (unsigned char)__float_as_int(v);
+        else if (r == kStateFloats - 2) S.active[gi] = __float_as_int(v);
+        else if (r == kStateFloats - 1) S.iters[gi] = __float_as_int(v);
+      }
+      __syncthreads();
+    } else {
 
     // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
     if (tid < 5 * nsim) {
@@ -549,7 +572,9 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     }
     __syncthreads();
 
-    for (int it = 0; it < P.T; ++it) {
+    }  // initial simplices
+
+    for (int it = 0; it < t_run; ++it) {
       int nact = 0;
       for (int gi = 0; gi < nsim; ++gi) nact += S.active[gi];
       if (!nact) break;
@@ -659,6 +684,22 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       __syncthreads();
     }
 
+    if (gstate) {
+      // save the simplices for the next launch
+      for (int idx = tid; idx < nsim * kStateFloats; idx += NT) {
+        const int gi = idx / kStateFloats, r = idx - gi * kStateFloats;
+        float v;
+        if (r < kNV * kNumParams) v = (&S.U[gi][0][0])[r];
+        else if (r < kNV * kNumParams + kNV) v = S.F[gi][r - kNV * kNumParams];
+        else if (r < kNV * kNumParams + kNV + kNumParams) v = S.XB[gi][r - kNV * kNumParams - kNV];
+        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) v = __int_as_float((int)S.ord[gi][r - kNV * kNumParams - kNV - kNumParams]);
+        else if (r == kStateFloats - 2) v = __int_as_float(S.active[gi]);
+        else if (r == kStateFloats - 1) v = __int_as_float(S.iters[gi]);
+        else v = 0.0f;
+        gstate[idx] = v;
+      }
+    }
+
     // ---- unit result: lowest value, ties to the lowest simplex index
     if (warp == 0) {
       float f = INFINITY;
@@ -670,7 +711,6 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
         if (f2 < f || (f2 == f && b2 < best)) { f = f2; best = b2; }
       }
-      float* rec = P.unit_best + (size_t)unit * kUnitRec;
       if (best < nsim) {
         if (lane < kNumParams) rec[4 + lane] = S.U[best][S.ord[best][0]][lane];
         if (lane == 0) {
@@ -685,56 +725,139 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
 }
 
 // ------------------------------------------------------------------ finalize
-// FP64 re-computation of the winner's error with the literal RK4 stages (the
-// serial check next to the parallel value, as Fig. 4's CPU_check column).
-struct Drive64 { double na, nn, ita, itn; };   // drives and reciprocal time constants
-
-struct Plant64 {
-  double kse_ag, kse_ant, klt_ag, klt_ant, kp, bp, iJ, iBa, iBn;
+// FP64 re-computation of the winner's error (the serial check next to the
+// parallel value, as Fig. 4's CPU_check column).  The same RK4 map is applied
+// in double precision as dense 6x6 step matrices: within one input phase one
+// RK4 step of e' = A e is e <- e + Q e with Q = hA(I + hA/2(I + hA/3(I + hA/4))),
+// raised to one sample interval by squaring; the pulse-end substep is split
+// into two RK4 steps.  Independent of the FP32 search formulation (dense
+// matrices, double precision, its own equilibria).
+struct M6 {
+  double a[6][6];
 };
 
-__device__ void deriv64(const Plant64& c, const double* s, const Drive64& d, double* ds) {
-  const double ta = c.kse_ag * (s[2] - s[0]);
-  const double tn = c.kse_ant * (s[3] + s[0]);
-  ds[0] = s[1];
-  ds[1] = (ta - tn - c.bp * s[1] - c.kp * s[0]) * c.iJ;
-  ds[2] = (s[4] - ta - c.klt_ag * s[2]) * c.iBa;
-  ds[3] = (s[5] - tn - c.klt_ant * s[3]) * c.iBn;
-  ds[4] = (d.na - s[4]) * d.ita;
-  ds[5] = (d.nn - s[5]) * d.itn;
+__device__ void m6_zero(M6& m) {
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) m.a[i][j] = 0.0;
 }
 
-__device__ void rk4_64(const Plant64& c, double* s, const Drive64& d, double h) {
-  double k1[6], k2[6], k3[6], k4[6], t[6];
-  deriv64(c, s, d, k1);
-  for (int i = 0; i < 6; ++i) t[i] = s[i] + 0.5 * h * k1[i];
-  deriv64(c, t, d, k2);
-  for (int i = 0; i < 6; ++i) t[i] = s[i] + 0.5 * h * k2[i];
-  deriv64(c, t, d, k3);
-  for (int i = 0; i < 6; ++i) t[i] = s[i] + h * k3[i];
-  deriv64(c, t, d, k4);
-  for (int i = 0; i < 6; ++i) s[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+// r = a + b + a b (increment form of (I + a)(I + b)); r may alias neither
+__device__ void m6_mul_inc(const M6& a, const M6& b, M6& r) {
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double acc = a.a[i][j] + b.a[i][j];
+      for (int k = 0; k < 6; ++k) acc = fma(a.a[i][k], b.a[k][j], acc);
+      r.a[i][j] = acc;
+    }
 }
 
-__device__ void rest64(const double* p, double th, double* s, double* fa, double* fn) {
-  const double ta = p[kNcFix] + p[kNcAg] * th, tn = p[kNcFix] - p[kNcAnt] * th;
+// plant matrix of one phase (state theta, omega, x, y, Fa, Fn)
+__device__ void plant_matrix64(const double* p, double ita, double itn, M6& A) {
+  m6_zero(A);
+  const double kp = p[kNcAg] + p[kNcAnt];
+  const double iJ = 1.0 / p[kJ], iBa = 1.0 / p[kBAg], iBn = 1.0 / p[kBAnt];
+  A.a[0][1] = 1.0;
+  A.a[1][0] = -(p[kSeAg] + p[kSeAnt] + kp) * iJ;
+  A.a[1][1] = -p[kBp] * iJ;
+  A.a[1][2] = p[kSeAg] * iJ;
+  A.a[1][3] = -p[kSeAnt] * iJ;
+  A.a[2][0] = p[kSeAg] * iBa;
+  A.a[2][2] = -(p[kSeAg] + p[kLtAg]) * iBa;
+  A.a[2][4] = iBa;
+  A.a[3][0] = -p[kSeAnt] * iBn;
+  A.a[3][3] = -(p[kSeAnt] + p[kLtAnt]) * iBn;
+  A.a[3][5] = iBn;
+  A.a[4][4] = -ita;
+  A.a[5][5] = -itn;
+}
+
+// Q = T4(hA) - I by Horner
+__device__ void step_inc64(const M6& A, double h, M6& Q) {
+  M6 W, T;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) W.a[i][j] = (i == j ? 1.0 : 0.0) + 0.25 * h * A.a[i][j];
+  const double c[2] = {h / 3.0, 0.5 * h};
+  for (int lev = 0; lev < 2; ++lev) {
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < 6; ++k) acc = fma(A.a[i][k], W.a[k][j], acc);
+        T.a[i][j] = (i == j ? 1.0 : 0.0) + c[lev] * acc;
+      }
+    W = T;
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc = fma(A.a[i][k], W.a[k][j], acc);
+      Q.a[i][j] = h * acc;
+    }
+}
+
+__device__ void pow_inc64(const M6& q, int n, M6& out) {
+  M6 base = q, tmp;
+  bool have = false;
+  while (true) {
+    if (n & 1) {
+      if (have) { m6_mul_inc(out, base, tmp); out = tmp; }
+      else { out = base; have = true; }
+    }
+    n >>= 1;
+    if (!n) break;
+    m6_mul_inc(base, base, tmp);
+    base = tmp;
+  }
+}
+
+__device__ void apply_inc64(const M6& q, double* e) {
+  double n[6];
+  for (int i = 0; i < 6; ++i) {
+    double acc = e[i];
+    for (int k = 0; k < 6; ++k) acc = fma(q.a[i][k], e[k], acc);
+    n[i] = acc;
+  }
+  for (int i = 0; i < 6; ++i) e[i] = n[i];
+}
+
+// one RK4 step of length hs on e' = A e (Horner form of T4(hs A) e)
+__device__ void rk4_vec64(const M6& A, double hs, double* e) {
+  double w[6], v[6];
+  for (int i = 0; i < 6; ++i) w[i] = e[i];
+  const double c[4] = {0.25 * hs, hs / 3.0, 0.5 * hs, hs};
+  for (int lev = 0; lev < 4; ++lev) {
+    for (int i = 0; i < 6; ++i) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc = fma(A.a[i][k], w[k], acc);
+      v[i] = acc;
+    }
+    for (int i = 0; i < 6; ++i) w[i] = fma(c[lev], v[i], e[i]);
+  }
+  for (int i = 0; i < 6; ++i) e[i] = w[i];
+}
+
+// equilibrium under constant active-state tensions (fa, fn), double
+__device__ void equilibrium64(const double* p, double fa, double fn, double* s) {
+  const double ag = p[kSeAg] / (p[kSeAg] + p[kLtAg]);
+  const double an = p[kSeAnt] / (p[kSeAnt] + p[kLtAnt]);
+  const double kp = p[kNcAg] + p[kNcAnt];
+  const double th = (ag * fa - an * fn) / (kp + ag * p[kLtAg] + an * p[kLtAnt]);
+  const double ta = ag * (fa - p[kLtAg] * th), tn = an * (fn + p[kLtAnt] * th);
   s[0] = th; s[1] = 0.0;
   s[2] = th + ta / p[kSeAg];
   s[3] = tn / p[kSeAnt] - th;
-  *fa = ta * (1.0 + p[kLtAg] / p[kSeAg]) + p[kLtAg] * th;
-  *fn = tn * (1.0 + p[kLtAnt] / p[kSeAnt]) - p[kLtAnt] * th;
-  s[4] = *fa; s[5] = *fn;
+  s[4] = fa; s[5] = fn;
 }
 
-// Mean squared and mean absolute error of the winner's trajectory, FP64,
-// literal RK4 stages with the pulse-end substep split (the serial check).
+__device__ void step_levels64(const double* p, double th, double* fa, double* fn) {
+  const double ta = p[kNcFix] + p[kNcAg] * th, tn = p[kNcFix] - p[kNcAnt] * th;
+  *fa = ta * (1.0 + p[kLtAg] / p[kSeAg]) + p[kLtAg] * th;
+  *fn = tn * (1.0 + p[kLtAnt] / p[kSeAnt]) - p[kLtAnt] * th;
+}
+
+// Mean squared and mean absolute error of the winner's trajectory, FP64.
 __device__ void errors64(const float* pf, const DevSac& d, const float* y, double* mse, double* mae) {
   double p[kNumParams];
   for (int j = 0; j < kNumParams; ++j) p[j] = (double)pf[j];
-  Plant64 c;
-  c.kse_ag = p[kSeAg]; c.kse_ant = p[kSeAnt]; c.klt_ag = p[kLtAg]; c.klt_ant = p[kLtAnt];
-  c.kp = p[kNcAg] + p[kNcAnt]; c.bp = p[kBp];
-  c.iJ = 1.0 / p[kJ]; c.iBa = 1.0 / p[kBAg]; c.iBn = 1.0 / p[kBAnt];
   const double th0 = d.th0, thf = d.thf, sg = d.sign;
   const int nsub = d.nsub;
   const double h = 1.0 / ((double)d.fs * nsub);
@@ -742,44 +865,76 @@ __device__ void errors64(const float* pf, const DevSac& d, const float* y, doubl
   if (!(tau >= 0.0)) tau = 0.0;
   if (tau > 1.0e9) tau = 1.0e9;
   const double fl = floor(tau);
-  const long long J = (long long)fl;
   const double frac = tau - fl;
-  double s[6], fa0, fn0, faf, fnf, tmp[6];
-  rest64(p, th0, s, &fa0, &fn0);
-  rest64(p, thf, tmp, &faf, &fnf);
-  const double ide_ag = 1000.0 / p[kTdeAg], iac_ant = 1000.0 / p[kTacAnt];
-  const Drive64 d0{fa0, fn0, ide_ag, iac_ant};
-  const Drive64 d1{p[kNsacAg], p[kNsacAnt], 1000.0 / p[kTacAg], 1000.0 / p[kTdeAnt]};
-  const Drive64 d2{faf, fnf, ide_ag, iac_ant};
-  double s2 = 0.0, s1 = 0.0;
-  {
-    const double e = sg * s[0] - (double)y[0];
-    s2 += e * e; s1 += fabs(e);
+  double fa0, fn0, faf, fnf;
+  step_levels64(p, th0, &fa0, &fn0);
+  step_levels64(p, thf, &faf, &fnf);
+  double s0[6], s1[6], s2[6];
+  equilibrium64(p, fa0, fn0, s0);          // rest at th0
+  equilibrium64(p, p[kNsacAg], p[kNsacAnt], s1);
+  equilibrium64(p, faf, fnf, s2);          // rest at thf
+  double s2e = 0.0, s1e = 0.0;
+  const int kend = d.onset < d.L - 1 ? d.onset : d.L - 1;
+  for (int k = 0; k <= kend; ++k) {       // at rest up to onset
+    const double e = sg * th0 - (double)y[k];
+    s2e += e * e;
+    s1e += fabs(e);
   }
-  const long long g_on = (long long)d.onset * nsub;
-  for (int k = 0; k + 1 < d.L; ++k) {
-    for (int j = 0; j < nsub; ++j) {
-      const long long rel = (long long)k * nsub + j - g_on;
-      if (rel < 0) rk4_64(c, s, d0, h);
-      else if (rel < J) rk4_64(c, s, d1, h);
-      else if (rel == J) { rk4_64(c, s, d1, frac * h); rk4_64(c, s, d2, h - frac * h); }
-      else rk4_64(c, s, d2, h);
+  const int ntot = d.L - 1 - d.onset;
+  if (ntot > 0) {
+    M6 A1, A2, Q1, Q2, P1, P2;
+    plant_matrix64(p, 1000.0 / p[kTacAg], 1000.0 / p[kTdeAnt], A1);
+    plant_matrix64(p, 1000.0 / p[kTdeAg], 1000.0 / p[kTacAnt], A2);
+    step_inc64(A1, h, Q1);
+    step_inc64(A2, h, Q2);
+    pow_inc64(Q1, nsub, P1);
+    pow_inc64(Q2, nsub, P2);
+    long long n1;
+    int jsw = 0;
+    bool sw;
+    if (fl >= (double)ntot * nsub) { n1 = ntot; sw = false; }
+    else { const long long J = (long long)fl; n1 = J / nsub; jsw = (int)(J - n1 * nsub); sw = true; }
+    double e[6];
+    for (int i = 0; i < 6; ++i) e[i] = s0[i] - s1[i];
+    int k = d.onset + 1;
+    for (long long i = 0; i < n1; ++i, ++k) {
+      apply_inc64(P1, e);
+      const double r = sg * (s1[0] + e[0]) - (double)y[k];
+      s2e += r * r;
+      s1e += fabs(r);
     }
-    const double e = sg * s[0] - (double)y[k + 1];
-    s2 += e * e; s1 += fabs(e);
+    if (sw) {
+      for (int s = 0; s < jsw; ++s) apply_inc64(Q1, e);
+      rk4_vec64(A1, frac * h, e);
+      for (int i = 0; i < 6; ++i) e[i] += s1[i] - s2[i];
+      rk4_vec64(A2, h - frac * h, e);
+      for (int s = jsw + 1; s < nsub; ++s) apply_inc64(Q2, e);
+      double r = sg * (s2[0] + e[0]) - (double)y[k];
+      s2e += r * r;
+      s1e += fabs(r);
+      ++k;
+      for (; k < d.L; ++k) {
+        apply_inc64(P2, e);
+        r = sg * (s2[0] + e[0]) - (double)y[k];
+        s2e += r * r;
+        s1e += fabs(r);
+      }
+    }
   }
-  *mse = s2 / d.L;
-  *mae = s1 / d.L;
+  *mse = s2e / d.L;
+  *mae = s1e / d.L;
 }
 
 __global__ void k_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
                            int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
-                           opmm_fit_result* out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n) return;
+                           opmm_fit_result* out, const int* list) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = list ? list[i] : i;
   int w = -1, wsimp = 0x7fffffff, evals = 0;
   float wf = INFINITY;
-  for (int u = ustart[b]; u < ustart[b] + ngroups; ++u) {
+  const int u0 = ustart ? ustart[b] : b * ngroups;   // slot-major records when no start table
+  for (int u = u0; u < u0 + ngroups; ++u) {
     const float* rec = unit_best + (size_t)u * kUnitRec;
     const float f = rec[0];
     const int s = __float_as_int(rec[1]);
@@ -807,7 +962,48 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
     r.l1_deg = INFINITY;
     r.status = 1;
   }
-  out[b] = r;
+  out[i] = r;
+}
+
+// ------------------------------------------------------------------ serving
+// Place newly admitted requests into their slots: descriptor (offset rebased
+// to the slot's trace area), trace, box centre; progress reset.
+__global__ void k_admit(const DevSac* new_sacs, const float* new_traces, const float* new_pc, const int* slots, int n,
+                        DevSac* sacs, float* traces, float* pc, int* progress, int slot_stride) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int s = slots[i];
+  DevSac d = new_sacs[i];
+  const long long src = d.off;
+  d.off = (long long)s * slot_stride;
+  const int lp = (d.L + 3) & ~3;
+  for (int k = threadIdx.x; k < lp; k += blockDim.x) traces[d.off + k] = k < d.L ? new_traces[src + k] : 0.0f;
+  if (threadIdx.x < kNumParams) pc[(size_t)s * kNumParams + threadIdx.x] = new_pc[(size_t)i * kNumParams + threadIdx.x];
+  if (threadIdx.x == 0) {
+    sacs[s] = d;
+    progress[s] = 0;
+  }
+}
+
+// Iterations done after a scheduling round.
+__global__ void k_advance(const int* slots, int n, int* progress, int iters, int T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = slots[i];
+  progress[s] = min(T, progress[s] + iters);
+}
+
+cudaError_t launch_admit(const DevSac* new_sacs, const float* new_traces, const float* new_pc, const int* slots, int n,
+                         DevSac* sacs, float* traces, float* pc, int* progress, int slot_stride, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_admit<<<n, 128, 0, st>>>(new_sacs, new_traces, new_pc, slots, n, sacs, traces, pc, progress, slot_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const int* slots, int n, int* progress, int iters, int T, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_advance<<<(n + 127) / 128, 128, 0, st>>>(slots, n, progress, iters, T);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launch wrappers
@@ -937,11 +1133,11 @@ cudaError_t launch_search(int G, const SearchParams& P, int blocks_per_sm, int n
 
 cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
                             int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
-                            opmm_fit_result* out, cudaStream_t st) {
+                            opmm_fit_result* out, cudaStream_t st, const int* list) {
   if (n <= 0) return cudaSuccess;
   // the FP64 recomputation is latency bound per thread and the FP64 pipe is
   // narrow: spread the saccades over all SMs, a few threads per block
-  k_finalize<<<(n + 7) / 8, 8, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n, out);
+  k_finalize<<<(n + 3) / 4, 4, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n, out, list);
   return cudaGetLastError();
 }
 

@@ -30,7 +30,15 @@ struct SearchParams {
   int* counter;            // work-queue head, zeroed before each launch
   float* unit_best;        // [n_units][24] results per unit
   unsigned* err;           // error bits
+  // resumable mode (serving); state == nullptr for a one-launch fit
+  const int* slot_list;    // if set, unit u is (slot_list[u / ngroups], u % ngroups)
+  int ngroups;             // simplex groups per saccade (with slot_list)
+  float* state;            // [slots][S][kStateFloats] saved simplices
+  const int* progress;     // [slots] iterations already run
+  int round_iters;         // iterations per launch
 };
+
+constexpr int kSearchStateFloats = 19 * 18 + 19 + 18 + 19 + 2;   // per saved simplex
 
 cudaError_t launch_gather(const float* const* src, const DevSac* sacs, float* dst, int n, cudaStream_t st);
 cudaError_t launch_nominal(const DevSac* sacs, int n, int pulse_mode, const float* init_opc, float* pc,
@@ -52,7 +60,11 @@ cudaError_t search_occupancy(int G, int lcap, int* blocks_per_sm);
 cudaError_t launch_search(int G, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st);
 cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
                             int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
-                            opmm_fit_result* out, cudaStream_t st);
+                            opmm_fit_result* out, cudaStream_t st, const int* list = nullptr);
+
+cudaError_t launch_admit(const DevSac* new_sacs, const float* new_traces, const float* new_pc, const int* slots, int n,
+                         DevSac* sacs, float* traces, float* pc, int* progress, int slot_stride, cudaStream_t st);
+cudaError_t launch_advance(const int* slots, int n, int* progress, int iters, int T, cudaStream_t st);
 
 constexpr int kUnitRecFloats = 24;
 

@@ -27,6 +27,7 @@ struct Status {
 };
 
 Status cuda_status(cudaError_t e, const char* what);
+void set_last_error(const std::string& msg);   // per-thread text for opmm_last_error
 bool is_device_ptr(const void* p);
 int nsub_for(float fs);
 Status check_saccade(const opmm_saccade& s, int i, bool need_duration);
@@ -75,7 +76,6 @@ struct opmm_ctx {
   int num_sms = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
-  std::string err;
   int forced_variant = -1;            // -1: autotune; else a search kernel variant
   opmm::DevBuf d_err;                 // device error word of the kernels
   opmm::DevBuf scratch[16];           // per-call scratch of the synchronous entry points

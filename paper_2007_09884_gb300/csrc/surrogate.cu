@@ -60,6 +60,7 @@ struct SurrogateState {
   DevBuf w, g, m1, m2, wb, wt;           // FP32 master, gradient, Adam moments; BF16 copies
   DevBuf cal_amp, cal_pulse;             // agonist pulse by amplitude (calibrated nominal)
   MlpBuffers buf;
+  MlpBuffers infer;                      // admission-time inference of the request loop
   // training data of one batch
   DevBuf sacs, traces, hidden, target, outoff, losses;
   int train_M = 0;
@@ -123,9 +124,8 @@ static Status refresh_copies(opmm_ctx* ctx) {
 
 // Forward pass of M rows from B.X (and B.Xt): hidden layers on the tensor
 // cores, output layer (and, with T, loss and its gradient) on CUDA cores.
-static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, const float* T, bool keep_transposes) {
+static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, const float* T, bool keep_transposes, cudaStream_t st) {
   SurrogateState& S = *ctx->surrogate;
-  cudaStream_t st = ctx->stream;
   for (int l = 0; l < kLayers; ++l) {
     GemmArgs a{};
     a.epi = kEpiBiasGelu;
@@ -178,6 +178,23 @@ static Status backward(opmm_ctx* ctx, MlpBuffers& B, int M) {
   return s;
 }
 
+// Re-centre n freshly staged requests (serving admission) on stream st.
+Status surrogate_centres(opmm_ctx* ctx, const DevSac* sacs, const float* traces, int n, float* pc, cudaStream_t st) {
+  if (!ctx->surrogate || !ctx->surrogate->ready) return Status(OPMM_EINVAL, "no surrogate");
+  MlpBuffers& B = ctx->surrogate->infer;
+  const int M = (n + kBM - 1) / kBM * kBM;
+  if (B.M < M) {
+    Status s = B.ensure(M);
+    if (!s.ok()) return s;
+    s = cuda_status(cudaMemsetAsync(B.X.ptr, 0, (size_t)M * kIn * 2, st), "clear features");
+    if (!s.ok()) return s;
+  }
+  Status s = cuda_status(featurize(sacs, traces, n, bf(B.X), nullptr, M, st), "featurize");
+  if (s.ok()) s = forward(ctx, B, M, nullptr, false, st);
+  if (s.ok()) s = cuda_status(apply_centres(f32(B.Y), n, pc, st), "centres");
+  return s;
+}
+
 void surrogate_release(opmm_ctx* ctx) {
   delete ctx->surrogate;
   ctx->surrogate = nullptr;
@@ -205,12 +222,11 @@ Status surrogate_prepare_plan(opmm_ctx* ctx, opmm_plan* p, const opmm_saccade*, 
   p->pre_search = [keep, M](opmm_plan* pl, cudaStream_t st) -> Status {
     opmm_ctx* c = pl->ctx;
     cudaStream_t saved = c->stream;
-    c->stream = st;
+    (void)saved;
     Status r = cuda_status(featurize(pl->d_sacs.as<DevSac>(), pl->d_traces.as<float>(), pl->n, bf(keep->X), nullptr, M, st),
                            "featurize");
-    if (r.ok()) r = forward(c, *keep, M, nullptr, false);
+    if (r.ok()) r = forward(c, *keep, M, nullptr, false, st);
     if (r.ok()) r = cuda_status(apply_centres(f32(keep->Y), pl->n, pl->d_pc.as<float>(), st), "centres");
-    c->stream = saved;
     return r;
   };
   return Status();
@@ -221,7 +237,8 @@ Status surrogate_prepare_plan(opmm_ctx* ctx, opmm_plan* p, const opmm_saccade*, 
 using namespace opmm;
 
 static int sfail(opmm_ctx* ctx, const Status& s) {
-  ctx->err = s.msg;
+  (void)ctx;
+  set_last_error(s.msg);
   return s.code;
 }
 
@@ -304,7 +321,7 @@ extern "C" int opmm_surrogate_grad(opmm_ctx* ctx, const float* x, const float* t
   STRY(cuda_status(cudaMemcpyAsync(B.Xt.ptr, xt.data(), xt.size() * 2, cudaMemcpyHostToDevice, st), "H2D Xt"));
   STRY(cuda_status(cudaMemcpyAsync(dt.ptr, t, (size_t)m * kOut * 4, cudaMemcpyHostToDevice, st), "H2D T"));
   STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, st), "clear error"));
-  STRY(forward(ctx, B, m, f32(dt), true));
+  STRY(forward(ctx, B, m, f32(dt), true, st));
   STRY(backward(ctx, B, m));
   std::vector<float> rl((size_t)m);
   STRY(cuda_status(cudaMemcpyAsync(rl.data(), B.rowloss.ptr, (size_t)m * 4, cudaMemcpyDeviceToHost, st), "D2H loss"));
@@ -352,7 +369,7 @@ extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch,
                                      f32(S.traces), st), "simulate"));
     STRY(cuda_status(add_noise(data_seed, base, S.sacs.as<DevSac>(), batch, f32(S.traces), 0.05f, st), "noise"));
     STRY(cuda_status(featurize(S.sacs.as<DevSac>(), f32(S.traces), batch, bf(B.X), bf(B.Xt), batch, st), "featurize"));
-    STRY(forward(ctx, B, batch, f32(S.target), true));
+    STRY(forward(ctx, B, batch, f32(S.target), true, st));
     STRY(backward(ctx, B, batch));
     S.step += 1;
     STRY(cuda_status(adamw(f32(S.w), f32(S.g), f32(S.m1), f32(S.m2), (int)kNumParams, lr, 0.9f, 0.999f, 1e-8f,
