@@ -6,7 +6,14 @@ Default workload: 1,024 synthetic saccades, 65,536 candidates x 30 iterations
 each (the plain batched-search configuration).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batch1024|uneven10k|single10]
+  python bench.py --workload surrogate   # plain vs surrogate-seeded search, 10,000 uneven saccades
+  python bench.py --workload serve       # Poisson arrivals, p50/p99 latency, plain vs seeded
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+At N=1 the default line also carries `surrogate`: the learned network trained
+on 10 M generated saccades, then saccades fitted/s at <= 0.1 deg RMS on the
+10,000-saccade uneven workload for the plain search and for the seeded search
+with plain fallback.
 
 Prints one JSON line (rank 0).  value = candidate OPC simulations per second
 over the whole job (all ranks), inputs resident in HBM; e2e = the same metric
@@ -367,6 +374,8 @@ def run_ours(args, ws, rank, local):
     }
     plan.destroy()
     plan_h.destroy()
+    if rank == 0 and ws == 1 and not args.no_surrogate and args.workload == "batch1024":
+        out["surrogate"] = surrogate_compare(G, ctx, args.quick)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
     G.opmm_destroy(ctx)
@@ -441,24 +450,134 @@ def serve_run(G, ctx, traces_desc, arrivals, fit, cfg):
             "slots": stats["slots"], "rounds": stats["rounds"]}
 
 
-def run_serve(args):
+# ------------------------------------------------------------------ learned surrogate
+# 2,441 steps of 4,096 generated saccades = 10 M training samples
+SURROGATE_SCHEDULE = [(800, 2e-3), (800, 1e-3), (500, 5e-4), (341, 2.5e-4)]
+SEEDED_FIT = dict(candidates=1024, iterations=20, box_lo=0.95, box_hi=1.05, init_step=0.025)
+# the plain search that re-fits the seeded search's misses (> 0.1 deg)
+FALLBACK_FIT = dict(candidates=4096, iterations=30)
+# forward 2 (4 512x512 + 18x512) FLOP per sample; backward twice that
+MLP_TRAIN_FLOP_PER_SAMPLE = 3 * 2 * (4 * 512 * 512 + 18 * 512)
+
+
+def train_surrogate(G, ctx, quick=False):
     import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.opmm_surrogate_init(ctx, 1)
+    base = 0
+    last = None
+    for steps, lr in (SURROGATE_SCHEDULE if not quick else [(100, 2e-3)]):
+        last = G.opmm_surrogate_train(ctx, steps, batch=4096, lr=lr, weight_decay=1e-4, data_seed=7,
+                                      sample_base=base)
+        base += steps * 4096
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"samples": base, "seconds": dt, "final_loss_mean_last_50": float(np.mean(last[-50:])),
+            "tflops_wall": base * MLP_TRAIN_FLOP_PER_SAMPLE / dt / 1e12}
+
+
+def surrogate_compare(G, ctx, quick=False):
+    """10,000 uneven saccades (250/500/1000 Hz, both directions, 1-40 deg,
+    40-400 samples): plain search at 16,384 x 30 against the surrogate-seeded
+    search at 1,024 x 20 in a +-5% box whose misses (> 0.1 deg) fall back to
+    the plain search; plus the network alone on 100,000 held-out saccades."""
+    import torch
+    training = train_surrogate(G, ctx, quick)
+    w = W.uneven10k(B=512 if quick else 10000)
+    traces, pulse = gpu_inputs(G, ctx, w)
+    batch = G.make_batch(traces, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms)
+    plain = dict(candidates=w.candidates, iterations=w.iterations, seed=w.seed, pulse_init=pulse)
+    seeded = dict(SEEDED_FIT, seed=w.seed, pulse_init=pulse)
+    warm = W.uneven10k(B=64, config_index=7)
+    wt, _ = gpu_inputs(G, ctx, warm)
+    wb = G.make_batch(wt, warm.fs, warm.onset, warm.theta0, warm.thetaf, warm.dur_ms)
+    G.opmm_fit_batch(ctx, wb, **plain)
+    G.opmm_fit_batch_seeded(ctx, wb, seeded, plain, 0.1)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    fallback = dict(FALLBACK_FIT, seed=w.seed, pulse_init=pulse)
+
+    def row(r, t, nfb=None):
+        ok = (r["rms_deg"] <= 0.1) & (r["status"] == 0)
+        out = {"seconds": t, "fitted_per_s_at_0p1deg": float(ok.sum()) / t,
+               "fraction_fitted_at_0p1deg": float(ok.mean()), "median_rms_deg": float(np.median(r["rms_deg"])),
+               "evaluations_per_saccade": float(np.mean(r["evaluations"].astype(np.float64)))}
+        if nfb is not None:
+            out["fallbacks"] = int(nfb)
+            out["kept_from_fallback"] = int(np.sum(r["source"] == G.OPMM_SOURCE_FALLBACK))
+        return out
+
+    rp, tp = timed(lambda: G.opmm_fit_batch(ctx, batch, **plain))
+    plain_row = row(rp, tp)
+    (rs, nfb), ts = timed(lambda: G.opmm_fit_batch_seeded(ctx, batch, seeded, fallback, 0.1))
+    seeded_row = row(rs, ts, nfb)
+    # the same with no fallback, with the full plain budget as fallback, and
+    # with a box of +-10% instead of +-5%
+    r1, t1 = timed(lambda: G.opmm_fit_batch(ctx, batch, use_surrogate=True, **seeded))
+    (r2, n2), t2 = timed(lambda: G.opmm_fit_batch_seeded(ctx, batch, seeded, plain, 0.1))
+    wide = dict(seeded, box_lo=0.9, box_hi=1.1, init_step=0.05)
+    (r3, n3), t3 = timed(lambda: G.opmm_fit_batch_seeded(ctx, batch, wide, fallback, 0.1))
+    variants = {"seeded_only": row(r1, t1), "seeded_full_budget_fallback": dict(row(r2, t2, n2), fallback=plain),
+                "seeded_box_10pct": dict(row(r3, t3, n3), search=wide)}
+
+    # the network alone on held-out saccades (drawn by the numpy generator;
+    # training draws its saccades on the device)
+    h = W.uneven10k(B=2000 if quick else 100000, config_index=5)
+    htr, _ = gpu_inputs(G, ctx, h)
+    hb = G.make_batch(htr, h.fs, h.onset, h.theta0, h.thetaf, h.dur_ms)
+    nominal = G.opmm_nominal_opc(ctx, hb, pulse)
+    hidden = nominal.astype(np.float64) * h.mult
+    (pred,), tpred = timed(lambda: (G.opmm_surrogate_predict(ctx, hb, pulse),))
+
+    def traj_rms(opc):
+        traj, offs = G.opmm_simulate(ctx, opc.astype(np.float32), hb)
+        return np.array([math.sqrt(np.mean((traj[offs[i]:offs[i] + len(htr[i])] - htr[i]) ** 2))
+                         for i in range(h.B)])
+
+    held = {"saccades": int(h.B), "predict_seconds": tpred,
+            "median_abs_log_error_nominal": float(np.median(np.abs(np.log(nominal / hidden)))),
+            "median_abs_log_error_surrogate": float(np.median(np.abs(np.log(pred / hidden)))),
+            "median_trace_rms_deg_nominal": float(np.median(traj_rms(nominal))),
+            "median_trace_rms_deg_surrogate": float(np.median(traj_rms(pred)))}
+    return {"workload": w.name, "saccades": int(w.B), "plain": dict(plain_row, search=plain),
+            "seeded_with_fallback": dict(seeded_row, search=seeded, fallback=fallback, fallback_rms_deg=0.1),
+            "fitted_per_s_ratio": seeded_row["fitted_per_s_at_0p1deg"] / plain_row["fitted_per_s_at_0p1deg"],
+            "variants": variants,
+            "training": training, "held_out": held}
+
+
+def run_surrogate(args):
+    import paper_2007_09884_gb300 as G
+    ctx = G.opmm_create(0)
+    cmp_ = surrogate_compare(G, ctx, args.quick)
+    G.opmm_destroy(ctx)
+    s = cmp_["seeded_with_fallback"]
+    return {"metric": "saccades fitted/s at <=0.1 deg RMS (surrogate-seeded search with plain fallback)",
+            "value": s["fitted_per_s_at_0p1deg"], "unit": "saccades/s", "n_gpus": 1, "higher_is_better": True,
+            "vs_baseline": None, "dtype": "f32 search, bf16 network", "data": "synthetic",
+            "config": {"workload": cmp_["workload"], "saccades": cmp_["saccades"],
+                       "l2": "inputs resident; one timed pass per arm"},
+            "surrogate": cmp_}
+
+
+def run_serve(args):
     import paper_2007_09884_gb300 as G
     ctx = G.opmm_create(0)
     w = W.uneven10k(B=2048, config_index=4)
     traces, pulse = gpu_inputs(G, ctx, w)
     batch = G.make_batch(traces, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms)
-    t0 = time.perf_counter()
-    G.opmm_surrogate_init(ctx, 1)
-    base = 0
-    for steps, lr in [(800, 2e-3), (800, 1e-3), (500, 5e-4), (341, 2.5e-4)]:
-        G.opmm_surrogate_train(ctx, steps, batch=4096, lr=lr, weight_decay=1e-4, data_seed=7, sample_base=base)
-        base += steps * 4096
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    training = train_surrogate(G, ctx)
+    train_s, base = training["seconds"], training["samples"]
     plain = dict(candidates=16384, iterations=30, seed=0, pulse_init=pulse)
-    seeded = dict(candidates=1024, iterations=20, seed=0, pulse_init=pulse, box_lo=0.95, box_hi=1.05,
-                  init_step=0.025, use_surrogate=True)
+    seeded = dict(SEEDED_FIT, seed=0, pulse_init=pulse, use_surrogate=True)
     rows = []
     for rate in args.rates:
         arr = W.poisson_arrivals(rate, args.serve_seconds, seed=int(rate))
@@ -548,7 +667,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch1024", choices=["batch1024", "uneven10k", "single10", "serve"])
+    ap.add_argument("--workload", default="batch1024",
+                    choices=["batch1024", "uneven10k", "single10", "serve", "surrogate"])
+    ap.add_argument("--no-surrogate", action="store_true", help="leave the surrogate comparison out of the line")
     ap.add_argument("--rates", type=float, nargs="+", default=[1000.0, 10000.0, 50000.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--serve-slots", type=int, default=4096)
@@ -563,6 +684,8 @@ def main():
         out = run_reference(args, ws, rank)
     elif args.workload == "serve":
         out = run_serve(args) if rank == 0 else None
+    elif args.workload == "surrogate":
+        out = run_surrogate(args) if rank == 0 else None
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:

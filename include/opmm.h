@@ -107,8 +107,14 @@ typedef struct {
   int32_t status;            /* 0 ok; 1 no finite candidate */
   int32_t winner;            /* index of the winning simplex */
   int32_t evaluations;       /* candidate OPC vectors simulated for this saccade */
-  int32_t reserved;
+  int32_t source;            /* OPMM_SOURCE_*: which search produced opc */
 } opmm_fit_result;
+
+enum {
+  OPMM_SOURCE_PLAIN = 0,     /* box around the given or nominal centres */
+  OPMM_SOURCE_SEEDED = 1,    /* narrowed box around the surrogate's estimate */
+  OPMM_SOURCE_FALLBACK = 2   /* plain search run after a seeded fit missed */
+};
 
 /* ------------------------------------------------------------- context */
 
@@ -245,6 +251,21 @@ int opmm_serve_stop(opmm_ctx* ctx);
  * difference) to y with OPC centre = nominal centre * exp(0.2 y).  It only
  * seeds a fit (opmm_fit_opts.use_surrogate) whose box is then narrowed; the
  * plain search is the fallback. */
+
+/* Surrogate-seeded fit with the plain search as fallback and judge: fit all n
+ * saccades with `seeded` (use_surrogate must be 1: a narrow box around the
+ * network's estimate), then fit every saccade whose seeded result has status
+ * != 0 or rms_deg > fallback_rms_deg again with `plain` (use_surrogate must be
+ * 0; its init_opc, if given, is indexed by the original saccade index).  A
+ * re-fitted saccade keeps whichever result has the lower FP64 rms_deg; its
+ * evaluations count both searches and source says which result was kept
+ * (OPMM_SOURCE_SEEDED or OPMM_SOURCE_FALLBACK).  n_fallback (nullable)
+ * receives the number of saccades re-fitted.  Host descriptors; traces host or
+ * device as for opmm_fit_batch.  Errors as for opmm_fit_batch; on error out is
+ * unspecified. */
+int opmm_fit_batch_seeded(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* seeded,
+                          const opmm_fit_opts* plain, float fallback_rms_deg, opmm_fit_result* out,
+                          int32_t* n_fallback);
 
 /* Fresh weights (uniform +-1/sqrt(512), seeded) and zeroed AdamW state; builds
  * the amplitude -> agonist-pulse table the training data uses. */

@@ -29,6 +29,7 @@ OPMM_EBUSY = -5
 OPMM_NPARAM = 18
 OPMM_MODEL_18 = 18
 OPMM_PULSE_TABLE1 = 0
+OPMM_SOURCE_PLAIN, OPMM_SOURCE_SEEDED, OPMM_SOURCE_FALLBACK = 0, 1, 2
 OPMM_PULSE_CALIBRATED = 1
 
 PARAM_NAMES = ["SE_ag", "SE_ant", "LT_ag", "LT_ant", "PE_ag", "PE_ant", "Vis", "FV_ag", "FV_ant",
@@ -86,7 +87,7 @@ class opmm_fit_result(ctypes.Structure):
     _fields_ = [("opc", ctypes.c_float * 18), ("f", ctypes.c_float),
                 ("iterations_run", ctypes.c_int32), ("rms_deg", ctypes.c_double),
                 ("l1_deg", ctypes.c_double), ("status", ctypes.c_int32), ("winner", ctypes.c_int32),
-                ("evaluations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("evaluations", ctypes.c_int32), ("source", ctypes.c_int32)]
 
 
 _lib = None
@@ -113,6 +114,9 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_simulate.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), i32, vp, i64p, vp]
     lib.opmm_score.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), vp]
     lib.opmm_nominal_opc.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
+    lib.opmm_fit_batch_seeded.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, ctypes.POINTER(opmm_fit_opts),
+                                          ctypes.POINTER(opmm_fit_opts), ctypes.c_float,
+                                          ctypes.POINTER(opmm_fit_result), ctypes.POINTER(ctypes.c_int32)]
     lib.opmm_fit_batch.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32,
                                    ctypes.POINTER(opmm_fit_opts), ctypes.POINTER(opmm_fit_result)]
     lib.opmm_plan_create.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32,
@@ -144,7 +148,7 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_serve_stats_get.argtypes = [vp, ctypes.POINTER(opmm_serve_stats)]
     lib.opmm_serve_stop.argtypes = [vp]
     for name in ["opmm_create", "opmm_set_stream", "opmm_set_search_variant", "opmm_search_variants", "opmm_simulate", "opmm_score", "opmm_nominal_opc",
-                 "opmm_fit_batch", "opmm_plan_create", "opmm_plan_execute", "opmm_plan_info",
+                 "opmm_fit_batch", "opmm_fit_batch_seeded", "opmm_plan_create", "opmm_plan_execute", "opmm_plan_info",
                  "opmm_plan_last_search_ms", "opmm_fit_saccade_static", "opmm_plan_tuning",
                  "opmm_surrogate_init", "opmm_surrogate_num_params", "opmm_surrogate_get_params",
                  "opmm_surrogate_set_params", "opmm_surrogate_grad", "opmm_surrogate_train",
@@ -253,7 +257,7 @@ def results_to_numpy(res) -> dict:
                                                      ("iterations_run", "<i4"), ("rms_deg", "<f8"),
                                                      ("l1_deg", "<f8"), ("status", "<i4"),
                                                      ("winner", "<i4"), ("evaluations", "<i4"),
-                                                     ("reserved", "<i4")]), count=n)
+                                                     ("source", "<i4")]), count=n)
     return {k: buf[k].copy() for k in buf.dtype.names}
 
 
@@ -344,6 +348,20 @@ def opmm_fit_batch(ctx, batch: SaccadeBatch, **opts) -> dict:
     res = (opmm_fit_result * len(batch))()
     _check(ctx, lib.opmm_fit_batch(ctx, descs, len(batch), ctypes.byref(o), res))
     return results_to_numpy(res)
+
+
+def opmm_fit_batch_seeded(ctx, batch: SaccadeBatch, seeded: dict, plain: dict, fallback_rms_deg=0.1):
+    """Surrogate-seeded fit; saccades it leaves above fallback_rms_deg are
+    fitted again with the plain search.  Returns (results, n_fallback)."""
+    lib = load_library()
+    so, keep_s = fit_opts(**dict(seeded, use_surrogate=True))
+    po, keep_p = fit_opts(**dict(plain, use_surrogate=False))
+    descs, keep = batch.descriptors()
+    res = (opmm_fit_result * len(batch))()
+    nfb = ctypes.c_int32(0)
+    _check(ctx, lib.opmm_fit_batch_seeded(ctx, descs, len(batch), ctypes.byref(so), ctypes.byref(po),
+                                          ctypes.c_float(fallback_rms_deg), res, ctypes.byref(nfb)))
+    return results_to_numpy(res), int(nfb.value)
 
 
 class Plan:

@@ -739,7 +739,11 @@ Status plan_run(opmm_plan* p, opmm_fit_result* out) {
   const unsigned e = *p->h_err.as<unsigned>();
   if (e & kErrWaitTimeout) return Status(OPMM_ETIMEDOUT, "a kernel's bounded TMA wait expired");
   if (e) return Status(OPMM_ECUDA, "kernel error bits " + std::to_string(e));
-  if (out) std::memcpy(out, p->h_results.ptr, sizeof(opmm_fit_result) * (size_t)p->n);
+  if (out) {
+    std::memcpy(out, p->h_results.ptr, sizeof(opmm_fit_result) * (size_t)p->n);
+    if (p->opts.use_surrogate)
+      for (int i = 0; i < p->n; ++i) out[i].source = OPMM_SOURCE_SEEDED;
+  }
   return Status();
 }
 
@@ -819,20 +823,68 @@ extern "C" void opmm_plan_destroy(opmm_plan* plan) {
   delete plan;
 }
 
+static Status fit_once(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o,
+                       opmm_fit_result* out) {
+  opmm_plan p;
+  Status s;
+  try {
+    if (o.use_surrogate) s = surrogate_prepare_plan(ctx, &p, sacs, n);
+    if (s.ok()) s = plan_build(ctx, sacs, n, o, false, false, &p);
+    if (s.ok()) s = plan_run(&p, out);
+  } catch (const std::bad_alloc&) {
+    s = Status(OPMM_ENOMEM, "host allocation failed");
+  }
+  return s;
+}
+
 extern "C" int opmm_fit_batch(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* opts,
                               opmm_fit_result* out) {
   if (!ctx) return OPMM_EINVAL;
   if (!opts || !out) return fail(ctx, Status(OPMM_EINVAL, "opmm_fit_batch: null argument"));
   TRY(ctx_bind(ctx));
-  opmm_plan p;
-  Status s;
-  try {
-    if (opts->use_surrogate) s = surrogate_prepare_plan(ctx, &p, sacs, n);
-    if (s.ok()) s = plan_build(ctx, sacs, n, *opts, false, false, &p);
-    if (s.ok()) s = plan_run(&p, out);
-  } catch (const std::bad_alloc&) {
-    s = Status(OPMM_ENOMEM, "host allocation failed");
+  TRY(fit_once(ctx, sacs, n, *opts, out));
+  return OPMM_OK;
+}
+
+extern "C" int opmm_fit_batch_seeded(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* seeded,
+                                     const opmm_fit_opts* plain, float fallback_rms_deg, opmm_fit_result* out,
+                                     int32_t* n_fallback) {
+  if (!ctx) return OPMM_EINVAL;
+  if (!seeded || !plain || !out) return fail(ctx, Status(OPMM_EINVAL, "opmm_fit_batch_seeded: null argument"));
+  if (!seeded->use_surrogate || plain->use_surrogate)
+    return fail(ctx, Status(OPMM_EINVAL, "opmm_fit_batch_seeded: seeded must use the surrogate, plain must not"));
+  if (!(fallback_rms_deg >= 0.0f)) return fail(ctx, Status(OPMM_EINVAL, "opmm_fit_batch_seeded: fallback_rms_deg < 0"));
+  if (n_fallback) *n_fallback = 0;
+  TRY(ctx_bind(ctx));
+  TRY(fit_once(ctx, sacs, n, *seeded, out));
+  // saccades the seeded search did not fit well enough go to the plain search
+  std::vector<int> miss;
+  for (int i = 0; i < n; ++i)
+    if (out[i].status != 0 || !(out[i].rms_deg <= (double)fallback_rms_deg)) miss.push_back(i);
+  if (n_fallback) *n_fallback = (int32_t)miss.size();
+  if (miss.empty()) return OPMM_OK;
+  const size_t m = miss.size();
+  std::vector<opmm_saccade> sub(m);
+  std::vector<float> sub_pc;
+  for (size_t j = 0; j < m; ++j) sub[j] = sacs[miss[j]];
+  opmm_fit_opts po = *plain;
+  if (plain->init_opc) {
+    sub_pc.resize(m * 18);
+    for (size_t j = 0; j < m; ++j)
+      std::memcpy(&sub_pc[j * 18], plain->init_opc + (size_t)miss[j] * 18, 18 * sizeof(float));
+    po.init_opc = sub_pc.data();
   }
-  if (!s.ok()) return fail(ctx, s);
+  std::vector<opmm_fit_result> fb(m);
+  TRY(fit_once(ctx, sub.data(), (int32_t)m, po, fb.data()));
+  for (size_t j = 0; j < m; ++j) {
+    opmm_fit_result& r = out[miss[j]];
+    const int32_t evals = r.evaluations + fb[j].evaluations;
+    const bool better = fb[j].status == 0 && (r.status != 0 || fb[j].rms_deg < r.rms_deg);
+    if (better) {
+      r = fb[j];
+      r.source = OPMM_SOURCE_FALLBACK;
+    }
+    r.evaluations = evals;
+  }
   return OPMM_OK;
 }

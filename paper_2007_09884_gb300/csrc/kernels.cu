@@ -950,7 +950,7 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
   r.iterations_run = __float_as_int(rec[2]);
   r.winner = wsimp;
   r.evaluations = evals;
-  r.reserved = 0;
+  r.source = OPMM_SOURCE_PLAIN;
   if (isfinite(wf)) {
     double mse, mae;
     errors64(r.opc, d, traces + d.off, &mse, &mae);

@@ -194,6 +194,7 @@ Status ServeState::round() {
       const int sl = comp[(size_t)i];
       const uint64_t tk = slot_ticket[(size_t)sl];
       done[tk] = Done{r[i], t - slot_t[(size_t)sl]};
+      if (seeded) done[tk].r.source = OPMM_SOURCE_SEEDED;
       slot_ticket[(size_t)sl] = 0;
       free_slots.push_back(sl);
     }

@@ -51,3 +51,24 @@ def to_batch(items, device=None):
 
 def centres(items):
     return np.stack([it["pn"] for it in items]).astype(np.float32)
+
+
+def _oracle_chunk(args):
+    w, idx = args
+    items = oracle_inputs(w)
+    for it, i in zip(items, idx):
+        it["i"] = int(i)
+    return items
+
+
+def oracle_inputs_parallel(w, procs=None):
+    """oracle_inputs over a whole workload in a pool of spawned processes (the
+    oracle's traces of 10,000 saccades take minutes on one core).  Spawned, so
+    that a CUDA context already open in this process is never forked."""
+    import multiprocessing as mp
+    import os
+    procs = procs or min(16, os.cpu_count() or 1)
+    chunks = [c for c in np.array_split(np.arange(w.B), procs * 4) if len(c)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        parts = pool.map(_oracle_chunk, [(w.subset(c), c) for c in chunks])
+    return [it for part in parts for it in part]

@@ -19,7 +19,7 @@ import pytest
 import oracle as O
 import paper_2007_09884_gb300 as G
 import workloads as W
-from _support import centres, f32, oracle_inputs, to_batch
+from _support import centres, f32, oracle_inputs, oracle_inputs_parallel, to_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -325,3 +325,63 @@ def test_every_search_variant_matches_oracle(ctx):
                 np.testing.assert_allclose(res["f"], base["f"], rtol=1e-4, atol=1e-7)
     finally:
         G.opmm_set_search_variant(ctx, -1)
+
+
+@pytest.mark.parametrize("name", ["batch1024", "uneven10k"])
+def test_full_size_plan_sampled_against_oracle(ctx, name):
+    """The two batched workloads at full size (1,024 saccades at 65,536
+    candidates x 30 iterations; 10,000 uneven saccades at 16,384 x 30) in the
+    launch configuration the benchmark times: one autotuned, graph-captured
+    plan over device-resident traces.  Over every saccade: status 0, the
+    winner inside its box, the evaluation count inside the budget.  For 24
+    seeded-sampled saccades the oracle recomputes the winner's FP64 error
+    (equal to 1e-9 relative), the FP32 objective agrees with it within the
+    trajectory bound, and the winner is no worse than the box centre (simplex
+    0 starts there and Nelder-Mead never loses its best vertex).  For one
+    sampled saccade the oracle runs the same estimator at the full budget
+    (same starts: the Philox counter carries the batch index) and the fitted
+    RMS agrees within 1e-3 deg."""
+    w = W.batch1024() if name == "batch1024" else W.uneven10k()
+    items = oracle_inputs_parallel(w)
+    assert [it["i"] for it in items] == list(range(w.B))
+    batch = to_batch(items, device="cuda")
+    pc = centres(items)
+    plan = G.Plan(ctx, batch, candidates=w.candidates, iterations=w.iterations, seed=w.seed, init_opc=pc)
+    res = plan.execute()
+    plan.destroy()
+    S = w.candidates // 22
+    assert np.all(res["status"] == 0)
+    ev = res["evaluations"].astype(np.int64)
+    assert np.all(ev >= S * 19) and np.all(ev <= S * (19 + 22 * w.iterations))
+    ratio = res["opc"].astype(np.float64) / pc
+    assert np.all(ratio >= 0.5 * (1 - 1e-5)) and np.all(ratio <= 2.0 * (1 + 1e-5))
+    assert np.mean(res["rms_deg"] <= 0.1) >= 0.8
+    rng = np.random.default_rng(20071)
+    for j in rng.choice(w.B, 24, replace=False):
+        it = items[j]
+        p = res["opc"][j].astype(np.float64)
+        mse, mae = O.errors(p, it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"])
+        assert res["rms_deg"][j] == pytest.approx(math.sqrt(mse), rel=1e-9)
+        assert res["l1_deg"][j] == pytest.approx(mae, rel=1e-9)
+        assert abs(res["f"][j] - mse) <= f_tol(mse), (j, res["f"][j], mse)
+        mse_c, _ = O.errors(it["pn"], it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"])
+        assert mse <= mse_c + f_tol(mse_c)
+    j = int(rng.integers(w.B))
+    it = items[j]
+    ref = O.fit(it["pn"], it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"], S, w.iterations,
+                seed=w.seed, sac_index=j)
+    assert abs(res["rms_deg"][j] - ref["rms"]) <= RMS_TOL, (j, res["rms_deg"][j], ref["rms"])
+
+
+def test_full_candidate_budget_initial_vertices_match_oracle(ctx):
+    """All 2,978 x 19 starting vertices of the 65,536-candidate budget (the
+    Philox starts across the whole counter range): with no iterations the
+    winner is the best of them, on the GPU as in the oracle."""
+    w = W.batch1024(B=3)
+    items = oracle_inputs(w)
+    S = w.candidates // 22
+    res, refs = _fit_both(ctx, items, S, 0)
+    for j in range(len(items)):
+        assert abs(res["rms_deg"][j] - refs[j]["rms"]) <= RMS_TOL
+        bf = refs[j]["best_f_all"]
+        assert bf[res["winner"][j]] - bf.min() <= f_tol(bf.min())

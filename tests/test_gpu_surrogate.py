@@ -136,3 +136,91 @@ def test_seeded_fit_stays_in_the_narrowed_box(ctx):
     assert np.all(res["status"] == 0)
     r = res["opc"] / pred
     assert np.all(r >= 0.95 * (1 - 1e-5)) and np.all(r <= 1.05 * (1 + 1e-5))
+
+
+# 10 M generated saccades: steps x rows, with a stepped learning rate
+TRAIN_SCHEDULE = [(800, 2e-3), (800, 1e-3), (500, 5e-4), (341, 2.5e-4)]
+
+
+def test_trained_surrogate_gains_over_plain_search(ctx):
+    """What the network adds to the estimator of Sec. 2.3, on held-out
+    saccades of the uneven workload (drawn by the numpy generator, never seen
+    in training, which draws on the device):
+    * its estimate alone traces the recording more closely than the nominal
+      centre it replaces;
+    * a 1,024 x 20 search in a +-5% box around it fits more saccades to
+      <= 0.1 deg RMS than the plain search with the same budget;
+    * with the plain search as fallback for its misses it fits at least as
+      many saccades as the plain full-budget search alone: with a full-budget
+      fallback at under 0.15 of the candidate simulations, with a 4,096 x 30
+      fallback at under a tenth."""
+    G.opmm_surrogate_init(ctx, 1)
+    base = 0
+    for steps, lr in TRAIN_SCHEDULE:
+        G.opmm_surrogate_train(ctx, steps, batch=4096, lr=lr, weight_decay=1e-4, data_seed=7, sample_base=base)
+        base += steps * 4096
+    items = oracle_inputs(W.uneven10k(B=400, config_index=3))
+    batch = to_batch(items)
+    pred = G.opmm_surrogate_predict(ctx, batch)
+    nominal = centres(items)
+
+    def rms_of(opc):
+        traj, offs = G.opmm_simulate(ctx, opc.astype(np.float32), batch)
+        return np.array([math.sqrt(np.mean((traj[offs[j]:offs[j] + it["L"]] - it["y"]) ** 2))
+                         for j, it in enumerate(items)])
+
+    assert np.median(rms_of(pred)) < 0.5 * np.median(rms_of(nominal))
+
+    small = dict(candidates=1024, iterations=20, seed=0)
+    seeded = dict(small, box_lo=0.95, box_hi=1.05, init_step=0.025)
+    full = dict(candidates=16384, iterations=30, seed=0)
+    r_seed = G.opmm_fit_batch(ctx, batch, use_surrogate=True, **seeded)
+    r_small = G.opmm_fit_batch(ctx, batch, **small)
+    r_full = G.opmm_fit_batch(ctx, batch, **full)
+    r_fb, n_fb = G.opmm_fit_batch_seeded(ctx, batch, seeded, full, fallback_rms_deg=0.1)
+
+    def fitted(r):
+        return float(np.mean((r["rms_deg"] <= 0.1) & (r["status"] == 0)))
+
+    f_seed, f_small, f_full, f_fb = fitted(r_seed), fitted(r_small), fitted(r_full), fitted(r_fb)
+    print(f"fitted<=0.1deg: seeded {f_seed:.3f} plain-same-budget {f_small:.3f} plain-full {f_full:.3f} "
+          f"seeded+fallback {f_fb:.3f} (fallbacks {n_fb})")
+    assert np.all(r_seed["source"] == G.OPMM_SOURCE_SEEDED) and np.all(r_small["source"] == G.OPMM_SOURCE_PLAIN)
+    assert f_seed >= f_small + 0.10
+    # the fallback re-fits exactly the misses and keeps the better result
+    miss = (r_seed["rms_deg"] > 0.1) | (r_seed["status"] != 0)
+    assert n_fb == int(miss.sum())
+    np.testing.assert_array_equal(r_fb["opc"][~miss], r_seed["opc"][~miss])
+    assert np.all(r_fb["rms_deg"][miss] <= r_seed["rms_deg"][miss])
+    assert np.all(np.isin(r_fb["source"][miss], [G.OPMM_SOURCE_SEEDED, G.OPMM_SOURCE_FALLBACK]))
+    assert f_fb >= f_full
+
+    def evals(r):
+        return float(np.sum(r["evaluations"].astype(np.float64)))
+
+    assert evals(r_fb) < 0.15 * evals(r_full), (evals(r_fb), evals(r_full))
+    light = dict(candidates=4096, iterations=30, seed=0)
+    r_lt, n_lt = G.opmm_fit_batch_seeded(ctx, batch, seeded, light, fallback_rms_deg=0.1)
+    print(f"seeded+4096x30 fallback {fitted(r_lt):.3f}")
+    assert n_lt == n_fb
+    assert fitted(r_lt) >= f_full
+    assert evals(r_lt) < 0.1 * evals(r_full), (evals(r_lt), evals(r_full))
+
+
+def test_seeded_fit_rejects_bad_option_pairs(ctx):
+    G.opmm_surrogate_init(ctx, 5)
+    batch = to_batch(oracle_inputs(W.uneven10k(B=2)))
+    lib = G.load_library()
+    so, _ = G.fit_opts(use_surrogate=False)
+    po, _ = G.fit_opts(use_surrogate=False)
+    descs, keep = batch.descriptors()
+    res = (G.opmm_fit_result * 2)()
+    import ctypes
+    nfb = ctypes.c_int32(0)
+    rc = lib.opmm_fit_batch_seeded(ctx, descs, 2, ctypes.byref(so), ctypes.byref(po), ctypes.c_float(0.1), res,
+                                   ctypes.byref(nfb))
+    assert rc == G.OPMM_EINVAL
+    so.use_surrogate = 1
+    rc = lib.opmm_fit_batch_seeded(ctx, descs, 2, ctypes.byref(so), ctypes.byref(po), ctypes.c_float(-1.0), res,
+                                   ctypes.byref(nfb))
+    assert rc == G.OPMM_EINVAL
