@@ -270,11 +270,12 @@ __global__ void k_score(const float* opc, int m, const DevSac* sac, const float*
 constexpr int kUnitRec = 24;
 constexpr int kNV = kNumParams + 1;      // vertices per simplex
 constexpr int kNT = kNumParams + 4;      // trial points per simplex and iteration
-constexpr int kSortBins = 1024;          // pulse-end time bins of the per-wave ordering
+constexpr int kSortBins = 512;           // pulse-end time bins of the per-wave ordering
 // Saved simplex (serving): vertices, values, centroid, order, active, iterations.
 constexpr int kStateFloats = kNV * kNumParams + kNV + kNumParams + kNV + 2;
 static_assert(kStateFloats == kSearchStateFloats, "saved simplex layout");
-constexpr int kHistLen = kSortBins + kSortBins / 32;   // bin b stored at b + b/32
+constexpr int kHistPer = kSortBins / 32;              // bins per lane of the scanning warp
+constexpr int kHistLen = kSortBins + 32;                // bin b stored at b + b / kHistPer
 
 template <int G>
 __host__ __device__ constexpr int search_threads() { return ((G * kNT + 31) / 32) * 32; }
@@ -372,7 +373,7 @@ __device__ __forceinline__ int switch_key(float u_pw, float pc_pw, float lnlo, f
 // Block-wide counting sort of this wave's candidates by key (key < 0: not
 // evaluated).  Afterwards S.perm[0 .. S.nvalid) lists candidate ids in key
 // order; candidate id = the thread index that computed the key.
-__device__ __forceinline__ int hist_slot(int b) { return b + (b >> 5); }
+__device__ __forceinline__ int hist_slot(int b) { return b + b / kHistPer; }
 
 // Two histogram buffers alternate between waves: the one not in use is
 // cleared during this wave's scatter, so a wave costs three block barriers.
@@ -385,24 +386,30 @@ __device__ __forceinline__ void order_wave(SearchSmem<G>& S, int key, int wave) 
   if (key >= 0) slot = atomicAdd(&h0[hist_slot(key)], 1);
   __syncthreads();
   if (tid < 32) {
-    // lane l owns bins [32 l, 32 l + 32), stored at 33 l + i: conflict-free
-    constexpr int per = kSortBins / 32;
+    // lane l owns bins [per l, per l + per), stored at hist_slot(per l + i) =
+    // (per + 1) l + i: one padding word per lane keeps the lanes on distinct
+    // banks; the counts are read once into registers
+    constexpr int per = kHistPer;
+    static_assert(per * 32 == kSortBins && (per + 1) * 31 + per <= kHistLen, "histogram layout");
     int* h = h0 + lane * (per + 1);
+    int v[per];
     int s = 0;
-#pragma unroll 8
-    for (int i = 0; i < per; ++i) s += h[i];
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+      v[i] = h[i];
+      s += v[i];
+    }
     int incl = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
+      const int x = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += x;
     }
     int run = incl - s;
-#pragma unroll 8
+#pragma unroll
     for (int i = 0; i < per; ++i) {
-      const int c = h[i];
       h[i] = run;
-      run += c;
+      run += v[i];
     }
     if (lane == 31) S.nvalid = incl;
   }
@@ -427,23 +434,26 @@ __device__ __forceinline__ int stable_rank19(float fr, int lane) {
 
 // Exit test (Sec. 2.3: every vertex within tol_x of the best in max-norm and
 // every value within tol_f of the best value) and the centroid of the best n
-// vertices for the next wave, for simplex gi, by one warp.
+// vertices for the next wave, for simplex gi, by one warp.  Lane r < 19 holds
+// the slot (my) and value (fl) of the vertex of rank r; the slots are
+// broadcast by shuffles, so the 19 vertex loads of each lane are independent.
 template <int G>
-__device__ __forceinline__ void test_and_centroid(SearchSmem<G>& S, int gi, int lane, float tolx, float tolf) {
-  const unsigned char* o = S.ord[gi];
-  bool ok = true;
-  if (lane < kNumParams) {
-    const float x1 = S.U[gi][o[0]][lane];
-    float acc = 0.0f;
-    for (int r = 0; r < kNumParams; ++r) {
-      const float x = S.U[gi][o[r]][lane];
-      acc += x;
-      if (r > 0) ok = ok && (fabsf(x - x1) <= tolx);
-    }
-    ok = ok && (fabsf(S.U[gi][o[kNumParams]][lane] - x1) <= tolx);
-    S.XB[gi][lane] = acc / (float)kNumParams;
-  }
-  if (lane >= 1 && lane < kNV) ok = ok && (fabsf(S.F[gi][o[lane]] - S.F[gi][o[0]]) <= tolf);
+__device__ __forceinline__ void test_and_centroid(SearchSmem<G>& S, int gi, int lane, float tolx, float tolf, int my,
+                                                  float fl) {
+  const int j = lane < kNumParams ? lane : 0;
+  float x[kNV];
+#pragma unroll
+  for (int r = 0; r < kNV; ++r) x[r] = S.U[gi][__shfl_sync(0xffffffffu, my, r)][j];
+  float acc = 0.0f;
+  bool okx = true;
+#pragma unroll
+  for (int r = 0; r < kNumParams; ++r) acc += x[r];
+#pragma unroll
+  for (int r = 1; r < kNV; ++r) okx = okx && (fabsf(x[r] - x[0]) <= tolx);
+  if (lane < kNumParams) S.XB[gi][lane] = acc / (float)kNumParams;
+  const float f0 = __shfl_sync(0xffffffffu, fl, 0);
+  bool ok = lane < kNumParams ? okx : true;
+  if (lane >= 1 && lane < kNV) ok = ok && (fabsf(fl - f0) <= tolf);
   const bool conv = __all_sync(0xffffffffu, ok);
   if (conv && lane == 0) S.active[gi] = 0;
 }
@@ -568,7 +578,8 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         S.iters[gi] = 0;
       }
       __syncwarp();
-      test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf);
+      const int my = lane < kNV ? (int)S.ord[gi][lane] : 0;
+      test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf, my, lane < kNV ? S.F[gi][my] : INFINITY);
     }
     __syncthreads();
 
@@ -629,11 +640,16 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       }
       __syncthreads();
 
-      // ---- Nelder-Mead decision and re-sort, one warp per simplex
+      // ---- Nelder-Mead decision and re-sort, one warp per simplex; lane r < 19
+      // holds the slot and value of the vertex of rank r
       for (int gi = warp; gi < nsim; gi += NW) {
         if (!S.active[gi]) continue;
         unsigned char* o = S.ord[gi];
-        const float f1 = S.F[gi][o[0]], fn = S.F[gi][o[kNumParams - 1]], fw = S.F[gi][o[kNumParams]];
+        int my_slot = lane < kNV ? (int)o[lane] : 0;
+        float fl = lane < kNV ? S.F[gi][my_slot] : INFINITY;
+        const float f1 = __shfl_sync(0xffffffffu, fl, 0);
+        const float fn = __shfl_sync(0xffffffffu, fl, kNumParams - 1);
+        const float fw = __shfl_sync(0xffffffffu, fl, kNumParams);
         const float fr = S.FT[gi][0], fe = S.FT[gi][1], fco = S.FT[gi][2], fci = S.FT[gi][3];
         int kind;
         float fnew = 0.0f;
@@ -646,28 +662,36 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         } else {
           if (fci < fw) { kind = 3; fnew = fci; } else kind = -1;
         }
-        // current order in registers: lane r < 19 holds the slot of rank r
-        const int my_slot = lane < kNV ? (int)o[lane] : 0;
         if (kind >= 0) {
           // replace the worst vertex; the new point goes after every vertex
           // with a value <= its own (ties stay in front of it)
           const int ws = __shfl_sync(0xffffffffu, my_slot, kNumParams);
           if (lane < kNumParams) S.U[gi][ws][lane] = S.XT[gi][kind][lane];
-          const float fr_l = lane < kNumParams ? S.F[gi][my_slot] : INFINITY;
-          const unsigned le = __ballot_sync(0xffffffffu, lane < kNumParams && fr_l <= fnew);
+          const unsigned le = __ballot_sync(0xffffffffu, lane < kNumParams && fl <= fnew);
           const int pos = __popc(le);                     // ranks 0..pos-1 keep their place
-          const int from = lane < pos ? lane : lane - 1;  // ranks above pos shift up by one
-          const int moved = __shfl_sync(0xffffffffu, my_slot, from < 0 ? 0 : from);
-          __syncwarp();
-          if (lane < kNV) o[lane] = (unsigned char)(lane < pos ? my_slot : (lane == pos ? ws : moved));
+          const int from = lane < pos ? lane : (lane > 0 ? lane - 1 : 0);  // ranks above pos shift up by one
+          const int moved = __shfl_sync(0xffffffffu, my_slot, from);
+          const float fmoved = __shfl_sync(0xffffffffu, fl, from);
+          if (lane < kNV) {
+            my_slot = lane < pos ? my_slot : (lane == pos ? ws : moved);
+            fl = lane < pos ? fl : (lane == pos ? fnew : fmoved);
+            o[lane] = (unsigned char)my_slot;
+          }
           if (lane == 0) S.F[gi][ws] = fnew;
         } else {
+          // shrink toward the best vertex: all 19 rows loaded first, then stored
+          int sr[kNV];
+#pragma unroll
+          for (int r = 0; r < kNV; ++r) sr[r] = __shfl_sync(0xffffffffu, my_slot, r);
           if (lane < kNumParams) {
-            const float x1 = S.U[gi][o[0]][lane];
-            for (int r = 1; r < kNV; ++r) S.U[gi][o[r]][lane] = shrink_coord(x1, S.U[gi][o[r]][lane]);
+            float x[kNV];
+#pragma unroll
+            for (int r = 0; r < kNV; ++r) x[r] = S.U[gi][sr[r]][lane];
+#pragma unroll
+            for (int r = 1; r < kNV; ++r) S.U[gi][sr[r]][lane] = shrink_coord(x[0], x[r]);
           }
           float fv = INFINITY;
-          if (lane == 0) fv = S.F[gi][my_slot];
+          if (lane == 0) fv = fl;
           if (lane >= 1 && lane < kNV) {
             fv = S.FT[gi][4 + lane - 1];
             S.F[gi][my_slot] = fv;
@@ -676,10 +700,13 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
           const int rank = stable_rank19(fv, lane);
           __syncwarp();
           if (lane < kNV) o[rank] = (unsigned char)my_slot;
+          __syncwarp();
+          my_slot = lane < kNV ? (int)o[lane] : 0;
+          fl = lane < kNV ? S.F[gi][my_slot] : INFINITY;
         }
         if (lane == 0) S.iters[gi] += 1;
         __syncwarp();
-        test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf);
+        test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf, my_slot, fl);
       }
       __syncthreads();
     }

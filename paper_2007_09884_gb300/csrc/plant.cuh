@@ -411,9 +411,9 @@ __device__ __forceinline__ void prop1_apply(const Prop1& q, float (&e)[6]) {
   for (int i = 0; i < 6; ++i) e[i] = n[i];
 }
 
-// e <- (I + P_phase) e for a phase-1 (PH = 1) or phase-2 (PH = 2) deviation.
-// Each row is summed as two three-term chains joined by one add: the
-// sample-to-sample dependency is four operations deep instead of six.
+// e <- (I + P_phase) e for a phase-1 (PH = 1) or phase-2 (PH = 2) deviation:
+// one fused multiply-add per matrix element, each row a single chain (the
+// search is bound by instruction issue, so no extra adds to shorten chains).
 template <int PH>
 __device__ __forceinline__ void prop_apply(const Prop2& q, float (&e)[6]) {
   const float (&c)[4][2] = PH == 1 ? q.c1 : q.c2;
@@ -424,10 +424,9 @@ __device__ __forceinline__ void prop_apply(const Prop2& q, float (&e)[6]) {
     float a = fmaf(q.m[i][0], e[0], e[i]);
     a = fmaf(q.m[i][1], e[1], a);
     a = fmaf(q.m[i][2], e[2], a);
-    float b = q.m[i][3] * e[3];
-    b = fmaf(c[i][0], e[4], b);
-    b = fmaf(c[i][1], e[5], b);
-    n[i] = a + b;
+    a = fmaf(q.m[i][3], e[3], a);
+    a = fmaf(c[i][0], e[4], a);
+    n[i] = fmaf(c[i][1], e[5], a);
   }
   n[4] = fmaf(d[0], e[4], e[4]);
   n[5] = fmaf(d[1], e[5], e[5]);
@@ -471,23 +470,93 @@ __device__ __forceinline__ bool too_stiff(const float* p, float h) {
 }
 
 // n sample intervals of one phase with the one-sample propagator, emitting
-// theta_k - thf (+ off) after each; the sink is told where each block of 4
-// samples ends (the residual sink compensates per block).
+// theta_k - thf after each: e[0] + off in the pulse phase (deviation from the
+// pulse equilibrium), e[0] itself in the step phase (PH = 2, whose equilibrium
+// is the end fixation).  The sink is told where each block of 4 samples ends
+// (the residual sink compensates per block).
 template <int PH, class Sink>
 __device__ __forceinline__ void run_samples(const Prop2& phi, float (&e)[6], float off, int& kk, int n,
                                             Sink& sink) {
   int i = 0;
+  // one block of 4 samples per trip: unrolling further only hoists trace loads
+#pragma unroll 1
   for (; i + 4 <= n; i += 4) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       prop_apply<PH>(phi, e);
-      sink.emit(kk++, e[0] + off);
+      sink.emit(kk++, PH == 2 ? e[0] : e[0] + off);
     }
     sink.block_end();
   }
   for (; i < n; ++i) {
     prop_apply<PH>(phi, e);
-    sink.emit(kk++, e[0] + off);
+    sink.emit(kk++, PH == 2 ? e[0] : e[0] + off);
+  }
+}
+
+// x <- x + y + x y (increment form of (I + x)(I + y)) in place, one block at
+// a time so that only one block of y is live: the coupling blocks first (they
+// read the old mechanical block of x), then the activation diagonals, then the
+// mechanical block row by row.  y is x itself (SQUARE: each block is copied
+// before it is overwritten) or the single-substep base in the thread's
+// shared-memory slot (element i at qs[i * stride], Prop2 order).
+template <bool SQUARE>
+__device__ __forceinline__ void prop_mul_inplace(Prop2& x, const float* qs, int stride) {
+#pragma unroll
+  for (int ph = 0; ph < 2; ++ph) {
+    float yc[4][2], yd[2];
+    const int oc = ph == 0 ? 16 : 24, od = ph == 0 ? 32 : 34;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int f = 0; f < 2; ++f) yc[i][f] = SQUARE ? (ph == 0 ? x.c1[i][f] : x.c2[i][f]) : qs[(oc + 2 * i + f) * stride];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) yd[f] = SQUARE ? (ph == 0 ? x.d1[f] : x.d2[f]) : qs[(od + f) * stride];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        const float c = ph == 0 ? x.c1[i][f] : x.c2[i][f];
+        float acc = fmaf(c, yd[f], c + yc[i][f]);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) acc = fmaf(x.m[i][kk], yc[kk][f], acc);
+        if (ph == 0) x.c1[i][f] = acc;
+        else x.c2[i][f] = acc;
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      if (ph == 0) x.d1[f] = fmaf(x.d1[f], yd[f], x.d1[f] + yd[f]);
+      else x.d2[f] = fmaf(x.d2[f], yd[f], x.d2[f] + yd[f]);
+    }
+  }
+  float ym[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ym[i][j] = SQUARE ? x.m[i][j] : qs[(4 * i + j) * stride];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float a[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) a[kk] = x.m[i][kk];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float acc = a[j] + ym[i][j];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc = fmaf(a[kk], ym[kk][j], acc);
+      x.m[i][j] = acc;
+    }
+  }
+}
+
+// x = (I + q)^n - I for n >= 1, x holding q on entry and q stored in the slot:
+// left-to-right binary powering with at most one propagator live.
+__device__ __forceinline__ void prop_pow_slot(Prop2& x, const float* qs, int stride, int n) {
+  const int msb = 31 - __clz(n);
+  for (int b = msb - 1; b >= 0; --b) {
+    prop_mul_inplace<true>(x, qs, stride);
+    if ((n >> b) & 1) prop_mul_inplace<false>(x, qs, stride);
   }
 }
 
@@ -544,10 +613,13 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
   for (int i = 0; i < 6; ++i) { e[i] = s0[i] - s1[i]; dl[i] = s1[i] - s2[i]; }
   const float off1 = s1[0] - sc.thf;
   Prop2 phi;
-  {
+  if (qs) {
+    step_increment(k, sc.h, phi);
+    prop_store(phi, qs, qstride);
+    prop_pow_slot(phi, qs, qstride, sc.nsub);
+  } else {
     Prop2 q;
     step_increment(k, sc.h, q);
-    if (qs) prop_store(q, qs, qstride);
     prop_pow(q, sc.nsub, phi);
   }
   int kk = sc.onset + 1;
