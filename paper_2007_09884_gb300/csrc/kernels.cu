@@ -10,10 +10,11 @@
 // The hot loop is k_search's candidate evaluation: one thread integrates one
 // trial OPC vector's plant in registers (plant.cuh), scoring each sample against
 // the trace staged once per block in shared memory by a TMA bulk copy, with a
-// compensated FP32 sum.  Per block, G simplices of one saccade advance together:
-// all 22 trial points of every simplex are evaluated in one wave (Sec. 2.3:
-// "all of the simplex transformations are calculated simultaneously"), then a
-// warp per simplex takes the Lagarias decision and re-sorts its vertices.
+// compensated FP32 sum.  Per block, two groups of G simplices of one saccade
+// advance in turn: all 22 trial points of every simplex of a group are
+// evaluated in one wave (Sec. 2.3: all simplex transformations are computed at
+// once), while the block's controller warp takes the Lagarias decisions of
+// the other group and orders its next wave.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -277,38 +278,63 @@ static_assert(kStateFloats == kSearchStateFloats, "saved simplex layout");
 constexpr int kHistPer = kSortBins / 32;              // bins per lane of the scanning warp
 constexpr int kHistLen = kSortBins + 32;                // bin b stored at b + b / kHistPer
 
+// One block runs G simplices in each of two groups (a unit of 2G simplices of
+// one saccade).  NE evaluation threads (11 per simplex of a group, rounded to
+// warps) evaluate the pending wave of one group while the block's last warp,
+// the controller, takes the Nelder-Mead decisions of the other group's last
+// wave and orders its next wave; the two swap at the single block barrier
+// that ends each step.
 template <int G>
-__host__ __device__ constexpr int search_threads() { return ((G * kNT + 31) / 32) * 32; }
+__host__ __device__ constexpr int search_eval_threads() { return ((G * kNT + 31) / 32) * 32; }
+template <int G>
+__host__ __device__ constexpr int search_threads() { return search_eval_threads<G>() + 32; }
 
+// State of one group of G simplices.
 template <int G>
-struct SearchSmem {
+struct GroupSmem {
   float U[G][kNV][kNumParams];   // vertices, by slot
   float XT[G][4][kNumParams];    // reflection, expansion, outside/inside contraction
   float XB[G][kNumParams];       // centroid of the best n vertices
   float F[G][kNV];               // vertex values, by slot
   float FT[G][kNT];              // trial values
-  float pc[kNumParams];          // box centre of the current saccade
-  int hist[2][kHistLen];          // counting sort by pulse-end time, double-buffered (padded)
-  unsigned short perm[search_threads<G>()];
+  int hist[kHistLen];            // counting sort of the pending wave by pulse-end time (padded)
+  unsigned short perm[G * kNT];  // candidate ids of the pending wave in key order
+  unsigned short ckey[G * kNT];  // per candidate: key, or kNoKey
+  unsigned short cslot[G * kNT]; // per candidate: rank within its bin
   unsigned char ord[G][kNV + 1]; // ord[r] = slot of rank r
   int active[G];
   int iters[G];
+  int nsim;     // simplices of this group (0: empty group)
+  int nvalid;   // candidates of the pending wave
+  int kind;     // pending wave: 0 initial vertices, 1 trial points
+  int state;    // kPending (a wave is ordered) or kDone; written by the controller only
+  int it;       // trial waves evaluated in this launch
+  int evals;    // candidate evaluations of this group
+};
+
+constexpr unsigned short kNoKey = 0xFFFFu;
+enum : int { kPending = 0, kDone = 2 };
+
+template <int G>
+struct SearchSmem {
+  GroupSmem<G> grp[2];
+  float pc[kNumParams];          // box centre of the current saccade
   SacConst sc;
   TraceStage st;
   int cur_b;
   int unit;
-  int nvalid;
+  int finished[2];               // by step parity: both groups done
   uint64_t bar;
 };
 
 constexpr int kQSlotFloats = (int)(sizeof(Prop2) / sizeof(float));
 
 // Dynamic shared memory: the block state, the raw and shifted traces (lcap
-// floats each) and one single-substep propagator slot per thread.
+// floats each) and one single-substep propagator slot per evaluation thread.
 template <int G>
 size_t search_smem_bytes(int lcap) {
   return ((sizeof(SearchSmem<G>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float) +
-         (size_t)kQSlotFloats * search_threads<G>() * sizeof(float);
+         (size_t)kQSlotFloats * search_eval_threads<G>() * sizeof(float);
 }
 
 // Trial point coordinate (Lagarias et al. coefficients rho 1, chi 2, gamma 1/2).
@@ -370,28 +396,32 @@ __device__ __forceinline__ int switch_key(float u_pw, float pc_pw, float lnlo, f
   return x >= (float)(kSortBins - 1) ? kSortBins - 1 : (int)x;
 }
 
-// Block-wide counting sort of this wave's candidates by key (key < 0: not
-// evaluated).  Afterwards S.perm[0 .. S.nvalid) lists candidate ids in key
-// order; candidate id = the thread index that computed the key.
 __device__ __forceinline__ int hist_slot(int b) { return b + b / kHistPer; }
 
-// Two histogram buffers alternate between waves: the one not in use is
-// cleared during this wave's scatter, so a wave costs three block barriers.
-template <int G>
-__device__ __forceinline__ void order_wave(SearchSmem<G>& S, int key, int wave) {
-  constexpr int NT = search_threads<G>();
-  const int tid = threadIdx.x, lane = tid & 31;
-  int* h0 = S.hist[wave & 1];
-  int slot = -1;
-  if (key >= 0) slot = atomicAdd(&h0[hist_slot(key)], 1);
-  __syncthreads();
-  if (tid < 32) {
+// Counting sort of a group's pending wave by one warp (the controller):
+// candidate c (c < ncand) gets its key from keyf(c) (negative: not evaluated);
+// afterwards g.perm[0 .. g.nvalid) lists the candidates in key order.
+template <int G, class KeyF>
+__device__ __forceinline__ void order_group(GroupSmem<G>& g, int ncand, int lane, KeyF keyf) {
+  for (int i = lane; i < kHistLen; i += 32) g.hist[i] = 0;
+  __syncwarp();
+  for (int c = lane; c < ncand; c += 32) {
+    const int key = keyf(c);
+    if (key >= 0) {
+      g.ckey[c] = (unsigned short)key;
+      g.cslot[c] = (unsigned short)atomicAdd(&g.hist[hist_slot(key)], 1);
+    } else {
+      g.ckey[c] = kNoKey;
+    }
+  }
+  __syncwarp();
+  {
     // lane l owns bins [per l, per l + per), stored at hist_slot(per l + i) =
     // (per + 1) l + i: one padding word per lane keeps the lanes on distinct
     // banks; the counts are read once into registers
     constexpr int per = kHistPer;
     static_assert(per * 32 == kSortBins && (per + 1) * 31 + per <= kHistLen, "histogram layout");
-    int* h = h0 + lane * (per + 1);
+    int* h = g.hist + lane * (per + 1);
     int v[per];
     int s = 0;
 #pragma unroll
@@ -411,73 +441,272 @@ __device__ __forceinline__ void order_wave(SearchSmem<G>& S, int key, int wave) 
       h[i] = run;
       run += v[i];
     }
-    if (lane == 31) S.nvalid = incl;
+    if (lane == 31) g.nvalid = incl;
   }
-  __syncthreads();
-  if (slot >= 0) S.perm[h0[hist_slot(key)] + slot] = (unsigned short)tid;
-  int* h1 = S.hist[(wave + 1) & 1];
-  for (int i = tid; i < kHistLen; i += NT) h1[i] = 0;
-  __syncthreads();
-}
-
-// Stable ranks of the 19 vertex values held by lanes 0..18 (lane r holds the
-// value at position r): rank = #{s : f_s < f_r or (f_s == f_r and s < r)}.
-__device__ __forceinline__ int stable_rank19(float fr, int lane) {
-  int rank = 0;
-#pragma unroll
-  for (int s = 0; s < kNV; ++s) {
-    const float fs = __shfl_sync(0xffffffffu, fr, s);
-    rank += (fs < fr || (fs == fr && s < lane)) ? 1 : 0;
+  __syncwarp();
+  for (int c = lane; c < ncand; c += 32) {
+    const int key = g.ckey[c];
+    if (key != kNoKey) g.perm[g.hist[hist_slot(key)] + g.cslot[c]] = (unsigned short)c;
   }
-  return rank;
+  __syncwarp();
 }
 
 // Exit test (Sec. 2.3: every vertex within tol_x of the best in max-norm and
 // every value within tol_f of the best value) and the centroid of the best n
-// vertices for the next wave, for simplex gi, by one warp.  Lane r < 19 holds
-// the slot (my) and value (fl) of the vertex of rank r; the slots are
-// broadcast by shuffles, so the 19 vertex loads of each lane are independent.
+// vertices, for simplex gi by one thread; sl / fv hold the slots and values
+// in rank order.
 template <int G>
-__device__ __forceinline__ void test_and_centroid(SearchSmem<G>& S, int gi, int lane, float tolx, float tolf, int my,
-                                                  float fl) {
-  const int j = lane < kNumParams ? lane : 0;
-  float x[kNV];
+__device__ __forceinline__ void test_and_centroid1(GroupSmem<G>& g, int gi, const int (&sl)[kNV],
+                                                   const float (&fv)[kNV], float tolx, float tolf) {
+  bool ok = true;
 #pragma unroll
-  for (int r = 0; r < kNV; ++r) x[r] = S.U[gi][__shfl_sync(0xffffffffu, my, r)][j];
-  float acc = 0.0f;
-  bool okx = true;
+  for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(fv[r] - fv[0]) <= tolf);
+#pragma unroll 2
+  for (int j = 0; j < kNumParams; ++j) {
+    float x[kNV];
 #pragma unroll
-  for (int r = 0; r < kNumParams; ++r) acc += x[r];
+    for (int r = 0; r < kNV; ++r) x[r] = g.U[gi][sl[r]][j];
+    float acc = 0.0f;
 #pragma unroll
-  for (int r = 1; r < kNV; ++r) okx = okx && (fabsf(x[r] - x[0]) <= tolx);
-  if (lane < kNumParams) S.XB[gi][lane] = acc / (float)kNumParams;
-  const float f0 = __shfl_sync(0xffffffffu, fl, 0);
-  bool ok = lane < kNumParams ? okx : true;
-  if (lane >= 1 && lane < kNV) ok = ok && (fabsf(fl - f0) <= tolf);
-  const bool conv = __all_sync(0xffffffffu, ok);
-  if (conv && lane == 0) S.active[gi] = 0;
+    for (int r = 0; r < kNumParams; ++r) acc += x[r];
+#pragma unroll
+    for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(x[r] - x[0]) <= tolx);
+    g.XB[gi][j] = acc / (float)kNumParams;
+  }
+  if (ok) g.active[gi] = 0;
+}
+
+// Stable ranking of 19 values by one thread: rank[r] = #{s : v_s < v_r or
+// (v_s == v_r and s < r)}; the slots are written to ord in rank order and
+// read back in rank order.
+template <int G>
+__device__ __forceinline__ void rank_simplex(GroupSmem<G>& g, int gi, int (&sl)[kNV], float (&fv)[kNV]) {
+#pragma unroll
+  for (int r = 0; r < kNV; ++r) {
+    int rank = 0;
+#pragma unroll
+    for (int t = 0; t < kNV; ++t) rank += (fv[t] < fv[r] || (fv[t] == fv[r] && t < r)) ? 1 : 0;
+    g.ord[gi][rank] = (unsigned char)sl[r];
+  }
+#pragma unroll
+  for (int r = 0; r < kNV; ++r) {
+    sl[r] = g.ord[gi][r];
+    fv[r] = g.F[gi][sl[r]];
+  }
+}
+
+// Ranking and first centroid of freshly evaluated initial simplices: one
+// lane of the controller warp per simplex.
+template <int G>
+__device__ __forceinline__ void init_rank(GroupSmem<G>& g, int lane, float tolx, float tolf) {
+  for (int gi = lane; gi < g.nsim; gi += 32) {
+    int sl[kNV];
+    float fv[kNV];
+#pragma unroll
+    for (int r = 0; r < kNV; ++r) {
+      sl[r] = r;
+      fv[r] = g.F[gi][r];
+    }
+    rank_simplex<G>(g, gi, sl, fv);
+    g.active[gi] = 1;
+    g.iters[gi] = 0;
+    test_and_centroid1<G>(g, gi, sl, fv, tolx, tolf);
+  }
+  __syncwarp();
+}
+
+// Lagarias decision and re-sort of every active simplex of a group after a
+// trial wave: one lane of the controller warp per simplex, the slots and
+// values of its 19 vertices in registers in rank order.
+template <int G>
+__device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float tolx, float tolf) {
+  for (int gi = lane; gi < g.nsim; gi += 32) {
+    if (!g.active[gi]) continue;
+    unsigned char* o = g.ord[gi];
+    int sl[kNV];
+    float fv[kNV];
+#pragma unroll
+    for (int r = 0; r < kNV; ++r) {
+      sl[r] = o[r];
+      fv[r] = g.F[gi][sl[r]];
+    }
+    const float f1 = fv[0], fn = fv[kNumParams - 1], fw = fv[kNumParams];
+    const float fr = g.FT[gi][0], fe = g.FT[gi][1], fco = g.FT[gi][2], fci = g.FT[gi][3];
+    int kind;
+    float fnew = 0.0f;
+    if (fr < f1) {
+      if (fe < fr) { kind = 1; fnew = fe; } else { kind = 0; fnew = fr; }
+    } else if (fr < fn) {
+      kind = 0; fnew = fr;
+    } else if (fr < fw) {
+      if (fco <= fr) { kind = 2; fnew = fco; } else kind = -1;
+    } else {
+      if (fci < fw) { kind = 3; fnew = fci; } else kind = -1;
+    }
+    if (kind >= 0) {
+      // replace the worst vertex; the new point goes after every vertex with
+      // a value <= its own (ties stay in front of it)
+      const int ws = sl[kNumParams];
+#pragma unroll
+      for (int j = 0; j < kNumParams; ++j) g.U[gi][ws][j] = g.XT[gi][kind][j];
+      g.F[gi][ws] = fnew;
+      int pos = 0;
+#pragma unroll
+      for (int r = 0; r < kNumParams; ++r) pos += fv[r] <= fnew ? 1 : 0;
+#pragma unroll
+      for (int r = kNumParams; r >= 1; --r)
+        if (r > pos) {
+          sl[r] = sl[r - 1];
+          fv[r] = fv[r - 1];
+        }
+#pragma unroll
+      for (int r = 0; r < kNV; ++r)
+        if (r == pos) {
+          sl[r] = ws;
+          fv[r] = fnew;
+        }
+#pragma unroll
+      for (int r = 0; r < kNV; ++r) o[r] = (unsigned char)sl[r];
+    } else {
+      // shrink toward the best vertex, then a stable sort by value
+      float x1[kNumParams];
+#pragma unroll
+      for (int j = 0; j < kNumParams; ++j) x1[j] = g.U[gi][sl[0]][j];
+#pragma unroll 1
+      for (int r = 1; r < kNV; ++r) {
+        float* row = g.U[gi][sl[r]];
+#pragma unroll
+        for (int j = 0; j < kNumParams; ++j) row[j] = shrink_coord(x1[j], row[j]);
+      }
+#pragma unroll
+      for (int r = 1; r < kNV; ++r) {
+        fv[r] = g.FT[gi][4 + r - 1];
+        g.F[gi][sl[r]] = fv[r];
+      }
+      rank_simplex<G>(g, gi, sl, fv);
+    }
+    g.iters[gi] += 1;
+    test_and_centroid1<G>(g, gi, sl, fv, tolx, tolf);
+  }
+  __syncwarp();
+}
+
+// Order a group's next wave (controller warp): the initial vertices (kind 0)
+// or the 22 trial points of every active simplex; a group with nothing left
+// to evaluate, or at its iteration cap, is done.
+template <int G>
+__device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, const SearchSmem<G>& S,
+                                          const SearchParams& P, int lane) {
+  int nact = 0;
+  if (kind == 1) {
+    for (int gi = 0; gi < g.nsim; ++gi) nact += g.active[gi];
+    if (g.it >= t_run || nact == 0) {
+      if (lane == 0) {
+        g.state = kDone;
+        g.nvalid = 0;
+      }
+      __syncwarp();
+      return;
+    }
+  }
+  const float lnlo = P.lnlo, lnhi = P.lnhi;
+  if (kind == 0) {
+    order_group<G>(g, kNV * g.nsim, lane, [&](int c) {
+      const int gi = c / kNV, v = c - gi * kNV;
+      return switch_key(g.U[gi][v][kPw], S.pc[kPw], lnlo, lnhi, S.sc);
+    });
+  } else {
+    order_group<G>(g, kNT * g.nsim, lane, [&](int c) {
+      const int gi = c / kNT, q = c - gi * kNT;
+      if (!g.active[gi]) return -1;
+      const unsigned char* o = g.ord[gi];
+      const float up = q < 4 ? trial_coord(q, g.XB[gi][kPw], g.U[gi][o[kNumParams]][kPw])
+                             : shrink_coord(g.U[gi][o[0]][kPw], g.U[gi][o[q - 3]][kPw]);
+      return switch_key(up, S.pc[kPw], lnlo, lnhi, S.sc);
+    });
+  }
+  if (lane == 0) {
+    g.kind = kind;
+    g.state = kPending;
+    if (kind == 1) g.evals += kNT * nact;
+  }
+  __syncwarp();
+}
+
+// Evaluate the pending wave of a group: evaluation thread t takes the t-th
+// candidate in key order.
+template <int G, bool LEAN>
+__device__ __forceinline__ void eval_wave(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P,
+                                          const float* z, float* qs, int tid) {
+  constexpr int NE = search_eval_threads<G>();
+  if (tid >= g.nvalid) return;
+  const SacConst& sc = S.sc;
+  const float sum0 = S.st.sum0, c0 = S.st.c0;
+  const int c = g.perm[tid];
+  if (g.kind == 0) {
+    const int gi = c / kNV, v = c - gi * kNV;
+    if (LEAN) {
+      const ULinSrc src{g.U[gi][v], g.U[gi][v], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
+      g.F[gi][v] = objective_lean(src, sc, z, sum0, c0);
+    } else {
+      float u[kNumParams];
+#pragma unroll
+      for (int j = 0; j < kNumParams; ++j) u[j] = g.U[gi][v][j];
+      g.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE);
+    }
+    return;
+  }
+  const int gi = c / kNT, q = c - gi * kNT;
+  const unsigned char* o = g.ord[gi];
+  if (LEAN) {
+    ULinSrc src;
+    if (q < 4) {
+      const int ws = o[kNumParams];
+#pragma unroll
+      for (int j = 0; j < kNumParams; ++j) g.XT[gi][q][j] = trial_coord(q, g.XB[gi][j], g.U[gi][ws][j]);
+      src = ULinSrc{g.XT[gi][q], g.XT[gi][q], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
+    } else {
+      src = ULinSrc{g.U[gi][o[0]], g.U[gi][o[q - 3]], 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
+    }
+    g.FT[gi][q] = objective_lean(src, sc, z, sum0, c0);
+  } else {
+    float u[kNumParams];
+    if (q < 4) {
+      const int ws = o[kNumParams];
+#pragma unroll
+      for (int j = 0; j < kNumParams; ++j) {
+        u[j] = trial_coord(q, g.XB[gi][j], g.U[gi][ws][j]);
+        g.XT[gi][q][j] = u[j];
+      }
+    } else {
+      const int s1 = o[0], si = o[q - 3];
+#pragma unroll
+      for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(g.U[gi][s1][j], g.U[gi][si][j]);
+    }
+    g.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE);
+  }
 }
 
 template <int G, int MINB, bool LEAN>
 __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchParams P) {
   constexpr int NT = search_threads<G>();
-  constexpr int NW = NT / 32;
+  constexpr int NE = search_eval_threads<G>();
+  constexpr int U2 = 2 * G;   // simplices per unit
   extern __shared__ __align__(128) unsigned char smraw[];
   SearchSmem<G>& S = *reinterpret_cast<SearchSmem<G>*>(smraw);
   float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G>) + 127) / 128) * 128);
   float* z = yraw + P.lcap;
   float* qslot = z + P.lcap;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool ctrl = tid >= NE;   // the controller warp
 
   if (tid == 0) {
     mbar_init(&S.bar, 1);
     fence_mbar_init();
     S.cur_b = -1;
   }
-  for (int i = tid; i < 2 * kHistLen; i += NT) (&S.hist[0][0])[i] = 0;
   __syncthreads();
   uint32_t phase = 0;
-  int wave = 0;
 
   for (;;) {
     if (tid == 0) S.unit = atomicAdd(P.counter, 1);
@@ -499,255 +728,160 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       }
       __syncthreads();
     }
-    const int nsim = min(G, P.S - g0 * G);
-    const SacConst sc = S.sc;
-    const float sum0 = S.st.sum0, c0 = S.st.c0;
+    const int nunit = min(U2, P.S - g0 * U2);   // simplices of this unit
     // resumable mode (serving): iterations already done by this saccade and
     // this launch's share; the simplex state lives in HBM between launches
     const int it0 = P.state ? P.progress[b] : 0;
     const int t_run = P.state ? min(P.round_iters, P.T - it0) : P.T;
-    float* gstate = P.state ? P.state + ((size_t)b * P.S + (size_t)g0 * G) * kStateFloats : nullptr;
-    float* rec = P.unit_best + (size_t)(P.slot_list ? b * P.ngroups + g0 : unit) * kUnitRec;
-    int evals = it0 > 0 ? __float_as_int(rec[3]) : kNV * nsim;
+    if (tid < 2) {
+      GroupSmem<G>& g = S.grp[tid];
+      g.nsim = max(0, min(G, nunit - tid * G));
+      g.it = 0;
+      g.evals = 0;
+      g.nvalid = 0;
+      g.state = g.nsim > 0 ? kPending : kDone;
+    }
     if (it0 > 0) {
       // restore the simplices: vertices, values, centroid, order, flags
-      for (int idx = tid; idx < nsim * kStateFloats; idx += NT) {
-        const int gi = idx / kStateFloats, r = idx - gi * kStateFloats;
+      const float* gstate = P.state + ((size_t)b * P.S + (size_t)g0 * U2) * kStateFloats;
+      for (int idx = tid; idx < nunit * kStateFloats; idx += NT) {
+        const int sg = idx / kStateFloats, r = idx - sg * kStateFloats;
+        GroupSmem<G>& g = S.grp[sg / G];
+        const int gi = sg % G;
         const float v = gstate[idx];
-        if (r < kNV * kNumParams) (&S.U[gi][0][0])[r] = v;
-        else if (r < kNV * kNumParams + kNV) S.F[gi][r - kNV * kNumParams] = v;
-        else if (r < kNV * kNumParams + kNV + kNumParams) S.XB[gi][r - kNV * kNumParams - kNV] = v;
-        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) S.ord[gi][r - kNV * kNumParams - kNV - kNumParams] = (unsigned char)__float_as_int(v);
-        else if (r == kStateFloats - 2) S.active[gi] = __float_as_int(v);
-        else if (r == kStateFloats - 1) S.iters[gi] = __float_as_int(v);
+        if (r < kNV * kNumParams) (&g.U[gi][0][0])[r] = v;
+        else if (r < kNV * kNumParams + kNV) g.F[gi][r - kNV * kNumParams] = v;
+        else if (r < kNV * kNumParams + kNV + kNumParams) g.XB[gi][r - kNV * kNumParams - kNV] = v;
+        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) g.ord[gi][r - kNV * kNumParams - kNV - kNumParams] = (unsigned char)__float_as_int(v);
+        else if (r == kStateFloats - 2) g.active[gi] = __float_as_int(v);
+        else if (r == kStateFloats - 1) g.iters[gi] = __float_as_int(v);
       }
-      __syncthreads();
     } else {
-
-    // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
-    if (tid < 5 * nsim) {
-      const int gi = tid / 5, blk = tid - gi * 5;
-      const int s = g0 * G + gi;
-      uint32_t r[4] = {0u, 0u, 0u, 0u};
-      if (s != 0) philox4x32_10((uint32_t)P.sac_index[b], (uint32_t)s, (uint32_t)blk, 0u, P.seed_lo, P.seed_hi, r);
+      // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
+      if (tid < 5 * nunit) {
+        const int sg = tid / 5, blk = tid - sg * 5;
+        GroupSmem<G>& g = S.grp[sg / G];
+        const int gi = sg % G;
+        const int s = g0 * U2 + sg;
+        uint32_t r[4] = {0u, 0u, 0u, 0u};
+        if (s != 0) philox4x32_10((uint32_t)P.sac_index[b], (uint32_t)s, (uint32_t)blk, 0u, P.seed_lo, P.seed_hi, r);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = 4 * blk + q;
-        if (j < kNumParams)
-          S.U[gi][0][j] = s == 0 ? 0.0f : P.lnlo + (P.lnhi - P.lnlo) * ((float)(r[q] >> 8) * (1.0f / 16777216.0f));
-      }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nsim * kNumParams * kNumParams; idx += NT) {
-      const int gi = idx / (kNumParams * kNumParams);
-      const int rem = idx - gi * kNumParams * kNumParams;
-      const int v = rem / kNumParams + 1, j = rem - (v - 1) * kNumParams;
-      float x = S.U[gi][0][j];
-      if (j == v - 1) x += P.step;
-      S.U[gi][v][j] = x;
-    }
-    __syncthreads();
-    {
-      int key = -1;
-      if (tid < kNV * nsim) {
-        const int gi = tid / kNV, v = tid - gi * kNV;
-        key = switch_key(S.U[gi][v][kPw], S.pc[kPw], P.lnlo, P.lnhi, sc);
-      }
-      order_wave<G>(S, key, wave++);
-      if (tid < S.nvalid) {
-        const int c = S.perm[tid];
-        const int gi = c / kNV, v = c - gi * kNV;
-        if (LEAN) {
-          const ULinSrc src{S.U[gi][v], S.U[gi][v], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
-          S.F[gi][v] = objective_lean(src, sc, z, sum0, c0);
-        } else {
-          float u[kNumParams];
-#pragma unroll
-          for (int j = 0; j < kNumParams; ++j) u[j] = S.U[gi][v][j];
-          S.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qslot + tid, NT);
-        }
-      }
-    }
-    __syncthreads();
-    for (int gi = warp; gi < nsim; gi += NW) {
-      const float fv = lane < kNV ? S.F[gi][lane] : INFINITY;
-      const int rank = stable_rank19(fv, lane);
-      if (lane < kNV) S.ord[gi][rank] = (unsigned char)lane;
-      if (lane == 0) {
-        S.active[gi] = 1;
-        S.iters[gi] = 0;
-      }
-      __syncwarp();
-      const int my = lane < kNV ? (int)S.ord[gi][lane] : 0;
-      test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf, my, lane < kNV ? S.F[gi][my] : INFINITY);
-    }
-    __syncthreads();
-
-    }  // initial simplices
-
-    for (int it = 0; it < t_run; ++it) {
-      int nact = 0;
-      for (int gi = 0; gi < nsim; ++gi) nact += S.active[gi];
-      if (!nact) break;
-      evals += kNT * nact;
-
-      // ---- one wave: all n + 4 trial points of every active simplex, ordered
-      // by pulse-end time
-      {
-        int key = -1;
-        if (tid < kNT * nsim) {
-          const int gi = tid / kNT, q = tid - gi * kNT;
-          if (S.active[gi]) {
-            const unsigned char* o = S.ord[gi];
-            const float up = q < 4 ? trial_coord(q, S.XB[gi][kPw], S.U[gi][o[kNumParams]][kPw])
-                                   : shrink_coord(S.U[gi][o[0]][kPw], S.U[gi][o[q - 3]][kPw]);
-            key = switch_key(up, S.pc[kPw], P.lnlo, P.lnhi, sc);
-          }
-        }
-        order_wave<G>(S, key, wave++);
-        if (tid < S.nvalid) {
-          const int c = S.perm[tid];
-          const int gi = c / kNT, q = c - gi * kNT;
-          const unsigned char* o = S.ord[gi];
-          if (LEAN) {
-            ULinSrc src;
-            if (q < 4) {
-              const int ws = o[kNumParams];
-#pragma unroll
-              for (int j = 0; j < kNumParams; ++j) S.XT[gi][q][j] = trial_coord(q, S.XB[gi][j], S.U[gi][ws][j]);
-              src = ULinSrc{S.XT[gi][q], S.XT[gi][q], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
-            } else {
-              src = ULinSrc{S.U[gi][o[0]], S.U[gi][o[q - 3]], 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
-            }
-            S.FT[gi][q] = objective_lean(src, sc, z, sum0, c0);
-          } else {
-            float u[kNumParams];
-            if (q < 4) {
-              const int ws = o[kNumParams];
-#pragma unroll
-              for (int j = 0; j < kNumParams; ++j) {
-                u[j] = trial_coord(q, S.XB[gi][j], S.U[gi][ws][j]);
-                S.XT[gi][q][j] = u[j];
-              }
-            } else {
-              const int s1 = o[0], si = o[q - 3];
-#pragma unroll
-              for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(S.U[gi][s1][j], S.U[gi][si][j]);
-            }
-            S.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qslot + tid, NT);
-          }
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * blk + q;
+          if (j < kNumParams)
+            g.U[gi][0][j] = s == 0 ? 0.0f : P.lnlo + (P.lnhi - P.lnlo) * ((float)(r[q] >> 8) * (1.0f / 16777216.0f));
         }
       }
       __syncthreads();
-
-      // ---- Nelder-Mead decision and re-sort, one warp per simplex; lane r < 19
-      // holds the slot and value of the vertex of rank r
-      for (int gi = warp; gi < nsim; gi += NW) {
-        if (!S.active[gi]) continue;
-        unsigned char* o = S.ord[gi];
-        int my_slot = lane < kNV ? (int)o[lane] : 0;
-        float fl = lane < kNV ? S.F[gi][my_slot] : INFINITY;
-        const float f1 = __shfl_sync(0xffffffffu, fl, 0);
-        const float fn = __shfl_sync(0xffffffffu, fl, kNumParams - 1);
-        const float fw = __shfl_sync(0xffffffffu, fl, kNumParams);
-        const float fr = S.FT[gi][0], fe = S.FT[gi][1], fco = S.FT[gi][2], fci = S.FT[gi][3];
-        int kind;
-        float fnew = 0.0f;
-        if (fr < f1) {
-          if (fe < fr) { kind = 1; fnew = fe; } else { kind = 0; fnew = fr; }
-        } else if (fr < fn) {
-          kind = 0; fnew = fr;
-        } else if (fr < fw) {
-          if (fco <= fr) { kind = 2; fnew = fco; } else kind = -1;
-        } else {
-          if (fci < fw) { kind = 3; fnew = fci; } else kind = -1;
-        }
-        if (kind >= 0) {
-          // replace the worst vertex; the new point goes after every vertex
-          // with a value <= its own (ties stay in front of it)
-          const int ws = __shfl_sync(0xffffffffu, my_slot, kNumParams);
-          if (lane < kNumParams) S.U[gi][ws][lane] = S.XT[gi][kind][lane];
-          const unsigned le = __ballot_sync(0xffffffffu, lane < kNumParams && fl <= fnew);
-          const int pos = __popc(le);                     // ranks 0..pos-1 keep their place
-          const int from = lane < pos ? lane : (lane > 0 ? lane - 1 : 0);  // ranks above pos shift up by one
-          const int moved = __shfl_sync(0xffffffffu, my_slot, from);
-          const float fmoved = __shfl_sync(0xffffffffu, fl, from);
-          if (lane < kNV) {
-            my_slot = lane < pos ? my_slot : (lane == pos ? ws : moved);
-            fl = lane < pos ? fl : (lane == pos ? fnew : fmoved);
-            o[lane] = (unsigned char)my_slot;
-          }
-          if (lane == 0) S.F[gi][ws] = fnew;
-        } else {
-          // shrink toward the best vertex: all 19 rows loaded first, then stored
-          int sr[kNV];
-#pragma unroll
-          for (int r = 0; r < kNV; ++r) sr[r] = __shfl_sync(0xffffffffu, my_slot, r);
-          if (lane < kNumParams) {
-            float x[kNV];
-#pragma unroll
-            for (int r = 0; r < kNV; ++r) x[r] = S.U[gi][sr[r]][lane];
-#pragma unroll
-            for (int r = 1; r < kNV; ++r) S.U[gi][sr[r]][lane] = shrink_coord(x[0], x[r]);
-          }
-          float fv = INFINITY;
-          if (lane == 0) fv = fl;
-          if (lane >= 1 && lane < kNV) {
-            fv = S.FT[gi][4 + lane - 1];
-            S.F[gi][my_slot] = fv;
-          }
-          // stable sort of [x1, xs2, ..., xs19] by value
-          const int rank = stable_rank19(fv, lane);
-          __syncwarp();
-          if (lane < kNV) o[rank] = (unsigned char)my_slot;
-          __syncwarp();
-          my_slot = lane < kNV ? (int)o[lane] : 0;
-          fl = lane < kNV ? S.F[gi][my_slot] : INFINITY;
-        }
-        if (lane == 0) S.iters[gi] += 1;
+      for (int idx = tid; idx < nunit * kNumParams * kNumParams; idx += NT) {
+        const int sg = idx / (kNumParams * kNumParams);
+        GroupSmem<G>& g = S.grp[sg / G];
+        const int gi = sg % G;
+        const int rem = idx - sg * kNumParams * kNumParams;
+        const int v = rem / kNumParams + 1, j = rem - (v - 1) * kNumParams;
+        float x = g.U[gi][0][j];
+        if (j == v - 1) x += P.step;
+        g.U[gi][v][j] = x;
+      }
+    }
+    __syncthreads();
+    // the controller orders both groups' first waves
+    if (ctrl) {
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        GroupSmem<G>& g = S.grp[h];
+        if (g.nsim == 0) continue;
+        if (it0 == 0 && lane == 0) g.evals = kNV * g.nsim;
         __syncwarp();
-        test_and_centroid<G>(S, gi, lane, P.tolx, P.tolf, my_slot, fl);
+        next_wave<G>(g, it0 > 0 ? 1 : 0, t_run, S, P, lane);
+      }
+    }
+    __syncthreads();
+
+    // ---- steps: the evaluation warps evaluate group cur's pending wave while
+    // the controller decides group 1 - cur (evaluated in the previous step)
+    // and orders its next wave.  Only the controller writes group states, so
+    // one block barrier per step suffices; the finished flag alternates
+    // between two words so that a late reader never sees the next step's.
+    int cur = 0;
+    bool decide_next = false;   // controller: the group evaluated this step is decided in the next
+#pragma unroll 1
+    for (int k = 0;; ++k) {
+      GroupSmem<G>& ge = S.grp[cur];
+      GroupSmem<G>& gd = S.grp[cur ^ 1];
+      if (!ctrl) {
+        if (ge.state == kPending) eval_wave<G, LEAN>(ge, S, P, z, qslot + tid, tid);
+      } else {
+        const bool ge_evaluated = ge.state == kPending;
+        if (decide_next) {
+          if (gd.kind == 0) {
+            init_rank<G>(gd, lane, P.tolx, P.tolf);
+          } else {
+            decide_group<G>(gd, lane, P.tolx, P.tolf);
+            if (lane == 0) gd.it += 1;
+            __syncwarp();
+          }
+          next_wave<G>(gd, 1, t_run, S, P, lane);
+        }
+        if (lane == 0) S.finished[k & 1] = (!ge_evaluated && gd.state == kDone) ? 1 : 0;
+        decide_next = ge_evaluated;
       }
       __syncthreads();
+      if (S.finished[k & 1]) break;
+      cur ^= 1;
     }
 
-    if (gstate) {
+    if (P.state) {
       // save the simplices for the next launch
-      for (int idx = tid; idx < nsim * kStateFloats; idx += NT) {
-        const int gi = idx / kStateFloats, r = idx - gi * kStateFloats;
+      float* gstate = P.state + ((size_t)b * P.S + (size_t)g0 * U2) * kStateFloats;
+      for (int idx = tid; idx < nunit * kStateFloats; idx += NT) {
+        const int sg = idx / kStateFloats, r = idx - sg * kStateFloats;
+        const GroupSmem<G>& g = S.grp[sg / G];
+        const int gi = sg % G;
         float v;
-        if (r < kNV * kNumParams) v = (&S.U[gi][0][0])[r];
-        else if (r < kNV * kNumParams + kNV) v = S.F[gi][r - kNV * kNumParams];
-        else if (r < kNV * kNumParams + kNV + kNumParams) v = S.XB[gi][r - kNV * kNumParams - kNV];
-        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) v = __int_as_float((int)S.ord[gi][r - kNV * kNumParams - kNV - kNumParams]);
-        else if (r == kStateFloats - 2) v = __int_as_float(S.active[gi]);
-        else if (r == kStateFloats - 1) v = __int_as_float(S.iters[gi]);
+        if (r < kNV * kNumParams) v = (&g.U[gi][0][0])[r];
+        else if (r < kNV * kNumParams + kNV) v = g.F[gi][r - kNV * kNumParams];
+        else if (r < kNV * kNumParams + kNV + kNumParams) v = g.XB[gi][r - kNV * kNumParams - kNV];
+        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) v = __int_as_float((int)g.ord[gi][r - kNV * kNumParams - kNV - kNumParams]);
+        else if (r == kStateFloats - 2) v = __int_as_float(g.active[gi]);
+        else if (r == kStateFloats - 1) v = __int_as_float(g.iters[gi]);
         else v = 0.0f;
         gstate[idx] = v;
       }
     }
 
     // ---- unit result: lowest value, ties to the lowest simplex index
-    if (warp == 0) {
+    if (tid < 32) {
+      float* rec = P.unit_best + (size_t)(P.slot_list ? b * P.ngroups + g0 : unit) * kUnitRec;
       float f = INFINITY;
       int best = 0x7fffffff;
-      if (lane < nsim) { f = S.F[lane][S.ord[lane][0]]; best = lane; }
+      for (int sg = lane; sg < nunit; sg += 32) {
+        const GroupSmem<G>& g = S.grp[sg / G];
+        const int gi = sg % G;
+        const float fv = g.F[gi][g.ord[gi][0]];
+        if (fv < f || (fv == f && sg < best)) { f = fv; best = sg; }
+      }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
         const float f2 = __shfl_xor_sync(0xffffffffu, f, o);
         const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
         if (f2 < f || (f2 == f && b2 < best)) { f = f2; best = b2; }
       }
-      if (best < nsim) {
-        if (lane < kNumParams) rec[4 + lane] = S.U[best][S.ord[best][0]][lane];
+      const int evals_prev = it0 > 0 ? __float_as_int(rec[3]) : 0;
+      __syncwarp();
+      if (best < nunit) {
+        const GroupSmem<G>& g = S.grp[best / G];
+        const int gi = best % G;
+        if (lane < kNumParams) rec[4 + lane] = g.U[gi][g.ord[gi][0]][lane];
         if (lane == 0) {
           rec[0] = f;
-          rec[1] = __int_as_float(g0 * G + best);
-          rec[2] = __int_as_float(S.iters[best]);
-          rec[3] = __int_as_float(evals);
+          rec[1] = __int_as_float(g0 * U2 + best);
+          rec[2] = __int_as_float(g.iters[gi]);
+          rec[3] = __int_as_float(evals_prev + S.grp[0].evals + S.grp[1].evals);
         }
       }
     }
+    __syncthreads();
   }
 }
 
@@ -1071,20 +1205,21 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
   return cudaGetLastError();
 }
 
-// Launch-shape variants of the search kernel: simplices per block G and the
-// minimum resident blocks per SM the register allocation is bounded for.
+// Launch-shape variants of the search kernel: simplices per group G (a block
+// runs a unit of 2 G simplices), the minimum resident blocks per SM the
+// register allocation is bounded for, and the register-lean walk.  The host
+// sees the unit size (simplices per block).
 struct SearchVariantDesc { int G, minb, lean; };
-static const SearchVariantDesc kVariants[] = {
-    {16, 1, 0}, {8, 2, 0}, {16, 1, 1}, {8, 2, 1}, {8, 3, 1}, {16, 2, 1}, {8, 4, 1}, {32, 1, 1}};
+static const SearchVariantDesc kVariants[] = {{16, 1, 0}, {16, 1, 1}, {8, 1, 0}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 int search_variant_count() { return kNumVariants; }
-int search_variant_g(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].G : 0; }
+int search_variant_g(int v) { return v >= 0 && v < kNumVariants ? 2 * kVariants[v].G : 0; }
 int search_variant_minb(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].minb : 0; }
 int search_variant_lean(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].lean : 0; }
-int search_variant_for_g(int G) {
+int search_variant_for_g(int unit) {
   for (int v = 0; v < kNumVariants; ++v)
-    if (kVariants[v].G == G) return v;
+    if (2 * kVariants[v].G == unit) return v;
   return -1;
 }
 
@@ -1109,13 +1244,8 @@ static cudaError_t launch_v(const SearchParams& P, int blocks_per_sm, int num_sm
 #define OPMM_VARIANT_SWITCH(v, CALL)        \
   switch (v) {                              \
     case 0: return CALL(16, 1, false);      \
-    case 1: return CALL(8, 2, false);       \
-    case 2: return CALL(16, 1, true);       \
-    case 3: return CALL(8, 2, true);        \
-    case 4: return CALL(8, 3, true);        \
-    case 5: return CALL(16, 2, true);       \
-    case 6: return CALL(8, 4, true);        \
-    case 7: return CALL(32, 1, true);       \
+    case 1: return CALL(16, 1, true);       \
+    case 2: return CALL(8, 1, false);       \
     default: return cudaErrorInvalidValue;  \
   }
 
@@ -1131,20 +1261,20 @@ cudaError_t launch_search_v(int v, const SearchParams& P, int blocks_per_sm, int
 #undef LAUNCH_CALL
 }
 
-int search_threads_for(int G) {
-  switch (G) {
-    case 8: return search_threads<8>();
-    case 16: return search_threads<16>();
-    case 32: return search_threads<32>();
+// Threads and dynamic shared memory of a block running units of `unit`
+// simplices.
+int search_threads_for(int unit) {
+  switch (unit) {
+    case 16: return search_threads<8>();
+    case 32: return search_threads<16>();
     default: return 0;
   }
 }
 
-size_t search_smem_for(int G, int lcap) {
-  switch (G) {
-    case 8: return search_smem_bytes<8>(lcap);
-    case 16: return search_smem_bytes<16>(lcap);
-    case 32: return search_smem_bytes<32>(lcap);
+size_t search_smem_for(int unit, int lcap) {
+  switch (unit) {
+    case 16: return search_smem_bytes<8>(lcap);
+    case 32: return search_smem_bytes<16>(lcap);
     default: return 0;
   }
 }

@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kStaticMaxSamples = 4096;        // longest trace accepted
 constexpr int kStaticMaxCandidates = 65536;    // largest per-iteration budget accepted
-constexpr int kStaticG = 16;                   // simplices per block
+constexpr int kStaticG = 32;                   // simplices per block (one unit)
 constexpr int kStaticMaxUnits = (kStaticMaxCandidates / 22 + kStaticG - 1) / kStaticG;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
