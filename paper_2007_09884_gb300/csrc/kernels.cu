@@ -299,11 +299,12 @@ struct GroupSmem {
   float FT[G][kNT];              // trial values
   int hist[kHistLen];            // counting sort of the pending wave by pulse-end time (padded)
   unsigned short perm[G * kNT];  // candidate ids of the pending wave in key order
-  unsigned short ckey[G * kNT];  // per candidate: key, or kNoKey
-  unsigned short cslot[G * kNT]; // per candidate: rank within its bin
   unsigned char ord[G][kNV + 1]; // ord[r] = slot of rank r
   int active[G];
   int iters[G];
+  int okf[G];   // controller scratch: value spread within tol_f
+  int okx[G];   // controller scratch: vertex spread within tol_x
+  int shr[G];   // controller scratch: the simplex shrinks this step
   int nsim;     // simplices of this group (0: empty group)
   int nvalid;   // candidates of the pending wave
   int kind;     // pending wave: 0 initial vertices, 1 trial points
@@ -312,7 +313,6 @@ struct GroupSmem {
   int evals;    // candidate evaluations of this group
 };
 
-constexpr unsigned short kNoKey = 0xFFFFu;
 enum : int { kPending = 0, kDone = 2 };
 
 template <int G>
@@ -398,27 +398,44 @@ __device__ __forceinline__ int switch_key(float u_pw, float pc_pw, float lnlo, f
 
 __device__ __forceinline__ int hist_slot(int b) { return b + b / kHistPer; }
 
-// Counting sort of a group's pending wave by one warp (the controller):
-// candidate c (c < ncand) gets its key from keyf(c) (negative: not evaluated);
-// afterwards g.perm[0 .. g.nvalid) lists the candidates in key order.
-template <int G, class KeyF>
-__device__ __forceinline__ void order_group(GroupSmem<G>& g, int ncand, int lane, KeyF keyf) {
-  for (int i = lane; i < kHistLen; i += 32) g.hist[i] = 0;
-  __syncwarp();
-  for (int c = lane; c < ncand; c += 32) {
-    const int key = keyf(c);
-    if (key >= 0) {
-      g.ckey[c] = (unsigned short)key;
-      g.cslot[c] = (unsigned short)atomicAdd(&g.hist[hist_slot(key)], 1);
+// Barrier of the evaluation threads only (the controller warp runs on).
+template <int NE>
+__device__ __forceinline__ void eval_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NE) : "memory");
+}
+
+// Counting sort of a group's due wave by pulse-end time, by the evaluation
+// threads at the start of the step that evaluates it: thread t keys candidate
+// t, one warp scans the histogram (cleared by the controller when it set the
+// wave up), and afterwards g.perm[0 .. g.nvalid) lists the candidates in key
+// order.
+template <int G>
+__device__ __forceinline__ void order_wave(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P, int tid) {
+  constexpr int NE = search_eval_threads<G>();
+  static_assert(G * kNT <= NE, "one candidate per evaluation thread");
+  const int ncand = (g.kind == 0 ? kNV : kNT) * g.nsim;
+  int key = -1, slot = 0;
+  if (tid < ncand) {
+    if (g.kind == 0) {
+      const int gi = tid / kNV, v = tid - gi * kNV;
+      key = switch_key(g.U[gi][v][kPw], S.pc[kPw], P.lnlo, P.lnhi, S.sc);
     } else {
-      g.ckey[c] = kNoKey;
+      const int gi = tid / kNT, q = tid - gi * kNT;
+      if (g.active[gi]) {
+        const unsigned char* o = g.ord[gi];
+        const float up = q < 4 ? trial_coord(q, g.XB[gi][kPw], g.U[gi][o[kNumParams]][kPw])
+                               : shrink_coord(g.U[gi][o[0]][kPw], g.U[gi][o[q - 3]][kPw]);
+        key = switch_key(up, S.pc[kPw], P.lnlo, P.lnhi, S.sc);
+      }
     }
+    if (key >= 0) slot = atomicAdd(&g.hist[hist_slot(key)], 1);
   }
-  __syncwarp();
-  {
+  eval_sync<NE>();
+  if (tid < 32) {
     // lane l owns bins [per l, per l + per), stored at hist_slot(per l + i) =
     // (per + 1) l + i: one padding word per lane keeps the lanes on distinct
     // banks; the counts are read once into registers
+    const int lane = tid;
     constexpr int per = kHistPer;
     static_assert(per * 32 == kSortBins && (per + 1) * 31 + per <= kHistLen, "histogram layout");
     int* h = g.hist + lane * (per + 1);
@@ -443,44 +460,40 @@ __device__ __forceinline__ void order_group(GroupSmem<G>& g, int ncand, int lane
     }
     if (lane == 31) g.nvalid = incl;
   }
-  __syncwarp();
-  for (int c = lane; c < ncand; c += 32) {
-    const int key = g.ckey[c];
-    if (key != kNoKey) g.perm[g.hist[hist_slot(key)] + g.cslot[c]] = (unsigned short)c;
-  }
-  __syncwarp();
+  eval_sync<NE>();
+  if (key >= 0) g.perm[g.hist[hist_slot(key)] + slot] = (unsigned short)tid;
+  eval_sync<NE>();
 }
 
-// Exit test (Sec. 2.3: every vertex within tol_x of the best in max-norm and
-// every value within tol_f of the best value) and the centroid of the best n
-// vertices, for simplex gi by one thread; sl / fv hold the slots and values
-// in rank order.
-template <int G>
-__device__ __forceinline__ void test_and_centroid1(GroupSmem<G>& g, int gi, const int (&sl)[kNV],
-                                                   const float (&fv)[kNV], float tolx, float tolf) {
-  bool ok = true;
-#pragma unroll
-  for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(fv[r] - fv[0]) <= tolf);
-#pragma unroll 2
-  for (int j = 0; j < kNumParams; ++j) {
+// Centroid of the best n vertices and the vertex-spread half of the exit test
+// (Sec. 2.3: every vertex within tol_x of the best in max-norm), spread over
+// the controller warp's lanes by (simplex, coordinate); `sel` picks the
+// simplices to process.  g.okx[gi] must be 1 on entry and is cleared by any
+// coordinate that fails.
+template <int G, class Sel>
+__device__ __forceinline__ void centroids(GroupSmem<G>& g, int lane, float tolx, Sel sel) {
+  for (int p = lane; p < g.nsim * kNumParams; p += 32) {
+    const int gi = p / kNumParams, j = p - gi * kNumParams;
+    if (!sel(gi)) continue;
+    const unsigned char* o = g.ord[gi];
     float x[kNV];
 #pragma unroll
-    for (int r = 0; r < kNV; ++r) x[r] = g.U[gi][sl[r]][j];
+    for (int r = 0; r < kNV; ++r) x[r] = g.U[gi][o[r]][j];
     float acc = 0.0f;
+    bool ok = true;
 #pragma unroll
     for (int r = 0; r < kNumParams; ++r) acc += x[r];
 #pragma unroll
     for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(x[r] - x[0]) <= tolx);
     g.XB[gi][j] = acc / (float)kNumParams;
+    if (!ok) g.okx[gi] = 0;
   }
-  if (ok) g.active[gi] = 0;
 }
 
 // Stable ranking of 19 values by one thread: rank[r] = #{s : v_s < v_r or
-// (v_s == v_r and s < r)}; the slots are written to ord in rank order and
-// read back in rank order.
+// (v_s == v_r and s < r)}; the slots are written to ord in rank order.
 template <int G>
-__device__ __forceinline__ void rank_simplex(GroupSmem<G>& g, int gi, int (&sl)[kNV], float (&fv)[kNV]) {
+__device__ __forceinline__ void rank_simplex(GroupSmem<G>& g, int gi, const int (&sl)[kNV], const float (&fv)[kNV]) {
 #pragma unroll
   for (int r = 0; r < kNV; ++r) {
     int rank = 0;
@@ -488,15 +501,20 @@ __device__ __forceinline__ void rank_simplex(GroupSmem<G>& g, int gi, int (&sl)[
     for (int t = 0; t < kNV; ++t) rank += (fv[t] < fv[r] || (fv[t] == fv[r] && t < r)) ? 1 : 0;
     g.ord[gi][rank] = (unsigned char)sl[r];
   }
-#pragma unroll
-  for (int r = 0; r < kNV; ++r) {
-    sl[r] = g.ord[gi][r];
-    fv[r] = g.F[gi][sl[r]];
-  }
 }
 
-// Ranking and first centroid of freshly evaluated initial simplices: one
-// lane of the controller warp per simplex.
+// Value spread within tol_f (the other half of the exit test) from the ranked
+// values in ord.
+template <int G>
+__device__ __forceinline__ int value_spread_ok(const GroupSmem<G>& g, int gi, float tolf) {
+  const float f0 = g.F[gi][g.ord[gi][0]];
+  bool ok = true;
+#pragma unroll
+  for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(g.F[gi][g.ord[gi][r]] - f0) <= tolf);
+  return ok ? 1 : 0;
+}
+
+// Ranking and first centroid of freshly evaluated initial simplices.
 template <int G>
 __device__ __forceinline__ void init_rank(GroupSmem<G>& g, int lane, float tolx, float tolf) {
   for (int gi = lane; gi < g.nsim; gi += 32) {
@@ -510,17 +528,26 @@ __device__ __forceinline__ void init_rank(GroupSmem<G>& g, int lane, float tolx,
     rank_simplex<G>(g, gi, sl, fv);
     g.active[gi] = 1;
     g.iters[gi] = 0;
-    test_and_centroid1<G>(g, gi, sl, fv, tolx, tolf);
+    g.okx[gi] = 1;
+    g.okf[gi] = value_spread_ok<G>(g, gi, tolf);
   }
+  __syncwarp();
+  centroids<G>(g, lane, tolx, [](int) { return true; });
+  __syncwarp();
+  for (int gi = lane; gi < g.nsim; gi += 32)
+    if (g.okx[gi] && g.okf[gi]) g.active[gi] = 0;
   __syncwarp();
 }
 
 // Lagarias decision and re-sort of every active simplex of a group after a
-// trial wave: one lane of the controller warp per simplex, the slots and
-// values of its 19 vertices in registers in rank order.
+// trial wave.  One lane per simplex takes the decision (the slots and values
+// of its 19 vertices in registers, in rank order) and applies a replacement;
+// shrinks, centroids and the vertex-spread test are spread over all lanes.
 template <int G>
 __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float tolx, float tolf) {
   for (int gi = lane; gi < g.nsim; gi += 32) {
+    g.shr[gi] = 0;
+    g.okx[gi] = 1;
     if (!g.active[gi]) continue;
     unsigned char* o = g.ord[gi];
     int sl[kNV];
@@ -543,6 +570,7 @@ __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float to
     } else {
       if (fci < fw) { kind = 3; fnew = fci; } else kind = -1;
     }
+    g.iters[gi] += 1;
     if (kind >= 0) {
       // replace the worst vertex; the new point goes after every vertex with
       // a value <= its own (ties stay in front of it)
@@ -567,36 +595,58 @@ __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float to
         }
 #pragma unroll
       for (int r = 0; r < kNV; ++r) o[r] = (unsigned char)sl[r];
+      bool okf = true;
+#pragma unroll
+      for (int r = 1; r < kNV; ++r) okf = okf && (fabsf(fv[r] - fv[0]) <= tolf);
+      g.okf[gi] = okf ? 1 : 0;
     } else {
-      // shrink toward the best vertex, then a stable sort by value
-      float x1[kNumParams];
+      // shrink toward the best vertex: the values now, the coordinates below
 #pragma unroll
-      for (int j = 0; j < kNumParams; ++j) x1[j] = g.U[gi][sl[0]][j];
-#pragma unroll 1
-      for (int r = 1; r < kNV; ++r) {
-        float* row = g.U[gi][sl[r]];
-#pragma unroll
-        for (int j = 0; j < kNumParams; ++j) row[j] = shrink_coord(x1[j], row[j]);
-      }
-#pragma unroll
-      for (int r = 1; r < kNV; ++r) {
-        fv[r] = g.FT[gi][4 + r - 1];
-        g.F[gi][sl[r]] = fv[r];
-      }
-      rank_simplex<G>(g, gi, sl, fv);
+      for (int r = 1; r < kNV; ++r) g.F[gi][sl[r]] = g.FT[gi][4 + r - 1];
+      g.shr[gi] = 1;
     }
-    g.iters[gi] += 1;
-    test_and_centroid1<G>(g, gi, sl, fv, tolx, tolf);
   }
+  __syncwarp();
+  // shrink coordinates: for each shrinking simplex, its 18 x 18 (vertex rank
+  // >= 1, coordinate) updates over the lanes (the best vertex's row is only read)
+  static_assert(G <= 32, "one ballot bit per simplex");
+  const unsigned smask = __ballot_sync(0xffffffffu, lane < g.nsim && g.shr[lane]);
+  for (unsigned m = smask; m; m &= m - 1) {
+    const int gi = __ffs(m) - 1;
+    const unsigned char* o = g.ord[gi];
+    for (int e = lane; e < kNumParams * kNumParams; e += 32) {
+      const int r = e / kNumParams + 1, j = e - (r - 1) * kNumParams;
+      g.U[gi][o[r]][j] = shrink_coord(g.U[gi][o[0]][j], g.U[gi][o[r]][j]);
+    }
+  }
+  __syncwarp();
+  // stable re-sort of the shrunk simplices
+  for (int gi = lane; gi < g.nsim; gi += 32) {
+    if (!g.shr[gi]) continue;
+    int sl[kNV];
+    float fv[kNV];
+#pragma unroll
+    for (int r = 0; r < kNV; ++r) {
+      sl[r] = g.ord[gi][r];
+      fv[r] = g.F[gi][sl[r]];
+    }
+    rank_simplex<G>(g, gi, sl, fv);
+    g.okf[gi] = value_spread_ok<G>(g, gi, tolf);
+  }
+  __syncwarp();
+  centroids<G>(g, lane, tolx, [&](int gi) { return g.active[gi] != 0; });
+  __syncwarp();
+  for (int gi = lane; gi < g.nsim; gi += 32)
+    if (g.active[gi] && g.okx[gi] && g.okf[gi]) g.active[gi] = 0;
   __syncwarp();
 }
 
-// Order a group's next wave (controller warp): the initial vertices (kind 0)
-// or the 22 trial points of every active simplex; a group with nothing left
-// to evaluate, or at its iteration cap, is done.
+// Set up a group's next wave (controller warp): the initial vertices (kind 0)
+// or the 22 trial points of every active simplex, ordered by the evaluation
+// threads when they take it; a group with nothing left to evaluate, or at its
+// iteration cap, is done.
 template <int G>
-__device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, const SearchSmem<G>& S,
-                                          const SearchParams& P, int lane) {
+__device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, int lane) {
   int nact = 0;
   if (kind == 1) {
     for (int gi = 0; gi < g.nsim; ++gi) nact += g.active[gi];
@@ -609,22 +659,7 @@ __device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, 
       return;
     }
   }
-  const float lnlo = P.lnlo, lnhi = P.lnhi;
-  if (kind == 0) {
-    order_group<G>(g, kNV * g.nsim, lane, [&](int c) {
-      const int gi = c / kNV, v = c - gi * kNV;
-      return switch_key(g.U[gi][v][kPw], S.pc[kPw], lnlo, lnhi, S.sc);
-    });
-  } else {
-    order_group<G>(g, kNT * g.nsim, lane, [&](int c) {
-      const int gi = c / kNT, q = c - gi * kNT;
-      if (!g.active[gi]) return -1;
-      const unsigned char* o = g.ord[gi];
-      const float up = q < 4 ? trial_coord(q, g.XB[gi][kPw], g.U[gi][o[kNumParams]][kPw])
-                             : shrink_coord(g.U[gi][o[0]][kPw], g.U[gi][o[q - 3]][kPw]);
-      return switch_key(up, S.pc[kPw], lnlo, lnhi, S.sc);
-    });
-  }
+  for (int i = lane; i < kHistLen; i += 32) g.hist[i] = 0;
   if (lane == 0) {
     g.kind = kind;
     g.state = kPending;
@@ -785,7 +820,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       }
     }
     __syncthreads();
-    // the controller orders both groups' first waves
+    // the controller sets up both groups' first waves
     if (ctrl) {
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
@@ -793,14 +828,14 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         if (g.nsim == 0) continue;
         if (it0 == 0 && lane == 0) g.evals = kNV * g.nsim;
         __syncwarp();
-        next_wave<G>(g, it0 > 0 ? 1 : 0, t_run, S, P, lane);
+        next_wave<G>(g, it0 > 0 ? 1 : 0, t_run, lane);
       }
     }
     __syncthreads();
 
-    // ---- steps: the evaluation warps evaluate group cur's pending wave while
-    // the controller decides group 1 - cur (evaluated in the previous step)
-    // and orders its next wave.  Only the controller writes group states, so
+    // ---- steps: the evaluation warps order and evaluate group cur's pending
+    // wave while the controller decides group 1 - cur (evaluated in the
+    // previous step) and sets up its next wave.  Only the controller writes group states, so
     // one block barrier per step suffices; the finished flag alternates
     // between two words so that a late reader never sees the next step's.
     int cur = 0;
@@ -810,7 +845,10 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       GroupSmem<G>& ge = S.grp[cur];
       GroupSmem<G>& gd = S.grp[cur ^ 1];
       if (!ctrl) {
-        if (ge.state == kPending) eval_wave<G, LEAN>(ge, S, P, z, qslot + tid, tid);
+        if (ge.state == kPending) {
+          order_wave<G>(ge, S, P, tid);
+          eval_wave<G, LEAN>(ge, S, P, z, qslot + tid, tid);
+        }
       } else {
         const bool ge_evaluated = ge.state == kPending;
         if (decide_next) {
@@ -821,7 +859,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
             if (lane == 0) gd.it += 1;
             __syncwarp();
           }
-          next_wave<G>(gd, 1, t_run, S, P, lane);
+          next_wave<G>(gd, 1, t_run, lane);
         }
         if (lane == 0) S.finished[k & 1] = (!ge_evaluated && gd.state == kDone) ? 1 : 0;
         decide_next = ge_evaluated;
