@@ -582,6 +582,8 @@ Status build_units(opmm_plan* p, int G) {
   if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "stage units");
   p->params.units = p->d_units.as<int2>();
   p->params.n_units = p->n_units;
+  p->params.ngroups = p->ngroups;
+  p->params.balanced = 0;
   p->params.unit_best = p->d_unit_best.as<float>();
   return s;
 }

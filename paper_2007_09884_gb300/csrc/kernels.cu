@@ -726,7 +726,6 @@ template <int G, int MINB, bool LEAN>
 __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchParams P) {
   constexpr int NT = search_threads<G>();
   constexpr int NE = search_eval_threads<G>();
-  constexpr int U2 = 2 * G;   // simplices per unit
   extern __shared__ __align__(128) unsigned char smraw[];
   SearchSmem<G>& S = *reinterpret_cast<SearchSmem<G>*>(smraw);
   float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G>) + 127) / 128) * 128);
@@ -763,14 +762,26 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       }
       __syncthreads();
     }
-    const int nunit = min(U2, P.S - g0 * U2);   // simplices of this unit
+    // this unit's simplices: units of 2 G (the last takes the rest), or, with
+    // P.balanced, the saccade's S simplices split evenly over its P.ngroups
+    // units; group 0 holds the unit's first nA
+    int s0, nunit, nA;
+    if (P.balanced) {
+      s0 = (int)(((long long)g0 * P.S) / P.ngroups);
+      nunit = (int)(((long long)(g0 + 1) * P.S) / P.ngroups) - s0;   // <= 2 G
+      nA = (nunit + 1) / 2;
+    } else {
+      s0 = g0 * 2 * G;
+      nunit = min(2 * G, P.S - s0);
+      nA = min(G, nunit);
+    }
     // resumable mode (serving): iterations already done by this saccade and
     // this launch's share; the simplex state lives in HBM between launches
     const int it0 = P.state ? P.progress[b] : 0;
     const int t_run = P.state ? min(P.round_iters, P.T - it0) : P.T;
     if (tid < 2) {
       GroupSmem<G>& g = S.grp[tid];
-      g.nsim = max(0, min(G, nunit - tid * G));
+      g.nsim = tid == 0 ? nA : nunit - nA;
       g.it = 0;
       g.evals = 0;
       g.nvalid = 0;
@@ -778,11 +789,11 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     }
     if (it0 > 0) {
       // restore the simplices: vertices, values, centroid, order, flags
-      const float* gstate = P.state + ((size_t)b * P.S + (size_t)g0 * U2) * kStateFloats;
+      const float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * kStateFloats;
       for (int idx = tid; idx < nunit * kStateFloats; idx += NT) {
         const int sg = idx / kStateFloats, r = idx - sg * kStateFloats;
-        GroupSmem<G>& g = S.grp[sg / G];
-        const int gi = sg % G;
+        GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+        const int gi = sg < nA ? sg : sg - nA;
         const float v = gstate[idx];
         if (r < kNV * kNumParams) (&g.U[gi][0][0])[r] = v;
         else if (r < kNV * kNumParams + kNV) g.F[gi][r - kNV * kNumParams] = v;
@@ -795,9 +806,9 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
       if (tid < 5 * nunit) {
         const int sg = tid / 5, blk = tid - sg * 5;
-        GroupSmem<G>& g = S.grp[sg / G];
-        const int gi = sg % G;
-        const int s = g0 * U2 + sg;
+        GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+        const int gi = sg < nA ? sg : sg - nA;
+        const int s = s0 + sg;
         uint32_t r[4] = {0u, 0u, 0u, 0u};
         if (s != 0) philox4x32_10((uint32_t)P.sac_index[b], (uint32_t)s, (uint32_t)blk, 0u, P.seed_lo, P.seed_hi, r);
 #pragma unroll
@@ -810,8 +821,8 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       __syncthreads();
       for (int idx = tid; idx < nunit * kNumParams * kNumParams; idx += NT) {
         const int sg = idx / (kNumParams * kNumParams);
-        GroupSmem<G>& g = S.grp[sg / G];
-        const int gi = sg % G;
+        GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+        const int gi = sg < nA ? sg : sg - nA;
         const int rem = idx - sg * kNumParams * kNumParams;
         const int v = rem / kNumParams + 1, j = rem - (v - 1) * kNumParams;
         float x = g.U[gi][0][j];
@@ -871,11 +882,11 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
 
     if (P.state) {
       // save the simplices for the next launch
-      float* gstate = P.state + ((size_t)b * P.S + (size_t)g0 * U2) * kStateFloats;
+      float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * kStateFloats;
       for (int idx = tid; idx < nunit * kStateFloats; idx += NT) {
         const int sg = idx / kStateFloats, r = idx - sg * kStateFloats;
-        const GroupSmem<G>& g = S.grp[sg / G];
-        const int gi = sg % G;
+        const GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+        const int gi = sg < nA ? sg : sg - nA;
         float v;
         if (r < kNV * kNumParams) v = (&g.U[gi][0][0])[r];
         else if (r < kNV * kNumParams + kNV) v = g.F[gi][r - kNV * kNumParams];
@@ -894,8 +905,8 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       float f = INFINITY;
       int best = 0x7fffffff;
       for (int sg = lane; sg < nunit; sg += 32) {
-        const GroupSmem<G>& g = S.grp[sg / G];
-        const int gi = sg % G;
+        const GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+        const int gi = sg < nA ? sg : sg - nA;
         const float fv = g.F[gi][g.ord[gi][0]];
         if (fv < f || (fv == f && sg < best)) { f = fv; best = sg; }
       }
@@ -908,12 +919,12 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       const int evals_prev = it0 > 0 ? __float_as_int(rec[3]) : 0;
       __syncwarp();
       if (best < nunit) {
-        const GroupSmem<G>& g = S.grp[best / G];
-        const int gi = best % G;
+        const GroupSmem<G>& g = S.grp[best < nA ? 0 : 1];
+        const int gi = best < nA ? best : best - nA;
         if (lane < kNumParams) rec[4 + lane] = g.U[gi][g.ord[gi][0]][lane];
         if (lane == 0) {
           rec[0] = f;
-          rec[1] = __int_as_float(g0 * U2 + best);
+          rec[1] = __int_as_float(s0 + best);
           rec[2] = __int_as_float(g.iters[gi]);
           rec[3] = __int_as_float(evals_prev + S.grp[0].evals + S.grp[1].evals);
         }

@@ -32,7 +32,9 @@ struct SearchParams {
   unsigned* err;           // error bits
   // resumable mode (serving); state == nullptr for a one-launch fit
   const int* slot_list;    // if set, unit u is (slot_list[u / ngroups], u % ngroups)
-  int ngroups;             // simplex groups per saccade (with slot_list)
+  int ngroups;             // units per saccade
+  int balanced;            // 1: unit g holds simplices [g S / ngroups, (g + 1) S / ngroups) (request
+                           // loop: short searches); 0: units of 2 G simplices, the last takes the rest
   float* state;            // [slots][S][kStateFloats] saved simplices
   const int* progress;     // [slots] iterations already run
   int round_iters;         // iterations per launch

@@ -344,6 +344,7 @@ extern "C" int opmm_serve_start(opmm_ctx* ctx, const opmm_serve_opts* cfg, const
   P.unit_best = sv->unit_best.as<float>();
   P.err = sv->err.as<unsigned>();
   P.ngroups = sv->ngroups;
+  P.balanced = 1;
   P.state = sv->state.as<float>();
   P.progress = sv->progress.as<int>();
   P.round_iters = cfg->round_iters;

@@ -162,6 +162,7 @@ extern "C" int opmm_fit_saccade_static(const opmm_saccade* sac, const opmm_fit_o
   P.sac_index = reinterpret_cast<const int*>(base + kOffIndex);
   P.units = reinterpret_cast<const int2*>(base + kOffUnits);
   P.n_units = ngroups;
+  P.ngroups = ngroups;
   P.S = S;
   P.T = opts->iterations;
   P.lcap = (d.L + 3) & ~3;
