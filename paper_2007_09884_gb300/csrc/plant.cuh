@@ -413,21 +413,26 @@ __device__ __forceinline__ void prop1_apply(const Prop1& q, float (&e)[6]) {
 
 // e <- (I + P_phase) e for a phase-1 (PH = 1) or phase-2 (PH = 2) deviation:
 // one fused multiply-add per matrix element, each row a single chain (the
-// search is bound by instruction issue, so no extra adds to shorten chains).
+// search is bound by instruction issue, so no extra adds to shorten chains),
+// issued column by column so that consecutive instructions share e[j].
 template <int PH>
 __device__ __forceinline__ void prop_apply(const Prop2& q, float (&e)[6]) {
   const float (&c)[4][2] = PH == 1 ? q.c1 : q.c2;
   const float (&d)[2] = PH == 1 ? q.d1 : q.d2;
   float n[6];
+  float a0 = e[0], a1 = e[1], a2 = e[2], a3 = e[3];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    float a = fmaf(q.m[i][0], e[0], e[i]);
-    a = fmaf(q.m[i][1], e[1], a);
-    a = fmaf(q.m[i][2], e[2], a);
-    a = fmaf(q.m[i][3], e[3], a);
-    a = fmaf(c[i][0], e[4], a);
-    n[i] = fmaf(c[i][1], e[5], a);
+  for (int j = 0; j < 6; ++j) {
+    const float ej = e[j];
+    a0 = fmaf(j < 4 ? q.m[0][j] : c[0][j - 4], ej, a0);
+    a1 = fmaf(j < 4 ? q.m[1][j] : c[1][j - 4], ej, a1);
+    a2 = fmaf(j < 4 ? q.m[2][j] : c[2][j - 4], ej, a2);
+    a3 = fmaf(j < 4 ? q.m[3][j] : c[3][j - 4], ej, a3);
   }
+  n[0] = a0;
+  n[1] = a1;
+  n[2] = a2;
+  n[3] = a3;
   n[4] = fmaf(d[0], e[4], e[4]);
   n[5] = fmaf(d[1], e[5], e[5]);
 #pragma unroll
