@@ -63,8 +63,8 @@ extern "C" {
 typedef struct opmm_ctx opmm_ctx;     /* opaque, library-owned */
 typedef struct opmm_plan opmm_plan;   /* opaque, library-owned */
 
-/* One recorded saccade (Sec. 2.3 "OPMM input": an extracted saccade, 1-D
- * horizontal or vertical position).  The window holds fixation, saccade and
+/* One recorded saccade, the OPMM's input in Sec. 2.3 (a saccade extracted
+ * from the recording, 1-D horizontal or vertical position).  The window holds fixation, saccade and
  * fixation; the pulse of the neural control signal starts at
  * onset_index / sample_rate_hz. */
 typedef struct {

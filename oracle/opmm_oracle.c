@@ -103,9 +103,9 @@ int or_nsub(double fs) {
 static double ta_eq(const double* p, double th) { return p[NC_FIX] + p[NC_AG] * th; }
 static double tn_eq(const double* p, double th) { return p[NC_FIX] - p[NC_ANT] * th; }
 
-/* Active-state tension that keeps the plant at rest at angle th (step level of
- * the pulse-step signal, Sec. 2.1 "The step indicates the magnitude of the
- * neuronal control signal during a fixation"). */
+/* Active-state tension that keeps the plant at rest at angle th: the step
+ * level of the pulse-step signal, i.e. the control signal's size while the eye
+ * holds a fixation (Sec. 2.1). */
 double or_step_ag(const double* p, double th) {
   return ta_eq(p, th) * (1.0 + p[KLT_AG] / p[KSE_AG]) + p[KLT_AG] * th;
 }
