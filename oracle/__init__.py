@@ -73,6 +73,8 @@ def _load():
             lib.or_expm7.argtypes = [_dp, _dp]
             lib.or_stiff.argtypes = [_dp, _d]
             lib.or_stiff.restype = _i
+            lib.or_substeps.argtypes = [_dp, _d]
+            lib.or_substeps.restype = _i
             lib.or_errors.argtypes = [_dp, _i, _d, _i, _d, _d, _dp, _dp, _dp]
             lib.or_errors.restype = _i
             lib.or_nominal_table1.argtypes = [_d, _dp]
@@ -172,6 +174,12 @@ def simulate_exact(p, L, fs, onset, th0, thf) -> np.ndarray:
 
 def stiff(p, fs) -> bool:
     return bool(_load().or_stiff(_dptr(_f64(p)), float(fs)))
+
+
+def substeps(p, fs) -> int:
+    """RK4 substeps per sample for candidate p (the base count, doubled for
+    stiff candidates)."""
+    return int(_load().or_substeps(_dptr(_f64(p)), float(fs)))
 
 
 def errors(p, L, fs, onset, th0, thf, y):

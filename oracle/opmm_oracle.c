@@ -91,6 +91,8 @@ static double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 /* Plant model                                                               */
 /* ------------------------------------------------------------------------ */
 
+#define OR_MAX_REFINE 6   /* at most 2^6 times the base substeps per sample */
+
 /* Substeps per sample so that the RK4 step is close to 0.1 ms. */
 int or_nsub(double fs) {
   int n = (int)floor(1.0e4 / fs + 0.5);
@@ -176,6 +178,8 @@ static void rk4_step(const double* p, double* s, const drive_t* d, double h) {
     s[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
+int or_substeps(const double* p, double fs);
+
 /* Position of the pulse end in RK4 substeps after onset: index J of the
  * substep that contains it and the fraction of that substep before it. */
 static void pulse_end(const double* p, double fs, int nsub, long* J, double* frac) {
@@ -196,7 +200,7 @@ int or_simulate_rk4(const double* p, int L, double fs, int onset, double th0,
   if (L <= 0 || !(fs > 0.0)) return -1;
   int mirror = thf < th0;
   if (mirror) { th0 = -th0; thf = -thf; }
-  int nsub = or_nsub(fs);
+  int nsub = or_substeps(p, fs);
   double h = 1.0 / (fs * nsub);
   long J; double frac;
   pulse_end(p, fs, nsub, &J, &frac);
@@ -323,7 +327,7 @@ int or_simulate_exact(const double* p, int L, double fs, int onset, double th0,
   if (L <= 0 || !(fs > 0.0)) return -1;
   int mirror = thf < th0;
   if (mirror) { th0 = -th0; thf = -thf; }
-  int nsub = or_nsub(fs);
+  int nsub = or_substeps(p, fs);
   double h = 1.0 / (fs * nsub);
   long J; double frac;
   pulse_end(p, fs, nsub, &J, &frac);
@@ -357,19 +361,36 @@ int or_simulate_exact(const double* p, int L, double fs, int onset, double th0,
 /* Objective                                                                 */
 /* ------------------------------------------------------------------------ */
 
-/* Stiffness guard: RK4 is stable on the negative real axis up to |h lambda|
- * ~ 2.78.  The negated trace of the plant matrix plus the fastest activation
- * rate is used as a cheap size estimate of the fastest mode; candidates whose
- * estimate times h exceeds 2.5 score +inf.  Same rule on both sides. */
-int or_stiff(const double* p, double fs) {
-  double h = 1.0 / (fs * or_nsub(fs));
+/* Size estimate of the plant's fastest mode (s^-1): the negated trace of the
+ * mechanical block plus the fastest activation rate. */
+static double stiff_est(const double* p) {
   double tmin = p[TAC_AG];
   if (p[TAC_ANT] < tmin) tmin = p[TAC_ANT];
   if (p[TDE_AG] < tmin) tmin = p[TDE_AG];
   if (p[TDE_ANT] < tmin) tmin = p[TDE_ANT];
-  double est = p[BP] / p[JIN] + (p[KSE_AG] + p[KLT_AG]) / p[B_AG] +
-               (p[KSE_ANT] + p[KLT_ANT]) / p[B_ANT] + 1000.0 / tmin;
-  return !(h * est <= 2.5);
+  return p[BP] / p[JIN] + (p[KSE_AG] + p[KLT_AG]) / p[B_AG] + (p[KSE_ANT] + p[KLT_ANT]) / p[B_ANT] + 1000.0 / tmin;
+}
+
+/* RK4 is stable on the negative real axis up to |h lambda| ~ 2.78.  Substeps
+ * per sample for candidate p: the base count (h ~ 0.1 ms) doubled until h
+ * times the estimate is at most 2.5, at most OR_MAX_REFINE times (stiff
+ * corners of a wide search box, Fig. 4's 10x and 0.1x values). */
+int or_substeps(const double* p, double fs) {
+  int n = or_nsub(fs);
+  double h = 1.0 / (fs * n);
+  const double est = stiff_est(p);
+  for (int k = 0; k < OR_MAX_REFINE && !(h * est <= 2.5); ++k) {
+    h *= 0.5;
+    n *= 2;
+  }
+  return n;
+}
+
+/* Stiffness guard: a candidate whose fastest mode is too fast even for the
+ * finest substep scores +inf.  Same rule on both sides. */
+int or_stiff(const double* p, double fs) {
+  double h = 1.0 / (fs * or_substeps(p, fs));
+  return !(h * stiff_est(p) <= 2.5);
 }
 
 /* Mean squared error and mean absolute error of the RK4 trajectory against

@@ -366,7 +366,7 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
     src.load(p);
     Coef k;
     make_coef(p, k);
-    if (too_stiff_coef(k, sc.h)) return INFINITY;
+    if (refine_shift(k, sc.h) < 0) return INFINITY;
   }
   KahanSink s{z, sum0, c0, 0.0f};
   walk_lean(src, sc, s);
@@ -1069,8 +1069,16 @@ __device__ void errors64(const float* pf, const DevSac& d, const float* y, doubl
   double p[kNumParams];
   for (int j = 0; j < kNumParams; ++j) p[j] = (double)pf[j];
   const double th0 = d.th0, thf = d.thf, sg = d.sign;
-  const int nsub = d.nsub;
-  const double h = 1.0 / ((double)d.fs * nsub);
+  // substeps refined for stiff candidates, the oracle's rule in double
+  const double tmin = fmin(fmin(p[kTacAg], p[kTacAnt]), fmin(p[kTdeAg], p[kTdeAnt]));
+  const double est = p[kBp] / p[kJ] + (p[kSeAg] + p[kLtAg]) / p[kBAg] + (p[kSeAnt] + p[kLtAnt]) / p[kBAnt] +
+                     1000.0 / tmin;
+  int nsub = d.nsub;
+  double h = 1.0 / ((double)d.fs * nsub);
+  for (int r = 0; r < kMaxRefine && !(h * est <= 2.5); ++r) {
+    h *= 0.5;
+    nsub *= 2;
+  }
   double tau = p[kPw] * (double)d.fs * (double)nsub / 1000.0;
   if (!(tau >= 0.0)) tau = 0.0;
   if (tau > 1.0e9) tau = 1.0e9;

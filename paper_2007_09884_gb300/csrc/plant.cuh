@@ -90,12 +90,35 @@ __device__ __forceinline__ void make_coef(const float* p, Coef& k) {
   k.iKn = 1.0f / p[kSeAnt];
 }
 
-// Stiffness guard from the coefficients (no divisions): h (B_P/J +
-// (K_SE_AG + K_LT_AG)/B_AG + (K_SE_ANT + K_LT_ANT)/B_ANT + 1/tau_min) <= 2.5.
-__device__ __forceinline__ bool too_stiff_coef(const Coef& k, float h) {
+// Substep refinement for stiff candidates.  RK4 is stable on the negative
+// real axis up to |h lambda| ~ 2.78; the size of the fastest mode is estimated
+// from the coefficients (no divisions) as est = B_P/J + (K_SE_AG + K_LT_AG)/B_AG
+// + (K_SE_ANT + K_LT_ANT)/B_ANT + 1/tau_min.  The base step h (~0.1 ms) is
+// halved until h est <= 2.5, at most kMaxRefine times; returns the number of
+// halvings, or -1 when even the finest step is too large (the candidate then
+// scores +inf).
+constexpr int kMaxRefine = 6;
+
+__device__ __forceinline__ int refine_shift(const Coef& k, float h) {
   const float rate = fmaxf(fmaxf(-k.da1, -k.dn1), fmaxf(-k.da2, -k.dn2));
   const float est = -(k.m11 + k.m22 + k.m33) + rate;
-  return !(h * est <= 2.5f);
+  int s = 0;
+  while (s < kMaxRefine && !(h * est <= 2.5f)) {
+    h *= 0.5f;
+    ++s;
+  }
+  return h * est <= 2.5f ? s : -1;
+}
+
+// 2^-s for 0 <= s <= kMaxRefine, exactly (built from the exponent bits).
+__device__ __forceinline__ float pow2neg(int s) { return __int_as_float((127 - s) << 23); }
+
+// Saccade constants with the substep refined s times (h / 2^s, nsub 2^s).
+__device__ __forceinline__ SacConst refined(const SacConst& sc, int s) {
+  SacConst r = sc;
+  r.nsub = sc.nsub << s;
+  r.h = sc.h * pow2neg(s);
+  return r;
 }
 
 // Rest state at fixation th with precomputed 1/K_SE.
@@ -465,13 +488,14 @@ __device__ __forceinline__ void rk4_vec(const Coef& k, float da, float dn, float
   for (int i = 0; i < 6; ++i) e[i] = w[i];
 }
 
-// Stiffness guard shared with the oracle's rule: h * (B_P/J + (K_SE_AG +
-// K_LT_AG)/B_AG + (K_SE_ANT + K_LT_ANT)/B_ANT + 1/min tau) must stay <= 2.5.
+// Stiffness guard shared with the oracle's rule: even at the finest substep
+// (h / 2^kMaxRefine), h * (B_P/J + (K_SE_AG + K_LT_AG)/B_AG + (K_SE_ANT +
+// K_LT_ANT)/B_ANT + 1/min tau) must stay <= 2.5.
 __device__ __forceinline__ bool too_stiff(const float* p, float h) {
   float tmin = fminf(fminf(p[kTacAg], p[kTacAnt]), fminf(p[kTdeAg], p[kTdeAnt]));
   float est = p[kBp] / p[kJ] + (p[kSeAg] + p[kLtAg]) / p[kBAg] +
               (p[kSeAnt] + p[kLtAnt]) / p[kBAnt] + 1000.0f / tmin;
-  return !(h * est <= 2.5f);
+  return !(h * pow2neg(kMaxRefine) * est <= 2.5f);
 }
 
 // n sample intervals of one phase with the one-sample propagator, emitting
@@ -583,30 +607,35 @@ __device__ __forceinline__ void prop_load(Prop2& q, const float* qs, int stride)
 // dth = theta_k - thf (positive frame), and block_end() after blocks of
 // samples.  Samples k <= onset sit at th0 and are handled by the caller.
 // Returns the number of samples emitted; with `guard` set, -1 (nothing
-// emitted) for a candidate outside RK4's stable step range (too_stiff_coef).
+// emitted) for a candidate too stiff even for the finest substep (refine_shift).
 // qs (optional): a shared-memory slot that keeps the single-substep
 // propagator from the set-up to the pulse-end interval instead of rebuilding it.
 template <class Sink>
-__device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& sink, float* qs = nullptr,
+__device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& sink, float* qs = nullptr,
                                     int qstride = 0, bool guard = false) {
   Coef k;
   make_coef(p, k);
-  if (guard && too_stiff_coef(k, sc.h)) return -1;
+  const int rs = refine_shift(k, sc0.h);
+  if (guard && rs < 0) return -1;
+  const int sh = rs < 0 ? kMaxRefine : rs;
+  const int nsub = sc0.nsub << sh;            // substeps per sample, refined
+  const float h = sc0.h * pow2neg(sh);        // substep, refined (exact power-of-two scale)
+  const SacConst& sc = sc0;
   const int ntot = sc.L - 1 - sc.onset;
   if (ntot <= 0) return 0;
   // pulse end, in substeps after onset
-  float tau = p[kPw] * sc.fs * (float)sc.nsub * 1e-3f;
+  float tau = p[kPw] * sc.fs * (float)nsub * 1e-3f;
   tau = fminf(fmaxf(tau, 0.0f), 1.0e9f);
   const float jf = floorf(tau);
   const float frac = tau - jf;
-  const float span = (float)ntot * (float)sc.nsub;
+  const float span = (float)ntot * (float)nsub;
   int n1, jsw = 0;
   bool sw;
   if (jf >= span) { n1 = ntot; sw = false; }
   else {
     const int J = (int)jf;
-    n1 = J / sc.nsub;
-    jsw = J - n1 * sc.nsub;
+    n1 = J / nsub;
+    jsw = J - n1 * nsub;
     sw = true;
   }
   float s0[6], s1[6], s2[6];
@@ -619,13 +648,13 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
   const float off1 = s1[0] - sc.thf;
   Prop2 phi;
   if (qs) {
-    step_increment(k, sc.h, phi);
+    step_increment(k, h, phi);
     prop_store(phi, qs, qstride);
-    prop_pow_slot(phi, qs, qstride, sc.nsub);
+    prop_pow_slot(phi, qs, qstride, nsub);
   } else {
     Prop2 q;
-    step_increment(k, sc.h, q);
-    prop_pow(q, sc.nsub, phi);
+    step_increment(k, h, q);
+    prop_pow(q, nsub, phi);
   }
   int kk = sc.onset + 1;
   run_samples<1>(phi, e, off1, kk, n1, sink);
@@ -634,14 +663,14 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc, Sink& si
     // substep (two RK4 steps around the switch), the rest of the step phase
     Prop2 q;
     if (qs) prop_load(q, qs, qstride);
-    else step_increment(k, sc.h, q);
+    else step_increment(k, h, q);
     for (int s = 0; s < jsw; ++s) prop_apply<1>(q, e);
-    const float h1 = frac * sc.h;
+    const float h1 = frac * h;
     rk4_vec(k, k.da1, k.dn1, h1, e);
 #pragma unroll
     for (int i = 0; i < 6; ++i) e[i] += dl[i];
-    rk4_vec(k, k.da2, k.dn2, sc.h - h1, e);
-    for (int s = jsw + 1; s < sc.nsub; ++s) prop_apply<2>(q, e);
+    rk4_vec(k, k.da2, k.dn2, h - h1, e);
+    for (int s = jsw + 1; s < nsub; ++s) prop_apply<2>(q, e);
     sink.emit(kk++, e[0]);
     const int n2 = ntot - n1 - 1;
     run_samples<2>(phi, e, 0.0f, kk, n2, sink);
@@ -676,15 +705,18 @@ __device__ __forceinline__ void run_samples1(const Prop1& phi, float (&e)[6], fl
 // matrices of both phases, the split step) and the step phase's one-sample
 // propagator, built only once the pulse phase is done.
 template <class PSrc, class Sink>
-__device__ __forceinline__ int walk_lean(const PSrc& src, const SacConst& sc, Sink& sink) {
-  const int ntot = sc.L - 1 - sc.onset;
+__device__ __forceinline__ int walk_lean(const PSrc& src, const SacConst& sc0, Sink& sink) {
+  const int ntot = sc0.L - 1 - sc0.onset;
   if (ntot <= 0) return 0;
   Prop1 phi;
+  SacConst sc;
   {
     float p[kNumParams];
     src.load(p);
     Coef k;
     make_coef(p, k);
+    const int rs = refine_shift(k, sc0.h);
+    sc = refined(sc0, rs < 0 ? kMaxRefine : rs);
     Prop1 q;
     step_increment1<1>(k, sc.h, q);
     prop1_pow(q, sc.nsub, phi);

@@ -121,7 +121,9 @@ def test_score_matches_oracle(ctx):
     rng = np.random.default_rng(3)
     m = 3000
     opc = (it["pn"] * rng.uniform(0.5, 2.0, (m, 18))).astype(np.float32)
-    opc[-1] = it["pn"].astype(np.float32) * np.array([1] * 6 + [10.0] + [1] * 2 + [0.1] + [1] * 8,
+    opc[-2] = it["pn"].astype(np.float32) * np.array([1] * 6 + [10.0] + [1] * 2 + [0.1] + [1] * 8,
+                                                     dtype=np.float32)   # stiff: refined substeps
+    opc[-1] = it["pn"].astype(np.float32) * np.array([1] * 6 + [1000.0] + [1] * 2 + [0.001] + [1] * 8,
                                                      dtype=np.float32)   # too stiff: +inf
     got = G.opmm_score(ctx, opc, batch)
     for i in range(m):
@@ -385,3 +387,50 @@ def test_full_candidate_budget_initial_vertices_match_oracle(ctx):
         assert abs(res["rms_deg"][j] - refs[j]["rms"]) <= RMS_TOL
         bf = refs[j]["best_f_all"]
         assert bf[res["winner"][j]] - bf.min() <= f_tol(bf.min())
+
+
+# In the wide box the plant's modes spread over up to five decades and its
+# trajectories over three (a strong pulse against weak tension slopes can
+# carry a candidate past 1,000 deg).  FP32 rounding in the one-sample
+# propagator and in the sample updates then costs a few millionths of the
+# trajectory's own scale (measured: 3e-6 to 7e-6 of max |theta| for the worst
+# random candidates; an FP32 emulation of the pipeline with either stage in
+# FP64 halves the error, with both it vanishes): the bound is 1e-4 deg plus
+# 2e-5 of the largest |theta| of the reference trajectory.
+def wide_traj_tol(ref):
+    return TRAJ_TOL + 2e-5 * float(np.max(np.abs(ref)))
+
+
+def test_wide_box_simulation_and_fit_match_oracle(ctx):
+    """The paper-scale box [0.1x, 10x] (Fig. 4's rows sit on its bounds):
+    stiff candidates integrate with refined substeps on both sides;
+    trajectories match within wide_traj_tol and fits in that box match the
+    oracle's RMS to 1e-3 deg."""
+    w = W.uneven10k(B=4)
+    items = oracle_inputs(w)
+    rng = np.random.default_rng(11)
+    for it in items:
+        batch = to_batch([it])
+        m = 64
+        opc = (it["pn"] * np.exp(rng.uniform(np.log(0.1), np.log(10.0), (m, 18)))).astype(np.float32)
+        corner = np.ones(18)
+        corner[6], corner[9] = 10.0, 0.1                  # B_P 10x, J 0.1x: 8x the substeps
+        opc[0] = (it["pn"] * corner).astype(np.float32)
+        traj, offs = G.opmm_simulate(ctx, opc, batch, sac_index=np.zeros(m, np.int32))
+        refined = 0
+        for i in range(m):
+            p = opc[i].astype(np.float64)
+            if O.stiff(p, it["fs"]):
+                continue
+            refined += O.substeps(p, it["fs"]) > O.nsub(it["fs"])
+            ref = O.simulate_rk4(p, it["L"], it["fs"], it["onset"], it["th0"], it["thf"])
+            got = traj[offs[i]:offs[i] + it["L"]]
+            assert np.max(np.abs(got - ref)) <= wide_traj_tol(ref), (i, np.max(np.abs(got - ref)),
+                                                                     np.max(np.abs(ref)))
+        assert refined >= 1
+    res, refs = _fit_both(ctx, items[:3], 6, 6, box_lo=0.1, box_hi=10.0)
+    for j in range(3):
+        assert res["status"][j] == 0
+        assert abs(res["rms_deg"][j] - refs[j]["rms"]) <= RMS_TOL, (j, res["rms_deg"][j], refs[j]["rms"])
+        r = res["opc"][j] / centres(items[:3])[j]
+        assert np.all(r >= 0.1 * (1 - 1e-5)) and np.all(r <= 10.0 * (1 + 1e-5))

@@ -234,15 +234,29 @@ def test_table1_ten_degree_saccade_is_slow_but_arrives():
     assert 9.0 < th[-1] < 10.0
 
 
-def test_stiffness_guard():
+def test_stiff_candidates_get_refined_substeps():
+    """Candidates whose fastest mode is too fast for RK4 at ~0.1 ms get the
+    step halved until h times the mode estimate is at most 2.5 (at most six
+    times); the refined trajectory still matches the exact piecewise
+    solution; beyond the finest step a candidate scores +inf."""
     p = O.nominal_table1(43.0)
-    assert not O.stiff(p, 1000.0)
+    assert O.substeps(p, 1000.0) == 10 and not O.stiff(p, 1000.0)
     corner = p.copy()
     corner[6] *= 2.0
     corner[9] *= 0.5
-    assert not O.stiff(corner, 1000.0)          # the [0.5x, 2x] box is safe
+    assert O.substeps(corner, 1000.0) == 10       # the [0.5x, 2x] box needs no refinement
     corner[6] = p[6] * 10.0
     corner[9] = p[9] * 0.1
-    assert O.stiff(corner, 1000.0)              # the [0.1x, 10x] corner is not
-    y = np.zeros(150)
-    assert O.errors(corner, 150, 1000.0, 10, 0.0, 10.0, y)[0] == math.inf
+    assert O.substeps(corner, 1000.0) == 80 and not O.stiff(corner, 1000.0)   # [0.1x, 10x]: 8x
+    assert O.substeps(corner, 250.0) == 320
+    for fs in (1000.0, 250.0):
+        L, on = int(0.15 * fs), int(math.ceil(0.01 * fs))
+        rk = O.simulate_rk4(corner, L, fs, on, 0.0, 10.0)
+        ex = O.simulate_exact(corner, L, fs, on, 0.0, 10.0)
+        assert np.max(np.abs(rk - ex)) < 1e-6
+    extreme = p.copy()
+    extreme[6] = p[6] * 1000.0
+    extreme[9] = p[9] * 0.001
+    assert O.stiff(extreme, 1000.0)
+    assert O.errors(extreme, 150, 1000.0, 10, 0.0, 10.0, np.zeros(150))[0] == math.inf
+
