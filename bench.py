@@ -41,7 +41,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "OPC candidate sims/s (% FP32 peak); saccades fitted/s at <=0.1 deg RMS; p99 latency"
 FP32_LANES_PER_SM = 128
-RESULT_BYTES = 112
+RESULT_BYTES = 120
 
 
 # ------------------------------------------------------------------ algorithmic work
@@ -58,10 +58,21 @@ def flops_per_sim(L: int, onset: int, nsub: int) -> int:
     plant coefficients (24), single-step RK4 increment matrices of both phases
     (560), binary powering to one sample interval (332 per product),
     equilibria (68), finish (2), and per integrated sample a 6x6 block update
-    plus the residual term (55).  The pulse-end interval (re-built step matrix,
-    nsub - 1 single-step updates, two split RK4 steps) is not counted."""
+    plus the residual term (55).  A candidate whose pulse ends inside the
+    window adds pulse_end_flops(nsub) on top (counted per candidate by the
+    kernel).  Candidates refined to a finer substep are credited at the base
+    substep (their extra work is not counted)."""
     n_int = max(0, L - 1 - onset)
     return 46 + 24 + 560 + 332 * pow_products(nsub) + 68 + 2 + 55 * n_int
+
+
+def pulse_end_flops(nsub: int) -> int:
+    """Extra FLOPs of the sample interval that holds the pulse end, over the
+    52 of the one-sample update already counted for it: nsub - 1 single-substep
+    block updates (52 each), two RK4 steps around the switch (4 levels of the
+    A-apply, 19, plus 6 FMAs, and 3 for the level coefficients: 127 each), the
+    two split step lengths (2) and the equilibrium shift (6)."""
+    return 52 * (nsub - 1) + 2 * 127 + 2 + 6 - 52
 
 
 def rk4_stage_flops_per_sim(L: int, nsub: int) -> int:
@@ -311,6 +322,7 @@ def run_ours(args, ws, rank, local):
         nsub = nsub_for(float(w.fs[i]))
         e = float(r["evaluations"][i])
         flops += e * flops_per_sim(int(w.L[i]), int(w.onset[i]), nsub)
+        flops += float(r["pulse_end_evals"][i]) * pulse_end_flops(nsub)
         rk4_eq += e * rk4_stage_flops_per_sim(int(w.L[i]), nsub)
     mean_search_ms = statistics.mean(search_ms)
     if not mean_search_ms > 0.0:

@@ -108,6 +108,11 @@ typedef struct {
   int32_t winner;            /* index of the winning simplex */
   int32_t evaluations;       /* candidate OPC vectors simulated for this saccade */
   int32_t source;            /* OPMM_SOURCE_*: which search produced opc */
+  int32_t pulse_end_evals;   /* of the evaluations, those whose pulse ended
+                                inside the recorded window (the sample holding
+                                the pulse end is integrated substep by
+                                substep); counted like evaluations */
+  int32_t reserved;          /* 0 */
 } opmm_fit_result;
 
 enum {
@@ -258,7 +263,7 @@ int opmm_serve_stop(opmm_ctx* ctx);
  * != 0 or rms_deg > fallback_rms_deg again with `plain` (use_surrogate must be
  * 0; its init_opc, if given, is indexed by the original saccade index).  A
  * re-fitted saccade keeps whichever result has the lower FP64 rms_deg; its
- * evaluations count both searches and source says which result was kept
+ * evaluations and pulse_end_evals count both searches and source says which result was kept
  * (OPMM_SOURCE_SEEDED or OPMM_SOURCE_FALLBACK).  n_fallback (nullable)
  * receives the number of saccades re-fitted.  Host descriptors; traces host or
  * device as for opmm_fit_batch.  Errors as for opmm_fit_batch; on error out is

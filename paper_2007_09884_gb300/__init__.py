@@ -87,7 +87,8 @@ class opmm_fit_result(ctypes.Structure):
     _fields_ = [("opc", ctypes.c_float * 18), ("f", ctypes.c_float),
                 ("iterations_run", ctypes.c_int32), ("rms_deg", ctypes.c_double),
                 ("l1_deg", ctypes.c_double), ("status", ctypes.c_int32), ("winner", ctypes.c_int32),
-                ("evaluations", ctypes.c_int32), ("source", ctypes.c_int32)]
+                ("evaluations", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("pulse_end_evals", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -257,7 +258,8 @@ def results_to_numpy(res) -> dict:
                                                      ("iterations_run", "<i4"), ("rms_deg", "<f8"),
                                                      ("l1_deg", "<f8"), ("status", "<i4"),
                                                      ("winner", "<i4"), ("evaluations", "<i4"),
-                                                     ("source", "<i4")]), count=n)
+                                                     ("source", "<i4"), ("pulse_end_evals", "<i4"),
+                                                     ("reserved", "<i4")]), count=n)
     return {k: buf[k].copy() for k in buf.dtype.names}
 
 

@@ -883,12 +883,14 @@ extern "C" int opmm_fit_batch_seeded(opmm_ctx* ctx, const opmm_saccade* sacs, in
   for (size_t j = 0; j < m; ++j) {
     opmm_fit_result& r = out[miss[j]];
     const int32_t evals = r.evaluations + fb[j].evaluations;
+    const int32_t pe = r.pulse_end_evals + fb[j].pulse_end_evals;
     const bool better = fb[j].status == 0 && (r.status != 0 || fb[j].rms_deg < r.rms_deg);
     if (better) {
       r = fb[j];
       r.source = OPMM_SOURCE_FALLBACK;
     }
     r.evaluations = evals;
+    r.pulse_end_evals = pe;
   }
   return OPMM_OK;
 }

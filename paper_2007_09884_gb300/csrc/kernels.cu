@@ -81,10 +81,12 @@ struct PeakSink {
 
 // Objective of one OPC vector: mean squared error over the window; the
 // samples up to onset (the plant at rest) are folded into (sum0, c0).
+// pe (optional): set to 1 when the pulse ends inside the window.
 __device__ __forceinline__ float objective(const float* p, const SacConst& sc, const float* z,
-                                           float sum0, float c0, float* qs = nullptr, int qstride = 0) {
+                                           float sum0, float c0, float* qs = nullptr, int qstride = 0,
+                                           int* pe = nullptr) {
   KahanSink s{z, sum0, c0, 0.0f};
-  if (walk(p, sc, s, qs, qstride, true) < 0) return INFINITY;
+  if (walk(p, sc, s, qs, qstride, true, pe) < 0) return INFINITY;
   s.block_end();
   const float f = (s.sum - s.c) / (float)sc.L;
   return isfinite(f) ? f : INFINITY;
@@ -266,9 +268,11 @@ __global__ void k_score(const float* opc, int m, const DevSac* sac, const float*
 }
 
 // ------------------------------------------------------------------ search
-// Unit record: [0] best f, [1] winning simplex (int), [2] its iterations (int),
-// [3] candidate evaluations of the unit (int), [4..21] best vertex (ln units).
-constexpr int kUnitRec = 24;
+// Unit record (kUnitRecFloats words): [0] best f, [1] winning simplex (int),
+// [2] its iterations (int), [3] candidate evaluations of the unit (int),
+// [4..21] best vertex (ln units), [22] evaluations whose pulse ends inside the
+// window (int), [23] unused.
+constexpr int kUnitRec = kUnitRecFloats;
 constexpr int kNV = kNumParams + 1;      // vertices per simplex
 constexpr int kNT = kNumParams + 4;      // trial points per simplex and iteration
 constexpr int kSortBins = 512;           // pulse-end time bins of the per-wave ordering
@@ -311,6 +315,7 @@ struct GroupSmem {
   int state;    // kPending (a wave is ordered) or kDone; written by the controller only
   int it;       // trial waves evaluated in this launch
   int evals;    // candidate evaluations of this group
+  int pe;       // of those, candidates whose pulse ends inside the window
 };
 
 enum : int { kPending = 0, kDone = 2 };
@@ -360,7 +365,7 @@ __device__ __forceinline__ void ULinSrc::load(float (&o)[kNumParams]) const {
 
 // Objective through the register-lean walk.
 __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacConst& sc, const float* z,
-                                                float sum0, float c0) {
+                                                float sum0, float c0, int* pe = nullptr) {
   {
     float p[kNumParams];
     src.load(p);
@@ -369,7 +374,7 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
     if (refine_shift(k, sc.h) < 0) return INFINITY;
   }
   KahanSink s{z, sum0, c0, 0.0f};
-  walk_lean(src, sc, s);
+  walk_lean(src, sc, s, pe);
   s.block_end();
   const float f = (s.sum - s.c) / (float)sc.L;
   return isfinite(f) ? f : INFINITY;
@@ -377,11 +382,11 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
 
 __device__ __forceinline__ float eval_u(const float (&u)[kNumParams], const float* pc, float lnlo,
                                         float lnhi, const SacConst& sc, const float* z, float sum0,
-                                        float c0, float* qs, int qstride) {
+                                        float c0, float* qs, int qstride, int* pe) {
   float p[kNumParams];
 #pragma unroll
   for (int j = 0; j < kNumParams; ++j) p[j] = pc[j] * __expf(fminf(fmaxf(u[j], lnlo), lnhi));
-  return objective(p, sc, z, sum0, c0, qs, qstride);
+  return objective(p, sc, z, sum0, c0, qs, qstride, pe);
 }
 
 // Sort key of a candidate: its pulse-end time, binned over the window (the
@@ -669,12 +674,14 @@ __device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, 
 }
 
 // Evaluate the pending wave of a group: evaluation thread t takes the t-th
-// candidate in key order.
+// candidate in key order.  Returns 1 when that candidate's pulse ends inside
+// the window (its pulse-end sample was integrated substep by substep), else 0.
 template <int G, bool LEAN>
-__device__ __forceinline__ void eval_wave(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P,
+__device__ __forceinline__ int eval_wave(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P,
                                           const float* z, float* qs, int tid) {
   constexpr int NE = search_eval_threads<G>();
-  if (tid >= g.nvalid) return;
+  if (tid >= g.nvalid) return 0;
+  int pe = 0;
   const SacConst& sc = S.sc;
   const float sum0 = S.st.sum0, c0 = S.st.c0;
   const int c = g.perm[tid];
@@ -682,14 +689,14 @@ __device__ __forceinline__ void eval_wave(GroupSmem<G>& g, const SearchSmem<G>& 
     const int gi = c / kNV, v = c - gi * kNV;
     if (LEAN) {
       const ULinSrc src{g.U[gi][v], g.U[gi][v], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
-      g.F[gi][v] = objective_lean(src, sc, z, sum0, c0);
+      g.F[gi][v] = objective_lean(src, sc, z, sum0, c0, &pe);
     } else {
       float u[kNumParams];
 #pragma unroll
       for (int j = 0; j < kNumParams; ++j) u[j] = g.U[gi][v][j];
-      g.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE);
+      g.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE, &pe);
     }
-    return;
+    return pe;
   }
   const int gi = c / kNT, q = c - gi * kNT;
   const unsigned char* o = g.ord[gi];
@@ -703,7 +710,7 @@ __device__ __forceinline__ void eval_wave(GroupSmem<G>& g, const SearchSmem<G>& 
     } else {
       src = ULinSrc{g.U[gi][o[0]], g.U[gi][o[q - 3]], 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
     }
-    g.FT[gi][q] = objective_lean(src, sc, z, sum0, c0);
+    g.FT[gi][q] = objective_lean(src, sc, z, sum0, c0, &pe);
   } else {
     float u[kNumParams];
     if (q < 4) {
@@ -718,8 +725,9 @@ __device__ __forceinline__ void eval_wave(GroupSmem<G>& g, const SearchSmem<G>& 
 #pragma unroll
       for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(g.U[gi][s1][j], g.U[gi][si][j]);
     }
-    g.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE);
+    g.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE, &pe);
   }
+  return pe;
 }
 
 template <int G, int MINB, bool LEAN>
@@ -784,6 +792,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       g.nsim = tid == 0 ? nA : nunit - nA;
       g.it = 0;
       g.evals = 0;
+      g.pe = 0;
       g.nvalid = 0;
       g.state = g.nsim > 0 ? kPending : kDone;
     }
@@ -858,7 +867,8 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       if (!ctrl) {
         if (ge.state == kPending) {
           order_wave<G>(ge, S, P, tid);
-          eval_wave<G, LEAN>(ge, S, P, z, qslot + tid, tid);
+          const unsigned m = __ballot_sync(0xffffffffu, eval_wave<G, LEAN>(ge, S, P, z, qslot + tid, tid));
+          if (lane == 0 && m) atomicAdd(&ge.pe, __popc(m));
         }
       } else {
         const bool ge_evaluated = ge.state == kPending;
@@ -917,6 +927,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         if (f2 < f || (f2 == f && b2 < best)) { f = f2; best = b2; }
       }
       const int evals_prev = it0 > 0 ? __float_as_int(rec[3]) : 0;
+      const int pe_prev = it0 > 0 ? __float_as_int(rec[22]) : 0;
       __syncwarp();
       if (best < nunit) {
         const GroupSmem<G>& g = S.grp[best < nA ? 0 : 1];
@@ -927,6 +938,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
           rec[1] = __int_as_float(s0 + best);
           rec[2] = __int_as_float(g.iters[gi]);
           rec[3] = __int_as_float(evals_prev + S.grp[0].evals + S.grp[1].evals);
+          rec[22] = __int_as_float(pe_prev + S.grp[0].pe + S.grp[1].pe);
         }
       }
     }
@@ -1149,7 +1161,7 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = list ? list[i] : i;
-  int w = -1, wsimp = 0x7fffffff, evals = 0;
+  int w = -1, wsimp = 0x7fffffff, evals = 0, pe = 0;
   float wf = INFINITY;
   const int u0 = ustart ? ustart[b] : b * ngroups;   // slot-major records when no start table
   for (int u = u0; u < u0 + ngroups; ++u) {
@@ -1157,6 +1169,7 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
     const float f = rec[0];
     const int s = __float_as_int(rec[1]);
     evals += __float_as_int(rec[3]);
+    pe += __float_as_int(rec[22]);
     if (w < 0 || f < wf || (f == wf && s < wsimp)) { w = u; wf = f; wsimp = s; }
   }
   opmm_fit_result r;
@@ -1168,6 +1181,8 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
   r.iterations_run = __float_as_int(rec[2]);
   r.winner = wsimp;
   r.evaluations = evals;
+  r.pulse_end_evals = pe;
+  r.reserved = 0;
   r.source = OPMM_SOURCE_PLAIN;
   if (isfinite(wf)) {
     double mse, mae;

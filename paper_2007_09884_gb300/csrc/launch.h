@@ -68,6 +68,7 @@ cudaError_t launch_admit(const DevSac* new_sacs, const float* new_traces, const 
                          DevSac* sacs, float* traces, float* pc, int* progress, int slot_stride, cudaStream_t st);
 cudaError_t launch_advance(const int* slots, int n, int* progress, int iters, int T, cudaStream_t st);
 
+// Words per (saccade, simplex-unit) result record of the search kernel.
 constexpr int kUnitRecFloats = 24;
 
 }  // namespace opmm

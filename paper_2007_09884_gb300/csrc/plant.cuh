@@ -610,9 +610,11 @@ __device__ __forceinline__ void prop_load(Prop2& q, const float* qs, int stride)
 // emitted) for a candidate too stiff even for the finest substep (refine_shift).
 // qs (optional): a shared-memory slot that keeps the single-substep
 // propagator from the set-up to the pulse-end interval instead of rebuilding it.
+// pulse_end (optional): set to 1 when the pulse ends inside the window (the
+// pulse-end sample was integrated substep by substep), else 0.
 template <class Sink>
 __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& sink, float* qs = nullptr,
-                                    int qstride = 0, bool guard = false) {
+                                    int qstride = 0, bool guard = false, int* pulse_end = nullptr) {
   Coef k;
   make_coef(p, k);
   const int rs = refine_shift(k, sc0.h);
@@ -658,6 +660,7 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
   }
   int kk = sc.onset + 1;
   run_samples<1>(phi, e, off1, kk, n1, sink);
+  if (pulse_end) *pulse_end = sw ? 1 : 0;
   if (sw) {
     // pulse-end interval: jsw whole substeps of the pulse phase, the split
     // substep (two RK4 steps around the switch), the rest of the step phase
@@ -705,7 +708,7 @@ __device__ __forceinline__ void run_samples1(const Prop1& phi, float (&e)[6], fl
 // matrices of both phases, the split step) and the step phase's one-sample
 // propagator, built only once the pulse phase is done.
 template <class PSrc, class Sink>
-__device__ __forceinline__ int walk_lean(const PSrc& src, const SacConst& sc0, Sink& sink) {
+__device__ __forceinline__ int walk_lean(const PSrc& src, const SacConst& sc0, Sink& sink, int* pulse_end = nullptr) {
   const int ntot = sc0.L - 1 - sc0.onset;
   if (ntot <= 0) return 0;
   Prop1 phi;
@@ -751,6 +754,7 @@ __device__ __forceinline__ int walk_lean(const PSrc& src, const SacConst& sc0, S
   }
   int kk = sc.onset + 1;
   run_samples1(phi, e, off1, kk, n1, sink);
+  if (pulse_end) *pulse_end = sw ? 1 : 0;
   if (sw) {
     {
       float p[kNumParams];

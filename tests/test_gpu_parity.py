@@ -434,3 +434,39 @@ def test_wide_box_simulation_and_fit_match_oracle(ctx):
         assert abs(res["rms_deg"][j] - refs[j]["rms"]) <= RMS_TOL, (j, res["rms_deg"][j], refs[j]["rms"])
         r = res["opc"][j] / centres(items[:3])[j]
         assert np.all(r >= 0.1 * (1 - 1e-5)) and np.all(r <= 10.0 * (1 + 1e-5))
+
+
+@pytest.mark.parametrize("box", [(0.5, 2.0), (0.1, 10.0)])
+def test_pulse_end_count_of_initial_vertices(ctx, box):
+    """pulse_end_evals counts the evaluated candidates whose pulse ends inside
+    the window (PW * fs < L - 1 - onset samples after onset, so that the
+    interval holding the pulse end is integrated substep by substep).  With no
+    iterations the evaluated candidates are exactly the starting vertices,
+    which the host rebuilds from the oracle's Philox starts; candidates the
+    stiffness rule rejects are not simulated and not counted.  A vertex whose
+    pulse ends within 1e-5 of a sample boundary may fall either way in FP32."""
+    lo, hi = box
+    w = W.uneven10k(B=6)
+    items = oracle_inputs(w)
+    S, step = 40, 0.05
+    res, _ = _fit_both(ctx, items, S, 0, box_lo=lo, box_hi=hi)
+    for j, it in enumerate(items):
+        ntot = it["L"] - 1 - it["onset"]
+        want = near = 0
+        for s in range(S):
+            c = O.start_centre(18, s, j, 0, lo, hi)
+            for v in range(19):
+                u = c.copy()
+                if v > 0:
+                    u[v - 1] += step
+                p = O.u_to_p(it["pn"], u, box_lo=lo, box_hi=hi)
+                if ntot <= 0 or O.stiff(p, it["fs"]):
+                    continue
+                x = p[17] * it["fs"] * 1e-3
+                want += x < ntot
+                near += abs(x - ntot) <= 1e-5 * ntot
+        assert res["evaluations"][j] == 19 * S
+        assert abs(int(res["pulse_end_evals"][j]) - want) <= near, (j, res["pulse_end_evals"][j], want, near)
+    res, _ = _fit_both(ctx, items, 8, 6)
+    assert np.all(res["pulse_end_evals"] >= 0) and np.all(res["pulse_end_evals"] <= res["evaluations"])
+    assert np.all(res["reserved"] == 0)
