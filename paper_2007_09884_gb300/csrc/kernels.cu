@@ -283,15 +283,25 @@ constexpr int kHistPer = kSortBins / 32;              // bins per lane of the sc
 constexpr int kHistLen = kSortBins + 32;                // bin b stored at b + b / kHistPer
 
 // One block runs G simplices in each of two groups (a unit of 2G simplices of
-// one saccade).  NE evaluation threads (11 per simplex of a group, rounded to
-// warps) evaluate the pending wave of one group while the block's last warp,
-// the controller, takes the Nelder-Mead decisions of the other group's last
-// wave and orders its next wave; the two swap at the single block barrier
-// that ends each step.
+// one saccade).  NE evaluation threads (22 per simplex of a group rounded to
+// warps, at most 11 warps) evaluate the pending wave of one group while the
+// block's last warp, the controller, takes the Nelder-Mead decisions of the
+// other group's last wave and sets up its next wave; the two swap at the
+// single block barrier that ends each step.  Eleven evaluation warps and the
+// controller at 168 registers per thread fill the SM's register file (3 warps
+// per SM sub-partition); a wave larger than NE (G = 32: 704 candidates) is
+// taken in chunks of 32 candidates that the evaluation warps pull in turn, so
+// that warps sharing a sub-partition with fewer others take more chunks.
+constexpr int kMaxEvalThreads = 352;
 template <int G>
-__host__ __device__ constexpr int search_eval_threads() { return ((G * kNT + 31) / 32) * 32; }
+__host__ __device__ constexpr int search_eval_threads() {
+  return ((G * kNT + 31) / 32) * 32 < kMaxEvalThreads ? ((G * kNT + 31) / 32) * 32 : kMaxEvalThreads;
+}
 template <int G>
 __host__ __device__ constexpr int search_threads() { return search_eval_threads<G>() + 32; }
+// candidates per evaluation thread in one wave (ordering)
+template <int G>
+__host__ __device__ constexpr int wave_per_thread() { return (G * kNT + search_eval_threads<G>() - 1) / search_eval_threads<G>(); }
 
 // State of one group of G simplices.
 template <int G>
@@ -316,6 +326,7 @@ struct GroupSmem {
   int it;       // trial waves evaluated in this launch
   int evals;    // candidate evaluations of this group
   int pe;       // of those, candidates whose pulse ends inside the window
+  int chunk;    // next chunk of 32 candidates (in key order) of the pending wave
 };
 
 enum : int { kPending = 0, kDone = 2 };
@@ -403,6 +414,17 @@ __device__ __forceinline__ int switch_key(float u_pw, float pc_pw, float lnlo, f
 
 __device__ __forceinline__ int hist_slot(int b) { return b + b / kHistPer; }
 
+// Rows of trial point q of simplex gi, as u = a + (b - a) / 2 coordinate by
+// coordinate: a = b = the controller's XT row for q < 4 (so u = a exactly),
+// the best vertex and vertex q - 3 for the shrink points.  One form for every
+// lane, so a warp holding both kinds does not diverge.
+template <int G>
+__device__ __forceinline__ void trial_rows(const GroupSmem<G>& g, int gi, int q, const float*& a, const float*& b) {
+  const unsigned char* o = g.ord[gi];
+  a = q < 4 ? g.XT[gi][q] : g.U[gi][o[0]];
+  b = q < 4 ? g.XT[gi][q] : g.U[gi][o[q - 3]];
+}
+
 // Barrier of the evaluation threads only (the controller warp runs on).
 template <int NE>
 __device__ __forceinline__ void eval_sync() {
@@ -410,30 +432,37 @@ __device__ __forceinline__ void eval_sync() {
 }
 
 // Counting sort of a group's due wave by pulse-end time, by the evaluation
-// threads at the start of the step that evaluates it: thread t keys candidate
-// t, one warp scans the histogram (cleared by the controller when it set the
-// wave up), and afterwards g.perm[0 .. g.nvalid) lists the candidates in key
-// order.
+// threads at the start of the step that evaluates it: thread t keys
+// candidates t, t + NE, ..., one warp scans the histogram (cleared by the
+// controller when it set the wave up), and afterwards g.perm[0 .. g.nvalid)
+// lists the candidates in key order.
 template <int G>
 __device__ __forceinline__ void order_wave(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P, int tid) {
   constexpr int NE = search_eval_threads<G>();
-  static_assert(G * kNT <= NE, "one candidate per evaluation thread");
+  constexpr int R = wave_per_thread<G>();
+  static_assert(G * kNT <= NE * R, "every candidate keyed");
   const int ncand = (g.kind == 0 ? kNV : kNT) * g.nsim;
-  int key = -1, slot = 0;
-  if (tid < ncand) {
-    if (g.kind == 0) {
-      const int gi = tid / kNV, v = tid - gi * kNV;
-      key = switch_key(g.U[gi][v][kPw], S.pc[kPw], P.lnlo, P.lnhi, S.sc);
-    } else {
-      const int gi = tid / kNT, q = tid - gi * kNT;
-      if (g.active[gi]) {
-        const unsigned char* o = g.ord[gi];
-        const float up = q < 4 ? trial_coord(q, g.XB[gi][kPw], g.U[gi][o[kNumParams]][kPw])
-                               : shrink_coord(g.U[gi][o[0]][kPw], g.U[gi][o[q - 3]][kPw]);
-        key = switch_key(up, S.pc[kPw], P.lnlo, P.lnhi, S.sc);
+  int key[R], slot[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int c = tid + r * NE;
+    key[r] = -1;
+    slot[r] = 0;
+    if (c < ncand) {
+      if (g.kind == 0) {
+        const int gi = c / kNV, v = c - gi * kNV;
+        key[r] = switch_key(g.U[gi][v][kPw], S.pc[kPw], P.lnlo, P.lnhi, S.sc);
+      } else {
+        const int gi = c / kNT, q = c - gi * kNT;
+        if (g.active[gi]) {
+          const float* a;
+          const float* bb;
+          trial_rows(g, gi, q, a, bb);
+          key[r] = switch_key(shrink_coord(a[kPw], bb[kPw]), S.pc[kPw], P.lnlo, P.lnhi, S.sc);
+        }
       }
+      if (key[r] >= 0) slot[r] = atomicAdd(&g.hist[hist_slot(key[r])], 1);
     }
-    if (key >= 0) slot = atomicAdd(&g.hist[hist_slot(key)], 1);
   }
   eval_sync<NE>();
   if (tid < 32) {
@@ -466,7 +495,9 @@ __device__ __forceinline__ void order_wave(GroupSmem<G>& g, const SearchSmem<G>&
     if (lane == 31) g.nvalid = incl;
   }
   eval_sync<NE>();
-  if (key >= 0) g.perm[g.hist[hist_slot(key)] + slot] = (unsigned short)tid;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (key[r] >= 0) g.perm[g.hist[hist_slot(key[r])] + slot[r]] = (unsigned short)(tid + r * NE);
   eval_sync<NE>();
 }
 
@@ -649,7 +680,9 @@ __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float to
 // Set up a group's next wave (controller warp): the initial vertices (kind 0)
 // or the 22 trial points of every active simplex, ordered by the evaluation
 // threads when they take it; a group with nothing left to evaluate, or at its
-// iteration cap, is done.
+// iteration cap, is done.  The controller writes the four trial points
+// (reflection, expansion, both contractions) to XT; the 18 shrink points are
+// formed by the evaluation threads from the vertices.
 template <int G>
 __device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, int lane) {
   int nact = 0;
@@ -665,26 +698,35 @@ __device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, 
     }
   }
   for (int i = lane; i < kHistLen; i += 32) g.hist[i] = 0;
+  if (kind == 1) {
+    for (int e = lane; e < g.nsim * 4 * kNumParams; e += 32) {
+      const int gi = e / (4 * kNumParams), r = e - gi * 4 * kNumParams;
+      const int q = r / kNumParams, j = r - q * kNumParams;
+      if (g.active[gi]) g.XT[gi][q][j] = trial_coord(q, g.XB[gi][j], g.U[gi][g.ord[gi][kNumParams]][j]);
+    }
+  }
   if (lane == 0) {
     g.kind = kind;
+    g.chunk = 0;
     g.state = kPending;
     if (kind == 1) g.evals += kNT * nact;
   }
   __syncwarp();
 }
 
-// Evaluate the pending wave of a group: evaluation thread t takes the t-th
-// candidate in key order.  Returns 1 when that candidate's pulse ends inside
-// the window (its pulse-end sample was integrated substep by substep), else 0.
+// Evaluate the candidate at position pos (key order) of a group's pending
+// wave; qs is the calling thread's propagator slot.  Returns 1 when that
+// candidate's pulse ends inside the window (its pulse-end sample was
+// integrated substep by substep), else 0 (also for pos past the wave).
 template <int G, bool LEAN>
-__device__ __forceinline__ int eval_wave(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P,
-                                          const float* z, float* qs, int tid) {
+__device__ __forceinline__ int eval_candidate(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P,
+                                              const float* z, float* qs, int pos) {
   constexpr int NE = search_eval_threads<G>();
-  if (tid >= g.nvalid) return 0;
+  if (pos >= g.nvalid) return 0;
   int pe = 0;
   const SacConst& sc = S.sc;
   const float sum0 = S.st.sum0, c0 = S.st.c0;
-  const int c = g.perm[tid];
+  const int c = g.perm[pos];
   if (g.kind == 0) {
     const int gi = c / kNV, v = c - gi * kNV;
     if (LEAN) {
@@ -699,32 +741,16 @@ __device__ __forceinline__ int eval_wave(GroupSmem<G>& g, const SearchSmem<G>& S
     return pe;
   }
   const int gi = c / kNT, q = c - gi * kNT;
-  const unsigned char* o = g.ord[gi];
+  const float* a;
+  const float* bb;
+  trial_rows(g, gi, q, a, bb);
   if (LEAN) {
-    ULinSrc src;
-    if (q < 4) {
-      const int ws = o[kNumParams];
-#pragma unroll
-      for (int j = 0; j < kNumParams; ++j) g.XT[gi][q][j] = trial_coord(q, g.XB[gi][j], g.U[gi][ws][j]);
-      src = ULinSrc{g.XT[gi][q], g.XT[gi][q], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
-    } else {
-      src = ULinSrc{g.U[gi][o[0]], g.U[gi][o[q - 3]], 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
-    }
+    const ULinSrc src{a, bb, 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
     g.FT[gi][q] = objective_lean(src, sc, z, sum0, c0, &pe);
   } else {
     float u[kNumParams];
-    if (q < 4) {
-      const int ws = o[kNumParams];
 #pragma unroll
-      for (int j = 0; j < kNumParams; ++j) {
-        u[j] = trial_coord(q, g.XB[gi][j], g.U[gi][ws][j]);
-        g.XT[gi][q][j] = u[j];
-      }
-    } else {
-      const int s1 = o[0], si = o[q - 3];
-#pragma unroll
-      for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(g.U[gi][s1][j], g.U[gi][si][j]);
-    }
+    for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(a[j], bb[j]);
     g.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE, &pe);
   }
   return pe;
@@ -813,8 +839,8 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       }
     } else {
       // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
-      if (tid < 5 * nunit) {
-        const int sg = tid / 5, blk = tid - sg * 5;
+      for (int t5 = tid; t5 < 5 * nunit; t5 += NT) {
+        const int sg = t5 / 5, blk = t5 - sg * 5;
         GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
         const int gi = sg < nA ? sg : sg - nA;
         const int s = s0 + sg;
@@ -867,8 +893,18 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       if (!ctrl) {
         if (ge.state == kPending) {
           order_wave<G>(ge, S, P, tid);
-          const unsigned m = __ballot_sync(0xffffffffu, eval_wave<G, LEAN>(ge, S, P, z, qslot + tid, tid));
-          if (lane == 0 && m) atomicAdd(&ge.pe, __popc(m));
+          // pull chunks of 32 candidates in key order until the wave is taken
+          int npe = 0;
+#pragma unroll 1
+          for (;;) {
+            int ch = 0;
+            if (lane == 0) ch = atomicAdd(&ge.chunk, 1);
+            ch = __shfl_sync(0xffffffffu, ch, 0);
+            if (ch * 32 >= ge.nvalid) break;
+            npe += __popc(__ballot_sync(0xffffffffu,
+                                        eval_candidate<G, LEAN>(ge, S, P, z, qslot + tid, ch * 32 + lane)));
+          }
+          if (lane == 0 && npe) atomicAdd(&ge.pe, npe);
         }
       } else {
         const bool ge_evaluated = ge.state == kPending;
@@ -1282,7 +1318,7 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
 // register allocation is bounded for, and the register-lean walk.  The host
 // sees the unit size (simplices per block).
 struct SearchVariantDesc { int G, minb, lean; };
-static const SearchVariantDesc kVariants[] = {{16, 1, 0}, {16, 1, 1}, {8, 1, 0}};
+static const SearchVariantDesc kVariants[] = {{16, 1, 0}, {16, 1, 1}, {8, 1, 0}, {32, 1, 0}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 int search_variant_count() { return kNumVariants; }
@@ -1318,6 +1354,7 @@ static cudaError_t launch_v(const SearchParams& P, int blocks_per_sm, int num_sm
     case 0: return CALL(16, 1, false);      \
     case 1: return CALL(16, 1, true);       \
     case 2: return CALL(8, 1, false);       \
+    case 3: return CALL(32, 1, false);      \
     default: return cudaErrorInvalidValue;  \
   }
 
@@ -1339,6 +1376,7 @@ int search_threads_for(int unit) {
   switch (unit) {
     case 16: return search_threads<8>();
     case 32: return search_threads<16>();
+    case 64: return search_threads<32>();
     default: return 0;
   }
 }
@@ -1347,6 +1385,7 @@ size_t search_smem_for(int unit, int lcap) {
   switch (unit) {
     case 16: return search_smem_bytes<8>(lcap);
     case 32: return search_smem_bytes<16>(lcap);
+    case 64: return search_smem_bytes<32>(lcap);
     default: return 0;
   }
 }

@@ -307,10 +307,12 @@ def test_invalid_arguments_are_rejected(ctx, bad):
 
 def test_every_search_variant_matches_oracle(ctx):
     """All launch-shape variants of the search kernel (simplices per block,
-    register budget, register-lean schedule) run the same estimator."""
+    register budget, register-lean schedule) run the same estimator; 70
+    simplices fill a 64-simplex unit (waves of 704 candidates, two per
+    evaluation thread) and leave a partial one."""
     w = W.uneven10k(B=4)
     items = oracle_inputs(w)
-    S, T = 19, 5
+    S, T = 70, 5
     refs = [O.fit(it["pn"], it["L"], it["fs"], it["onset"], it["th0"], it["thf"], it["y"], S, T,
                   sac_index=j) for j, it in enumerate(items)]
     base = None
