@@ -29,6 +29,16 @@ NAMES = ["SE_ag", "SE_ant", "LT_ag", "LT_ant", "PE_ag", "PE_ant", "Vis", "FV_ag"
          "FV_ant", "Inert", "Act_ag", "Act_ant", "Deact_ag", "Deact_ant", "Step",
          "H_ag", "H_ant", "W"]
 ALL_FREE = (1 << NP) - 1
+# 9-parameter model (Sec. 2.2.2, Table 2): its parameters in the table's order
+NAMES9 = ["K_SE", "K_LT", "B_AG", "B_ANT", "B_P", "N_C_AG", "N_C_ANT", "J", "N_C_FIX"]
+
+
+def model_dim(model: int) -> int:
+    return {18: NP, 9: 9}[int(model)]
+
+
+def _mask(model: int, free_mask) -> int:
+    return (1 << model_dim(model)) - 1 if free_mask is None else int(free_mask)
 
 _d = ctypes.c_double
 _i = ctypes.c_int
@@ -85,12 +95,13 @@ def _load():
             lib.or_nm_one_step_testfn.argtypes = [_i, _i, _dp, _dp]
             lib.or_nm_one_step_testfn.restype = _i
             lib.or_start_centre.argtypes = [_i, _i, _u32, _u64, _d, _d, _dp]
-            lib.or_fit.argtypes = [_dp, _u32, _i, _d, _i, _d, _d, _dp, _i, _i, _d, _d, _d,
+            lib.or_fit.argtypes = [_dp, _i, _u32, _i, _d, _i, _d, _d, _dp, _i, _i, _d, _d, _d,
                                    _d, _d, _u64, _u32, _i, _dp, _dp, _ip, _ip]
             lib.or_fit.restype = _i
-            lib.or_score.argtypes = [_dp, _u32, _i, _d, _i, _d, _d, _dp, _d, _d, _dp, _i, _dp]
+            lib.or_score.argtypes = [_dp, _i, _u32, _i, _d, _i, _d, _d, _dp, _d, _d, _dp, _i, _dp]
             lib.or_score.restype = _i
-            lib.or_u_to_p.argtypes = [_dp, _u32, _d, _d, _dp, _dp]
+            lib.or_u_to_p.argtypes = [_dp, _i, _u32, _d, _d, _dp, _dp]
+            lib.or_u_to_p.restype = _i
             _lib = lib
     return _lib
 
@@ -239,18 +250,20 @@ def start_centre(n, s, sac_index, seed, box_lo, box_hi) -> np.ndarray:
     return c
 
 
-def fit(pc, L, fs, onset, th0, thf, y, S, T, *, free_mask=ALL_FREE, box_lo=0.5, box_hi=2.0,
+def fit(pc, L, fs, onset, th0, thf, y, S, T, *, model=18, free_mask=None, box_lo=0.5, box_hi=2.0,
         step=0.05, tolx=1e-4, tolf=1e-4, seed=0, sac_index=0, nthreads=None):
-    """Multi-start parallel Nelder-Mead fit of one saccade (Algorithm 1)."""
+    """Multi-start parallel Nelder-Mead fit of one saccade (Algorithm 1) over
+    the search coordinates of the 18- or 9-parameter model (Sec. 2.2)."""
     pc, y = _f64(pc), _f64(y)
-    n = bin(int(free_mask)).count("1")
+    mask = _mask(model, free_mask)
+    n = bin(mask).count("1")
     if nthreads is None:
         nthreads = os.cpu_count() or 1
     bu = np.zeros((S, n))
     bf = np.zeros(S)
     it = np.zeros(S, dtype=np.int32)
     w = _i()
-    rc = _load().or_fit(_dptr(pc), int(free_mask), int(L), float(fs), int(onset), float(th0),
+    rc = _load().or_fit(_dptr(pc), int(model), mask, int(L), float(fs), int(onset), float(th0),
                         float(thf), _dptr(y), int(S), int(T), float(box_lo), float(box_hi),
                         float(step), float(tolx), float(tolf), int(seed), int(sac_index),
                         int(nthreads), _dptr(bu), _dptr(bf), it.ctypes.data_as(_ip),
@@ -258,24 +271,29 @@ def fit(pc, L, fs, onset, th0, thf, y, S, T, *, free_mask=ALL_FREE, box_lo=0.5, 
     if rc != 0:
         raise ValueError("bad fit arguments")
     win = w.value
-    p = u_to_p(pc, bu[win], free_mask, box_lo, box_hi)
+    p = u_to_p(pc, bu[win], model=model, free_mask=mask, box_lo=box_lo, box_hi=box_hi)
     mse, mae = errors(p, L, fs, onset, th0, thf, y)
     return {"u": bu[win].copy(), "p": p, "f": float(bf[win]), "rms": float(np.sqrt(mse)),
             "l1": float(mae), "winner": win, "iters": it, "best_f_all": bf, "best_u_all": bu}
 
 
-def score(pc, L, fs, onset, th0, thf, y, u, *, free_mask=ALL_FREE, box_lo=0.5, box_hi=2.0):
+def score(pc, L, fs, onset, th0, thf, y, u, *, model=18, free_mask=None, box_lo=0.5, box_hi=2.0):
     pc, y, u = _f64(pc), _f64(y), _f64(u)
     m = u.shape[0]
     f = np.zeros(m)
-    _load().or_score(_dptr(pc), int(free_mask), int(L), float(fs), int(onset), float(th0),
-                     float(thf), _dptr(y), float(box_lo), float(box_hi), _dptr(u), m, _dptr(f))
+    rc = _load().or_score(_dptr(pc), int(model), _mask(model, free_mask), int(L), float(fs), int(onset),
+                          float(th0), float(thf), _dptr(y), float(box_lo), float(box_hi), _dptr(u), m, _dptr(f))
+    if rc != 0:
+        raise ValueError("bad score arguments")
     return f
 
 
-def u_to_p(pc, u, free_mask=ALL_FREE, box_lo=0.5, box_hi=2.0) -> np.ndarray:
+def u_to_p(pc, u, *, model=18, free_mask=None, box_lo=0.5, box_hi=2.0) -> np.ndarray:
+    """Full OPC vector of search point u (the objective's clamp applied)."""
     pc, u = _f64(pc), _f64(u)
     p = np.zeros(NP)
-    _load().or_u_to_p(_dptr(pc), int(free_mask), float(box_lo), float(box_hi), _dptr(u),
-                      _dptr(p))
+    rc = _load().or_u_to_p(_dptr(pc), int(model), _mask(model, free_mask), float(box_lo), float(box_hi),
+                           _dptr(u), _dptr(p))
+    if rc != 0:
+        raise ValueError("bad model or centre")
     return p

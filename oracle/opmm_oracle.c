@@ -640,9 +640,40 @@ int or_nm_one_step_testfn(int id, int n, double* verts, double* fvals) {
 /* ------------------------------------------------------------------------ */
 /* OPMM objective in log-parameter coordinates                               */
 /* ------------------------------------------------------------------------ */
+/* Search coordinates of the 9-parameter model (Sec. 2.2.2, Table 2), in the
+ * table's order: K_SE (both muscles), K_LT (both), B_AG, B_ANT, B_P, N_C_AG,
+ * N_C_ANT, J, N_C_FIX.  The model shares one series elasticity and one
+ * length-tension coefficient between the muscles and does not estimate the
+ * neural control signal.  For each OPC entry (Fig. 4 order) the model
+ * coordinate that scales it, or -1 for the entries held at the box centre
+ * (activation and deactivation times, pulse heights, pulse width). */
+static const int kModel9Coord[NP] = {0, 0, 1, 1, 5, 6, 4, 2, 3, 7, -1, -1, -1, -1, 8, -1, -1, -1};
+
+/* Coordinate map of a model: coord[j] = the search coordinate that scales OPC
+ * entry j, or -1 (held at the centre).  free_mask selects, among the model's
+ * own parameters (18: the OPC entries; 9: the Table 2 entries in order), those
+ * estimated.  A 9-parameter centre must give both muscles the same series
+ * elasticity and the same length-tension coefficient.  Returns the search
+ * dimension n, or -1 for an unknown model or an untied centre. */
+static int model_map(int model, uint32_t free_mask, const double* pc, int* coord) {
+  int n = 0;
+  if (model == 18) {
+    for (int j = 0; j < NP; ++j) coord[j] = (free_mask >> j & 1u) ? n++ : -1;
+    return n;
+  }
+  if (model == 9) {
+    if (pc && (pc[0] != pc[1] || pc[2] != pc[3])) return -1;
+    int idx[9];
+    for (int i = 0; i < 9; ++i) idx[i] = (free_mask >> i & 1u) ? n++ : -1;
+    for (int j = 0; j < NP; ++j) coord[j] = kModel9Coord[j] < 0 ? -1 : idx[kModel9Coord[j]];
+    return n;
+  }
+  return -1;
+}
+
 typedef struct {
   const double* pc;        /* box centre (nominal OPC) [18] */
-  const int* free_idx;     /* free parameter indices [n] */
+  const int* coord;        /* search coordinate of each OPC entry, or -1 [18] */
   int n;
   double lnlo, lnhi;
   int L, onset;
@@ -650,14 +681,16 @@ typedef struct {
   const double* y;
 } opmm_ctx_t;
 
-/* p_j = pc_j exp(clamp(u_j)) for free j; fixed parameters stay at pc_j. */
+/* p_j = pc_j exp(clamp(u_coord(j))) for estimated entries; the others stay
+ * at pc_j. */
 static void u_to_p(const opmm_ctx_t* c, const double* u, double* p) {
   memcpy(p, c->pc, sizeof(double) * NP);
-  for (int i = 0; i < c->n; ++i) {
-    double v = u[i];
+  for (int j = 0; j < NP; ++j) {
+    if (c->coord[j] < 0) continue;
+    double v = u[c->coord[j]];
     if (v < c->lnlo) v = c->lnlo;
     if (v > c->lnhi) v = c->lnhi;
-    p[c->free_idx[i]] = c->pc[c->free_idx[i]] * exp(v);
+    p[j] = c->pc[j] * exp(v);
   }
 }
 
@@ -727,21 +760,22 @@ static void* fit_worker(void* arg) {
 
 /* Multi-start parallel NM fit of one recorded saccade.
  *   pc[18]      box centre (nominal OPC)
- *   free_mask   bit j set = parameter j is estimated
+ *   model       18 or 9 (the search coordinates, model_map)
+ *   free_mask   bit j set = the model's parameter j is estimated
  *   y[L]        recorded trace
  *   S, T        simplices, iteration cap
  * Outputs: per-simplex best value and vertex, iterations, and the index of
  * the winning simplex (lowest value, ties to the lowest index). */
-int or_fit(const double* pc, uint32_t free_mask, int L, double fs, int onset,
+int or_fit(const double* pc, int model, uint32_t free_mask, int L, double fs, int onset,
            double th0, double thf, const double* y, int S, int T, double box_lo,
            double box_hi, double step, double tolx, double tolf, uint64_t seed,
            uint32_t sac_index, int nthreads, double* best_u_all,
            double* best_f_all, int* iters_all, int* winner) {
-  int free_idx[NP], n = 0;
-  for (int j = 0; j < NP; ++j) if (free_mask >> j & 1u) free_idx[n++] = j;
+  int coord[NP];
+  const int n = model_map(model, free_mask, pc, coord);
   if (n < 1 || S < 1 || T < 0 || L < 1 || !(box_lo > 0.0) || !(box_hi >= box_lo))
     return -1;
-  opmm_ctx_t c = {pc, free_idx, n, log(box_lo), log(box_hi), L, onset, fs, th0, thf, y};
+  opmm_ctx_t c = {pc, coord, n, log(box_lo), log(box_hi), L, onset, fs, th0, thf, y};
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
   fit_job_t jobs[256];
@@ -763,21 +797,24 @@ int or_fit(const double* pc, uint32_t free_mask, int L, double fs, int onset,
 }
 
 /* Objective values at a list of points u[m][n] (grid search and scoring). */
-int or_score(const double* pc, uint32_t free_mask, int L, double fs, int onset,
+int or_score(const double* pc, int model, uint32_t free_mask, int L, double fs, int onset,
              double th0, double thf, const double* y, double box_lo,
              double box_hi, const double* u, int m, double* f) {
-  int free_idx[NP], n = 0;
-  for (int j = 0; j < NP; ++j) if (free_mask >> j & 1u) free_idx[n++] = j;
-  opmm_ctx_t c = {pc, free_idx, n, log(box_lo), log(box_hi), L, onset, fs, th0, thf, y};
+  int coord[NP];
+  const int n = model_map(model, free_mask, pc, coord);
+  if (n < 1) return -1;
+  opmm_ctx_t c = {pc, coord, n, log(box_lo), log(box_hi), L, onset, fs, th0, thf, y};
   for (int i = 0; i < m; ++i) f[i] = opmm_objective(u + (size_t)i * n, &c);
   return 0;
 }
 
 /* Full OPC vector at a point u (applies the same clamp as the objective). */
-void or_u_to_p(const double* pc, uint32_t free_mask, double box_lo, double box_hi,
-               const double* u, double* p) {
-  int free_idx[NP], n = 0;
-  for (int j = 0; j < NP; ++j) if (free_mask >> j & 1u) free_idx[n++] = j;
-  opmm_ctx_t c = {pc, free_idx, n, log(box_lo), log(box_hi), 0, 0, 0, 0, 0, NULL};
+int or_u_to_p(const double* pc, int model, uint32_t free_mask, double box_lo, double box_hi,
+              const double* u, double* p) {
+  int coord[NP];
+  const int n = model_map(model, free_mask, pc, coord);
+  if (n < 1) return -1;
+  opmm_ctx_t c = {pc, coord, n, log(box_lo), log(box_hi), 0, 0, 0, 0, 0, NULL};
   u_to_p(&c, u, p);
+  return 0;
 }
