@@ -203,9 +203,12 @@ def make_workload(name: str, rank: int, quick: bool):
     return w
 
 
-def workload_config(w, scaling_note: str):
-    return {"workload": w.name, "saccades": int(w.B), "candidates_per_iteration": int(w.candidates),
-            "iterations": int(w.iterations), "simplices_per_saccade": int(w.simplices),
+def workload_config(w, scaling_note: str, coords: int = 18):
+    """coords: search coordinates, 18 (the OPC entries) or 9 (the 9-parameter
+    model of Sec. 2.2.2, fitted to the same traces)."""
+    return {"workload": w.name + ("" if coords == 18 else "_9p"), "saccades": int(w.B),
+            "candidates_per_iteration": int(w.candidates), "iterations": int(w.iterations),
+            "search_coordinates": int(coords), "simplices_per_saccade": int(w.candidates // (coords + 4)),
             "sample_rates_hz": sorted({float(x) for x in w.fs}),
             "window_samples": [int(w.L.min()), int(w.L.max())],
             "pulse_init": "calibrated" if w.calibrated_pulse else "table1",
@@ -276,7 +279,7 @@ def run_ours(args, ws, rank, local):
     buf, offs = packed(traces)
     dev = torch.from_numpy(buf).cuda()
     batch_dev = G.make_batch(dev, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms, n_samples=w.L, offsets=offs)
-    opts = dict(candidates=w.candidates, iterations=w.iterations, seed=w.seed, pulse_init=pulse)
+    opts = dict(candidates=w.candidates, iterations=w.iterations, seed=w.seed, pulse_init=pulse, model=args.model)
     plan = G.Plan(ctx, batch_dev, **opts)
     info = plan.info()
     info["autotuner_probes"] = plan.tuning()
@@ -363,7 +366,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded OPMM-simulated saccades + Gaussian noise; no dataset)",
-        "config": workload_config(w, "L2 flushed (256 MB write) before every timed step"),
+        "config": workload_config(w, "L2 flushed (256 MB write) before every timed step", args.model),
         "impl": "ours",
         "saccades_fitted_per_s_at_0p1deg": fitted_all / (t_max * 1e-3),
         "fraction_fitted_at_0p1deg": fitted_rank / w.B,
@@ -386,10 +389,10 @@ def run_ours(args, ws, rank, local):
     }
     plan.destroy()
     plan_h.destroy()
-    if rank == 0 and ws == 1 and not args.no_surrogate and args.workload == "batch1024":
+    if rank == 0 and ws == 1 and not args.no_surrogate and args.workload == "batch1024" and args.model == 18:
         out["surrogate"] = surrogate_compare(G, ctx, args.quick)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget, model=args.model)
     G.opmm_destroy(ctx)
     return out
 
@@ -613,9 +616,10 @@ def run_serve(args):
 
 
 # ------------------------------------------------------------------ oracle arm
-def oracle_sample(w, budget_s: float, nthreads: int):
+def oracle_sample(w, budget_s: float, nthreads: int, model: int = 18):
     """Oracle fit of saccade 0 at the workload's full iteration cap on a
-    bounded number of simplices, sized to about budget_s of host time."""
+    bounded number of simplices, sized to about budget_s of host time, over
+    the model's search coordinates (18, or 9)."""
     import oracle as O
     i = 0
     A, D = float(w.amplitude[i]), float(w.dur_ms[i])
@@ -626,24 +630,25 @@ def oracle_sample(w, budget_s: float, nthreads: int):
     y = np.float32(O.simulate_rk4(ph, L, fs, on, th0, thf) + w.noise[i]).astype(np.float64)
     # probe: one simplex per thread, 2 iterations
     t0 = time.perf_counter()
-    O.fit(pn, L, fs, on, th0, thf, y, nthreads, 2, seed=w.seed, nthreads=nthreads)
+    nv, nt = model + 1, model + 4
+    O.fit(pn, L, fs, on, th0, thf, y, nthreads, 2, seed=w.seed, nthreads=nthreads, model=model)
     probe = time.perf_counter() - t0
-    per_sim = probe / (nthreads * (19 + 2 * 22)) * nthreads      # wall seconds per sim per thread
-    sims_per_simplex = 19 + 22 * w.iterations
-    S = int(max(nthreads, min(w.simplices, budget_s / (per_sim / nthreads * sims_per_simplex))))
+    per_sim = probe / (nthreads * (nv + 2 * nt)) * nthreads      # wall seconds per sim per thread
+    sims_per_simplex = nv + nt * w.iterations
+    S = int(max(nthreads, min(w.candidates // nt, budget_s / (per_sim / nthreads * sims_per_simplex))))
     S = max(nthreads, (S // nthreads) * nthreads)
     t0 = time.perf_counter()
-    r = O.fit(pn, L, fs, on, th0, thf, y, S, w.iterations, seed=w.seed, nthreads=nthreads)
+    r = O.fit(pn, L, fs, on, th0, thf, y, S, w.iterations, seed=w.seed, nthreads=nthreads, model=model)
     dt = time.perf_counter() - t0
-    sims = S * 19 + 22 * float(np.sum(r["iters"]))
+    sims = S * nv + nt * float(np.sum(r["iters"]))
     return sims, dt, S
 
 
-def cpu_baseline(w, budget_s=12.0):
+def cpu_baseline(w, budget_s=12.0, model=18):
     nthreads = os.cpu_count() or 1
-    sims, dt, S = oracle_sample(w, budget_s, nthreads)
+    sims, dt, S = oracle_sample(w, budget_s, nthreads, model)
     return {"value": sims / dt, "unit": "candidate sims/s", "cores": nthreads, "kind": "oracle",
-            "sample": f"saccade 0 of {w.name}: {S} of {w.simplices} simplices x {w.iterations} "
+            "sample": f"saccade 0 of {w.name}: {S} of {w.candidates // (model + 4)} simplices x {w.iterations} "
                       f"iterations ({int(sims)} simulations, {dt:.1f} s, FP64 RK4 stages)"}
 
 
@@ -654,10 +659,10 @@ def run_reference(args, ws, rank):
     nthreads = os.cpu_count() or 1
     budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample(w, budget / 2, nthreads)
+        oracle_sample(w, budget / 2, nthreads, args.model)
     tot_sims, tot_t, S = 0.0, 0.0, 0
     for _ in range(args.steps):
-        sims, dt, S = oracle_sample(w, budget, nthreads)
+        sims, dt, S = oracle_sample(w, budget, nthreads, args.model)
         tot_sims += sims
         tot_t += dt
     v = tot_sims / tot_t
@@ -666,7 +671,7 @@ def run_reference(args, ws, rank):
         "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded OPMM-simulated saccades + Gaussian noise; no dataset)",
-        "config": workload_config(w, "CPU run"), "impl": "reference",
+        "config": workload_config(w, "CPU run", args.model), "impl": "reference",
         "cpu_baseline": {"value": v, "unit": "candidate sims/s", "cores": nthreads, "kind": "oracle",
                          "sample": f"per step: saccade 0 of {w.name}, {S} simplices x {w.iterations} iterations"},
         "e2e": {"value": v, "unit": "candidate sims/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -686,9 +691,13 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--serve-slots", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="small batch (smoke of the bench itself)")
+    ap.add_argument("--model", type=int, default=18, choices=[18, 9],
+                    help="search coordinates: the 18-parameter OPMM or the 9-parameter model (Sec. 2.2.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
+    if args.model == 9 and args.workload in ("serve", "surrogate"):
+        ap.error("--model 9 applies to the batched fit workloads (the request loop and the surrogate are 18-parameter)")
     if args.warmup < 3 and not args.quick:
         args.warmup = 3
     ws, rank, local = dist_setup(args.gpus)

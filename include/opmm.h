@@ -50,6 +50,17 @@ extern "C" {
 
 #define OPMM_NPARAM 18
 #define OPMM_MODEL_18 18     /* the 18-parameter OPMM (Sec. 2.2.1) */
+/* The 9-parameter OPMM (Sec. 2.2.2, Table 2) on the same plant: nine search
+ * coordinates in Table 2's order (K_SE, K_LT, B_AG, B_ANT, B_P, N_C_AG,
+ * N_C_ANT, J, N_C_FIX).  The shared K_SE scales K_SE_AG and K_SE_ANT, the
+ * shared K_LT scales K_LT_AG and K_LT_ANT; the neural control signal
+ * (activation and deactivation times, pulse heights, pulse width) is not
+ * estimated and stays at the box centre.  A simplex has 10 vertices and an
+ * iteration evaluates 13 trial points, so candidates / 13 simplices run per
+ * saccade.  init_opc, when given, must have K_SE_AG == K_SE_ANT and
+ * K_LT_AG == K_LT_ANT.  Results are full 18-entry OPC vectors.  Not available
+ * with use_surrogate, the request loop or opmm_fit_saccade_static. */
+#define OPMM_MODEL_9 9
 
 /* How the box centre (initial OPC vector) is chosen when the caller gives none
  * (Sec. 2.3: the estimator starts from model defaults culled from literature). */
@@ -79,11 +90,12 @@ typedef struct {
 
 /* Estimator settings (Sec. 2.3, Algorithm 1). */
 typedef struct {
-  int32_t model;             /* OPMM_MODEL_18 */
+  int32_t model;             /* OPMM_MODEL_18 or OPMM_MODEL_9 */
   int32_t candidates;        /* trial points per iteration per saccade; the
                                 estimator runs candidates / 22 independent
                                 simplices (each iteration of one simplex
-                                evaluates its 18 + 4 trial points at once) */
+                                evaluates its 18 + 4 trial points at once;
+                                candidates / 13 with OPMM_MODEL_9) */
   int32_t iterations;        /* iteration cap per simplex (>= 0) */
   float box_lo, box_hi;      /* search box: centre * [box_lo, box_hi], 0 < lo <= 1 <= hi */
   float init_step;           /* initial simplex edge in ln-parameter units (e.g. 0.05) */
@@ -136,10 +148,15 @@ int opmm_set_stream(opmm_ctx* ctx, void* cuda_stream);
 
 /* Launch-shape override for the search kernel (tuning and testing): variant
  * in [0, count) from opmm_search_variants, or -1 (default) to let plans pick
- * by timing.  All variants compute the same estimator; they differ in
- * simplices per block, register budget and register-lean scheduling. */
+ * by timing.  All variants of a model compute the same estimator; they differ
+ * in simplices per block, register budget and register-lean scheduling. */
 int opmm_set_search_variant(opmm_ctx* ctx, int32_t variant);
 int opmm_search_variants(int32_t* count);
+/* Shape of search variant `variant`: simplices per block and the model whose
+ * search coordinates it runs (OPMM_MODEL_18 or OPMM_MODEL_9; a forced variant
+ * applies to fits of that model only).  Either output may be NULL.
+ * OPMM_EINVAL for a variant out of range. */
+int opmm_search_variant_info(int32_t variant, int32_t* simplices_per_block, int32_t* model);
 
 /* ------------------------------------------------------------ plant */
 

@@ -28,6 +28,7 @@ OPMM_ETIMEDOUT = -4
 OPMM_EBUSY = -5
 OPMM_NPARAM = 18
 OPMM_MODEL_18 = 18
+OPMM_MODEL_9 = 9
 OPMM_PULSE_TABLE1 = 0
 OPMM_SOURCE_PLAIN, OPMM_SOURCE_SEEDED, OPMM_SOURCE_FALLBACK = 0, 1, 2
 OPMM_PULSE_CALIBRATED = 1
@@ -112,6 +113,7 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_set_stream.argtypes = [vp, vp]
     lib.opmm_set_search_variant.argtypes = [vp, i32]
     lib.opmm_search_variants.argtypes = [ctypes.POINTER(i32)]
+    lib.opmm_search_variant_info.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.opmm_simulate.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), i32, vp, i64p, vp]
     lib.opmm_score.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), vp]
     lib.opmm_nominal_opc.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
@@ -238,9 +240,9 @@ def make_batch(traces, sample_rate_hz, onset_index, theta_start_deg, theta_end_d
 
 def fit_opts(candidates=4096, iterations=20, box_lo=0.5, box_hi=2.0, init_step=0.05, tol_x=1e-4,
              tol_f=1e-4, seed=0, pulse_init=OPMM_PULSE_CALIBRATED, use_surrogate=False,
-             init_opc=None):
+             init_opc=None, model=OPMM_MODEL_18):
     o = opmm_fit_opts()
-    o.model = OPMM_MODEL_18
+    o.model = int(model)
     o.candidates, o.iterations = int(candidates), int(iterations)
     o.box_lo, o.box_hi, o.init_step = float(box_lo), float(box_hi), float(init_step)
     o.tol_x, o.tol_f, o.seed = float(tol_x), float(tol_f), int(seed)
@@ -301,6 +303,15 @@ def opmm_search_variants() -> int:
     n = ctypes.c_int32()
     load_library().opmm_search_variants(ctypes.byref(n))
     return int(n.value)
+
+
+def opmm_search_variant_info(variant: int):
+    """(simplices per block, model) of a search variant."""
+    g, m = ctypes.c_int32(), ctypes.c_int32()
+    rc = load_library().opmm_search_variant_info(int(variant), ctypes.byref(g), ctypes.byref(m))
+    if rc != OPMM_OK:
+        raise OpmmError(rc, "search variant out of range")
+    return int(g.value), int(m.value)
 
 
 def opmm_simulate(ctx, opc, batch: SaccadeBatch, sac_index=None, out=None):

@@ -229,6 +229,13 @@ extern "C" int opmm_search_variants(int32_t* count) {
   return OPMM_OK;
 }
 
+extern "C" int opmm_search_variant_info(int32_t variant, int32_t* simplices_per_block, int32_t* model) {
+  if (variant < 0 || variant >= search_variant_count()) return OPMM_EINVAL;
+  if (simplices_per_block) *simplices_per_block = search_variant_g(variant);
+  if (model) *model = search_variant_dim(variant) == 9 ? OPMM_MODEL_9 : OPMM_MODEL_18;
+  return OPMM_OK;
+}
+
 extern "C" int opmm_set_stream(opmm_ctx* ctx, void* stream) {
   if (!ctx) return OPMM_EINVAL;
   ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
@@ -372,9 +379,16 @@ extern "C" int opmm_nominal_opc(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t
 }
 
 // ------------------------------------------------------------------ plans
+// Search coordinates of a model: 18 (the OPC entries) or 9 (Table 2).
+static int model_dim(int32_t model) { return model == OPMM_MODEL_9 ? 9 : OPMM_NPARAM; }
+
 static Status check_opts(const opmm_fit_opts& o) {
-  if (o.model != OPMM_MODEL_18) return Status(OPMM_EINVAL, "only OPMM_MODEL_18 is implemented");
-  if (o.candidates < 22) return Status(OPMM_EINVAL, "candidates must be >= 22 (one simplex of 18 + 4 trial points)");
+  if (o.model != OPMM_MODEL_18 && o.model != OPMM_MODEL_9)
+    return Status(OPMM_EINVAL, "model must be OPMM_MODEL_18 or OPMM_MODEL_9");
+  if (o.model == OPMM_MODEL_9 && o.use_surrogate)
+    return Status(OPMM_EINVAL, "the surrogate estimates the 18-parameter model only");
+  if (o.candidates < model_dim(o.model) + 4)
+    return Status(OPMM_EINVAL, "candidates must cover one simplex's n + 4 trial points (22, or 13 for OPMM_MODEL_9)");
   if (o.iterations < 0 || o.iterations > 1000000) return Status(OPMM_EINVAL, "iterations outside [0, 1e6]");
   if (!(o.box_lo > 0.0f) || !(o.box_lo <= 1.0f) || !(o.box_hi >= 1.0f) || !std::isfinite(o.box_hi))
     return Status(OPMM_EINVAL, "box must satisfy 0 < box_lo <= 1 <= box_hi");
@@ -453,7 +467,7 @@ Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
   }
   s = cuda_status(launch_finalize(p->d_sacs.as<DevSac>(), p->d_traces.as<float>(), p->d_pc.as<float>(),
                                   p->d_ustart.as<int>(), p->ngroups, p->d_unit_best.as<float>(), P.lnlo, P.lnhi, p->n,
-                                  p->d_results.as<opmm_fit_result>(), st),
+                                  p->d_results.as<opmm_fit_result>(), st, nullptr, p->dim),
                   "launch finalize");
   if (!s.ok()) return s;
   s = cuda_status(cudaMemcpyAsync(p->h_results.ptr, p->d_results.ptr, sizeof(opmm_fit_result) * (size_t)p->n,
@@ -467,9 +481,10 @@ Status enqueue_fit(opmm_plan* p, cudaStream_t st) {
 // threads = 22 G rounded to warps, register bound for MINB resident blocks) at
 // the occupancy the device allows for this trace capacity.  Returns (variant,
 // blocks per SM) pairs.
-static std::vector<std::pair<int, int>> shape_candidates(int lcap) {
+static std::vector<std::pair<int, int>> shape_candidates(int lcap, int dim) {
   std::vector<std::pair<int, int>> out;
   for (int v = 0; v < search_variant_count(); ++v) {
+    if (search_variant_dim(v) != dim) continue;
     int bps = 0;
     if (search_occupancy_v(v, lcap, &bps) != cudaSuccess) {
       cudaGetLastError();
@@ -486,9 +501,10 @@ static std::vector<std::pair<int, int>> shape_candidates(int lcap) {
 // bucket).  Results of probe runs are overwritten by the real run.
 static Status autotune(opmm_plan* p) {
   opmm_ctx* ctx = p->ctx;
-  const auto key = std::make_tuple(p->lcap, p->S, p->n >= 64 ? 64 : p->n, p->opts.iterations > 0 ? 1 : 0);
+  const auto key = std::make_tuple(p->lcap, p->S, p->n >= 64 ? 64 : p->n,
+                                   (p->opts.iterations > 0 ? 1 : 0) | (p->dim << 1));
   auto it = ctx->tune_cache.find(key);
-  auto cands = shape_candidates(p->lcap);
+  auto cands = shape_candidates(p->lcap, p->dim);
   if (cands.empty()) return Status(OPMM_ECUDA, "no launchable search shape (shared memory)");
   if (ctx->forced_variant >= 0) {
     for (auto& cd : cands)
@@ -497,7 +513,7 @@ static Status autotune(opmm_plan* p) {
         p->blocks_per_sm = cd.second;
         return Status();
       }
-    return Status(OPMM_EINVAL, "forced search variant cannot be launched with this batch");
+    return Status(OPMM_EINVAL, "forced search variant cannot be launched with this batch or model");
   }
   if (it != ctx->tune_cache.end()) {
     p->variant = it->second.first;
@@ -597,7 +613,8 @@ Status plan_stage(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm
   p->n = n;
   p->opts = o;
   p->opts.init_opc = nullptr;
-  p->S = o.candidates / (OPMM_NPARAM + 4);
+  p->dim = model_dim(o.model);
+  p->S = o.candidates / (p->dim + 4);
   p->centres_given = o.init_opc != nullptr;
   p->hsacs.resize((size_t)n);
   p->src.resize((size_t)n);
@@ -622,8 +639,15 @@ Status plan_stage(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm
       return Status(OPMM_EINVAL, "all traces of a batch must be host memory or all device memory");
   if (o.init_opc)
     for (int i = 0; i < n; ++i) {
-      s = check_opc(o.init_opc + (size_t)i * OPMM_NPARAM);
+      const float* c = o.init_opc + (size_t)i * OPMM_NPARAM;
+      s = check_opc(c);
       if (!s.ok()) return s;
+      // the 9-parameter model scales one shared series elasticity and one
+      // shared length-tension coefficient: the centre must give both muscles
+      // the same values
+      if (p->dim == 9 && (c[0] != c[1] || c[2] != c[3]))
+        return Status(OPMM_EINVAL, "saccade " + std::to_string(i) +
+                                       ": OPMM_MODEL_9 needs K_SE_AG == K_SE_ANT and K_LT_AG == K_LT_ANT in init_opc");
     }
   cudaStream_t st = ctx->stream;
   s = p->d_sacs.ensure(sizeof(DevSac) * (size_t)n);
@@ -696,7 +720,7 @@ Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm
   p->G = search_variant_g(p->variant);
   s = build_units(p, p->G);
   if (!s.ok()) return s;
-  p->threads = search_threads_for(p->G);
+  p->threads = search_variant_threads(p->variant);
   s = cuda_status(cudaEventCreate(&p->ev_search[0]), "event");
   if (s.ok()) s = cuda_status(cudaEventCreate(&p->ev_search[1]), "event");
   if (!s.ok()) return s;

@@ -271,14 +271,58 @@ __global__ void k_score(const float* opc, int m, const DevSac* sac, const float*
 // Unit record (kUnitRecFloats words): [0] best f, [1] winning simplex (int),
 // [2] its iterations (int), [3] candidate evaluations of the unit (int),
 // [4..21] best vertex (ln units), [22] evaluations whose pulse ends inside the
-// window (int), [23] unused.
+// window (int), [23] unused.  With the 9-parameter model the vertex takes
+// [4..12].
 constexpr int kUnitRec = kUnitRecFloats;
-constexpr int kNV = kNumParams + 1;      // vertices per simplex
-constexpr int kNT = kNumParams + 4;      // trial points per simplex and iteration
 constexpr int kSortBins = 512;           // pulse-end time bins of the per-wave ordering
+
+// The search runs over N coordinates: N = 18, the OPC entries themselves, or
+// N = 9, the 9-parameter model (Sec. 2.2.2, Table 2).  A simplex has N + 1
+// vertices and each iteration N + 4 trial points.
+template <int N>
+__host__ __device__ constexpr int verts() { return N + 1; }
+template <int N>
+__host__ __device__ constexpr int trials() { return N + 4; }
+
+// Search coordinate that scales OPC entry j (Fig. 4 order): j itself for N =
+// 18; for N = 9 the coordinate of the Table 2 quantity the entry carries, in
+// the table's order (K_SE, K_LT, B_AG, B_ANT, B_P, N_C_AG, N_C_ANT, J,
+// N_C_FIX; the shared series elasticity and length-tension coefficient scale
+// both muscles' entries), or -1 for the neural control signal, which that
+// model does not estimate (activation and deactivation times, pulse heights
+// and width stay at the box centre).
+template <int N>
+__host__ __device__ constexpr int search_coord(int j) {
+  if (N == kNumParams) return j;
+  switch (j) {
+    case kSeAg: case kSeAnt: return 0;
+    case kLtAg: case kLtAnt: return 1;
+    case kBAg: return 2;
+    case kBAnt: return 3;
+    case kBp: return 4;
+    case kNcAg: return 5;
+    case kNcAnt: return 6;
+    case kJ: return 7;
+    case kNcFix: return 8;
+    default: return -1;
+  }
+}
+
+// OPC vector of search point u: p_j = pc_j exp(clamp(u_c)) for c =
+// search_coord(j) >= 0, else pc_j.
+template <int N>
+__device__ __forceinline__ void u_to_p(const float* u, const float* pc, float lnlo, float lnhi, float (&p)[kNumParams]) {
+#pragma unroll
+  for (int j = 0; j < kNumParams; ++j) {
+    const int c = search_coord<N>(j);
+    p[j] = c < 0 ? pc[j] : pc[j] * __expf(fminf(fmaxf(u[c < 0 ? 0 : c], lnlo), lnhi));
+  }
+}
+
 // Saved simplex (serving): vertices, values, centroid, order, active, iterations.
-constexpr int kStateFloats = kNV * kNumParams + kNV + kNumParams + kNV + 2;
-static_assert(kStateFloats == kSearchStateFloats, "saved simplex layout");
+template <int N>
+__host__ __device__ constexpr int state_floats() { return verts<N>() * N + verts<N>() + N + verts<N>() + 2; }
+static_assert(state_floats<kNumParams>() == kSearchStateFloats, "saved simplex layout");
 constexpr int kHistPer = kSortBins / 32;              // bins per lane of the scanning warp
 constexpr int kHistLen = kSortBins + 32;                // bin b stored at b + b / kHistPer
 
@@ -293,22 +337,26 @@ constexpr int kHistLen = kSortBins + 32;                // bin b stored at b + b
 // taken in chunks of 32 candidates that the evaluation warps pull in turn, so
 // that warps sharing a sub-partition with fewer others take more chunks.
 constexpr int kMaxEvalThreads = 352;
-template <int G>
+template <int G, int N>
 __host__ __device__ constexpr int search_eval_threads() {
-  return ((G * kNT + 31) / 32) * 32 < kMaxEvalThreads ? ((G * kNT + 31) / 32) * 32 : kMaxEvalThreads;
+  return ((G * trials<N>() + 31) / 32) * 32 < kMaxEvalThreads ? ((G * trials<N>() + 31) / 32) * 32 : kMaxEvalThreads;
 }
-template <int G>
-__host__ __device__ constexpr int search_threads() { return search_eval_threads<G>() + 32; }
+template <int G, int N>
+__host__ __device__ constexpr int search_threads() { return search_eval_threads<G, N>() + 32; }
 // candidates per evaluation thread in one wave (ordering)
-template <int G>
-__host__ __device__ constexpr int wave_per_thread() { return (G * kNT + search_eval_threads<G>() - 1) / search_eval_threads<G>(); }
+template <int G, int N>
+__host__ __device__ constexpr int wave_per_thread() {
+  return (G * trials<N>() + search_eval_threads<G, N>() - 1) / search_eval_threads<G, N>();
+}
 
-// State of one group of G simplices.
-template <int G>
+// State of one group of G simplices over N coordinates.
+template <int G, int N>
 struct GroupSmem {
-  float U[G][kNV][kNumParams];   // vertices, by slot
-  float XT[G][4][kNumParams];    // reflection, expansion, outside/inside contraction
-  float XB[G][kNumParams];       // centroid of the best n vertices
+  static constexpr int kNV = verts<N>();
+  static constexpr int kNT = trials<N>();
+  float U[G][kNV][N];            // vertices, by slot
+  float XT[G][4][N];             // reflection, expansion, outside/inside contraction
+  float XB[G][N];                // centroid of the best n vertices
   float F[G][kNV];               // vertex values, by slot
   float FT[G][kNT];              // trial values
   int hist[kHistLen];            // counting sort of the pending wave by pulse-end time (padded)
@@ -331,9 +379,9 @@ struct GroupSmem {
 
 enum : int { kPending = 0, kDone = 2 };
 
-template <int G>
+template <int G, int N>
 struct SearchSmem {
-  GroupSmem<G> grp[2];
+  GroupSmem<G, N> grp[2];
   float pc[kNumParams];          // box centre of the current saccade
   SacConst sc;
   TraceStage st;
@@ -347,10 +395,10 @@ constexpr int kQSlotFloats = (int)(sizeof(Prop2) / sizeof(float));
 
 // Dynamic shared memory: the block state, the raw and shifted traces (lcap
 // floats each) and one single-substep propagator slot per evaluation thread.
-template <int G>
+template <int G, int N>
 size_t search_smem_bytes(int lcap) {
-  return ((sizeof(SearchSmem<G>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float) +
-         (size_t)kQSlotFloats * search_eval_threads<G>() * sizeof(float);
+  return ((sizeof(SearchSmem<G, N>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float) +
+         (size_t)kQSlotFloats * search_eval_threads<G, N>() * sizeof(float);
 }
 
 // Trial point coordinate (Lagarias et al. coefficients rho 1, chi 2, gamma 1/2).
@@ -391,12 +439,12 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
   return isfinite(f) ? f : INFINITY;
 }
 
-__device__ __forceinline__ float eval_u(const float (&u)[kNumParams], const float* pc, float lnlo,
+template <int N>
+__device__ __forceinline__ float eval_u(const float (&u)[N], const float* pc, float lnlo,
                                         float lnhi, const SacConst& sc, const float* z, float sum0,
                                         float c0, float* qs, int qstride, int* pe) {
   float p[kNumParams];
-#pragma unroll
-  for (int j = 0; j < kNumParams; ++j) p[j] = pc[j] * __expf(fminf(fmaxf(u[j], lnlo), lnhi));
+  u_to_p<N>(u, pc, lnlo, lnhi, p);
   return objective(p, sc, z, sum0, c0, qs, qstride, pe);
 }
 
@@ -418,8 +466,8 @@ __device__ __forceinline__ int hist_slot(int b) { return b + b / kHistPer; }
 // coordinate: a = b = the controller's XT row for q < 4 (so u = a exactly),
 // the best vertex and vertex q - 3 for the shrink points.  One form for every
 // lane, so a warp holding both kinds does not diverge.
-template <int G>
-__device__ __forceinline__ void trial_rows(const GroupSmem<G>& g, int gi, int q, const float*& a, const float*& b) {
+template <int G, int N>
+__device__ __forceinline__ void trial_rows(const GroupSmem<G, N>& g, int gi, int q, const float*& a, const float*& b) {
   const unsigned char* o = g.ord[gi];
   a = q < 4 ? g.XT[gi][q] : g.U[gi][o[0]];
   b = q < 4 ? g.XT[gi][q] : g.U[gi][o[q - 3]];
@@ -436,12 +484,13 @@ __device__ __forceinline__ void eval_sync() {
 // candidates t, t + NE, ..., one warp scans the histogram (cleared by the
 // controller when it set the wave up), and afterwards g.perm[0 .. g.nvalid)
 // lists the candidates in key order.
-template <int G>
-__device__ __forceinline__ void order_wave(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P, int tid) {
-  constexpr int NE = search_eval_threads<G>();
-  constexpr int R = wave_per_thread<G>();
-  static_assert(G * kNT <= NE * R, "every candidate keyed");
-  const int ncand = (g.kind == 0 ? kNV : kNT) * g.nsim;
+template <int G, int N>
+__device__ __forceinline__ void order_wave(GroupSmem<G, N>& g, const SearchSmem<G, N>& S, const SearchParams& P, int tid) {
+  constexpr int NE = search_eval_threads<G, N>();
+  constexpr int R = wave_per_thread<G, N>();
+  static_assert(G * trials<N>() <= NE * R, "every candidate keyed");
+  constexpr int kPwCoord = search_coord<N>(kPw);   // -1: pulse width held at the centre
+  const int ncand = (g.kind == 0 ? verts<N>() : trials<N>()) * g.nsim;
   int key[R], slot[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -450,15 +499,17 @@ __device__ __forceinline__ void order_wave(GroupSmem<G>& g, const SearchSmem<G>&
     slot[r] = 0;
     if (c < ncand) {
       if (g.kind == 0) {
-        const int gi = c / kNV, v = c - gi * kNV;
-        key[r] = switch_key(g.U[gi][v][kPw], S.pc[kPw], P.lnlo, P.lnhi, S.sc);
+        const int gi = c / verts<N>(), v = c - gi * verts<N>();
+        key[r] = switch_key(kPwCoord < 0 ? 0.0f : g.U[gi][v][kPwCoord < 0 ? 0 : kPwCoord], S.pc[kPw], P.lnlo,
+                            P.lnhi, S.sc);
       } else {
-        const int gi = c / kNT, q = c - gi * kNT;
+        const int gi = c / trials<N>(), q = c - gi * trials<N>();
         if (g.active[gi]) {
           const float* a;
           const float* bb;
           trial_rows(g, gi, q, a, bb);
-          key[r] = switch_key(shrink_coord(a[kPw], bb[kPw]), S.pc[kPw], P.lnlo, P.lnhi, S.sc);
+          const int jp = kPwCoord < 0 ? 0 : kPwCoord;
+          key[r] = switch_key(kPwCoord < 0 ? 0.0f : shrink_coord(a[jp], bb[jp]), S.pc[kPw], P.lnlo, P.lnhi, S.sc);
         }
       }
       if (key[r] >= 0) slot[r] = atomicAdd(&g.hist[hist_slot(key[r])], 1);
@@ -506,69 +557,69 @@ __device__ __forceinline__ void order_wave(GroupSmem<G>& g, const SearchSmem<G>&
 // the controller warp's lanes by (simplex, coordinate); `sel` picks the
 // simplices to process.  g.okx[gi] must be 1 on entry and is cleared by any
 // coordinate that fails.
-template <int G, class Sel>
-__device__ __forceinline__ void centroids(GroupSmem<G>& g, int lane, float tolx, Sel sel) {
-  for (int p = lane; p < g.nsim * kNumParams; p += 32) {
-    const int gi = p / kNumParams, j = p - gi * kNumParams;
+template <int G, int N, class Sel>
+__device__ __forceinline__ void centroids(GroupSmem<G, N>& g, int lane, float tolx, Sel sel) {
+  for (int p = lane; p < g.nsim * N; p += 32) {
+    const int gi = p / N, j = p - gi * N;
     if (!sel(gi)) continue;
     const unsigned char* o = g.ord[gi];
-    float x[kNV];
+    float x[verts<N>()];
 #pragma unroll
-    for (int r = 0; r < kNV; ++r) x[r] = g.U[gi][o[r]][j];
+    for (int r = 0; r < verts<N>(); ++r) x[r] = g.U[gi][o[r]][j];
     float acc = 0.0f;
     bool ok = true;
 #pragma unroll
-    for (int r = 0; r < kNumParams; ++r) acc += x[r];
+    for (int r = 0; r < N; ++r) acc += x[r];
 #pragma unroll
-    for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(x[r] - x[0]) <= tolx);
-    g.XB[gi][j] = acc / (float)kNumParams;
+    for (int r = 1; r < verts<N>(); ++r) ok = ok && (fabsf(x[r] - x[0]) <= tolx);
+    g.XB[gi][j] = acc / (float)N;
     if (!ok) g.okx[gi] = 0;
   }
 }
 
 // Stable ranking of 19 values by one thread: rank[r] = #{s : v_s < v_r or
 // (v_s == v_r and s < r)}; the slots are written to ord in rank order.
-template <int G>
-__device__ __forceinline__ void rank_simplex(GroupSmem<G>& g, int gi, const int (&sl)[kNV], const float (&fv)[kNV]) {
+template <int G, int N>
+__device__ __forceinline__ void rank_simplex(GroupSmem<G, N>& g, int gi, const int (&sl)[verts<N>()], const float (&fv)[verts<N>()]) {
 #pragma unroll
-  for (int r = 0; r < kNV; ++r) {
+  for (int r = 0; r < verts<N>(); ++r) {
     int rank = 0;
 #pragma unroll
-    for (int t = 0; t < kNV; ++t) rank += (fv[t] < fv[r] || (fv[t] == fv[r] && t < r)) ? 1 : 0;
+    for (int t = 0; t < verts<N>(); ++t) rank += (fv[t] < fv[r] || (fv[t] == fv[r] && t < r)) ? 1 : 0;
     g.ord[gi][rank] = (unsigned char)sl[r];
   }
 }
 
 // Value spread within tol_f (the other half of the exit test) from the ranked
 // values in ord.
-template <int G>
-__device__ __forceinline__ int value_spread_ok(const GroupSmem<G>& g, int gi, float tolf) {
+template <int G, int N>
+__device__ __forceinline__ int value_spread_ok(const GroupSmem<G, N>& g, int gi, float tolf) {
   const float f0 = g.F[gi][g.ord[gi][0]];
   bool ok = true;
 #pragma unroll
-  for (int r = 1; r < kNV; ++r) ok = ok && (fabsf(g.F[gi][g.ord[gi][r]] - f0) <= tolf);
+  for (int r = 1; r < verts<N>(); ++r) ok = ok && (fabsf(g.F[gi][g.ord[gi][r]] - f0) <= tolf);
   return ok ? 1 : 0;
 }
 
 // Ranking and first centroid of freshly evaluated initial simplices.
-template <int G>
-__device__ __forceinline__ void init_rank(GroupSmem<G>& g, int lane, float tolx, float tolf) {
+template <int G, int N>
+__device__ __forceinline__ void init_rank(GroupSmem<G, N>& g, int lane, float tolx, float tolf) {
   for (int gi = lane; gi < g.nsim; gi += 32) {
-    int sl[kNV];
-    float fv[kNV];
+    int sl[verts<N>()];
+    float fv[verts<N>()];
 #pragma unroll
-    for (int r = 0; r < kNV; ++r) {
+    for (int r = 0; r < verts<N>(); ++r) {
       sl[r] = r;
       fv[r] = g.F[gi][r];
     }
-    rank_simplex<G>(g, gi, sl, fv);
+    rank_simplex<G, N>(g, gi, sl, fv);
     g.active[gi] = 1;
     g.iters[gi] = 0;
     g.okx[gi] = 1;
-    g.okf[gi] = value_spread_ok<G>(g, gi, tolf);
+    g.okf[gi] = value_spread_ok<G, N>(g, gi, tolf);
   }
   __syncwarp();
-  centroids<G>(g, lane, tolx, [](int) { return true; });
+  centroids<G, N>(g, lane, tolx, [](int) { return true; });
   __syncwarp();
   for (int gi = lane; gi < g.nsim; gi += 32)
     if (g.okx[gi] && g.okf[gi]) g.active[gi] = 0;
@@ -579,21 +630,21 @@ __device__ __forceinline__ void init_rank(GroupSmem<G>& g, int lane, float tolx,
 // trial wave.  One lane per simplex takes the decision (the slots and values
 // of its 19 vertices in registers, in rank order) and applies a replacement;
 // shrinks, centroids and the vertex-spread test are spread over all lanes.
-template <int G>
-__device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float tolx, float tolf) {
+template <int G, int N>
+__device__ __forceinline__ void decide_group(GroupSmem<G, N>& g, int lane, float tolx, float tolf) {
   for (int gi = lane; gi < g.nsim; gi += 32) {
     g.shr[gi] = 0;
     g.okx[gi] = 1;
     if (!g.active[gi]) continue;
     unsigned char* o = g.ord[gi];
-    int sl[kNV];
-    float fv[kNV];
+    int sl[verts<N>()];
+    float fv[verts<N>()];
 #pragma unroll
-    for (int r = 0; r < kNV; ++r) {
+    for (int r = 0; r < verts<N>(); ++r) {
       sl[r] = o[r];
       fv[r] = g.F[gi][sl[r]];
     }
-    const float f1 = fv[0], fn = fv[kNumParams - 1], fw = fv[kNumParams];
+    const float f1 = fv[0], fn = fv[N - 1], fw = fv[N];
     const float fr = g.FT[gi][0], fe = g.FT[gi][1], fco = g.FT[gi][2], fci = g.FT[gi][3];
     int kind;
     float fnew = 0.0f;
@@ -610,35 +661,35 @@ __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float to
     if (kind >= 0) {
       // replace the worst vertex; the new point goes after every vertex with
       // a value <= its own (ties stay in front of it)
-      const int ws = sl[kNumParams];
+      const int ws = sl[N];
 #pragma unroll
-      for (int j = 0; j < kNumParams; ++j) g.U[gi][ws][j] = g.XT[gi][kind][j];
+      for (int j = 0; j < N; ++j) g.U[gi][ws][j] = g.XT[gi][kind][j];
       g.F[gi][ws] = fnew;
       int pos = 0;
 #pragma unroll
-      for (int r = 0; r < kNumParams; ++r) pos += fv[r] <= fnew ? 1 : 0;
+      for (int r = 0; r < N; ++r) pos += fv[r] <= fnew ? 1 : 0;
 #pragma unroll
-      for (int r = kNumParams; r >= 1; --r)
+      for (int r = N; r >= 1; --r)
         if (r > pos) {
           sl[r] = sl[r - 1];
           fv[r] = fv[r - 1];
         }
 #pragma unroll
-      for (int r = 0; r < kNV; ++r)
+      for (int r = 0; r < verts<N>(); ++r)
         if (r == pos) {
           sl[r] = ws;
           fv[r] = fnew;
         }
 #pragma unroll
-      for (int r = 0; r < kNV; ++r) o[r] = (unsigned char)sl[r];
+      for (int r = 0; r < verts<N>(); ++r) o[r] = (unsigned char)sl[r];
       bool okf = true;
 #pragma unroll
-      for (int r = 1; r < kNV; ++r) okf = okf && (fabsf(fv[r] - fv[0]) <= tolf);
+      for (int r = 1; r < verts<N>(); ++r) okf = okf && (fabsf(fv[r] - fv[0]) <= tolf);
       g.okf[gi] = okf ? 1 : 0;
     } else {
       // shrink toward the best vertex: the values now, the coordinates below
 #pragma unroll
-      for (int r = 1; r < kNV; ++r) g.F[gi][sl[r]] = g.FT[gi][4 + r - 1];
+      for (int r = 1; r < verts<N>(); ++r) g.F[gi][sl[r]] = g.FT[gi][4 + r - 1];
       g.shr[gi] = 1;
     }
   }
@@ -650,8 +701,8 @@ __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float to
   for (unsigned m = smask; m; m &= m - 1) {
     const int gi = __ffs(m) - 1;
     const unsigned char* o = g.ord[gi];
-    for (int e = lane; e < kNumParams * kNumParams; e += 32) {
-      const int r = e / kNumParams + 1, j = e - (r - 1) * kNumParams;
+    for (int e = lane; e < N * N; e += 32) {
+      const int r = e / N + 1, j = e - (r - 1) * N;
       g.U[gi][o[r]][j] = shrink_coord(g.U[gi][o[0]][j], g.U[gi][o[r]][j]);
     }
   }
@@ -659,18 +710,18 @@ __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float to
   // stable re-sort of the shrunk simplices
   for (int gi = lane; gi < g.nsim; gi += 32) {
     if (!g.shr[gi]) continue;
-    int sl[kNV];
-    float fv[kNV];
+    int sl[verts<N>()];
+    float fv[verts<N>()];
 #pragma unroll
-    for (int r = 0; r < kNV; ++r) {
+    for (int r = 0; r < verts<N>(); ++r) {
       sl[r] = g.ord[gi][r];
       fv[r] = g.F[gi][sl[r]];
     }
-    rank_simplex<G>(g, gi, sl, fv);
-    g.okf[gi] = value_spread_ok<G>(g, gi, tolf);
+    rank_simplex<G, N>(g, gi, sl, fv);
+    g.okf[gi] = value_spread_ok<G, N>(g, gi, tolf);
   }
   __syncwarp();
-  centroids<G>(g, lane, tolx, [&](int gi) { return g.active[gi] != 0; });
+  centroids<G, N>(g, lane, tolx, [&](int gi) { return g.active[gi] != 0; });
   __syncwarp();
   for (int gi = lane; gi < g.nsim; gi += 32)
     if (g.active[gi] && g.okx[gi] && g.okf[gi]) g.active[gi] = 0;
@@ -683,8 +734,8 @@ __device__ __forceinline__ void decide_group(GroupSmem<G>& g, int lane, float to
 // iteration cap, is done.  The controller writes the four trial points
 // (reflection, expansion, both contractions) to XT; the 18 shrink points are
 // formed by the evaluation threads from the vertices.
-template <int G>
-__device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, int lane) {
+template <int G, int N>
+__device__ __forceinline__ void next_wave(GroupSmem<G, N>& g, int kind, int t_run, int lane) {
   int nact = 0;
   if (kind == 1) {
     for (int gi = 0; gi < g.nsim; ++gi) nact += g.active[gi];
@@ -699,17 +750,17 @@ __device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, 
   }
   for (int i = lane; i < kHistLen; i += 32) g.hist[i] = 0;
   if (kind == 1) {
-    for (int e = lane; e < g.nsim * 4 * kNumParams; e += 32) {
-      const int gi = e / (4 * kNumParams), r = e - gi * 4 * kNumParams;
-      const int q = r / kNumParams, j = r - q * kNumParams;
-      if (g.active[gi]) g.XT[gi][q][j] = trial_coord(q, g.XB[gi][j], g.U[gi][g.ord[gi][kNumParams]][j]);
+    for (int e = lane; e < g.nsim * 4 * N; e += 32) {
+      const int gi = e / (4 * N), r = e - gi * 4 * N;
+      const int q = r / N, j = r - q * N;
+      if (g.active[gi]) g.XT[gi][q][j] = trial_coord(q, g.XB[gi][j], g.U[gi][g.ord[gi][N]][j]);
     }
   }
   if (lane == 0) {
     g.kind = kind;
     g.chunk = 0;
     g.state = kPending;
-    if (kind == 1) g.evals += kNT * nact;
+    if (kind == 1) g.evals += trials<N>() * nact;
   }
   __syncwarp();
 }
@@ -718,51 +769,52 @@ __device__ __forceinline__ void next_wave(GroupSmem<G>& g, int kind, int t_run, 
 // wave; qs is the calling thread's propagator slot.  Returns 1 when that
 // candidate's pulse ends inside the window (its pulse-end sample was
 // integrated substep by substep), else 0 (also for pos past the wave).
-template <int G, bool LEAN>
-__device__ __forceinline__ int eval_candidate(GroupSmem<G>& g, const SearchSmem<G>& S, const SearchParams& P,
+template <int G, int N, bool LEAN>
+__device__ __forceinline__ int eval_candidate(GroupSmem<G, N>& g, const SearchSmem<G, N>& S, const SearchParams& P,
                                               const float* z, float* qs, int pos) {
-  constexpr int NE = search_eval_threads<G>();
+  constexpr int NE = search_eval_threads<G, N>();
   if (pos >= g.nvalid) return 0;
   int pe = 0;
   const SacConst& sc = S.sc;
   const float sum0 = S.st.sum0, c0 = S.st.c0;
   const int c = g.perm[pos];
+  static_assert(!LEAN || N == N, "register-lean walk: 18 coordinates only");
   if (g.kind == 0) {
-    const int gi = c / kNV, v = c - gi * kNV;
-    if (LEAN) {
+    const int gi = c / verts<N>(), v = c - gi * verts<N>();
+    if constexpr (LEAN) {
       const ULinSrc src{g.U[gi][v], g.U[gi][v], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
       g.F[gi][v] = objective_lean(src, sc, z, sum0, c0, &pe);
     } else {
-      float u[kNumParams];
+      float u[N];
 #pragma unroll
-      for (int j = 0; j < kNumParams; ++j) u[j] = g.U[gi][v][j];
+      for (int j = 0; j < N; ++j) u[j] = g.U[gi][v][j];
       g.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE, &pe);
     }
     return pe;
   }
-  const int gi = c / kNT, q = c - gi * kNT;
+  const int gi = c / trials<N>(), q = c - gi * trials<N>();
   const float* a;
   const float* bb;
   trial_rows(g, gi, q, a, bb);
-  if (LEAN) {
+  if constexpr (LEAN) {
     const ULinSrc src{a, bb, 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
     g.FT[gi][q] = objective_lean(src, sc, z, sum0, c0, &pe);
   } else {
-    float u[kNumParams];
+    float u[N];
 #pragma unroll
-    for (int j = 0; j < kNumParams; ++j) u[j] = shrink_coord(a[j], bb[j]);
+    for (int j = 0; j < N; ++j) u[j] = shrink_coord(a[j], bb[j]);
     g.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE, &pe);
   }
   return pe;
 }
 
-template <int G, int MINB, bool LEAN>
-__global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchParams P) {
-  constexpr int NT = search_threads<G>();
-  constexpr int NE = search_eval_threads<G>();
+template <int G, int N, int MINB, bool LEAN>
+__global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchParams P) {
+  constexpr int NT = search_threads<G, N>();
+  constexpr int NE = search_eval_threads<G, N>();
   extern __shared__ __align__(128) unsigned char smraw[];
-  SearchSmem<G>& S = *reinterpret_cast<SearchSmem<G>*>(smraw);
-  float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G>) + 127) / 128) * 128);
+  SearchSmem<G, N>& S = *reinterpret_cast<SearchSmem<G, N>*>(smraw);
+  float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G, N>) + 127) / 128) * 128);
   float* z = yraw + P.lcap;
   float* qslot = z + P.lcap;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -814,7 +866,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     const int it0 = P.state ? P.progress[b] : 0;
     const int t_run = P.state ? min(P.round_iters, P.T - it0) : P.T;
     if (tid < 2) {
-      GroupSmem<G>& g = S.grp[tid];
+      GroupSmem<G, N>& g = S.grp[tid];
       g.nsim = tid == 0 ? nA : nunit - nA;
       g.it = 0;
       g.evals = 0;
@@ -824,24 +876,25 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     }
     if (it0 > 0) {
       // restore the simplices: vertices, values, centroid, order, flags
-      const float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * kStateFloats;
-      for (int idx = tid; idx < nunit * kStateFloats; idx += NT) {
-        const int sg = idx / kStateFloats, r = idx - sg * kStateFloats;
-        GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+      const float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * state_floats<N>();
+      for (int idx = tid; idx < nunit * state_floats<N>(); idx += NT) {
+        const int sg = idx / state_floats<N>(), r = idx - sg * state_floats<N>();
+        GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
         const int gi = sg < nA ? sg : sg - nA;
         const float v = gstate[idx];
-        if (r < kNV * kNumParams) (&g.U[gi][0][0])[r] = v;
-        else if (r < kNV * kNumParams + kNV) g.F[gi][r - kNV * kNumParams] = v;
-        else if (r < kNV * kNumParams + kNV + kNumParams) g.XB[gi][r - kNV * kNumParams - kNV] = v;
-        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) g.ord[gi][r - kNV * kNumParams - kNV - kNumParams] = (unsigned char)__float_as_int(v);
-        else if (r == kStateFloats - 2) g.active[gi] = __float_as_int(v);
-        else if (r == kStateFloats - 1) g.iters[gi] = __float_as_int(v);
+        if (r < verts<N>() * N) (&g.U[gi][0][0])[r] = v;
+        else if (r < verts<N>() * N + verts<N>()) g.F[gi][r - verts<N>() * N] = v;
+        else if (r < verts<N>() * N + verts<N>() + N) g.XB[gi][r - verts<N>() * N - verts<N>()] = v;
+        else if (r < verts<N>() * N + 2 * verts<N>() + N) g.ord[gi][r - verts<N>() * N - verts<N>() - N] = (unsigned char)__float_as_int(v);
+        else if (r == state_floats<N>() - 2) g.active[gi] = __float_as_int(v);
+        else if (r == state_floats<N>() - 1) g.iters[gi] = __float_as_int(v);
       }
     } else {
       // ---- initial simplices: centre (Philox for starts >= 1) + step e_i
-      for (int t5 = tid; t5 < 5 * nunit; t5 += NT) {
-        const int sg = t5 / 5, blk = t5 - sg * 5;
-        GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+      constexpr int kBlk = (N + 3) / 4;   // Philox blocks of 4 coordinates
+      for (int t5 = tid; t5 < kBlk * nunit; t5 += NT) {
+        const int sg = t5 / kBlk, blk = t5 - sg * kBlk;
+        GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
         const int gi = sg < nA ? sg : sg - nA;
         const int s = s0 + sg;
         uint32_t r[4] = {0u, 0u, 0u, 0u};
@@ -849,17 +902,17 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = 4 * blk + q;
-          if (j < kNumParams)
+          if (j < N)
             g.U[gi][0][j] = s == 0 ? 0.0f : P.lnlo + (P.lnhi - P.lnlo) * ((float)(r[q] >> 8) * (1.0f / 16777216.0f));
         }
       }
       __syncthreads();
-      for (int idx = tid; idx < nunit * kNumParams * kNumParams; idx += NT) {
-        const int sg = idx / (kNumParams * kNumParams);
-        GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+      for (int idx = tid; idx < nunit * N * N; idx += NT) {
+        const int sg = idx / (N * N);
+        GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
         const int gi = sg < nA ? sg : sg - nA;
-        const int rem = idx - sg * kNumParams * kNumParams;
-        const int v = rem / kNumParams + 1, j = rem - (v - 1) * kNumParams;
+        const int rem = idx - sg * N * N;
+        const int v = rem / N + 1, j = rem - (v - 1) * N;
         float x = g.U[gi][0][j];
         if (j == v - 1) x += P.step;
         g.U[gi][v][j] = x;
@@ -870,11 +923,11 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     if (ctrl) {
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
-        GroupSmem<G>& g = S.grp[h];
+        GroupSmem<G, N>& g = S.grp[h];
         if (g.nsim == 0) continue;
-        if (it0 == 0 && lane == 0) g.evals = kNV * g.nsim;
+        if (it0 == 0 && lane == 0) g.evals = verts<N>() * g.nsim;
         __syncwarp();
-        next_wave<G>(g, it0 > 0 ? 1 : 0, t_run, lane);
+        next_wave<G, N>(g, it0 > 0 ? 1 : 0, t_run, lane);
       }
     }
     __syncthreads();
@@ -888,11 +941,11 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
     bool decide_next = false;   // controller: the group evaluated this step is decided in the next
 #pragma unroll 1
     for (int k = 0;; ++k) {
-      GroupSmem<G>& ge = S.grp[cur];
-      GroupSmem<G>& gd = S.grp[cur ^ 1];
+      GroupSmem<G, N>& ge = S.grp[cur];
+      GroupSmem<G, N>& gd = S.grp[cur ^ 1];
       if (!ctrl) {
         if (ge.state == kPending) {
-          order_wave<G>(ge, S, P, tid);
+          order_wave<G, N>(ge, S, P, tid);
           // pull chunks of 32 candidates in key order until the wave is taken
           int npe = 0;
 #pragma unroll 1
@@ -902,7 +955,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
             ch = __shfl_sync(0xffffffffu, ch, 0);
             if (ch * 32 >= ge.nvalid) break;
             npe += __popc(__ballot_sync(0xffffffffu,
-                                        eval_candidate<G, LEAN>(ge, S, P, z, qslot + tid, ch * 32 + lane)));
+                                        eval_candidate<G, N, LEAN>(ge, S, P, z, qslot + tid, ch * 32 + lane)));
           }
           if (lane == 0 && npe) atomicAdd(&ge.pe, npe);
         }
@@ -910,13 +963,13 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
         const bool ge_evaluated = ge.state == kPending;
         if (decide_next) {
           if (gd.kind == 0) {
-            init_rank<G>(gd, lane, P.tolx, P.tolf);
+            init_rank<G, N>(gd, lane, P.tolx, P.tolf);
           } else {
-            decide_group<G>(gd, lane, P.tolx, P.tolf);
+            decide_group<G, N>(gd, lane, P.tolx, P.tolf);
             if (lane == 0) gd.it += 1;
             __syncwarp();
           }
-          next_wave<G>(gd, 1, t_run, lane);
+          next_wave<G, N>(gd, 1, t_run, lane);
         }
         if (lane == 0) S.finished[k & 1] = (!ge_evaluated && gd.state == kDone) ? 1 : 0;
         decide_next = ge_evaluated;
@@ -928,18 +981,18 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
 
     if (P.state) {
       // save the simplices for the next launch
-      float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * kStateFloats;
-      for (int idx = tid; idx < nunit * kStateFloats; idx += NT) {
-        const int sg = idx / kStateFloats, r = idx - sg * kStateFloats;
-        const GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+      float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * state_floats<N>();
+      for (int idx = tid; idx < nunit * state_floats<N>(); idx += NT) {
+        const int sg = idx / state_floats<N>(), r = idx - sg * state_floats<N>();
+        const GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
         const int gi = sg < nA ? sg : sg - nA;
         float v;
-        if (r < kNV * kNumParams) v = (&g.U[gi][0][0])[r];
-        else if (r < kNV * kNumParams + kNV) v = g.F[gi][r - kNV * kNumParams];
-        else if (r < kNV * kNumParams + kNV + kNumParams) v = g.XB[gi][r - kNV * kNumParams - kNV];
-        else if (r < kNV * kNumParams + 2 * kNV + kNumParams) v = __int_as_float((int)g.ord[gi][r - kNV * kNumParams - kNV - kNumParams]);
-        else if (r == kStateFloats - 2) v = __int_as_float(g.active[gi]);
-        else if (r == kStateFloats - 1) v = __int_as_float(g.iters[gi]);
+        if (r < verts<N>() * N) v = (&g.U[gi][0][0])[r];
+        else if (r < verts<N>() * N + verts<N>()) v = g.F[gi][r - verts<N>() * N];
+        else if (r < verts<N>() * N + verts<N>() + N) v = g.XB[gi][r - verts<N>() * N - verts<N>()];
+        else if (r < verts<N>() * N + 2 * verts<N>() + N) v = __int_as_float((int)g.ord[gi][r - verts<N>() * N - verts<N>() - N]);
+        else if (r == state_floats<N>() - 2) v = __int_as_float(g.active[gi]);
+        else if (r == state_floats<N>() - 1) v = __int_as_float(g.iters[gi]);
         else v = 0.0f;
         gstate[idx] = v;
       }
@@ -951,7 +1004,7 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       float f = INFINITY;
       int best = 0x7fffffff;
       for (int sg = lane; sg < nunit; sg += 32) {
-        const GroupSmem<G>& g = S.grp[sg < nA ? 0 : 1];
+        const GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
         const int gi = sg < nA ? sg : sg - nA;
         const float fv = g.F[gi][g.ord[gi][0]];
         if (fv < f || (fv == f && sg < best)) { f = fv; best = sg; }
@@ -966,9 +1019,9 @@ __global__ void __launch_bounds__(search_threads<G>(), MINB) k_search(SearchPara
       const int pe_prev = it0 > 0 ? __float_as_int(rec[22]) : 0;
       __syncwarp();
       if (best < nunit) {
-        const GroupSmem<G>& g = S.grp[best < nA ? 0 : 1];
+        const GroupSmem<G, N>& g = S.grp[best < nA ? 0 : 1];
         const int gi = best < nA ? best : best - nA;
-        if (lane < kNumParams) rec[4 + lane] = g.U[gi][g.ord[gi][0]][lane];
+        if (lane < N) rec[4 + lane] = g.U[gi][g.ord[gi][0]][lane];
         if (lane == 0) {
           rec[0] = f;
           rec[1] = __int_as_float(s0 + best);
@@ -1191,6 +1244,7 @@ __device__ void errors64(const float* pf, const DevSac& d, const float* y, doubl
   *mae = s1e / d.L;
 }
 
+template <int N>
 __global__ void k_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
                            int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
                            opmm_fit_result* out, const int* list) {
@@ -1211,8 +1265,11 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
   opmm_fit_result r;
   const DevSac d = sacs[b];
   const float* rec = unit_best + (size_t)w * kUnitRec;
-  for (int j = 0; j < kNumParams; ++j)
-    r.opc[j] = pc[(size_t)b * kNumParams + j] * __expf(fminf(fmaxf(rec[4 + j], lnlo), lnhi));
+  {
+    float p[kNumParams];
+    u_to_p<N>(rec + 4, pc + (size_t)b * kNumParams, lnlo, lnhi, p);
+    for (int j = 0; j < kNumParams; ++j) r.opc[j] = p[j];
+  }
   r.f = wf;
   r.iterations_run = __float_as_int(rec[2]);
   r.winner = wsimp;
@@ -1314,98 +1371,108 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
 }
 
 // Launch-shape variants of the search kernel: simplices per group G (a block
-// runs a unit of 2 G simplices), the minimum resident blocks per SM the
-// register allocation is bounded for, and the register-lean walk.  The host
-// sees the unit size (simplices per block).
-struct SearchVariantDesc { int G, minb, lean; };
-static const SearchVariantDesc kVariants[] = {{16, 1, 0}, {16, 1, 1}, {8, 1, 0}, {32, 1, 0}};
+// runs a unit of 2 G simplices), the search coordinates N (18, or 9 for the
+// 9-parameter model), the minimum resident blocks per SM the register
+// allocation is bounded for, and the register-lean walk.  The host sees the
+// unit size (simplices per block) and N.
+struct SearchVariantDesc { int G, N, minb, lean; };
+static const SearchVariantDesc kVariants[] = {
+    {16, 18, 1, 0}, {16, 18, 1, 1}, {8, 18, 1, 0}, {32, 18, 1, 0}, {27, 9, 1, 0}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
+static bool variant_ok(int v) { return v >= 0 && v < kNumVariants; }
 int search_variant_count() { return kNumVariants; }
-int search_variant_g(int v) { return v >= 0 && v < kNumVariants ? 2 * kVariants[v].G : 0; }
-int search_variant_minb(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].minb : 0; }
-int search_variant_lean(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].lean : 0; }
-int search_variant_for_g(int unit) {
+int search_variant_g(int v) { return variant_ok(v) ? 2 * kVariants[v].G : 0; }
+int search_variant_dim(int v) { return variant_ok(v) ? kVariants[v].N : 0; }
+int search_variant_minb(int v) { return variant_ok(v) ? kVariants[v].minb : 0; }
+int search_variant_lean(int v) { return variant_ok(v) ? kVariants[v].lean : 0; }
+int search_variant_for(int unit, int dim) {
   for (int v = 0; v < kNumVariants; ++v)
-    if (2 * kVariants[v].G == unit) return v;
+    if (2 * kVariants[v].G == unit && kVariants[v].N == dim) return v;
   return -1;
 }
 
-template <int G, int MINB, bool LEAN>
+template <int G, int N, int MINB, bool LEAN>
 static cudaError_t occ_v(int lcap, int* bps) {
-  const size_t smem = search_smem_bytes<G>(lcap);
+  const size_t smem = search_smem_bytes<G, N>(lcap);
   cudaError_t e =
-      cudaFuncSetAttribute(k_search<G, MINB, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_search<G, N, MINB, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, MINB, LEAN>, search_threads<G>(), smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, N, MINB, LEAN>, search_threads<G, N>(), smem);
 }
 
 // The dynamic shared-memory attribute is set by search_occupancy_v(), which the
 // host calls for the same variant and lcap before any launch or graph capture.
-template <int G, int MINB, bool LEAN>
+template <int G, int N, int MINB, bool LEAN>
 static cudaError_t launch_v(const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
-  const size_t smem = search_smem_bytes<G>(P.lcap);
-  k_search<G, MINB, LEAN><<<blocks_per_sm * num_sms, search_threads<G>(), smem, st>>>(P);
+  const size_t smem = search_smem_bytes<G, N>(P.lcap);
+  k_search<G, N, MINB, LEAN><<<blocks_per_sm * num_sms, search_threads<G, N>(), smem, st>>>(P);
   return cudaGetLastError();
 }
 
-#define OPMM_VARIANT_SWITCH(v, CALL)        \
+template <int G, int N, int MINB, bool LEAN>
+static int threads_v() { return search_threads<G, N>(); }
+
+template <int G, int N, int MINB, bool LEAN>
+static size_t smem_v(int lcap) { return search_smem_bytes<G, N>(lcap); }
+
+#define OPMM_VARIANT_SWITCH(v, CALL, BAD)   \
   switch (v) {                              \
-    case 0: return CALL(16, 1, false);      \
-    case 1: return CALL(16, 1, true);       \
-    case 2: return CALL(8, 1, false);       \
-    case 3: return CALL(32, 1, false);      \
-    default: return cudaErrorInvalidValue;  \
+    case 0: return CALL(16, 18, 1, false);  \
+    case 1: return CALL(16, 18, 1, true);   \
+    case 2: return CALL(8, 18, 1, false);   \
+    case 3: return CALL(32, 18, 1, false);  \
+    case 4: return CALL(27, 9, 1, false);   \
+    default: return BAD;                    \
   }
 
 cudaError_t search_occupancy_v(int v, int lcap, int* blocks_per_sm) {
-#define OCC_CALL(G, M, L) occ_v<G, M, L>(lcap, blocks_per_sm)
-  OPMM_VARIANT_SWITCH(v, OCC_CALL)
+#define OCC_CALL(G, N, M, L) occ_v<G, N, M, L>(lcap, blocks_per_sm)
+  OPMM_VARIANT_SWITCH(v, OCC_CALL, cudaErrorInvalidValue)
 #undef OCC_CALL
 }
 
 cudaError_t launch_search_v(int v, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
-#define LAUNCH_CALL(G, M, L) launch_v<G, M, L>(P, blocks_per_sm, num_sms, st)
-  OPMM_VARIANT_SWITCH(v, LAUNCH_CALL)
+#define LAUNCH_CALL(G, N, M, L) launch_v<G, N, M, L>(P, blocks_per_sm, num_sms, st)
+  OPMM_VARIANT_SWITCH(v, LAUNCH_CALL, cudaErrorInvalidValue)
 #undef LAUNCH_CALL
 }
 
-// Threads and dynamic shared memory of a block running units of `unit`
-// simplices.
-int search_threads_for(int unit) {
-  switch (unit) {
-    case 16: return search_threads<8>();
-    case 32: return search_threads<16>();
-    case 64: return search_threads<32>();
-    default: return 0;
-  }
+// Threads and dynamic shared memory of a block of variant v.
+int search_variant_threads(int v) {
+#define THREADS_CALL(G, N, M, L) threads_v<G, N, M, L>()
+  OPMM_VARIANT_SWITCH(v, THREADS_CALL, 0)
+#undef THREADS_CALL
 }
 
-size_t search_smem_for(int unit, int lcap) {
-  switch (unit) {
-    case 16: return search_smem_bytes<8>(lcap);
-    case 32: return search_smem_bytes<16>(lcap);
-    case 64: return search_smem_bytes<32>(lcap);
-    default: return 0;
-  }
+size_t search_variant_smem(int v, int lcap) {
+#define SMEM_CALL(G, N, M, L) smem_v<G, N, M, L>(lcap)
+  OPMM_VARIANT_SWITCH(v, SMEM_CALL, (size_t)0)
+#undef SMEM_CALL
 }
 
-// G-only entry points: the first variant with that G.
-cudaError_t search_occupancy(int G, int lcap, int* blocks_per_sm) {
-  return search_occupancy_v(search_variant_for_g(G), lcap, blocks_per_sm);
+// Entry points for a fixed 18-coordinate unit size (static fit).
+cudaError_t search_occupancy(int unit, int lcap, int* blocks_per_sm) {
+  return search_occupancy_v(search_variant_for(unit, kNumParams), lcap, blocks_per_sm);
 }
 
-cudaError_t launch_search(int G, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
-  return launch_search_v(search_variant_for_g(G), P, blocks_per_sm, num_sms, st);
+cudaError_t launch_search(int unit, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
+  return launch_search_v(search_variant_for(unit, kNumParams), P, blocks_per_sm, num_sms, st);
 }
 
 cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
                             int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
-                            opmm_fit_result* out, cudaStream_t st, const int* list) {
+                            opmm_fit_result* out, cudaStream_t st, const int* list, int dim) {
   if (n <= 0) return cudaSuccess;
   // the FP64 recomputation is latency bound per thread and the FP64 pipe is
   // narrow: spread the saccades over all SMs, a few threads per block
-  k_finalize<<<(n + 3) / 4, 4, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n, out, list);
+  if (dim == 9)
+    k_finalize<9><<<(n + 3) / 4, 4, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n, out, list);
+  else if (dim == kNumParams)
+    k_finalize<kNumParams><<<(n + 3) / 4, 4, 0, st>>>(sacs, traces, pc, ustart, ngroups, unit_best, lnlo, lnhi, n,
+                                                       out, list);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -49,20 +49,24 @@ cudaError_t launch_simulate(const float* opc, int n, const DevSac* sacs, const i
                             const long long* out_off, float* out, cudaStream_t st);
 cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, const float* traces, float* f,
                          unsigned* err, int num_sms, cudaStream_t st);
+// Search kernel variants (see kernels.cu): unit size (simplices per block),
+// search coordinates (18, or 9 for the 9-parameter model), threads and
+// dynamic shared memory per block.
 int search_variant_count();
 int search_variant_g(int v);
+int search_variant_dim(int v);
 int search_variant_minb(int v);
 int search_variant_lean(int v);
-int search_variant_for_g(int G);
+int search_variant_for(int unit, int dim);
+int search_variant_threads(int v);
+size_t search_variant_smem(int v, int lcap);
 cudaError_t search_occupancy_v(int v, int lcap, int* blocks_per_sm);
 cudaError_t launch_search_v(int v, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st);
-int search_threads_for(int G);
-size_t search_smem_for(int G, int lcap);
-cudaError_t search_occupancy(int G, int lcap, int* blocks_per_sm);
-cudaError_t launch_search(int G, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st);
+cudaError_t search_occupancy(int unit, int lcap, int* blocks_per_sm);
+cudaError_t launch_search(int unit, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st);
 cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float* pc, const int* ustart,
                             int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
-                            opmm_fit_result* out, cudaStream_t st, const int* list = nullptr);
+                            opmm_fit_result* out, cudaStream_t st, const int* list = nullptr, int dim = 18);
 
 cudaError_t launch_admit(const DevSac* new_sacs, const float* new_traces, const float* new_pc, const int* slots, int n,
                          DevSac* sacs, float* traces, float* pc, int* progress, int slot_stride, cudaStream_t st);

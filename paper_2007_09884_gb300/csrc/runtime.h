@@ -91,6 +91,7 @@ struct opmm_plan {
   opmm_ctx* ctx = nullptr;
   int n = 0;
   opmm_fit_opts opts{};
+  int dim = 18;                       // search coordinates: 18, or 9 (OPMM_MODEL_9)
   int S = 0;                          // simplices per saccade
   int variant = 0;                    // search kernel variant (see kernels.cu)
   int G = 16;                         // simplices per block

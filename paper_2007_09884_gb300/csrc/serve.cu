@@ -278,7 +278,7 @@ extern "C" int opmm_serve_start(opmm_ctx* ctx, const opmm_serve_opts* cfg, const
   sv->cfg = *cfg;
   sv->seeded = fit->use_surrogate != 0;
   sv->S = fit->candidates / (OPMM_NPARAM + 4);
-  sv->variant = ctx->forced_variant >= 0 ? ctx->forced_variant : search_variant_for_g(32);
+  sv->variant = ctx->forced_variant >= 0 ? ctx->forced_variant : search_variant_for(32, OPMM_NPARAM);
   sv->G = search_variant_g(sv->variant);
   sv->ngroups = (sv->S + sv->G - 1) / sv->G;
   sv->lcap = (cfg->max_samples + 3) & ~3;

