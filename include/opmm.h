@@ -5,7 +5,7 @@
  * saccades: "recorded eye movement data as input ... an OPC vector as output"
  * (paper Sec. 2, "Oculomotor plant mathematical model").  The model is the
  * 18-parameter oculomotor plant (Sec. 2.2.1, Table 1), the estimator the
- * parallel Nelder-Mead search of Sec. 2.3 / Algorithm 1.  All numerical work
+ * parallel Nelder-Mead search of Sec. 3.3 / Algorithm 1.  All numerical work
  * runs in the library's CUDA kernels on one GPU (sm_103a); there is no CPU
  * fallback: a call on a machine without a usable device fails with
  * OPMM_ECUDA.
@@ -63,7 +63,7 @@ extern "C" {
 #define OPMM_MODEL_9 9
 
 /* How the box centre (initial OPC vector) is chosen when the caller gives none
- * (Sec. 2.3: the estimator starts from model defaults culled from literature). */
+ * (Sec. 3.2: the estimator starts from model defaults culled from literature). */
 #define OPMM_PULSE_TABLE1 0      /* Table 1 verbatim; W = duration - 6 ms */
 #define OPMM_PULSE_CALIBRATED 1  /* Table 1, W = duration - 6 ms, agonist pulse
                                     height set so that the default plant's
@@ -74,7 +74,7 @@ extern "C" {
 typedef struct opmm_ctx opmm_ctx;     /* opaque, library-owned */
 typedef struct opmm_plan opmm_plan;   /* opaque, library-owned */
 
-/* One recorded saccade, the OPMM's input in Sec. 2.3 (a saccade extracted
+/* One recorded saccade, the OPMM's input in Sec. 3.1 (a saccade extracted
  * from the recording, 1-D horizontal or vertical position).  The window holds fixation, saccade and
  * fixation; the pulse of the neural control signal starts at
  * onset_index / sample_rate_hz. */
@@ -88,7 +88,7 @@ typedef struct {
   float duration_ms;         /* detected duration; nominal W = duration - 6 ms */
 } opmm_saccade;
 
-/* Estimator settings (Sec. 2.3, Algorithm 1). */
+/* Estimator settings (Sec. 3.3, Algorithm 1). */
 typedef struct {
   int32_t model;             /* OPMM_MODEL_18 or OPMM_MODEL_9 */
   int32_t candidates;        /* trial points per iteration per saccade; the
@@ -225,7 +225,7 @@ void opmm_plan_destroy(opmm_plan* plan);
 
 /* ------------------------------------------------------------ serving */
 /* Real-time request loop with continuous batching (the paper's motivation:
- * estimation as fast as the recording, Sec. 4).  Single saccades arrive
+ * estimation as fast as the recording, Sec. 5).  Single saccades arrive
  * with opmm_serve_submit; a scheduler thread admits them into device slots
  * while earlier requests are still being searched, advances all resident
  * requests together a few Nelder-Mead iterations per round (search state

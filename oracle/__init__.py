@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  The product package never imports this module; only
 the tests, the smoke check and the benchmark's CPU-baseline leg do.  It shares no
 code with the CUDA path.  See opmm_oracle.c for the model reading and the paper
-passages each function follows (Sec. 2.1-2.3, Table 1, Algorithm 1, Fig. 4).
+passages each function follows (Sec. 2.1-3.4, Table 1, Algorithm 1, Fig. 4).
 
 Parity status: the plant equations are a reading of a paper that prints none,
 so agreement with the authors' unpublished implementation is parity unpinned;

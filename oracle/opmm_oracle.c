@@ -20,10 +20,10 @@
  *     that contains the pulse end split in two (model silent on integration);
  *   - an exact piecewise solver (matrix exponential per constant-input
  *     segment) used only to pin the RK4 integrator;
- *   - the optimisation error (Sec. 2.3 "OPMM output": difference between the
+ *   - the optimisation error (Sec. 3.4 "OPMM output": difference between the
  *     recorded and simulated trajectory), minimised as the mean squared
  *     error and reported also as the mean absolute error;
- *   - the parallel Nelder-Mead estimator (Sec. 2.3 "Parameter estimation",
+ *   - the parallel Nelder-Mead estimator (Sec. 3.3 "Parameter estimation",
  *     Algorithm 1): all reflection, expansion, contraction and shrink points
  *     of a simplex are evaluated in one wave, then the Lagarias et al. decision
  *     is taken and the vertices sorted; exit on the distance and function
@@ -501,7 +501,7 @@ static void simplex_insert(simplex_t* s, const double* xn, double fn) {
   memcpy(s->x[i], xn, sizeof(double) * s->n);
 }
 
-/* Exit test (Sec. 2.3): every vertex within tolx of the best in max-norm and
+/* Exit test (Sec. 3.3): every vertex within tolx of the best in max-norm and
  * every value within tolf of the best value. */
 int or_nm_converged(const simplex_t* s, double tolx, double tolf) {
   double dx = 0.0, df = 0.0;

@@ -12,7 +12,7 @@
 // the trace staged once per block in shared memory by a TMA bulk copy, with a
 // compensated FP32 sum.  Per block, two groups of G simplices of one saccade
 // advance in turn: all 22 trial points of every simplex of a group are
-// evaluated in one wave (Sec. 2.3: all simplex transformations are computed at
+// evaluated in one wave (Sec. 3.3: all simplex transformations are computed at
 // once), while the block's controller warp takes the Lagarias decisions of
 // the other group and orders its next wave.
 #include <cuda_runtime.h>
@@ -553,7 +553,7 @@ __device__ __forceinline__ void order_wave(GroupSmem<G, N>& g, const SearchSmem<
 }
 
 // Centroid of the best n vertices and the vertex-spread half of the exit test
-// (Sec. 2.3: every vertex within tol_x of the best in max-norm), spread over
+// (Sec. 3.3: every vertex within tol_x of the best in max-norm), spread over
 // the controller warp's lanes by (simplex, coordinate); `sel` picks the
 // simplices to process.  g.okx[gi] must be 1 on entry and is cleared by any
 // coordinate that fails.

@@ -143,7 +143,7 @@ TRAIN_SCHEDULE = [(800, 2e-3), (800, 1e-3), (500, 5e-4), (341, 2.5e-4)]
 
 
 def test_trained_surrogate_gains_over_plain_search(ctx):
-    """What the network adds to the estimator of Sec. 2.3, on held-out
+    """What the network adds to the estimator of Sec. 3.3, on held-out
     saccades of the uneven workload (drawn by the numpy generator, never seen
     in training, which draws on the device):
     * its estimate alone traces the recording more closely than the nominal
