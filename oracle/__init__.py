@@ -101,6 +101,11 @@ def _load():
             lib.or_score.argtypes = [_dp, _i, _u32, _i, _d, _i, _d, _d, _dp, _d, _d, _dp, _i, _dp]
             lib.or_score.restype = _i
             lib.or_u_to_p.argtypes = [_dp, _i, _u32, _d, _d, _dp, _dp]
+            lib.or_refine.argtypes = [_dp, _i, _u32, _i, _d, _i, _d, _d, _dp, _d, _d, _dp, _i, _d, _d,
+                                      _dp, _ip, ctypes.POINTER(ctypes.c_long)]
+            lib.or_refine.restype = _i
+            lib.or_lm_testfn.argtypes = [_i, _dp, _i, _d, _d, _d, _d, _dp, _ip]
+            lib.or_lm_testfn.restype = _i
             lib.or_u_to_p.restype = _i
             _lib = lib
     return _lib
@@ -297,3 +302,38 @@ def u_to_p(pc, u, *, model=18, free_mask=None, box_lo=0.5, box_hi=2.0) -> np.nda
     if rc != 0:
         raise ValueError("bad model or centre")
     return p
+
+
+def refine(pc, L, fs, onset, th0, thf, y, u0, K, *, model=18, free_mask=None, box_lo=0.5, box_hi=2.0,
+           delta=1e-2, lambda0=1e-3):
+    """Levenberg-Marquardt refinement of search point u0 (Sec. 5's gradient
+    alternative): K iterations, central-difference Jacobian of step delta
+    (ln units), damping lambda0.  Returns u, p, f (MSE), rms, accepted steps
+    and residual evaluations."""
+    pc, y = _f64(pc), _f64(y)
+    u = _f64(u0).copy()
+    f = _d()
+    acc = _i()
+    nres = ctypes.c_long()
+    rc = _load().or_refine(_dptr(pc), int(model), _mask(model, free_mask), int(L), float(fs), int(onset),
+                           float(th0), float(thf), _dptr(y), float(box_lo), float(box_hi), _dptr(u), int(K),
+                           float(delta), float(lambda0), ctypes.byref(f), ctypes.byref(acc), ctypes.byref(nres))
+    if rc != 0:
+        raise ValueError("bad refine arguments")
+    p = u_to_p(pc, u, model=model, free_mask=free_mask, box_lo=box_lo, box_hi=box_hi)
+    mse, mae = errors(p, L, fs, onset, th0, thf, y)
+    return {"u": u, "p": p, "f": float(f.value), "rms": float(np.sqrt(mse)), "l1": float(mae),
+            "accepted": int(acc.value), "evaluations": int(nres.value)}
+
+
+def lm_testfn(fn_id: int, u0, K: int, lo=-np.inf, hi=np.inf, delta=1e-6, lambda0=1e-3):
+    """Levenberg-Marquardt on a textbook residual (0: linear least squares,
+    1: Rosenbrock)."""
+    u = _f64(u0).copy()
+    f = _d()
+    acc = _i()
+    rc = _load().or_lm_testfn(int(fn_id), _dptr(u), int(K), float(lo), float(hi), float(delta), float(lambda0),
+                              ctypes.byref(f), ctypes.byref(acc))
+    if rc != 0:
+        raise ValueError("bad test function")
+    return u, float(f.value), int(acc.value)

@@ -818,3 +818,185 @@ int or_u_to_p(const double* pc, int model, uint32_t free_mask, double box_lo, do
   u_to_p(&c, u, p);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient-based refinement (Sec. 5 names gradient methods as the            */
+/* alternative estimator to test): Levenberg-Marquardt on the residual vector */
+/* ------------------------------------------------------------------------ */
+
+/* Residual vector r(u) of length m; returns 0, or nonzero when u cannot be
+ * simulated (too stiff): that point counts as f = +inf. */
+typedef int (*residual_fn)(const double* u, double* r, void* ctx);
+
+/* Levenberg-Marquardt from u (n coordinates, projected onto [lnlo, lnhi]),
+ * K iterations, central-difference Jacobian of step delta, initial damping
+ * lambda0.  One iteration:
+ *   - at a new point, J[k][j] = (r_k(u + delta e_j) - r_k(u - delta e_j)) /
+ *     (2 delta) (a column whose two points cannot be simulated is zero),
+ *     A = J^T J, g = J^T r(u);
+ *   - solve (A + lambda D) du = -g, D = diag(max(A_jj, 1e-9 max_i A_ii))
+ *     (Marquardt's scaling with a floor), by Cholesky;
+ *   - u' = clamp(u + du); accept when f(u') < f(u) (then lambda / 10, floor
+ *     1e-12, and a new Jacobian), else lambda * 10 (ceiling 1e12).
+ * f(u) = sum_k r_k^2 / m.  Stops early when max_i A_ii = 0 or the system is not
+ * positive definite.  Outputs u, f, the accepted steps and the residual
+ * evaluations. */
+static int lm_run(residual_fn res, void* ctx, int n, int m, double lnlo, double lnhi, double* u, int K,
+                  double delta, double lambda0, double* f_out, int* accepted, long* nres) {
+  double* r = (double*)malloc(sizeof(double) * (size_t)m * (2 * (size_t)n + 2));
+  if (!r) return -2;
+  double* rp = r + m;                 /* r(u + delta e_j) */
+  double* rm = rp + m;                /* r(u - delta e_j) */
+  double* rt = rm + m;                /* r(u') */
+  double* J = rt + m;                 /* [m][n] stored by column: J + j * m */
+  double A[NMAX * NMAX], g[NMAX], M[NMAX * NMAX], du[NMAX], ut[NMAX], uj[NMAX];
+  for (int j = 0; j < n; ++j) u[j] = u[j] < lnlo ? lnlo : (u[j] > lnhi ? lnhi : u[j]);
+  long evals = 0;
+  int acc = 0;
+  double f = INFINITY;
+  if (res(u, r, ctx) == 0) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += r[k] * r[k];
+    f = s / m;
+  }
+  ++evals;
+  double lambda = lambda0;
+  int need_jac = 1;
+  for (int it = 0; it < K && isfinite(f); ++it) {
+    if (need_jac) {
+      for (int j = 0; j < n; ++j) {
+        memcpy(uj, u, sizeof(double) * n);
+        uj[j] = u[j] + delta;
+        const int bp = res(uj, rp, ctx);
+        uj[j] = u[j] - delta;
+        const int bm = res(uj, rm, ctx);
+        evals += 2;
+        double* col = J + (size_t)j * m;
+        for (int k = 0; k < m; ++k) col[k] = (bp || bm) ? 0.0 : (rp[k] - rm[k]) / (2.0 * delta);
+      }
+      for (int a = 0; a < n; ++a) {
+        const double* ca = J + (size_t)a * m;
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s += ca[k] * r[k];
+        g[a] = s;
+        for (int b = 0; b <= a; ++b) {
+          const double* cb = J + (size_t)b * m;
+          double t = 0.0;
+          for (int k = 0; k < m; ++k) t += ca[k] * cb[k];
+          A[a * n + b] = A[b * n + a] = t;
+        }
+      }
+      need_jac = 0;
+    }
+    double amax = 0.0;
+    for (int j = 0; j < n; ++j) amax = A[j * n + j] > amax ? A[j * n + j] : amax;
+    if (!(amax > 0.0)) break;
+    memcpy(M, A, sizeof(double) * n * n);
+    for (int j = 0; j < n; ++j) {
+      const double d = A[j * n + j] > 1e-9 * amax ? A[j * n + j] : 1e-9 * amax;
+      M[j * n + j] += lambda * d;
+    }
+    /* Cholesky M = L L^T in place (lower triangle), then L y = -g, L^T du = y */
+    int ok = 1;
+    for (int j = 0; j < n && ok; ++j) {
+      double s = M[j * n + j];
+      for (int k = 0; k < j; ++k) s -= M[j * n + k] * M[j * n + k];
+      if (!(s > 0.0)) { ok = 0; break; }
+      const double ljj = sqrt(s);
+      M[j * n + j] = ljj;
+      for (int i = j + 1; i < n; ++i) {
+        double t = M[i * n + j];
+        for (int k = 0; k < j; ++k) t -= M[i * n + k] * M[j * n + k];
+        M[i * n + j] = t / ljj;
+      }
+    }
+    if (!ok) break;
+    for (int i = 0; i < n; ++i) {
+      double t = -g[i];
+      for (int k = 0; k < i; ++k) t -= M[i * n + k] * du[k];
+      du[i] = t / M[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = du[i];
+      for (int k = i + 1; k < n; ++k) t -= M[k * n + i] * du[k];
+      du[i] = t / M[i * n + i];
+    }
+    for (int j = 0; j < n; ++j) {
+      const double v = u[j] + du[j];
+      ut[j] = v < lnlo ? lnlo : (v > lnhi ? lnhi : v);
+    }
+    double ft = INFINITY;
+    if (res(ut, rt, ctx) == 0) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += rt[k] * rt[k];
+      ft = s / m;
+    }
+    ++evals;
+    if (ft < f) {
+      memcpy(u, ut, sizeof(double) * n);
+      memcpy(r, rt, sizeof(double) * m);
+      f = ft;
+      ++acc;
+      lambda = lambda / 10.0 > 1e-12 ? lambda / 10.0 : 1e-12;
+      need_jac = 1;
+    } else {
+      lambda = lambda * 10.0 < 1e12 ? lambda * 10.0 : 1e12;
+    }
+  }
+  free(r);
+  *f_out = f;
+  if (accepted) *accepted = acc;
+  if (nres) *nres = evals;
+  return 0;
+}
+
+/* OPMM residual: the RK4 trajectory of p(u) minus the recorded trace. */
+static int opmm_residual(const double* u, double* r, void* vctx) {
+  const opmm_ctx_t* c = (const opmm_ctx_t*)vctx;
+  double p[NP];
+  u_to_p(c, u, p);
+  if (or_stiff(p, c->fs)) return 1;
+  or_simulate_rk4(p, c->L, c->fs, c->onset, c->th0, c->thf, r, NULL);
+  for (int k = 0; k < c->L; ++k) r[k] -= c->y[k];
+  return 0;
+}
+
+/* Refine one saccade's OPC vector from search point u (in/out, n
+ * coordinates of the model) with lm_run; the box is centre * [box_lo,
+ * box_hi] as in the search. */
+int or_refine(const double* pc, int model, uint32_t free_mask, int L, double fs, int onset,
+              double th0, double thf, const double* y, double box_lo, double box_hi,
+              double* u, int K, double delta, double lambda0, double* f, int* accepted,
+              long* nres) {
+  int coord[NP];
+  const int n = model_map(model, free_mask, pc, coord);
+  if (n < 1 || L < 1 || K < 0 || !(delta > 0.0) || !(lambda0 > 0.0) || !(box_lo > 0.0) ||
+      !(box_hi >= box_lo))
+    return -1;
+  opmm_ctx_t c = {pc, coord, n, log(box_lo), log(box_hi), L, onset, fs, th0, thf, y};
+  return lm_run(opmm_residual, &c, n, L, c.lnlo, c.lnhi, u, K, delta, lambda0, f, accepted, nres);
+}
+
+/* Textbook residuals that pin lm_run: id 0, a linear least-squares problem
+ * r = A u - b with A = [[1,2,0],[0,1,1],[1,0,3],[2,1,1],[0,0,1],[1,1,1]] and
+ * b = [1,2,3,4,5,6] (m = 6, n = 3); id 1, Rosenbrock's function as residuals
+ * (10 (u1 - u0^2), 1 - u0) (m = 2, n = 2). */
+static int lm_testres(const double* u, double* r, void* vctx) {
+  const int id = *(const int*)vctx;
+  if (id == 0) {
+    static const double Am[6][3] = {{1, 2, 0}, {0, 1, 1}, {1, 0, 3}, {2, 1, 1}, {0, 0, 1}, {1, 1, 1}};
+    for (int k = 0; k < 6; ++k) r[k] = Am[k][0] * u[0] + Am[k][1] * u[1] + Am[k][2] * u[2] - (k + 1);
+  } else {
+    r[0] = 10.0 * (u[1] - u[0] * u[0]);
+    r[1] = 1.0 - u[0];
+  }
+  return 0;
+}
+
+int or_lm_testfn(int id, double* u, int K, double lo, double hi, double delta, double lambda0,
+                 double* f, int* accepted) {
+  if (id != 0 && id != 1) return -1;
+  const int n = id == 0 ? 3 : 2, m = id == 0 ? 6 : 2;
+  long nres = 0;
+  return lm_run(lm_testres, &id, n, m, lo, hi, u, K, delta, lambda0, f, accepted, &nres);
+}
