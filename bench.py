@@ -389,12 +389,35 @@ def run_ours(args, ws, rank, local):
     }
     plan.destroy()
     plan_h.destroy()
+    if rank == 0 and ws == 1 and not args.no_refine:
+        out["refine"] = refine_after_search(G, ctx, batch_dev, r, args, pulse)
     if rank == 0 and ws == 1 and not args.no_surrogate and args.workload == "batch1024" and args.model == 18:
         out["surrogate"] = surrogate_compare(G, ctx, args.quick)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget, model=args.model)
     G.opmm_destroy(ctx)
     return out
+
+
+def refine_after_search(G, ctx, batch, r, args, pulse, iterations=10):
+    """Levenberg-Marquardt refinement (opmm_refine_batch) of the timed step's
+    search results on the same saccades: wall time of the call (staging,
+    refinement kernel, FP64 check, results), trajectories simulated, and the
+    fit before and after."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref = G.opmm_refine_batch(ctx, batch, r["opc"], iterations=iterations, model=args.model, pulse_init=pulse)
+    dt = time.perf_counter() - t0
+    sims = float(np.sum(ref["evaluations"].astype(np.float64)))
+    ok0 = (r["status"] == 0) & (r["rms_deg"] <= 0.1)
+    ok1 = (ref["status"] == 0) & (ref["rms_deg"] <= 0.1)
+    return {"iterations": iterations, "seconds": dt, "saccades_per_s": len(ref["status"]) / dt,
+            "trajectories_per_s": sims / dt, "accepted_steps_mean": float(np.mean(ref["iterations_run"])),
+            "median_rms_deg_before": float(np.median(r["rms_deg"])),
+            "median_rms_deg_after": float(np.median(ref["rms_deg"])),
+            "fraction_fitted_at_0p1deg_before": float(np.mean(ok0)),
+            "fraction_fitted_at_0p1deg_after": float(np.mean(ok1))}
 
 
 # ------------------------------------------------------------------ serving
@@ -694,6 +717,7 @@ def main():
     ap.add_argument("--model", type=int, default=18, choices=[18, 9],
                     help="search coordinates: the 18-parameter OPMM or the 9-parameter model (Sec. 2.2.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-refine", action="store_true", help="leave the refinement after the search out of the line")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
     if args.model == 9 and args.workload in ("serve", "surrogate"):

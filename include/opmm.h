@@ -130,7 +130,8 @@ typedef struct {
 enum {
   OPMM_SOURCE_PLAIN = 0,     /* box around the given or nominal centres */
   OPMM_SOURCE_SEEDED = 1,    /* narrowed box around the surrogate's estimate */
-  OPMM_SOURCE_FALLBACK = 2   /* plain search run after a seeded fit missed */
+  OPMM_SOURCE_FALLBACK = 2,  /* plain search run after a seeded fit missed */
+  OPMM_SOURCE_REFINED = 3    /* opmm_refine_batch (Levenberg-Marquardt) */
 };
 
 /* ------------------------------------------------------------- context */
@@ -288,6 +289,39 @@ int opmm_serve_stop(opmm_ctx* ctx);
 int opmm_fit_batch_seeded(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* seeded,
                           const opmm_fit_opts* plain, float fallback_rms_deg, opmm_fit_result* out,
                           int32_t* n_fallback);
+
+/* Gradient-based refinement (Sec. 5 proposes testing gradient methods
+ * against Nelder-Mead): Levenberg-Marquardt steps on the residual vector
+ * theta_k - y_k of each saccade, from start_opc (e.g. a search's or the
+ * surrogate's result), in the search's ln coordinates around the box centre,
+ * clamped to the box.  The Jacobian is taken by central differences of step
+ * fd_step (ln units) through the same RK4 plant, A = J^T J and g = J^T r in
+ * FP64, (A + lambda D) du = -g with D = diag(max(A_jj, 1e-9 max A_ii)); a step
+ * is kept when it lowers the mean squared error (lambda / 10), else lambda * 10.
+ * With OPMM_MODEL_9 the nine Table 2 coordinates are refined (start_opc gives
+ * each through its first OPC entry) and the neural signal stays at the centre. */
+typedef struct {
+  int32_t model;             /* OPMM_MODEL_18 or OPMM_MODEL_9 */
+  int32_t iterations;        /* Levenberg-Marquardt iterations, [0, 1e4] */
+  float box_lo, box_hi;      /* search box around the centre, as opmm_fit_opts */
+  float fd_step;             /* central-difference step, ln units (e.g. 0.01) */
+  float lambda0;             /* initial damping (e.g. 1e-3) */
+  int32_t pulse_init;        /* OPMM_PULSE_*: centre when centre_opc is NULL */
+  const float* centre_opc;   /* nullable, host [n][18] box centres (all > 0) */
+} opmm_refine_opts;
+
+/* Refine n saccades from start_opc (host [n][18], all entries > 0) and write
+ * one result each: opc, f (MSE of the refined vector, FP64 sum of the FP32
+ * trajectory), rms_deg and l1_deg recomputed in FP64 as for the search,
+ * iterations_run = accepted steps, evaluations = trajectories simulated
+ * (pulse_end_evals of them with the pulse end inside the window), winner 0,
+ * source OPMM_SOURCE_REFINED, status 1 when the start cannot be simulated.
+ * Descriptors and traces as for opmm_fit_batch.  Errors: OPMM_EINVAL for bad
+ * arguments (as opmm_fit_batch for descriptors, box and centres; non-positive
+ * or non-finite fd_step or lambda0); OPMM_ECUDA / OPMM_ETIMEDOUT as for
+ * opmm_fit_batch; on error out is unspecified. */
+int opmm_refine_batch(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const float* start_opc,
+                      const opmm_refine_opts* opts, opmm_fit_result* out);
 
 /* Fresh weights (uniform +-1/sqrt(512), seeded) and zeroed AdamW state; builds
  * the amplitude -> agonist-pulse table the training data uses. */

@@ -29,6 +29,7 @@ OPMM_EBUSY = -5
 OPMM_NPARAM = 18
 OPMM_MODEL_18 = 18
 OPMM_MODEL_9 = 9
+OPMM_SOURCE_REFINED = 3
 OPMM_PULSE_TABLE1 = 0
 OPMM_SOURCE_PLAIN, OPMM_SOURCE_SEEDED, OPMM_SOURCE_FALLBACK = 0, 1, 2
 OPMM_PULSE_CALIBRATED = 1
@@ -117,6 +118,8 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_simulate.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), i32, vp, i64p, vp]
     lib.opmm_score.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), vp]
     lib.opmm_nominal_opc.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
+    lib.opmm_refine_batch.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, vp, ctypes.POINTER(opmm_refine_opts),
+                                      ctypes.POINTER(opmm_fit_result)]
     lib.opmm_fit_batch_seeded.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, ctypes.POINTER(opmm_fit_opts),
                                           ctypes.POINTER(opmm_fit_opts), ctypes.c_float,
                                           ctypes.POINTER(opmm_fit_result), ctypes.POINTER(ctypes.c_int32)]
@@ -360,6 +363,31 @@ def opmm_fit_batch(ctx, batch: SaccadeBatch, **opts) -> dict:
     descs, keep = batch.descriptors()
     res = (opmm_fit_result * len(batch))()
     _check(ctx, lib.opmm_fit_batch(ctx, descs, len(batch), ctypes.byref(o), res))
+    return results_to_numpy(res)
+
+
+class opmm_refine_opts(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("iterations", ctypes.c_int32), ("box_lo", ctypes.c_float),
+                ("box_hi", ctypes.c_float), ("fd_step", ctypes.c_float), ("lambda0", ctypes.c_float),
+                ("pulse_init", ctypes.c_int32), ("centre_opc", ctypes.c_void_p)]
+
+
+def opmm_refine_batch(ctx, batch: SaccadeBatch, start_opc, iterations=10, box_lo=0.5, box_hi=2.0, fd_step=1e-2,
+                      lambda0=1e-3, model=OPMM_MODEL_18, pulse_init=OPMM_PULSE_CALIBRATED, centre_opc=None) -> dict:
+    """Levenberg-Marquardt refinement of start_opc ([n][18]) on each saccade."""
+    lib = load_library()
+    o = opmm_refine_opts()
+    o.model, o.iterations = int(model), int(iterations)
+    o.box_lo, o.box_hi, o.fd_step, o.lambda0 = float(box_lo), float(box_hi), float(fd_step), float(lambda0)
+    o.pulse_init = int(pulse_init)
+    keep_c = None
+    if centre_opc is not None:
+        keep_c = np.ascontiguousarray(centre_opc, dtype=np.float32)
+        o.centre_opc = keep_c.ctypes.data
+    start = np.ascontiguousarray(start_opc, dtype=np.float32)
+    descs, keep = batch.descriptors()
+    res = (opmm_fit_result * len(batch))()
+    _check(ctx, lib.opmm_refine_batch(ctx, descs, len(batch), start.ctypes.data, ctypes.byref(o), res))
     return results_to_numpy(res)
 
 

@@ -874,6 +874,56 @@ extern "C" int opmm_fit_batch(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n
   return OPMM_OK;
 }
 
+// Levenberg-Marquardt refinement of given OPC vectors (see kernels.cu,
+// k_refine): staging and box centres as a plan of the same model, then one
+// block per saccade.
+extern "C" int opmm_refine_batch(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const float* start_opc,
+                                 const opmm_refine_opts* ro, opmm_fit_result* out) {
+  if (!ctx) return OPMM_EINVAL;
+  if (!ro || !out || !start_opc) return fail(ctx, Status(OPMM_EINVAL, "opmm_refine_batch: null argument"));
+  if (ro->iterations < 0 || ro->iterations > 10000)
+    return fail(ctx, Status(OPMM_EINVAL, "opmm_refine_batch: iterations outside [0, 1e4]"));
+  if (!(ro->fd_step > 0.0f) || !std::isfinite(ro->fd_step) || !(ro->lambda0 > 0.0f) || !std::isfinite(ro->lambda0))
+    return fail(ctx, Status(OPMM_EINVAL, "opmm_refine_batch: fd_step and lambda0 must be finite and > 0"));
+  if (n < 1) return fail(ctx, Status(OPMM_EINVAL, "opmm_refine_batch: empty batch"));
+  if (is_device_ptr(start_opc)) return fail(ctx, Status(OPMM_EINVAL, "opmm_refine_batch: start_opc must be host memory"));
+  for (int i = 0; i < n; ++i) TRY(check_opc(start_opc + (size_t)i * OPMM_NPARAM));
+  TRY(ctx_bind(ctx));
+  opmm_fit_opts fo{};
+  fo.model = ro->model;
+  fo.candidates = (ro->model == OPMM_MODEL_9 ? 9 : OPMM_NPARAM) + 4;
+  fo.iterations = 0;
+  fo.box_lo = ro->box_lo;
+  fo.box_hi = ro->box_hi;
+  fo.init_step = 0.05f;
+  fo.pulse_init = ro->pulse_init;
+  fo.init_opc = ro->centre_opc;
+  opmm_plan p;
+  TRY(plan_stage(ctx, sacs, n, fo, &p));
+  cudaStream_t st = ctx->stream;
+  DevBuf& b_start = ctx->scratch[8];
+  DevBuf& b_rows = ctx->scratch[9];
+  DevBuf& b_out = ctx->scratch[10];
+  const size_t rows = (size_t)n * (2 * (size_t)p.dim + 2) * (size_t)p.lcap;
+  TRY(b_start.ensure(sizeof(float) * OPMM_NPARAM * (size_t)n));
+  TRY(b_rows.ensure(sizeof(float) * rows));
+  TRY(b_out.ensure(sizeof(opmm_fit_result) * (size_t)n));
+  CUDA_TRY(cudaMemcpyAsync(b_start.ptr, start_opc, sizeof(float) * OPMM_NPARAM * (size_t)n, cudaMemcpyHostToDevice, st),
+           "H2D start");
+  CUDA_TRY(cudaMemsetAsync(ctx->d_err.ptr, 0, sizeof(unsigned), st), "clear error word");
+  CUDA_TRY(launch_refine(p.dim, p.d_sacs.as<DevSac>(), p.d_traces.as<float>(), p.d_pc.as<float>(), b_start.as<float>(), n,
+                         ro->iterations, p.params.lnlo, p.params.lnhi, ro->fd_step, ro->lambda0, p.lcap,
+                         b_rows.as<float>(), b_out.as<opmm_fit_result>(), ctx->d_err.as<unsigned>(), st),
+           "launch refine");
+  unsigned e = 0;
+  CUDA_TRY(cudaMemcpyAsync(out, b_out.ptr, sizeof(opmm_fit_result) * (size_t)n, cudaMemcpyDeviceToHost, st), "D2H results");
+  CUDA_TRY(cudaMemcpyAsync(&e, ctx->d_err.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "D2H error word");
+  CUDA_TRY(cudaStreamSynchronize(st), "refine");
+  if (e & kErrWaitTimeout) return fail(ctx, Status(OPMM_ETIMEDOUT, "a kernel's bounded TMA wait expired"));
+  if (e) return fail(ctx, Status(OPMM_ECUDA, "kernel error bits " + std::to_string(e)));
+  return OPMM_OK;
+}
+
 extern "C" int opmm_fit_batch_seeded(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* seeded,
                                      const opmm_fit_opts* plain, float fallback_rms_deg, opmm_fit_result* out,
                                      int32_t* n_fallback) {

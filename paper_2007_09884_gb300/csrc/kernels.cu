@@ -1291,6 +1291,308 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
   out[i] = r;
 }
 
+// ------------------------------------------------------------------ refinement
+// Gradient-based refinement after the search (Sec. 5 proposes gradient
+// methods as the alternative to Nelder-Mead): Levenberg-Marquardt on the
+// residual vector r_k = theta_k(u) - y_k of one saccade per block, in the
+// search's ln coordinates, box and clamp.  One iteration: at a new point the
+// Jacobian by central differences of step delta (2N trajectories, one per
+// thread; a column whose two points are too stiff is zero), A = J^T J and
+// g = J^T r in FP64; (A + lambda D) du = -g with D = diag(max(A_jj, 1e-9
+// max_i A_ii)) solved by Cholesky in FP64; u' = clamp(u + du); accept when
+// f(u') < f(u) (lambda / 10, floor 1e-12, new Jacobian), else lambda * 10
+// (ceiling 1e12).  f = sum_k r_k^2 / L over every sample.  Stops early when
+// A is zero or the system is not positive definite.  Trajectories go to a
+// per-block scratch area in global memory (2N + 2 rows of lcap floats).
+constexpr int kRefineThreads = 64;
+
+struct RowSink {
+  float* out;
+  __device__ __forceinline__ void emit(int k, float dth) { out[k] = dth; }
+  __device__ __forceinline__ void block_end() {}
+};
+
+// theta_k - thf (positive frame) for every sample of the window into row;
+// false (row untouched past onset) when the candidate is too stiff.
+__device__ bool refine_row(const float (&p)[kNumParams], const SacConst& sc, float* row, int* pe) {
+  const int kend = min(sc.onset, sc.L - 1);
+  for (int k = 0; k <= kend; ++k) row[k] = sc.th0 - sc.thf;
+  RowSink s{row};
+  return walk(p, sc, s, nullptr, 0, true, pe) >= 0;
+}
+
+template <int N>
+struct RefineSmem {
+  double A[N * N];
+  double M[N * N];   // damped system, factored in place
+  double du[N];
+  double g[N];
+  double red[kRefineThreads];
+  float u[N], ut[N];
+  float pc[kNumParams];
+  double f, ft, lambda;
+  int bad[2 * N];
+  int need_jac, go, trial_ok, cur, acc, evals, pe;
+  SacConst sc;
+  TraceStage st;
+  uint64_t bar;
+};
+
+// Block sum of per-thread FP64 partials (all threads call it).
+template <int N>
+__device__ double refine_sum(RefineSmem<N>& S, double v) {
+  S.red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kRefineThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) S.red[threadIdx.x] += S.red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = S.red[0];
+  __syncthreads();
+  return r;
+}
+
+// f of a stored trajectory row against the staged trace (all threads).
+template <int N>
+__device__ double refine_f(RefineSmem<N>& S, const float* row, const float* z, int L) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < L; k += kRefineThreads) {
+    const double e = (double)row[k] - (double)z[k];
+    acc += e * e;
+  }
+  return refine_sum<N>(S, acc) / (double)L;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRefineThreads) k_refine(const DevSac* sacs, const float* traces, const float* pcs,
+                                                            const float* start, int K, float lnlo, float lnhi,
+                                                            float delta, float lambda0, int lcap, float* scratch,
+                                                            opmm_fit_result* out, unsigned* err) {
+  __shared__ RefineSmem<N> S;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* yraw = reinterpret_cast<float*>(smraw);
+  float* z = yraw + lcap;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const DevSac d = sacs[b];
+  float* rows = scratch + (size_t)b * (2 * N + 2) * (size_t)lcap;
+  if (tid == 0) {
+    mbar_init(&S.bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  if (!stage_trace(d, traces, yraw, z, &S.bar, phase, &S.st)) {
+    if (tid == 0) raise_error(err, kErrWaitTimeout);
+    return;
+  }
+  if (tid < kNumParams) S.pc[tid] = pcs[(size_t)b * kNumParams + tid];
+  if (tid == 0) {
+    S.sc = sac_const(d);
+    S.lambda = lambda0;
+    S.need_jac = 1;
+    S.cur = 0;
+    S.acc = 0;
+    S.evals = 1;
+    S.pe = 0;
+  }
+  __syncthreads();
+  // start point: the coordinate of the first OPC entry each one scales
+  if (tid < N) {
+    int j0 = 0;
+    for (int j = kNumParams - 1; j >= 0; --j)
+      if (search_coord<N>(j) == tid) j0 = j;
+    const float u = logf(start[(size_t)b * kNumParams + j0] / S.pc[j0]);
+    S.u[tid] = fminf(fmaxf(u, lnlo), lnhi);
+  }
+  __syncthreads();
+  const SacConst sc = S.sc;
+  float* rcur[2] = {rows + (size_t)(2 * N) * lcap, rows + (size_t)(2 * N + 1) * lcap};
+  if (tid == 0) {
+    float p[kNumParams];
+    u_to_p<N>(S.u, S.pc, lnlo, lnhi, p);
+    int pe = 0;
+    S.trial_ok = refine_row(p, sc, rcur[0], &pe) ? 1 : 0;
+    S.pe += pe;
+  }
+  __syncthreads();
+  {
+    const double f = refine_f<N>(S, rcur[0], z, sc.L);
+    if (tid == 0) S.f = S.trial_ok && isfinite(f) ? f : INFINITY;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < K; ++it) {
+    if (!isfinite(S.f)) break;
+    const float* r0 = rcur[S.cur];
+    if (S.need_jac) {
+      if (tid < 2 * N) {
+        const int j = tid >> 1;
+        float ut[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) ut[c] = S.u[c];
+        ut[j] += (tid & 1) ? -delta : delta;
+        float p[kNumParams];
+        u_to_p<N>(ut, S.pc, lnlo, lnhi, p);
+        int pe = 0;
+        S.bad[tid] = refine_row(p, sc, rows + (size_t)tid * lcap, &pe) ? 0 : 1;
+        if (pe) atomicAdd(&S.pe, 1);
+      }
+      __syncthreads();
+      // A (lower triangle) and g: one task per entry, FP64
+      constexpr int kTasks = N * (N + 1) / 2 + N;
+      const double inv2d = 1.0 / (2.0 * (double)delta);
+      for (int t = tid; t < kTasks; t += kRefineThreads) {
+        int a, bb;
+        const bool is_g = t >= N * (N + 1) / 2;
+        if (is_g) {
+          a = t - N * (N + 1) / 2;
+          bb = -1;
+        } else {
+          a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+          while ((a + 1) * (a + 2) / 2 <= t) ++a;
+          while (a * (a + 1) / 2 > t) --a;
+          bb = t - a * (a + 1) / 2;
+        }
+        const bool za = S.bad[2 * a] || S.bad[2 * a + 1];
+        const bool zb = bb >= 0 && (S.bad[2 * bb] || S.bad[2 * bb + 1]);
+        double acc = 0.0;
+        if (!za && !zb) {
+          const float* ap = rows + (size_t)(2 * a) * lcap;
+          const float* am = rows + (size_t)(2 * a + 1) * lcap;
+          for (int k = 0; k < sc.L; ++k) {
+            const double ja = ((double)ap[k] - (double)am[k]) * inv2d;
+            double other;
+            if (is_g) other = (double)r0[k] - (double)z[k];
+            else other = ((double)rows[(size_t)(2 * bb) * lcap + k] - (double)rows[(size_t)(2 * bb + 1) * lcap + k]) * inv2d;
+            acc += ja * other;
+          }
+        }
+        if (is_g) S.g[a] = acc;
+        else S.A[a * N + bb] = S.A[bb * N + a] = acc;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        S.need_jac = 0;
+        S.evals += 2 * N;
+      }
+    }
+    // damped normal equations, one thread, FP64
+    if (tid == 0) {
+      double amax = 0.0;
+      for (int j = 0; j < N; ++j) amax = S.A[j * N + j] > amax ? S.A[j * N + j] : amax;
+      S.go = amax > 0.0 ? 1 : 0;
+      if (S.go) {
+        double* M = S.M;
+        double* du = S.du;
+        for (int i = 0; i < N * N; ++i) M[i] = S.A[i];
+        for (int j = 0; j < N; ++j) {
+          const double dj = S.A[j * N + j] > 1e-9 * amax ? S.A[j * N + j] : 1e-9 * amax;
+          M[j * N + j] += S.lambda * dj;
+        }
+        for (int j = 0; j < N && S.go; ++j) {
+          double sjj = M[j * N + j];
+          for (int k = 0; k < j; ++k) sjj -= M[j * N + k] * M[j * N + k];
+          if (!(sjj > 0.0)) { S.go = 0; break; }
+          const double ljj = sqrt(sjj);
+          M[j * N + j] = ljj;
+          for (int i = j + 1; i < N; ++i) {
+            double t = M[i * N + j];
+            for (int k = 0; k < j; ++k) t -= M[i * N + k] * M[j * N + k];
+            M[i * N + j] = t / ljj;
+          }
+        }
+        if (S.go) {
+          for (int i = 0; i < N; ++i) {
+            double t = -S.g[i];
+            for (int k = 0; k < i; ++k) t -= M[i * N + k] * du[k];
+            du[i] = t / M[i * N + i];
+          }
+          for (int i = N - 1; i >= 0; --i) {
+            double t = du[i];
+            for (int k = i + 1; k < N; ++k) t -= M[k * N + i] * du[k];
+            du[i] = t / M[i * N + i];
+          }
+          for (int j = 0; j < N; ++j) {
+            const double v = (double)S.u[j] + du[j];
+            S.ut[j] = (float)(v < (double)lnlo ? (double)lnlo : (v > (double)lnhi ? (double)lnhi : v));
+          }
+          float p[kNumParams];
+          u_to_p<N>(S.ut, S.pc, lnlo, lnhi, p);
+          int pe = 0;
+          S.trial_ok = refine_row(p, sc, rcur[S.cur ^ 1], &pe) ? 1 : 0;
+          S.pe += pe;
+          S.evals += 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (!S.go) break;
+    {
+      const double ft = refine_f<N>(S, rcur[S.cur ^ 1], z, sc.L);
+      if (tid == 0) {
+        const double f2 = S.trial_ok && isfinite(ft) ? ft : INFINITY;
+        if (f2 < S.f) {
+          for (int j = 0; j < N; ++j) S.u[j] = S.ut[j];
+          S.f = f2;
+          S.cur ^= 1;
+          S.acc += 1;
+          S.lambda = S.lambda / 10.0 > 1e-12 ? S.lambda / 10.0 : 1e-12;
+          S.need_jac = 1;
+        } else {
+          S.lambda = S.lambda * 10.0 < 1e12 ? S.lambda * 10.0 : 1e12;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    opmm_fit_result r;
+    float p[kNumParams];
+    u_to_p<N>(S.u, S.pc, lnlo, lnhi, p);
+    for (int j = 0; j < kNumParams; ++j) r.opc[j] = p[j];
+    r.f = (float)S.f;
+    r.iterations_run = S.acc;
+    r.winner = 0;
+    r.evaluations = S.evals;
+    r.pulse_end_evals = S.pe;
+    r.reserved = 0;
+    r.source = OPMM_SOURCE_REFINED;
+    if (isfinite(S.f)) {
+      double mse, mae;
+      errors64(r.opc, d, traces + d.off, &mse, &mae);
+      r.rms_deg = sqrt(mse);
+      r.l1_deg = mae;
+      r.status = 0;
+    } else {
+      r.rms_deg = INFINITY;
+      r.l1_deg = INFINITY;
+      r.status = 1;
+    }
+    out[b] = r;
+  }
+}
+
+cudaError_t launch_refine(int dim, const DevSac* sacs, const float* traces, const float* pcs, const float* start,
+                          int n, int K, float lnlo, float lnhi, float delta, float lambda0, int lcap, float* scratch,
+                          opmm_fit_result* out, unsigned* err, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const size_t smem = 2 * (size_t)lcap * sizeof(float);
+  if (dim == 9) {
+    cudaError_t e = cudaFuncSetAttribute(k_refine<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_refine<9><<<n, kRefineThreads, smem, st>>>(sacs, traces, pcs, start, K, lnlo, lnhi, delta, lambda0, lcap,
+                                                 scratch, out, err);
+  } else if (dim == kNumParams) {
+    cudaError_t e = cudaFuncSetAttribute(k_refine<kNumParams>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_refine<kNumParams><<<n, kRefineThreads, smem, st>>>(sacs, traces, pcs, start, K, lnlo, lnhi, delta, lambda0,
+                                                          lcap, scratch, out, err);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ serving
 // Place newly admitted requests into their slots: descriptor (offset rebased
 // to the slot's trace area), trace, box centre; progress reset.

@@ -68,6 +68,12 @@ cudaError_t launch_finalize(const DevSac* sacs, const float* traces, const float
                             int ngroups, const float* unit_best, float lnlo, float lnhi, int n,
                             opmm_fit_result* out, cudaStream_t st, const int* list = nullptr, int dim = 18);
 
+// Levenberg-Marquardt refinement of n saccades (dim 18 or 9); scratch holds
+// n * (2 dim + 2) * lcap floats.
+cudaError_t launch_refine(int dim, const DevSac* sacs, const float* traces, const float* pcs, const float* start,
+                          int n, int K, float lnlo, float lnhi, float delta, float lambda0, int lcap, float* scratch,
+                          opmm_fit_result* out, unsigned* err, cudaStream_t st);
+
 cudaError_t launch_admit(const DevSac* new_sacs, const float* new_traces, const float* new_pc, const int* slots, int n,
                          DevSac* sacs, float* traces, float* pc, int* progress, int slot_stride, cudaStream_t st);
 cudaError_t launch_advance(const int* slots, int n, int* progress, int iters, int T, cudaStream_t st);
