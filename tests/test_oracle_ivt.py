@@ -1,0 +1,74 @@
+"""Pins of the I-VT front end's reference definition (oracle/ivt.py) on
+streams whose saccades are known in closed form: a linear ramp, a step, a
+sub-threshold drift, a blink, two saccades, and the 6 ms / 4 deg filters the
+paper applies (Sec. 4)."""
+import numpy as np
+
+from oracle.ivt import ivt
+
+
+def _ramp(n, at, length, amp, base=0.0):
+    """Fixation at base, a linear ramp of amp deg over length steps starting
+    after sample at, fixation at base + amp."""
+    x = np.full(n, base, np.float32)
+    for i in range(1, length + 1):
+        x[at + i] = base + amp * i / length
+    x[at + length + 1:] = base + amp
+    return x
+
+
+def test_linear_ramp_gives_one_saccade_with_its_closed_form():
+    x = _ramp(400, 100, 12, 12.0)      # 12 deg in 12 ms at 1 kHz: 1000 deg/s
+    ev = ivt(x, 1000.0)
+    assert len(ev) == 1
+    e = ev[0]
+    assert (e["onset"], e["end"]) == (100, 112)
+    assert e["amplitude"] == np.float32(12.0) and e["duration_ms"] == np.float32(12.0)
+    assert abs(e["peak_velocity"] - 1000.0) < 1e-3
+    assert (e["window_start"], e["n_samples"], e["onset_index"]) == (90, 63, 10)
+    assert (e["theta_start"], e["theta_end"]) == (0.0, 12.0)
+
+
+def test_step_is_too_short_unless_the_duration_filter_is_off():
+    x = _ramp(300, 100, 1, 10.0)
+    assert ivt(x, 1000.0) == []
+    ev = ivt(x, 1000.0, min_duration_ms=0.0)
+    assert len(ev) == 1 and ev[0]["duration_ms"] == np.float32(1.0) and ev[0]["amplitude"] == np.float32(10.0)
+
+
+def test_subthreshold_drift_and_small_saccades_are_not_saccades():
+    drift = _ramp(600, 50, 400, 8.0)   # 20 deg/s < 30 deg/s
+    assert ivt(drift, 1000.0) == []
+    small = _ramp(300, 100, 10, 3.0)   # 300 deg/s but 3 deg < 4 deg
+    assert ivt(small, 1000.0) == []
+    assert len(ivt(small, 1000.0, min_amplitude_deg=2.0)) == 1
+
+
+def test_blink_in_the_window_discards_the_saccade():
+    x = _ramp(400, 100, 12, 12.0)
+    y = x.copy()
+    y[140] = np.nan                    # inside the post window (112 + 40)
+    assert ivt(y, 1000.0) == []
+    z = x.copy()
+    z[200] = np.nan                    # outside it
+    assert len(ivt(z, 1000.0)) == 1
+    w = x.copy()
+    w[95] = 500.0                      # out-of-range sample in the pre window
+    assert ivt(w, 1000.0) == []
+
+
+def test_two_saccades_and_the_window_edges():
+    x = _ramp(800, 100, 10, 10.0)
+    x[500:] = 10.0 - np.float32(8.0) * np.minimum(np.arange(300, dtype=np.float32) / 8.0, 1.0)
+    ev = ivt(x, 1000.0)
+    assert [(e["onset"], e["end"]) for e in ev] == [(100, 110), (500, 508)]
+    assert ev[1]["amplitude"] == np.float32(8.0)
+    # a saccade too close to the stream's start has no complete window
+    assert ivt(_ramp(400, 5, 12, 12.0), 1000.0) == []
+
+
+def test_velocity_scales_with_the_rate():
+    x = _ramp(400, 100, 12, 12.0)      # per-sample step 1 deg
+    ev = ivt(x, 250.0)                 # 250 deg/s at 250 Hz, 48 ms
+    assert len(ev) == 1 and ev[0]["duration_ms"] == np.float32(48.0)
+    assert ivt(x, 20.0) == []          # 20 deg/s: below threshold
