@@ -323,6 +323,56 @@ typedef struct {
 int opmm_refine_batch(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const float* start_opc,
                       const opmm_refine_opts* opts, opmm_fit_result* out);
 
+/* ------------------------------------------------------------- front end */
+
+/* Velocity-threshold (I-VT) saccade detection and cleaning of a raw position
+ * stream (the paper segments its recordings with I-VT and discards saccades
+ * shorter than 6 ms or smaller than 4 deg, Sec. 4; it gives no velocity
+ * threshold and no cleaning rule, so both are the caller's).  Step k, between
+ * samples k - 1 and k, is fast when both samples are valid (finite and in
+ * [valid_min_deg, valid_max_deg]: track loss and blinks appear as NaN or
+ * out-of-range positions) and |x_k - x_(k-1)| * fs > threshold_dps, in FP32.
+ * A saccade is a maximal run of fast steps [a, b): onset sample s = a - 1,
+ * end sample e = b - 1.  It is kept when (e - s) * 1000 / fs >=
+ * min_duration_ms, |x_e - x_s| >= min_amplitude_deg, and the window
+ * [s - pre_samples, e + post_samples] lies in the stream with every sample
+ * valid; that window, with onset index pre_samples, start fixation x_s, end
+ * fixation x_e and duration (e - s) / fs, is the descriptor the estimator
+ * takes (opmm_saccade). */
+typedef struct {
+  float threshold_dps;       /* velocity threshold, deg/s (e.g. 30) */
+  float min_duration_ms;     /* 6 in the paper */
+  float min_amplitude_deg;   /* 4 in the paper */
+  float valid_min_deg, valid_max_deg;   /* valid position range, e.g. -90, 90 */
+  int32_t pre_samples;       /* window samples before the onset sample */
+  int32_t post_samples;      /* window samples after the end sample */
+} opmm_ivt_opts;
+
+typedef struct {
+  int64_t onset;             /* s: last sample before the movement */
+  int64_t end;               /* e: first sample after it */
+  int64_t window_start;      /* s - pre_samples */
+  int32_t n_samples;         /* window length, e - s + pre + post + 1 */
+  int32_t onset_index;       /* s - window_start (= pre_samples) */
+  float theta_start_deg;     /* x_s */
+  float theta_end_deg;       /* x_e */
+  float amplitude_deg;       /* |x_e - x_s| */
+  float duration_ms;         /* (e - s) * 1000 / fs */
+  float peak_velocity_dps;   /* largest |step| * fs of the run */
+  int32_t reserved;          /* 0 */
+} opmm_ivt_event;
+
+/* Detect the saccades of stream_deg (n_samples positions at sample_rate_hz,
+ * host or device memory, read only).  Writes the first min(max_events, found)
+ * kept events to out (host, caller-owned) in onset order and the number found
+ * to *n_events.  Errors: OPMM_EINVAL for bad arguments (n_samples < 2,
+ * non-positive rate or threshold, negative filters, windows or max_events,
+ * valid_min_deg > valid_max_deg); OPMM_ENOMEM when the stream has more than
+ * 2^24 runs of fast steps (a threshold below the noise) or scratch allocation
+ * fails; OPMM_ECUDA for CUDA errors. */
+int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int64_t n_samples, float sample_rate_hz,
+                         const opmm_ivt_opts* opts, opmm_ivt_event* out, int32_t max_events, int32_t* n_events);
+
 /* Fresh weights (uniform +-1/sqrt(512), seeded) and zeroed AdamW state; builds
  * the amplitude -> agonist-pulse table the training data uses. */
 int opmm_surrogate_init(opmm_ctx* ctx, uint64_t seed);

@@ -9,7 +9,7 @@ The paper segments its recordings with the Velocity-Threshold algorithm and
 discards saccades shorter than 6 ms or smaller than 4 deg (Sec. 4); it gives
 no velocity threshold and no cleaning rule.  The reading written out here:
 
-* a sample is valid when it is finite and inside [valid_min, valid_max]
+* a sample is valid when it is finite and inside [valid_min_deg, valid_max_deg]
   (track loss and blinks show as NaN or out-of-range positions);
 * step k (between samples k - 1 and k, k >= 1) is fast when both samples are
   valid and |theta_k - theta_(k-1)| * fs > threshold;
@@ -32,13 +32,13 @@ from __future__ import annotations
 import numpy as np
 
 
-def ivt(theta, fs, threshold_dps=30.0, min_duration_ms=6.0, min_amplitude_deg=4.0, valid_min=-90.0,
-        valid_max=90.0, pre_samples=10, post_samples=40):
+def ivt(theta, fs, threshold_dps=30.0, min_duration_ms=6.0, min_amplitude_deg=4.0, valid_min_deg=-90.0,
+        valid_max_deg=90.0, pre_samples=10, post_samples=40):
     x = np.asarray(theta, dtype=np.float32)
     n = len(x)
     f = np.float32(fs)
     thr = np.float32(threshold_dps)
-    valid = np.isfinite(x) & (x >= np.float32(valid_min)) & (x <= np.float32(valid_max))
+    valid = np.isfinite(x) & (x >= np.float32(valid_min_deg)) & (x <= np.float32(valid_max_deg))
     fast = np.zeros(n, dtype=bool)
     speed = np.zeros(n, dtype=np.float32)
     if n > 1:

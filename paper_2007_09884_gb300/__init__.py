@@ -120,6 +120,8 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_nominal_opc.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
     lib.opmm_refine_batch.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, vp, ctypes.POINTER(opmm_refine_opts),
                                       ctypes.POINTER(opmm_fit_result)]
+    lib.opmm_detect_saccades.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(opmm_ivt_opts), vp,
+                                         i32, ctypes.POINTER(i32)]
     lib.opmm_fit_batch_seeded.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, ctypes.POINTER(opmm_fit_opts),
                                           ctypes.POINTER(opmm_fit_opts), ctypes.c_float,
                                           ctypes.POINTER(opmm_fit_result), ctypes.POINTER(ctypes.c_int32)]
@@ -389,6 +391,51 @@ def opmm_refine_batch(ctx, batch: SaccadeBatch, start_opc, iterations=10, box_lo
     res = (opmm_fit_result * len(batch))()
     _check(ctx, lib.opmm_refine_batch(ctx, descs, len(batch), start.ctypes.data, ctypes.byref(o), res))
     return results_to_numpy(res)
+
+
+class opmm_ivt_opts(ctypes.Structure):
+    _fields_ = [("threshold_dps", ctypes.c_float), ("min_duration_ms", ctypes.c_float),
+                ("min_amplitude_deg", ctypes.c_float), ("valid_min_deg", ctypes.c_float),
+                ("valid_max_deg", ctypes.c_float), ("pre_samples", ctypes.c_int32), ("post_samples", ctypes.c_int32)]
+
+
+IVT_EVENT_DTYPE = np.dtype([("onset", "<i8"), ("end", "<i8"), ("window_start", "<i8"), ("n_samples", "<i4"),
+                            ("onset_index", "<i4"), ("theta_start_deg", "<f4"), ("theta_end_deg", "<f4"),
+                            ("amplitude_deg", "<f4"), ("duration_ms", "<f4"), ("peak_velocity_dps", "<f4"),
+                            ("reserved", "<i4")])
+
+
+def opmm_detect_saccades(ctx, stream, sample_rate_hz, threshold_dps=30.0, min_duration_ms=6.0,
+                         min_amplitude_deg=4.0, valid_min_deg=-90.0, valid_max_deg=90.0, pre_samples=10,
+                         post_samples=40, max_events=None) -> np.ndarray:
+    """I-VT detection on a position stream (numpy host array or torch CUDA
+    tensor of float32); returns the kept events (IVT_EVENT_DTYPE) in onset
+    order."""
+    lib = load_library()
+    o = opmm_ivt_opts(float(threshold_dps), float(min_duration_ms), float(min_amplitude_deg), float(valid_min_deg),
+                      float(valid_max_deg), int(pre_samples), int(post_samples))
+    if _is_torch(stream) and stream.dtype.__repr__() != "torch.float32":
+        raise ValueError("stream tensor must be float32")
+    ptr, keep = _ptr(stream)
+    n = int(stream.numel()) if _is_torch(stream) else int(keep.size)
+    cap = int(max_events) if max_events is not None else max(16, n // 64)
+    out = np.zeros(cap, dtype=IVT_EVENT_DTYPE)
+    found = ctypes.c_int32()
+    _check(ctx, lib.opmm_detect_saccades(ctx, ptr, ctypes.c_int64(n), ctypes.c_float(sample_rate_hz),
+                                         ctypes.byref(o), out.ctypes.data, cap, ctypes.byref(found)))
+    if found.value > cap and max_events is None:
+        return opmm_detect_saccades(ctx, stream, sample_rate_hz, threshold_dps, min_duration_ms, min_amplitude_deg,
+                                    valid_min_deg, valid_max_deg, pre_samples, post_samples, found.value)
+    return out[:min(found.value, cap)].copy()
+
+
+def batch_from_events(stream, events, sample_rate_hz) -> SaccadeBatch:
+    """Descriptors and host traces of detected saccades (the event windows)."""
+    x = np.asarray(stream, dtype=np.float32)
+    traces = [x[int(e["window_start"]):int(e["window_start"]) + int(e["n_samples"])].copy() for e in events]
+    n = len(events)
+    return make_batch(traces, [float(sample_rate_hz)] * n, events["onset_index"], events["theta_start_deg"],
+                      events["theta_end_deg"], events["duration_ms"])
 
 
 def opmm_fit_batch_seeded(ctx, batch: SaccadeBatch, seeded: dict, plain: dict, fallback_rms_deg=0.1):

@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libopmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]
-UNITS = ["kernels.cu", "capi.cu", "surrogate.cu", "mlp.cu", "serve.cu", "static_fit.cu"]
+UNITS = ["kernels.cu", "capi.cu", "surrogate.cu", "mlp.cu", "serve.cu", "static_fit.cu", "ivt.cu"]
 
 
 def nvcc() -> str:

@@ -40,18 +40,22 @@ int main(void) {
   printf("%zu %zu %zu\\n", sizeof(opmm_saccade), sizeof(opmm_fit_opts), sizeof(opmm_fit_result));
   printf("%zu %zu %zu %zu\\n", offsetof(opmm_fit_result, f), offsetof(opmm_fit_result, rms_deg),
          offsetof(opmm_fit_result, status), offsetof(opmm_fit_opts, init_opc));
+  printf("%zu %zu %zu %zu\\n", sizeof(opmm_ivt_event), sizeof(opmm_ivt_opts), sizeof(opmm_refine_opts),
+         offsetof(opmm_refine_opts, centre_opc));
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(G.opmm_saccade), ctypes.sizeof(G.opmm_fit_opts),
                      ctypes.sizeof(G.opmm_fit_result)]
     assert offs == [G.opmm_fit_result.f.offset, G.opmm_fit_result.rms_deg.offset,
                     G.opmm_fit_result.status.offset, G.opmm_fit_opts.init_opc.offset]
+    assert [int(x) for x in c.split()] == [G.IVT_EVENT_DTYPE.itemsize, ctypes.sizeof(G.opmm_ivt_opts),
+                                           ctypes.sizeof(G.opmm_refine_opts), G.opmm_refine_opts.centre_opc.offset]
 
 
 def test_no_device_fails_loudly():

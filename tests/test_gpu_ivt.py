@@ -1,0 +1,90 @@
+"""The I-VT front end on the GPU (opmm_detect_saccades, through the C ABI)
+against the reference definition (oracle/ivt.py): both take every decision in
+FP32, so the event lists agree exactly: onset and end samples, windows, and
+the float fields bit for bit."""
+import numpy as np
+import pytest
+
+import paper_2007_09884_gb300 as G
+import workloads as W
+from oracle.ivt import ivt
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = [("onset", "onset"), ("end", "end"), ("window_start", "window_start"), ("n_samples", "n_samples"),
+          ("onset_index", "onset_index"), ("theta_start_deg", "theta_start"), ("theta_end_deg", "theta_end"),
+          ("amplitude_deg", "amplitude"), ("duration_ms", "duration_ms"), ("peak_velocity_dps", "peak_velocity")]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    h = G.opmm_create(0)
+    yield h
+    G.opmm_destroy(h)
+
+
+def _same(got, want):
+    assert len(got) == len(want), (len(got), len(want))
+    for g, w in zip(got, want):
+        for a, b in FIELDS:
+            if a in ("theta_start_deg", "theta_end_deg", "amplitude_deg", "duration_ms", "peak_velocity_dps"):
+                assert np.float32(g[a]) == np.float32(w[b]), (a, g[a], w[b])
+            else:
+                assert int(g[a]) == int(w[b]), (a, g[a], w[b])
+
+
+def _ramp(n, at, length, amp):
+    x = np.zeros(n, np.float32)
+    for i in range(1, length + 1):
+        x[at + i] = amp * i / length
+    x[at + length + 1:] = amp
+    return x
+
+
+def test_closed_form_streams(ctx):
+    cases = [_ramp(400, 100, 12, 12.0), _ramp(300, 100, 1, 10.0), _ramp(300, 100, 10, 3.0), _ramp(400, 5, 12, 12.0)]
+    blink = _ramp(400, 100, 12, 12.0)
+    blink[140] = np.nan
+    cases.append(blink)
+    for x in cases:
+        for kw in ({}, {"min_duration_ms": 0.0, "min_amplitude_deg": 0.0}):
+            _same(G.opmm_detect_saccades(ctx, x, 1000.0, **kw), ivt(x, 1000.0, **kw))
+
+
+@pytest.mark.parametrize("fs", [1000.0, 500.0, 250.0])
+def test_synthetic_stream_matches_the_definition(ctx, fs):
+    x, planted = W.raw_stream(400_000 if fs == 1000.0 else 150_000, fs=fs, seed=int(fs))
+    want = ivt(x, fs)
+    got = G.opmm_detect_saccades(ctx, x, fs)
+    assert len(want) > 100
+    _same(got, want)
+
+
+def test_device_stream_window_options_and_truncation(ctx):
+    torch = pytest.importorskip("torch")
+    x, _ = W.raw_stream(200_000, seed=11)
+    kw = dict(threshold_dps=45.0, min_duration_ms=10.0, min_amplitude_deg=2.0, pre_samples=25, post_samples=60,
+              valid_min_deg=-25.0, valid_max_deg=25.0)
+    want = ivt(x, 1000.0, **kw)
+    got = G.opmm_detect_saccades(ctx, torch.from_numpy(x).cuda(), 1000.0, **kw)
+    _same(got, want)
+    few = G.opmm_detect_saccades(ctx, x, 1000.0, max_events=5, **kw)
+    _same(few, want[:5])
+    # the detected windows are descriptors the estimator takes
+    batch = G.batch_from_events(x, got[:8], 1000.0)
+    res = G.opmm_fit_batch(ctx, batch, candidates=22 * 8, iterations=4)
+    assert np.all(res["status"] == 0)
+
+
+def test_rejected_arguments(ctx):
+    x = np.zeros(100, np.float32)
+    for bad in (dict(threshold_dps=0.0), dict(pre_samples=-1), dict(valid_min_deg=5.0, valid_max_deg=-5.0)):
+        with pytest.raises(G.OpmmError) as e:
+            G.opmm_detect_saccades(ctx, x, 1000.0, **bad)
+        assert e.value.code == G.OPMM_EINVAL
+    with pytest.raises(G.OpmmError) as e:
+        G.opmm_detect_saccades(ctx, x[:1], 1000.0)
+    assert e.value.code == G.OPMM_EINVAL

@@ -161,3 +161,43 @@ def poisson_arrivals(rate_hz: float, seconds: float, seed: int) -> np.ndarray:
 
 def by_name(name: str, **kw) -> Workload:
     return {"single10": single10, "batch1024": batch1024, "uneven10k": uneven10k}[name](**kw)
+
+
+def raw_stream(n_samples: int, fs: float = 1000.0, seed: int = 7, noise_deg: float = 0.005,
+               blink_rate_hz: float = 0.2):
+    """Seeded raw horizontal position stream for the I-VT front end: fixations
+    (Gaussian noise of noise_deg) at positions in [-20, 20] deg joined by
+    saccades of amplitude 1-30 deg whose position follows a raised-cosine
+    profile over the main-sequence duration 2.2 ms/deg * A + 21 ms, fixation
+    lengths uniform in [150, 1200] ms, and blinks (runs of 80-200 ms of NaN) at
+    blink_rate_hz on average.  Returns (stream float32, list of planted
+    (start sample, end sample, amplitude))."""
+    g = np.random.default_rng(np.random.SeedSequence([0x1F7, seed]))
+    x = np.empty(n_samples, np.float32)
+    planted = []
+    pos = float(g.uniform(-10.0, 10.0))
+    k = 0
+    while k < n_samples:
+        fix = int(g.uniform(0.15, 1.2) * fs)
+        m = min(fix, n_samples - k)
+        x[k:k + m] = pos + g.normal(0.0, noise_deg, m)
+        k += m
+        if k >= n_samples:
+            break
+        A = float(g.uniform(1.0, 30.0))
+        target = pos + (A if g.random() < 0.5 else -A)
+        if abs(target) > 20.0:
+            target = pos - math.copysign(A, target - pos)
+        dur = int(round(duration_ms(A) * fs / 1000.0))
+        m = min(dur, n_samples - k)
+        t = (np.arange(1, m + 1) / dur).astype(np.float64)
+        x[k:k + m] = pos + (target - pos) * 0.5 * (1.0 - np.cos(np.pi * t)) + g.normal(0.0, noise_deg, m)
+        planted.append((k, k + m, abs(target - pos)))
+        k += m
+        pos = target
+    nb = g.poisson(blink_rate_hz * n_samples / fs)
+    for _ in range(int(nb)):
+        b0 = int(g.integers(0, max(1, n_samples - 1)))
+        bl = int(g.uniform(0.08, 0.2) * fs)
+        x[b0:b0 + bl] = np.nan
+    return x, planted
