@@ -7,8 +7,10 @@
 // Step k (samples k - 1, k) is fast when both samples are valid (finite, in
 // [valid_min, valid_max]) and |x_k - x_(k-1)| * fs > threshold, in FP32.  A
 // saccade is a maximal run of fast steps [a, b): onset sample s = a - 1, end
-// sample e = b - 1.  Pass 1 (HBM bound, grid-stride over the stream) records
-// every run start; pass 2 walks each run and its window, one thread per run.
+// sample e = b - 1.  Run starts are compacted in stream order in two HBM
+// passes over tiles of kTile steps (count per tile, scan of the counts, write
+// at the tile's offset by warp ballots); then one thread per run walks the
+// run and its window.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,25 +44,90 @@ __device__ __forceinline__ float ivt_speed(const IvtDev& P, long long k) {
   return fabsf(b - a) * P.fs;
 }
 
-// Pass 1: the first step of every run of fast steps.
-__global__ void k_ivt_starts(IvtDev P, long long* starts, int cap, int* count) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long k = 1 + (long long)blockIdx.x * blockDim.x + threadIdx.x; k < P.n; k += stride) {
-    const bool f = ivt_speed(P, k) > P.thr;
-    if (!f) continue;
-    const bool fp = ivt_speed(P, k - 1) > P.thr;
-    if (fp) continue;
-    const int i = atomicAdd(count, 1);
-    if (i < cap) starts[i] = k;
+constexpr int kIvtThreads = 256;
+constexpr int kIvtIters = 16;
+constexpr long long kTile = (long long)kIvtThreads * kIvtIters;   // steps per tile (one block)
+
+// step k starts a run of fast steps
+__device__ __forceinline__ bool ivt_run_start(const IvtDev& P, long long k) {
+  return ivt_speed(P, k) > P.thr && !(ivt_speed(P, k - 1) > P.thr);
+}
+
+// Pass 1a: run starts per tile.  Steps of a tile are visited in order
+// (iteration, warp, lane), consecutive lanes on consecutive samples.
+__global__ void __launch_bounds__(kIvtThreads) k_ivt_count(IvtDev P, int* tile_count) {
+  const long long t0 = 1 + (long long)blockIdx.x * kTile;
+  int c = 0;
+#pragma unroll 4
+  for (int it = 0; it < kIvtIters; ++it) {
+    const long long k = t0 + (long long)it * kIvtThreads + threadIdx.x;
+    c += (k < P.n && ivt_run_start(P, k)) ? 1 : 0;
+  }
+  __shared__ int warp_sum[kIvtThreads / 32];
+  int v = c;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sum = 0;
+    for (int w = 0; w < kIvtThreads / 32; ++w) sum += warp_sum[w];
+    tile_count[blockIdx.x] = sum;
+  }
+}
+
+// Exclusive scan of the tile counts (one block); total written to *total.
+__global__ void k_ivt_scan(const int* tile_count, int ntiles, long long* tile_off, long long* total) {
+  __shared__ long long part[1024];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += 1024) {
+    const int i = base + (int)threadIdx.x;
+    const long long v = i < ntiles ? tile_count[i] : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const long long add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < ntiles) tile_off[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// Pass 1b: write each tile's run starts at its offset, in stream order.
+__global__ void __launch_bounds__(kIvtThreads) k_ivt_write(IvtDev P, const long long* tile_off, long long* starts) {
+  __shared__ int warp_cnt[kIvtThreads / 32];
+  const long long t0 = 1 + (long long)blockIdx.x * kTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long run = tile_off[blockIdx.x];
+  for (int it = 0; it < kIvtIters; ++it) {
+    const long long k = t0 + (long long)it * kIvtThreads + threadIdx.x;
+    const bool f = k < P.n && ivt_run_start(P, k);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_cnt[warp] = __popc(m);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < kIvtThreads / 32; ++w) {
+      before += w < warp ? warp_cnt[w] : 0;
+      all += warp_cnt[w];
+    }
+    if (f) starts[run + before + __popc(m & ((1u << lane) - 1u))] = k;
+    run += all;
+    __syncthreads();
   }
 }
 
 // Pass 2: one thread per run: its end, amplitude, duration, peak velocity,
 // the window check and the event record; keep[i] = 1 for a kept saccade.
-__global__ void k_ivt_events(IvtDev P, const long long* starts, const int* count, int cap, opmm_ivt_event* ev,
-                             int* keep) {
+__global__ void k_ivt_events(IvtDev P, const long long* starts, int m, opmm_ivt_event* ev, int* keep) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = min(*count, cap);
   if (i >= m) return;
   const long long a = starts[i];
   long long b = a;
@@ -127,6 +194,7 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
   DevBuf& b_ev = ctx->scratch[13];
   DevBuf& b_keep = ctx->scratch[14];
   DevBuf& b_count = ctx->scratch[15];
+  DevBuf& b_off = ctx->scratch[10];
   if (!is_device_ptr(stream_deg)) {
     s = b_x.ensure(sizeof(float) * (size_t)n_samples);
     if (s.ok())
@@ -135,36 +203,36 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
     if (!s.ok()) return ivt_fail(s);
     x = b_x.as<float>();
   }
-  // a run needs a fast step and a slower one before it: at most n / 2 starts,
-  // and at most 2^24 are kept track of (a noisier stream is refused)
-  const long long cap_ll = std::min<long long>(n_samples / 2 + 1, (long long)1 << 24);
-  const int cap = (int)cap_ll;
-  s = b_starts.ensure(sizeof(long long) * (size_t)cap);
-  if (s.ok()) s = b_count.ensure(sizeof(int));
-  if (s.ok()) s = cuda_status(cudaMemsetAsync(b_count.ptr, 0, sizeof(int), st), "clear count");
-  if (!s.ok()) return ivt_fail(s);
   IvtDev P{x, (long long)n_samples, sample_rate_hz, opts->threshold_dps, opts->valid_min_deg, opts->valid_max_deg,
            opts->min_duration_ms, opts->min_amplitude_deg, opts->pre_samples, opts->post_samples};
-  const int threads = 256;
-  const long long want = (n_samples + threads - 1) / threads;
-  const int blocks = (int)std::min<long long>(want, (long long)ctx->num_sms * 8);
-  k_ivt_starts<<<blocks, threads, 0, st>>>(P, b_starts.as<long long>(), cap, b_count.as<int>());
-  s = cuda_status(cudaGetLastError(), "launch I-VT starts");
-  int count = 0;
-  if (s.ok()) s = cuda_status(cudaMemcpyAsync(&count, b_count.ptr, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H count");
-  if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "I-VT starts");
+  // run starts in stream order: count per tile, scan, write
+  const long long ntiles_ll = (n_samples - 1 + kTile - 1) / kTile;
+  if (ntiles_ll > 0x7fffffffLL) return ivt_fail(Status(OPMM_EINVAL, "opmm_detect_saccades: stream too long"));
+  const int ntiles = (int)ntiles_ll;
+  s = b_count.ensure(sizeof(int) * (size_t)ntiles);
+  if (s.ok()) s = b_off.ensure(sizeof(long long) * ((size_t)ntiles + 1));
   if (!s.ok()) return ivt_fail(s);
-  if (count > cap)
-    return ivt_fail(Status(OPMM_ENOMEM, "opmm_detect_saccades: more than 2^24 velocity runs (raise the threshold)"));
-  const int m = std::min(count, cap);
+  long long* d_off = b_off.as<long long>();
+  k_ivt_count<<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>());
+  k_ivt_scan<<<1, 1024, 0, st>>>(b_count.as<int>(), ntiles, d_off, d_off + ntiles);
+  s = cuda_status(cudaGetLastError(), "launch I-VT count");
+  long long total = 0;
+  if (s.ok()) s = cuda_status(cudaMemcpyAsync(&total, d_off + ntiles, sizeof total, cudaMemcpyDeviceToHost, st), "D2H runs");
+  if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "I-VT count");
+  if (!s.ok()) return ivt_fail(s);
+  if (total > (1LL << 26))
+    return ivt_fail(Status(OPMM_ENOMEM, "opmm_detect_saccades: more than 2^26 velocity runs (raise the threshold)"));
+  const int m = (int)total;
   std::vector<opmm_ivt_event> hev((size_t)m);
   std::vector<int> hkeep((size_t)m);
   if (m > 0) {
-    s = b_ev.ensure(sizeof(opmm_ivt_event) * (size_t)m);
+    s = b_starts.ensure(sizeof(long long) * (size_t)m);
+    if (s.ok()) s = b_ev.ensure(sizeof(opmm_ivt_event) * (size_t)m);
     if (s.ok()) s = b_keep.ensure(sizeof(int) * (size_t)m);
     if (!s.ok()) return ivt_fail(s);
-    k_ivt_events<<<(m + 127) / 128, 128, 0, st>>>(P, b_starts.as<long long>(), b_count.as<int>(), cap,
-                                                  b_ev.as<opmm_ivt_event>(), b_keep.as<int>());
+    k_ivt_write<<<ntiles, kIvtThreads, 0, st>>>(P, d_off, b_starts.as<long long>());
+    k_ivt_events<<<(m + 127) / 128, 128, 0, st>>>(P, b_starts.as<long long>(), m, b_ev.as<opmm_ivt_event>(),
+                                                  b_keep.as<int>());
     s = cuda_status(cudaGetLastError(), "launch I-VT events");
     if (s.ok())
       s = cuda_status(cudaMemcpyAsync(hev.data(), b_ev.ptr, sizeof(opmm_ivt_event) * (size_t)m, cudaMemcpyDeviceToHost, st),
@@ -175,14 +243,13 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
     if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "I-VT events");
     if (!s.ok()) return ivt_fail(s);
   }
-  // kept events in onset order (pass 1 finds runs in no particular order)
-  std::vector<opmm_ivt_event> kept;
-  kept.reserve((size_t)m);
-  for (int i = 0; i < m; ++i)
-    if (hkeep[(size_t)i]) kept.push_back(hev[(size_t)i]);
-  std::sort(kept.begin(), kept.end(), [](const opmm_ivt_event& a, const opmm_ivt_event& b) { return a.onset < b.onset; });
-  *n_events = (int32_t)std::min<size_t>(kept.size(), (size_t)0x7fffffff);
-  const size_t w = std::min<size_t>(kept.size(), (size_t)max_events);
-  for (size_t i = 0; i < w; ++i) out[i] = kept[i];
+  // kept events, already in onset order
+  size_t found = 0;
+  for (int i = 0; i < m; ++i) {
+    if (!hkeep[(size_t)i]) continue;
+    if (found < (size_t)max_events) out[found] = hev[(size_t)i];
+    ++found;
+  }
+  *n_events = (int32_t)std::min<size_t>(found, (size_t)0x7fffffff);
   return OPMM_OK;
 }

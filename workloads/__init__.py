@@ -166,8 +166,8 @@ def by_name(name: str, **kw) -> Workload:
 def raw_stream(n_samples: int, fs: float = 1000.0, seed: int = 7, noise_deg: float = 0.005,
                blink_rate_hz: float = 0.2):
     """Seeded raw horizontal position stream for the I-VT front end: fixations
-    (Gaussian noise of noise_deg) at positions in [-20, 20] deg joined by
-    saccades of amplitude 1-30 deg whose position follows a raised-cosine
+    (Gaussian noise of noise_deg) at positions uniform in [-20, 20] deg joined
+    by saccades of amplitude 1-30 deg whose position follows a raised-cosine
     profile over the main-sequence duration 2.2 ms/deg * A + 21 ms, fixation
     lengths uniform in [150, 1200] ms, and blinks (runs of 80-200 ms of NaN) at
     blink_rate_hz on average.  Returns (stream float32, list of planted
@@ -184,10 +184,11 @@ def raw_stream(n_samples: int, fs: float = 1000.0, seed: int = 7, noise_deg: flo
         k += m
         if k >= n_samples:
             break
-        A = float(g.uniform(1.0, 30.0))
-        target = pos + (A if g.random() < 0.5 else -A)
-        if abs(target) > 20.0:
-            target = pos - math.copysign(A, target - pos)
+        while True:
+            target = float(g.uniform(-20.0, 20.0))
+            A = abs(target - pos)
+            if 1.0 <= A <= 30.0:
+                break
         dur = int(round(duration_ms(A) * fs / 1000.0))
         m = min(dur, n_samples - k)
         t = (np.arange(1, m + 1) / dur).astype(np.float64)
