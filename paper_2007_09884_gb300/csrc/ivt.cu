@@ -223,31 +223,36 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
   if (total > (1LL << 26))
     return ivt_fail(Status(OPMM_ENOMEM, "opmm_detect_saccades: more than 2^26 velocity runs (raise the threshold)"));
   const int m = (int)total;
-  std::vector<opmm_ivt_event> hev((size_t)m);
-  std::vector<int> hkeep((size_t)m);
+  // run records come back through pinned staging
+  HostBuf& h_ev = ctx->h_scratch[0];
+  HostBuf& h_keep = ctx->h_scratch[1];
   if (m > 0) {
     s = b_starts.ensure(sizeof(long long) * (size_t)m);
     if (s.ok()) s = b_ev.ensure(sizeof(opmm_ivt_event) * (size_t)m);
     if (s.ok()) s = b_keep.ensure(sizeof(int) * (size_t)m);
+    if (s.ok()) s = h_ev.ensure(sizeof(opmm_ivt_event) * (size_t)m);
+    if (s.ok()) s = h_keep.ensure(sizeof(int) * (size_t)m);
     if (!s.ok()) return ivt_fail(s);
     k_ivt_write<<<ntiles, kIvtThreads, 0, st>>>(P, d_off, b_starts.as<long long>());
     k_ivt_events<<<(m + 127) / 128, 128, 0, st>>>(P, b_starts.as<long long>(), m, b_ev.as<opmm_ivt_event>(),
                                                   b_keep.as<int>());
     s = cuda_status(cudaGetLastError(), "launch I-VT events");
     if (s.ok())
-      s = cuda_status(cudaMemcpyAsync(hev.data(), b_ev.ptr, sizeof(opmm_ivt_event) * (size_t)m, cudaMemcpyDeviceToHost, st),
+      s = cuda_status(cudaMemcpyAsync(h_ev.ptr, b_ev.ptr, sizeof(opmm_ivt_event) * (size_t)m, cudaMemcpyDeviceToHost, st),
                       "D2H events");
     if (s.ok())
-      s = cuda_status(cudaMemcpyAsync(hkeep.data(), b_keep.ptr, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, st),
+      s = cuda_status(cudaMemcpyAsync(h_keep.ptr, b_keep.ptr, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, st),
                       "D2H keep");
     if (s.ok()) s = cuda_status(cudaStreamSynchronize(st), "I-VT events");
     if (!s.ok()) return ivt_fail(s);
   }
   // kept events, already in onset order
   size_t found = 0;
+  const opmm_ivt_event* hev = h_ev.as<opmm_ivt_event>();
+  const int* hkeep = h_keep.as<int>();
   for (int i = 0; i < m; ++i) {
-    if (!hkeep[(size_t)i]) continue;
-    if (found < (size_t)max_events) out[found] = hev[(size_t)i];
+    if (!hkeep[i]) continue;
+    if (found < (size_t)max_events) out[found] = hev[i];
     ++found;
   }
   *n_events = (int32_t)std::min<size_t>(found, (size_t)0x7fffffff);

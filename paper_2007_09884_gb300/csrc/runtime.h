@@ -79,6 +79,7 @@ struct opmm_ctx {
   int forced_variant = -1;            // -1: autotune; else a search kernel variant
   opmm::DevBuf d_err;                 // device error word of the kernels
   opmm::DevBuf scratch[16];           // per-call scratch of the synchronous entry points
+  opmm::HostBuf h_scratch[2];         // pinned host scratch of the synchronous entry points
   std::map<std::tuple<int, int, int, int>, std::pair<int, int>> tune_cache;
   std::map<std::tuple<int, int, int, int>, std::vector<opmm::TuneProbe>> tune_logs;
   opmm::SurrogateState* surrogate = nullptr;   // owned, released by surrogate_release
