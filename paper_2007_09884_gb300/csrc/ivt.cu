@@ -9,11 +9,12 @@
 // saccade is a maximal run of fast steps [a, b): onset sample s = a - 1, end
 // sample e = b - 1.  Run starts are compacted in stream order in two HBM
 // passes over tiles of kTile steps (count per tile, scan of the counts, write
-// at the tile's offset by warp ballots); then one thread per run walks the
-// run and its window.
+// at the tile's offset by warp scans), four steps per thread from one 16-byte
+// load; then one warp per run walks the run and checks its window.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <vector>
 
@@ -45,29 +46,57 @@ __device__ __forceinline__ float ivt_speed(const IvtDev& P, long long k) {
 }
 
 constexpr int kIvtThreads = 256;
-constexpr int kIvtIters = 16;
-constexpr long long kTile = (long long)kIvtThreads * kIvtIters;   // steps per tile (one block)
+constexpr int kIvtIters = 8;
+constexpr int kVec = 4;                                                     // steps per thread and iteration
+constexpr long long kTile = (long long)kIvtThreads * kIvtIters * kVec;     // steps per tile (one block)
 
-// step k starts a run of fast steps
-__device__ __forceinline__ bool ivt_run_start(const IvtDev& P, long long k) {
-  return ivt_speed(P, k) > P.thr && !(ivt_speed(P, k - 1) > P.thr);
+__device__ __forceinline__ bool ivt_fast(float a, float b, const IvtDev& P) {
+  return ivt_valid(a, P) && ivt_valid(b, P) && fabsf(b - a) * P.fs > P.thr;
 }
 
-// Pass 1a: run starts per tile.  Steps of a tile are visited in order
-// (iteration, warp, lane), consecutive lanes on consecutive samples.
+// Run starts among steps 4m+1 .. 4m+4 (bit i for step 4m+1+i).  Group m's
+// samples 4m .. 4m+3 come in one 16-byte load when the stream is aligned;
+// sample 4m-1 (for step 4m) and sample 4m+4 from the neighbouring lanes.
+// Every lane of the warp calls it, with consecutive m on consecutive lanes.
+template <bool VEC>
+__device__ __forceinline__ unsigned ivt_group_starts(const IvtDev& P, long long m) {
+  const float nan = __int_as_float(0x7fc00000);
+  const long long b = 4 * m;
+  float x0, x1, x2, x3;
+  if (VEC && b + 3 < P.n) {
+    const float4 v = *reinterpret_cast<const float4*>(P.x + b);
+    x0 = v.x; x1 = v.y; x2 = v.z; x3 = v.w;
+  } else {
+    x0 = b < P.n ? P.x[b] : nan;
+    x1 = b + 1 < P.n ? P.x[b + 1] : nan;
+    x2 = b + 2 < P.n ? P.x[b + 2] : nan;
+    x3 = b + 3 < P.n ? P.x[b + 3] : nan;
+  }
+  const int lane = threadIdx.x & 31;
+  float xm = __shfl_up_sync(0xffffffffu, x3, 1);
+  float x4 = __shfl_down_sync(0xffffffffu, x0, 1);
+  if (lane == 0) xm = (b >= 1 && b - 1 < P.n) ? P.x[b - 1] : nan;
+  if (lane == 31) x4 = b + 4 < P.n ? P.x[b + 4] : nan;
+  // fast steps 4m .. 4m+4 (step 0 does not exist: sample -1 reads as NaN)
+  const bool f0 = ivt_fast(xm, x0, P), f1 = ivt_fast(x0, x1, P), f2 = ivt_fast(x1, x2, P);
+  const bool f3 = ivt_fast(x2, x3, P), f4 = ivt_fast(x3, x4, P);
+  return (f1 && !f0 ? 1u : 0u) | (f2 && !f1 ? 2u : 0u) | (f3 && !f2 ? 4u : 0u) | (f4 && !f3 ? 8u : 0u);
+}
+
+__device__ __forceinline__ long long ivt_group(int it) {
+  return (long long)blockIdx.x * (kIvtThreads * kIvtIters) + (long long)it * kIvtThreads + threadIdx.x;
+}
+
+// Pass 1a: run starts per tile.
+template <bool VEC>
 __global__ void __launch_bounds__(kIvtThreads) k_ivt_count(IvtDev P, int* tile_count) {
-  const long long t0 = 1 + (long long)blockIdx.x * kTile;
   int c = 0;
 #pragma unroll 4
-  for (int it = 0; it < kIvtIters; ++it) {
-    const long long k = t0 + (long long)it * kIvtThreads + threadIdx.x;
-    c += (k < P.n && ivt_run_start(P, k)) ? 1 : 0;
-  }
+  for (int it = 0; it < kIvtIters; ++it) c += __popc(ivt_group_starts<VEC>(P, ivt_group(it)));
   __shared__ int warp_sum[kIvtThreads / 32];
-  int v = c;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = v;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
     int sum = 0;
@@ -76,89 +105,124 @@ __global__ void __launch_bounds__(kIvtThreads) k_ivt_count(IvtDev P, int* tile_c
   }
 }
 
-// Exclusive scan of the tile counts (one block); total written to *total.
-__global__ void k_ivt_scan(const int* tile_count, int ntiles, long long* tile_off, long long* total) {
-  __shared__ long long part[1024];
-  __shared__ long long carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < ntiles; base += 1024) {
-    const int i = base + (int)threadIdx.x;
-    const long long v = i < ntiles ? tile_count[i] : 0;
-    part[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const long long add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-      __syncthreads();
-      part[threadIdx.x] += add;
-      __syncthreads();
-    }
-    if (i < ntiles) tile_off[i] = carry + part[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
-    __syncthreads();
+// Exclusive scan of the tile counts (one block of 1024 threads, each taking
+// a contiguous run of tiles); the total goes to *total.
+__global__ void __launch_bounds__(1024) k_ivt_scan(const int* tile_count, int ntiles, long long* tile_off,
+                                                   long long* total) {
+  __shared__ long long warp_tot[32];
+  const int per = (ntiles + 1023) / 1024;
+  const int t0 = (int)threadIdx.x * per;
+  long long mine = 0;
+  for (int i = t0; i < t0 + per && i < ntiles; ++i) mine += tile_count[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
   }
-  if (threadIdx.x == 0) *total = carry;
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    long long v = warp_tot[lane], wi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    warp_tot[lane] = wi - v;   // exclusive prefix of the warps
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  long long run = warp_tot[warp] + inc - mine;
+  for (int i = t0; i < t0 + per && i < ntiles; ++i) {
+    tile_off[i] = run;
+    run += tile_count[i];
+  }
 }
 
-// Pass 1b: write each tile's run starts at its offset, in stream order.
+// Pass 1b: write each tile's run starts at its offset, in stream order
+// (iteration, warp, lane, step).
+template <bool VEC>
 __global__ void __launch_bounds__(kIvtThreads) k_ivt_write(IvtDev P, const long long* tile_off, long long* starts) {
   __shared__ int warp_cnt[kIvtThreads / 32];
-  const long long t0 = 1 + (long long)blockIdx.x * kTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long run = tile_off[blockIdx.x];
   for (int it = 0; it < kIvtIters; ++it) {
-    const long long k = t0 + (long long)it * kIvtThreads + threadIdx.x;
-    const bool f = k < P.n && ivt_run_start(P, k);
-    const unsigned m = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) warp_cnt[warp] = __popc(m);
+    const long long m = ivt_group(it);
+    const unsigned bits = ivt_group_starts<VEC>(P, m);
+    const int c = __popc(bits);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_cnt[warp] = inc;
     __syncthreads();
     int before = 0, all = 0;
     for (int w = 0; w < kIvtThreads / 32; ++w) {
       before += w < warp ? warp_cnt[w] : 0;
       all += warp_cnt[w];
     }
-    if (f) starts[run + before + __popc(m & ((1u << lane) - 1u))] = k;
+    long long pos = run + before + inc - c;
+    for (int i = 0; i < kVec; ++i)
+      if (bits >> i & 1u) starts[pos++] = 4 * m + 1 + i;
     run += all;
     __syncthreads();
   }
 }
 
-// Pass 2: one thread per run: its end, amplitude, duration, peak velocity,
-// the window check and the event record; keep[i] = 1 for a kept saccade.
+// Pass 2: one warp per run: the run's end (the first slow step, found 32
+// steps at a time), peak velocity, the window check, the event record;
+// keep[i] = 1 for a kept saccade.
 __global__ void k_ivt_events(IvtDev P, const long long* starts, int m, opmm_ivt_event* ev, int* keep) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (i >= m) return;
   const long long a = starts[i];
   long long b = a;
   float peak = 0.0f;
-  for (;;) {
-    const float sp = ivt_speed(P, b);
-    if (!(sp > P.thr)) break;
-    peak = fmaxf(peak, sp);
-    ++b;
+  for (long long k0 = a;; k0 += 32) {
+    const float sp = ivt_speed(P, k0 + lane);
+    const bool fast = sp > P.thr;
+    const unsigned slow = __ballot_sync(0xffffffffu, !fast);
+    const int stop = slow ? __ffs(slow) - 1 : 32;      // lanes before it are the run's
+    if (lane < stop) peak = fmaxf(peak, sp);
+    if (slow) {
+      b = k0 + stop;
+      break;
+    }
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) peak = fmaxf(peak, __shfl_xor_sync(0xffffffffu, peak, o));
   const long long s = a - 1, e = b - 1;
   const float xs = P.x[s], xe = P.x[e];
   const float amp = fabsf(xe - xs);
   const float dur = ((float)(e - s) * 1000.0f) / P.fs;
   const long long ws = s - P.pre, we = e + P.post;
   bool ok = dur >= P.min_dur && amp >= P.min_amp && ws >= 0 && we <= P.n - 1;
-  for (long long k = ws; ok && k <= we; ++k) ok = ivt_valid(P.x[k], P);
-  opmm_ivt_event r;
-  r.onset = s;
-  r.end = e;
-  r.window_start = ws;
-  r.n_samples = (int32_t)(we - ws + 1);
-  r.onset_index = (int32_t)(s - ws);
-  r.theta_start_deg = xs;
-  r.theta_end_deg = xe;
-  r.amplitude_deg = amp;
-  r.duration_ms = dur;
-  r.peak_velocity_dps = peak;
-  r.reserved = 0;
-  ev[i] = r;
-  keep[i] = ok ? 1 : 0;
+  if (ok) {
+    bool good = true;
+    for (long long k = ws + lane; k <= we; k += 32) good = good && ivt_valid(P.x[k], P);
+    ok = __all_sync(0xffffffffu, good);
+  }
+  if (lane == 0) {
+    opmm_ivt_event r;
+    r.onset = s;
+    r.end = e;
+    r.window_start = ws;
+    r.n_samples = (int32_t)(we - ws + 1);
+    r.onset_index = (int32_t)(s - ws);
+    r.theta_start_deg = xs;
+    r.theta_end_deg = xe;
+    r.amplitude_deg = amp;
+    r.duration_ms = dur;
+    r.peak_velocity_dps = peak;
+    r.reserved = 0;
+    ev[i] = r;
+    keep[i] = ok ? 1 : 0;
+  }
 }
 
 int ivt_fail(const Status& s) {
@@ -213,7 +277,9 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
   if (s.ok()) s = b_off.ensure(sizeof(long long) * ((size_t)ntiles + 1));
   if (!s.ok()) return ivt_fail(s);
   long long* d_off = b_off.as<long long>();
-  k_ivt_count<<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>());
+  const bool vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;   // 16-byte loads need an aligned stream
+  if (vec) k_ivt_count<true><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>());
+  else k_ivt_count<false><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>());
   k_ivt_scan<<<1, 1024, 0, st>>>(b_count.as<int>(), ntiles, d_off, d_off + ntiles);
   s = cuda_status(cudaGetLastError(), "launch I-VT count");
   long long total = 0;
@@ -233,9 +299,11 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
     if (s.ok()) s = h_ev.ensure(sizeof(opmm_ivt_event) * (size_t)m);
     if (s.ok()) s = h_keep.ensure(sizeof(int) * (size_t)m);
     if (!s.ok()) return ivt_fail(s);
-    k_ivt_write<<<ntiles, kIvtThreads, 0, st>>>(P, d_off, b_starts.as<long long>());
-    k_ivt_events<<<(m + 127) / 128, 128, 0, st>>>(P, b_starts.as<long long>(), m, b_ev.as<opmm_ivt_event>(),
-                                                  b_keep.as<int>());
+    if (vec) k_ivt_write<true><<<ntiles, kIvtThreads, 0, st>>>(P, d_off, b_starts.as<long long>());
+    else k_ivt_write<false><<<ntiles, kIvtThreads, 0, st>>>(P, d_off, b_starts.as<long long>());
+    const long long warps_per_block = 4;
+    k_ivt_events<<<(unsigned)((m + warps_per_block - 1) / warps_per_block), 32 * warps_per_block, 0, st>>>(
+        P, b_starts.as<long long>(), m, b_ev.as<opmm_ivt_event>(), b_keep.as<int>());
     s = cuda_status(cudaGetLastError(), "launch I-VT events");
     if (s.ok())
       s = cuda_status(cudaMemcpyAsync(h_ev.ptr, b_ev.ptr, sizeof(opmm_ivt_event) * (size_t)m, cudaMemcpyDeviceToHost, st),
