@@ -488,6 +488,31 @@ def ivt_measure(G, ctx, n, reps=5, with_oracle=True):
     return out
 
 
+def run_ivt(args):
+    """The I-VT front end alone (--workload ivt): one JSON line for a raw
+    stream of 2^26 samples (2^22 with --quick)."""
+    import torch
+    import paper_2007_09884_gb300 as G
+    torch.cuda.set_device(0)
+    ctx = G.opmm_create(0)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    r = ivt_measure(G, ctx, 1 << (22 if args.quick else 26), reps=max(3, args.steps),
+                    with_oracle=not args.no_cpu_baseline)
+    clk = clocks.stop()
+    G.opmm_destroy(ctx)
+    out = {"metric": "raw stream samples/s through I-VT detection (saccade windows out)", "value": r["samples_per_s"],
+           "unit": "samples/s", "n_gpus": 1, "steps": max(3, args.steps), "warmup": 2,
+           "ms_per_step": 1e3 * r["seconds_median"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic raw stream (workloads.raw_stream)",
+           "config": {"workload": "ivt_stream", "samples": r["samples"], "sample_rate_hz": 1000.0,
+                      "l2": "stream larger than L2"},
+           "impl": "ours", "ivt": r, "clocks": clk}
+    if "cpu_baseline" in r:
+        out["cpu_baseline"] = r["cpu_baseline"]
+    return out
+
+
 # ------------------------------------------------------------------ serving
 def serve_run(G, ctx, traces_desc, arrivals, fit, cfg):
     """Submit saccades at the given arrival times (s), collect every result;
@@ -776,7 +801,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch1024",
-                    choices=["batch1024", "uneven10k", "single10", "serve", "surrogate"])
+                    choices=["batch1024", "uneven10k", "single10", "serve", "surrogate", "ivt"])
     ap.add_argument("--no-surrogate", action="store_true", help="leave the surrogate comparison out of the line")
     ap.add_argument("--rates", type=float, nargs="+", default=[1000.0, 10000.0, 50000.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -800,6 +825,8 @@ def main():
         out = run_serve(args) if rank == 0 else None
     elif args.workload == "surrogate":
         out = run_surrogate(args) if rank == 0 else None
+    elif args.workload == "ivt":
+        out = run_ivt(args) if rank == 0 else None
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:
