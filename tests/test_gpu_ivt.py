@@ -79,6 +79,17 @@ def test_device_stream_window_options_and_truncation(ctx):
     assert np.all(res["status"] == 0)
 
 
+def test_unaligned_device_stream_takes_the_scalar_path(ctx):
+    """A stream starting 4 bytes past a 16-byte boundary is read sample by
+    sample (no 16-byte loads); the events are the same."""
+    torch = pytest.importorskip("torch")
+    x, _ = W.raw_stream(100_003, seed=5)
+    full = torch.from_numpy(np.concatenate([np.zeros(1, np.float32), x])).cuda()
+    view = full[1:]
+    assert view.data_ptr() % 16 != 0
+    _same(G.opmm_detect_saccades(ctx, view, 1000.0), ivt(x, 1000.0))
+
+
 def test_rejected_arguments(ctx):
     x = np.zeros(100, np.float32)
     for bad in (dict(threshold_dps=0.0), dict(pre_samples=-1), dict(valid_min_deg=5.0, valid_max_deg=-5.0)):
