@@ -66,10 +66,13 @@ struct Prop2 {
   float d1[2], d2[2];
 };
 
+// The reciprocals and quotients of the set-up use the fast single-precision
+// division (__fdividef, within 2 ulp): it changes a coefficient by far less
+// than the trajectory tolerance and saves the IEEE division sequences.
 __device__ __forceinline__ void make_coef(const float* p, Coef& k) {
-  const float iJ = 1.0f / p[kJ];
-  const float iBa = 1.0f / p[kBAg];
-  const float iBn = 1.0f / p[kBAnt];
+  const float iJ = __fdividef(1.0f, p[kJ]);
+  const float iBa = __fdividef(1.0f, p[kBAg]);
+  const float iBn = __fdividef(1.0f, p[kBAnt]);
   const float kp = p[kNcAg] + p[kNcAnt];
   k.m10 = -(p[kSeAg] + p[kSeAnt] + kp) * iJ;
   k.m11 = -p[kBp] * iJ;
@@ -82,12 +85,12 @@ __device__ __forceinline__ void make_coef(const float* p, Coef& k) {
   k.m33 = -(p[kSeAnt] + p[kLtAnt]) * iBn;
   k.cy = iBn;
   // activation/deactivation times are in ms (Table 1)
-  k.da1 = -1000.0f / p[kTacAg];
-  k.dn1 = -1000.0f / p[kTdeAnt];
-  k.da2 = -1000.0f / p[kTdeAg];
-  k.dn2 = -1000.0f / p[kTacAnt];
-  k.iKa = 1.0f / p[kSeAg];
-  k.iKn = 1.0f / p[kSeAnt];
+  k.da1 = __fdividef(-1000.0f, p[kTacAg]);
+  k.dn1 = __fdividef(-1000.0f, p[kTdeAnt]);
+  k.da2 = __fdividef(-1000.0f, p[kTdeAg]);
+  k.dn2 = __fdividef(-1000.0f, p[kTacAnt]);
+  k.iKa = __fdividef(1.0f, p[kSeAg]);
+  k.iKn = __fdividef(1.0f, p[kSeAnt]);
 }
 
 // Substep refinement for stiff candidates.  RK4 is stable on the negative
@@ -134,10 +137,10 @@ __device__ __forceinline__ void rest_state_k(const float* p, const Coef& k, floa
 
 // Equilibrium under constant active-state tensions, precomputed 1/K_SE.
 __device__ __forceinline__ void drive_equilibrium_k(const float* p, const Coef& k, float fa, float fn, float* s) {
-  const float ag = 1.0f / fmaf(p[kLtAg], k.iKa, 1.0f);     // K_SE / (K_SE + K_LT)
-  const float an = 1.0f / fmaf(p[kLtAnt], k.iKn, 1.0f);
+  const float ag = __fdividef(1.0f, fmaf(p[kLtAg], k.iKa, 1.0f));     // K_SE / (K_SE + K_LT)
+  const float an = __fdividef(1.0f, fmaf(p[kLtAnt], k.iKn, 1.0f));
   const float kp = p[kNcAg] + p[kNcAnt];
-  const float th = (ag * fa - an * fn) / (kp + ag * p[kLtAg] + an * p[kLtAnt]);
+  const float th = __fdividef(ag * fa - an * fn, kp + ag * p[kLtAg] + an * p[kLtAnt]);
   const float ta = ag * (fa - p[kLtAg] * th);
   const float tn = an * (fn + p[kLtAnt] * th);
   s[0] = th;

@@ -107,12 +107,16 @@ def test_forward_backward_match_fp64_oracle(ctx):
 
 def test_training_reduces_loss_and_weights_round_trip(ctx, tmp_path):
     # targets ln(U(0.8, 1.2)) / 0.2 have variance ~0.333 per output: an untrained
-    # network starts there; 600 steps of 2,048 generated saccades must cut it
+    # network starts there; 600 steps of 2,048 generated saccades must cut it.
+    # The mean of the last 50 losses is known to about 0.2% (batch noise), but
+    # where 600 steps land varies from run to run of the same schedule: seeds
+    # (3, 11), (3, 12), (4, 11) ended at 0.913-0.948 of the first losses, so the
+    # bound is 0.96.
     G.opmm_surrogate_init(ctx, 3)
     losses = G.opmm_surrogate_train(ctx, 600, batch=2048, lr=2e-3, data_seed=11)
     assert np.all(np.isfinite(losses))
     assert 0.30 < losses[:5].mean() < 0.37
-    assert losses[-50:].mean() < 0.93 * losses[:5].mean(), (losses[:5], losses[-50:])
+    assert losses[-50:].mean() < 0.96 * losses[:5].mean(), (losses[:5], losses[-50:])
     path = str(tmp_path / "w.bin")
     G.opmm_surrogate_save(ctx, path)
     p1 = G.opmm_surrogate_get_params(ctx)
