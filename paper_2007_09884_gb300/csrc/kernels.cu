@@ -102,22 +102,19 @@ struct PtrSrc {
   }
 };
 
-// Candidate in ln-parameter space: u_j = a_j + s (b_j - a_j), or a trial
-// point given by trial_coord/shrink_coord (see the search kernel).
+// Candidate in ln-parameter space, from two rows in shared memory: a vertex
+// (u = a), or the search's trial-point form u = a + (b - a) / 2 (a = b for the
+// controller's four trial points, best vertex and vertex q - 3 for a shrink
+// point).
 struct ULinSrc {
-  const float* a;   // base point (shared memory)
-  const float* b;   // second point (shared memory)
-  float s;          // coefficient: u = a + s (b - a); a trial point uses its own form
-  int mode;         // 0: u = a (vertex), 1: trial_coord(q, a = centroid, b = worst), 2: shrink (a = best, b = vertex)
-  int q;
-  const float* pc;
+  const float* a;   // first row
+  const float* b;   // second row
+  bool half;        // u = a + (b - a) / 2, else u = a
+  const float* pc;  // box centre
   float lnlo, lnhi;
   __device__ __forceinline__ void load(float (&o)[kNumParams]) const;
 };
 
-__device__ __forceinline__ float objective_lean_guard(const float (&p)[kNumParams], const SacConst& sc) {
-  return too_stiff(p, sc.h) ? INFINITY : 0.0f;
-}
 
 // Stage one saccade for a block: TMA bulk copy of the raw trace, then the
 // positive-frame trace minus the end fixation and the compensated sum of the
@@ -417,7 +414,7 @@ __device__ __forceinline__ float shrink_coord(float x1, float xi) { return x1 + 
 __device__ __forceinline__ void ULinSrc::load(float (&o)[kNumParams]) const {
 #pragma unroll
   for (int j = 0; j < kNumParams; ++j) {
-    const float u = mode == 0 ? a[j] : (mode == 1 ? trial_coord(q, a[j], b[j]) : shrink_coord(a[j], b[j]));
+    const float u = half ? shrink_coord(a[j], b[j]) : a[j];
     o[j] = pc[j] * __expf(fminf(fmaxf(u, lnlo), lnhi));
   }
 }
@@ -782,7 +779,7 @@ __device__ __forceinline__ int eval_candidate(GroupSmem<G, N>& g, const SearchSm
   if (g.kind == 0) {
     const int gi = c / verts<N>(), v = c - gi * verts<N>();
     if constexpr (LEAN) {
-      const ULinSrc src{g.U[gi][v], g.U[gi][v], 0.0f, 0, 0, S.pc, P.lnlo, P.lnhi};
+      const ULinSrc src{g.U[gi][v], g.U[gi][v], false, S.pc, P.lnlo, P.lnhi};
       g.F[gi][v] = objective_lean(src, sc, z, sum0, c0, &pe);
     } else {
       float u[N];
@@ -797,7 +794,7 @@ __device__ __forceinline__ int eval_candidate(GroupSmem<G, N>& g, const SearchSm
   const float* bb;
   trial_rows(g, gi, q, a, bb);
   if constexpr (LEAN) {
-    const ULinSrc src{a, bb, 0.0f, 2, 0, S.pc, P.lnlo, P.lnhi};
+    const ULinSrc src{a, bb, true, S.pc, P.lnlo, P.lnhi};
     g.FT[gi][q] = objective_lean(src, sc, z, sum0, c0, &pe);
   } else {
     float u[N];

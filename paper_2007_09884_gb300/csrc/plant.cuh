@@ -491,16 +491,6 @@ __device__ __forceinline__ void rk4_vec(const Coef& k, float da, float dn, float
   for (int i = 0; i < 6; ++i) e[i] = w[i];
 }
 
-// Stiffness guard shared with the oracle's rule: even at the finest substep
-// (h / 2^kMaxRefine), h * (B_P/J + (K_SE_AG + K_LT_AG)/B_AG + (K_SE_ANT +
-// K_LT_ANT)/B_ANT + 1/min tau) must stay <= 2.5.
-__device__ __forceinline__ bool too_stiff(const float* p, float h) {
-  float tmin = fminf(fminf(p[kTacAg], p[kTacAnt]), fminf(p[kTdeAg], p[kTdeAnt]));
-  float est = p[kBp] / p[kJ] + (p[kSeAg] + p[kLtAg]) / p[kBAg] +
-              (p[kSeAnt] + p[kLtAnt]) / p[kBAnt] + 1000.0f / tmin;
-  return !(h * pow2neg(kMaxRefine) * est <= 2.5f);
-}
-
 // n sample intervals of one phase with the one-sample propagator, emitting
 // theta_k - thf after each: e[0] + off in the pulse phase (deviation from the
 // pulse equilibrium), e[0] itself in the step phase (PH = 2, whose equilibrium
