@@ -513,6 +513,65 @@ def run_ivt(args):
     return out
 
 
+def run_gemm(args):
+    """The surrogate's tensor-core GEMM (opmm_gemm_bf16: tcgen05, TMEM
+    accumulator, TMA ring) alone (--workload gemm): D = A.B^T in BF16 with FP32
+    accumulation at the surrogate's layer shape (4,096 x 512 x 512) and at a
+    large square shape, each call timed with CUDA events on the library's
+    stream (the call also clears and reads back the error word), against the
+    measured BF16 peak; cuBLAS (torch.matmul) on the same shapes beside it."""
+    import torch
+    import paper_2007_09884_gb300 as G
+    torch.cuda.set_device(0)
+    ctx = G.opmm_create(0)
+    stream = torch.cuda.current_stream()
+    G.opmm_set_stream(ctx, stream.cuda_stream)
+    mp = measured_peaks() or {}
+    peak = float(mp.get("bf16_tflops") or 1900.0)
+    rows = []
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for (M, N, K) in ((4096, 512, 512), (8192, 8192, 8192)):
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        Bm = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        D = torch.empty(M, N, device="cuda", dtype=torch.float32)
+        reps = max(3, args.steps) * (20 if M * N * K < 1 << 32 else 2)
+        for _ in range(3):
+            G.opmm_gemm_bf16(ctx, A, Bm, out=D)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            G.opmm_gemm_bf16(ctx, A, Bm, out=D)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ref = (A.float() @ Bm.float().t())
+        err = float((D - ref).abs().max() / ref.abs().max())
+        for _ in range(3):
+            torch.matmul(A, Bm.t())
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            torch.matmul(A, Bm.t())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_cublas = e0.elapsed_time(e1) / reps
+        fl = 2.0 * M * N * K
+        rows.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": fl / ms / 1e9, "frac_of_bf16_peak": fl / ms / 1e9 / peak,
+                     "max_rel_err_vs_fp32_product": err, "cublas_ms": ms_cublas, "cublas_tflops": fl / ms_cublas / 1e9})
+    G.opmm_destroy(ctx)
+    big = rows[-1]
+    return {"metric": "BF16 tensor-core GEMM TFLOP/s (surrogate layer primitive)", "value": big["tflops"],
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": 3, "ms_per_step": big["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (normal random operands)", "config": {"workload": "gemm", "shapes": [r["M"] for r in rows]},
+            "impl": "ours",
+            "roofline": {"bound": "tensor", "achieved": big["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": big["tflops"] / peak, "peak_basis": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"},
+            "rows": rows}
+
+
 # ------------------------------------------------------------------ serving
 def serve_run(G, ctx, traces_desc, arrivals, fit, cfg):
     """Submit saccades at the given arrival times (s), collect every result;
@@ -801,7 +860,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch1024",
-                    choices=["batch1024", "uneven10k", "single10", "serve", "surrogate", "ivt"])
+                    choices=["batch1024", "uneven10k", "single10", "serve", "surrogate", "ivt", "gemm"])
     ap.add_argument("--no-surrogate", action="store_true", help="leave the surrogate comparison out of the line")
     ap.add_argument("--rates", type=float, nargs="+", default=[1000.0, 10000.0, 50000.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -827,6 +886,8 @@ def main():
         out = run_surrogate(args) if rank == 0 else None
     elif args.workload == "ivt":
         out = run_ivt(args) if rank == 0 else None
+    elif args.workload == "gemm":
+        out = run_gemm(args) if rank == 0 else None
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:
