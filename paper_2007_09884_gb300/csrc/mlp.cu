@@ -5,7 +5,7 @@
 // 5th-generation tensor cores:
 //
 //   k_gemm_tn   D[M,N] = A[M,K] . B[N,K]^T, BF16 operands, FP32 accumulate.
-//               Warp 4 streams 128x64 tiles of A and B into a 4-stage shared
+//               Warp 4 streams 128x64 tiles of A and B into a 3-stage shared
 //               memory ring with TMA (cp.async.bulk.tensor, 128-byte swizzle);
 //               one thread of warp 5 issues tcgen05.mma (M = 128, N = 128,
 //               K = 16 per instruction) into an FP32 accumulator in tensor
@@ -110,7 +110,7 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 // ------------------------------------------------------------------ GEMM
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(kGemmThreads, 2)
     k_gemm_tn(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, GemmArgs g) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);

@@ -17,8 +17,10 @@ constexpr int kLayers = 4;                // hidden layers (tensor-core GEMMs)
 constexpr int kOut = 18;                  // OPC vector in log units
 constexpr float kTargetScale = 0.2f;      // output y = ln(p / centre) / 0.2
 
-// GEMM tiling: 128 x 128 output tile, 64-wide K slices, 4-stage ring.
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
+// GEMM tiling: 128 x 128 output tile, 64-wide K slices, 3-stage ring (99 KB of
+// shared memory, so two CTAs share an SM and one's epilogue overlaps the
+// other's main loop).
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3;
 constexpr int kTileABytes = kBM * kBK * 2;
 constexpr int kTileBBytes = kBN * kBK * 2;
 constexpr int kStageBytes = kTileABytes + kTileBBytes;
