@@ -671,7 +671,8 @@ def surrogate_compare(G, ctx, quick=False):
     """10,000 uneven saccades (250/500/1000 Hz, both directions, 1-40 deg,
     40-400 samples): plain search at 16,384 x 30 against the surrogate-seeded
     search at 1,024 x 20 in a +-5% box whose misses (> 0.1 deg) fall back to
-    the plain search; plus the network alone on 100,000 held-out saccades."""
+    the plain search; each followed by the Levenberg-Marquardt refinement as
+    variants; plus the network alone on 100,000 held-out saccades."""
     import torch
     training = train_surrogate(G, ctx, quick)
     w = W.uneven10k(B=512 if quick else 10000)
@@ -715,8 +716,16 @@ def surrogate_compare(G, ctx, quick=False):
     (r2, n2), t2 = timed(lambda: G.opmm_fit_batch_seeded(ctx, batch, seeded, plain, 0.1))
     wide = dict(seeded, box_lo=0.9, box_hi=1.1, init_step=0.05)
     (r3, n3), t3 = timed(lambda: G.opmm_fit_batch_seeded(ctx, batch, wide, fallback, 0.1))
+    # Levenberg-Marquardt refinement (10 iterations) of each search's results
+    rpr, tpr = timed(lambda: G.opmm_refine_batch(ctx, batch, rp["opc"], iterations=10, pulse_init=pulse))
+    rsr, tsr = timed(lambda: G.opmm_refine_batch(ctx, batch, rs["opc"], iterations=10, pulse_init=pulse))
+    r1r, t1r = timed(lambda: G.opmm_refine_batch(ctx, batch, r1["opc"], iterations=10, pulse_init=pulse))
     variants = {"seeded_only": row(r1, t1), "seeded_full_budget_fallback": dict(row(r2, t2, n2), fallback=plain),
-                "seeded_box_10pct": dict(row(r3, t3, n3), search=wide)}
+                "seeded_box_10pct": dict(row(r3, t3, n3), search=wide),
+                "plain_then_refine": dict(row(rpr, tp + tpr), refine_seconds=tpr, refine_iterations=10),
+                "seeded_with_fallback_then_refine": dict(row(rsr, ts + tsr), refine_seconds=tsr,
+                                                         refine_iterations=10),
+                "seeded_only_then_refine": dict(row(r1r, t1 + t1r), refine_seconds=t1r, refine_iterations=10)}
 
     # the network alone on held-out saccades (drawn by the numpy generator;
     # training draws its saccades on the device)

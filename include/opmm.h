@@ -295,8 +295,9 @@ int opmm_fit_batch_seeded(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, co
  * theta_k - y_k of each saccade, from start_opc (e.g. a search's or the
  * surrogate's result), in the search's ln coordinates around the box centre,
  * clamped to the box.  The Jacobian is taken by central differences of step
- * fd_step (ln units) through the same RK4 plant, A = J^T J and g = J^T r in
- * FP64, (A + lambda D) du = -g with D = diag(max(A_jj, 1e-9 max A_ii)); a step
+ * fd_step (ln units) through the same RK4 plant, A = J^T J and g = J^T r
+ * (FP32 products, compensated sums), (A + lambda D) du = -g with
+ * D = diag(max(A_jj, 1e-9 max A_ii)) solved in FP64; a step
  * is kept when it lowers the mean squared error (lambda / 10), else lambda * 10.
  * With OPMM_MODEL_9 the nine Table 2 coordinates are refined (start_opc gives
  * each through its first OPC entry) and the neural signal stays at the centre. */

@@ -1295,12 +1295,14 @@ __global__ void k_finalize(const DevSac* sacs, const float* traces, const float*
 // search's ln coordinates, box and clamp.  One iteration: at a new point the
 // Jacobian by central differences of step delta (2N trajectories, one per
 // thread; a column whose two points are too stiff is zero), A = J^T J and
-// g = J^T r in FP64; (A + lambda D) du = -g with D = diag(max(A_jj, 1e-9
+// g = J^T r (FP32 products, compensated sums); (A + lambda D) du = -g with
+// D = diag(max(A_jj, 1e-9
 // max_i A_ii)) solved by Cholesky in FP64; u' = clamp(u + du); accept when
 // f(u') < f(u) (lambda / 10, floor 1e-12, new Jacobian), else lambda * 10
 // (ceiling 1e12).  f = sum_k r_k^2 / L over every sample.  Stops early when
-// A is zero or the system is not positive definite.  Trajectories go to a
-// per-block scratch area in global memory (2N + 2 rows of lcap floats).
+// A is zero or the system is not positive definite.  Trajectories (2N + 2
+// rows of lcap floats) go to shared memory when they fit, else to a per-block
+// scratch area in global memory.
 constexpr int kRefineThreads = 64;
 
 struct RowSink {
@@ -1311,11 +1313,13 @@ struct RowSink {
 
 // theta_k - thf (positive frame) for every sample of the window into row;
 // false (row untouched past onset) when the candidate is too stiff.
-__device__ bool refine_row(const float (&p)[kNumParams], const SacConst& sc, float* row, int* pe) {
+// qs: the calling thread's propagator slot in shared memory (stride
+// kRefineThreads), so that the powering runs in place as in the search.
+__device__ bool refine_row(const float (&p)[kNumParams], const SacConst& sc, float* row, int* pe, float* qs) {
   const int kend = min(sc.onset, sc.L - 1);
   for (int k = 0; k <= kend; ++k) row[k] = sc.th0 - sc.thf;
   RowSink s{row};
-  return walk(p, sc, s, nullptr, 0, true, pe) >= 0;
+  return walk(p, sc, s, qs, kRefineThreads, true, pe) >= 0;
 }
 
 template <int N>
@@ -1323,6 +1327,7 @@ struct RefineSmem {
   double A[N * N];
   double M[N * N];   // damped system, factored in place
   double du[N];
+  double inv[N];     // reciprocals of the factor's diagonal
   double g[N];
   double red[kRefineThreads];
   float u[N], ut[N];
@@ -1360,18 +1365,23 @@ __device__ double refine_f(RefineSmem<N>& S, const float* row, const float* z, i
   return refine_sum<N>(S, acc) / (double)L;
 }
 
+// rows_in_smem: the 2N + 2 trajectory rows live in dynamic shared memory after
+// the staged trace (short windows; the dot products of J^T J then read shared
+// memory), else in the per-block global scratch area.
 template <int N>
 __global__ void __launch_bounds__(kRefineThreads) k_refine(const DevSac* sacs, const float* traces, const float* pcs,
                                                             const float* start, int K, float lnlo, float lnhi,
                                                             float delta, float lambda0, int lcap, float* scratch,
-                                                            opmm_fit_result* out, unsigned* err) {
+                                                            int rows_in_smem, opmm_fit_result* out, unsigned* err) {
   __shared__ RefineSmem<N> S;
   extern __shared__ __align__(128) unsigned char smraw[];
   float* yraw = reinterpret_cast<float*>(smraw);
   float* z = yraw + lcap;
+  float* qslot = z + lcap;                                  // kQSlotFloats x kRefineThreads
   const int b = blockIdx.x, tid = threadIdx.x;
   const DevSac d = sacs[b];
-  float* rows = scratch + (size_t)b * (2 * N + 2) * (size_t)lcap;
+  float* rows = rows_in_smem ? qslot + kQSlotFloats * kRefineThreads
+                             : scratch + (size_t)b * (2 * N + 2) * (size_t)lcap;
   if (tid == 0) {
     mbar_init(&S.bar, 1);
     fence_mbar_init();
@@ -1408,7 +1418,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(const DevSac* sacs, c
     float p[kNumParams];
     u_to_p<N>(S.u, S.pc, lnlo, lnhi, p);
     int pe = 0;
-    S.trial_ok = refine_row(p, sc, rcur[0], &pe) ? 1 : 0;
+    S.trial_ok = refine_row(p, sc, rcur[0], &pe, qslot + tid) ? 1 : 0;
     S.pe += pe;
   }
   __syncthreads();
@@ -1431,13 +1441,22 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(const DevSac* sacs, c
         float p[kNumParams];
         u_to_p<N>(ut, S.pc, lnlo, lnhi, p);
         int pe = 0;
-        S.bad[tid] = refine_row(p, sc, rows + (size_t)tid * lcap, &pe) ? 0 : 1;
+        S.bad[tid] = refine_row(p, sc, rows + (size_t)tid * lcap, &pe, qslot + tid) ? 0 : 1;
         if (pe) atomicAdd(&S.pe, 1);
       }
       __syncthreads();
       // A (lower triangle) and g: one task per entry, FP64
       constexpr int kTasks = N * (N + 1) / 2 + N;
-      const double inv2d = 1.0 / (2.0 * (double)delta);
+      // J columns in place of the plus rows (FP32); the products below sum
+      // with compensation in FP32 (the GPU's FP64 rate is a small fraction of
+      // its FP32 rate) and enter the FP64 solve
+      const float inv2d = 1.0f / (2.0f * delta);
+      for (int e = tid; e < N * sc.L; e += kRefineThreads) {
+        const int j = e / sc.L, k = e - j * sc.L;
+        float* jp = rows + (size_t)(2 * j) * lcap;
+        jp[k] = (jp[k] - rows[(size_t)(2 * j + 1) * lcap + k]) * inv2d;
+      }
+      __syncthreads();
       for (int t = tid; t < kTasks; t += kRefineThreads) {
         int a, bb;
         const bool is_g = t >= N * (N + 1) / 2;
@@ -1454,15 +1473,17 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(const DevSac* sacs, c
         const bool zb = bb >= 0 && (S.bad[2 * bb] || S.bad[2 * bb + 1]);
         double acc = 0.0;
         if (!za && !zb) {
-          const float* ap = rows + (size_t)(2 * a) * lcap;
-          const float* am = rows + (size_t)(2 * a + 1) * lcap;
+          const float* ja = rows + (size_t)(2 * a) * lcap;
+          const float* jb = is_g ? r0 : rows + (size_t)(2 * bb) * lcap;
+          float sum = 0.0f, c = 0.0f;
           for (int k = 0; k < sc.L; ++k) {
-            const double ja = ((double)ap[k] - (double)am[k]) * inv2d;
-            double other;
-            if (is_g) other = (double)r0[k] - (double)z[k];
-            else other = ((double)rows[(size_t)(2 * bb) * lcap + k] - (double)rows[(size_t)(2 * bb + 1) * lcap + k]) * inv2d;
-            acc += ja * other;
+            const float other = is_g ? jb[k] - z[k] : jb[k];
+            const float y = fmaf(ja[k], other, -c);
+            const float tt = sum + y;
+            c = (tt - sum) - y;
+            sum = tt;
           }
+          acc = (double)sum - (double)c;
         }
         if (is_g) S.g[a] = acc;
         else S.A[a * N + bb] = S.A[bb * N + a] = acc;
@@ -1473,54 +1494,68 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(const DevSac* sacs, c
         S.evals += 2 * N;
       }
     }
-    // damped normal equations, one thread, FP64
-    if (tid == 0) {
+    // damped normal equations in FP64 by warp 0: the Cholesky factor column by
+    // column (every lane forms the diagonal, the rows below go over the lanes,
+    // multiplied by the diagonal's reciprocal), then lane 0 substitutes and
+    // simulates the trial point
+    if (tid < 32) {
       double amax = 0.0;
       for (int j = 0; j < N; ++j) amax = S.A[j * N + j] > amax ? S.A[j * N + j] : amax;
-      S.go = amax > 0.0 ? 1 : 0;
-      if (S.go) {
-        double* M = S.M;
-        double* du = S.du;
-        for (int i = 0; i < N * N; ++i) M[i] = S.A[i];
-        for (int j = 0; j < N; ++j) {
-          const double dj = S.A[j * N + j] > 1e-9 * amax ? S.A[j * N + j] : 1e-9 * amax;
-          M[j * N + j] += S.lambda * dj;
+      int go = amax > 0.0 ? 1 : 0;
+      double* M = S.M;
+      double* du = S.du;
+      if (go) {
+        for (int e = tid; e < N * N; e += 32) M[e] = S.A[e];
+        __syncwarp();
+        if (tid < N) {
+          const double dj = S.A[tid * N + tid] > 1e-9 * amax ? S.A[tid * N + tid] : 1e-9 * amax;
+          M[tid * N + tid] += S.lambda * dj;
         }
-        for (int j = 0; j < N && S.go; ++j) {
+        __syncwarp();
+        for (int j = 0; j < N; ++j) {
           double sjj = M[j * N + j];
           for (int k = 0; k < j; ++k) sjj -= M[j * N + k] * M[j * N + k];
-          if (!(sjj > 0.0)) { S.go = 0; break; }
-          const double ljj = sqrt(sjj);
-          M[j * N + j] = ljj;
-          for (int i = j + 1; i < N; ++i) {
+          if (!(sjj > 0.0)) {
+            go = 0;
+            break;
+          }
+          const double ljj = sqrt(sjj), il = 1.0 / ljj;
+          __syncwarp();
+          if (tid == 0) {
+            M[j * N + j] = ljj;
+            S.inv[j] = il;
+          }
+          for (int i = j + 1 + tid; i < N; i += 32) {
             double t = M[i * N + j];
             for (int k = 0; k < j; ++k) t -= M[i * N + k] * M[j * N + k];
-            M[i * N + j] = t / ljj;
+            M[i * N + j] = t * il;
           }
-        }
-        if (S.go) {
-          for (int i = 0; i < N; ++i) {
-            double t = -S.g[i];
-            for (int k = 0; k < i; ++k) t -= M[i * N + k] * du[k];
-            du[i] = t / M[i * N + i];
-          }
-          for (int i = N - 1; i >= 0; --i) {
-            double t = du[i];
-            for (int k = i + 1; k < N; ++k) t -= M[k * N + i] * du[k];
-            du[i] = t / M[i * N + i];
-          }
-          for (int j = 0; j < N; ++j) {
-            const double v = (double)S.u[j] + du[j];
-            S.ut[j] = (float)(v < (double)lnlo ? (double)lnlo : (v > (double)lnhi ? (double)lnhi : v));
-          }
-          float p[kNumParams];
-          u_to_p<N>(S.ut, S.pc, lnlo, lnhi, p);
-          int pe = 0;
-          S.trial_ok = refine_row(p, sc, rcur[S.cur ^ 1], &pe) ? 1 : 0;
-          S.pe += pe;
-          S.evals += 1;
+          __syncwarp();
         }
       }
+      if (go && tid == 0) {
+        for (int i = 0; i < N; ++i) {
+          double t = -S.g[i];
+          for (int k = 0; k < i; ++k) t -= M[i * N + k] * du[k];
+          du[i] = t * S.inv[i];
+        }
+        for (int i = N - 1; i >= 0; --i) {
+          double t = du[i];
+          for (int k = i + 1; k < N; ++k) t -= M[k * N + i] * du[k];
+          du[i] = t * S.inv[i];
+        }
+        for (int j = 0; j < N; ++j) {
+          const double v = (double)S.u[j] + du[j];
+          S.ut[j] = (float)(v < (double)lnlo ? (double)lnlo : (v > (double)lnhi ? (double)lnhi : v));
+        }
+        float p[kNumParams];
+        u_to_p<N>(S.ut, S.pc, lnlo, lnhi, p);
+        int pe = 0;
+        S.trial_ok = refine_row(p, sc, rcur[S.cur ^ 1], &pe, qslot + tid) ? 1 : 0;
+        S.pe += pe;
+        S.evals += 1;
+      }
+      if (tid == 0) S.go = go;
     }
     __syncthreads();
     if (!S.go) break;
@@ -1554,18 +1589,29 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(const DevSac* sacs, c
     r.pulse_end_evals = S.pe;
     r.reserved = 0;
     r.source = OPMM_SOURCE_REFINED;
-    if (isfinite(S.f)) {
-      double mse, mae;
-      errors64(r.opc, d, traces + d.off, &mse, &mae);
-      r.rms_deg = sqrt(mse);
-      r.l1_deg = mae;
-      r.status = 0;
-    } else {
-      r.rms_deg = INFINITY;
-      r.l1_deg = INFINITY;
-      r.status = 1;
-    }
+    // the FP64 check of the refined vector runs in k_refine_check
+    r.rms_deg = 0.0;
+    r.l1_deg = 0.0;
+    r.status = isfinite(S.f) ? 0 : 1;
     out[b] = r;
+  }
+}
+
+// FP64 re-computation of each refined vector's errors (as k_finalize does for
+// the search), one thread per saccade spread over the SMs.
+__global__ void k_refine_check(const DevSac* sacs, const float* traces, int n, opmm_fit_result* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  opmm_fit_result& r = out[i];
+  if (r.status == 0) {
+    const DevSac d = sacs[i];
+    double mse, mae;
+    errors64(r.opc, d, traces + d.off, &mse, &mae);
+    r.rms_deg = sqrt(mse);
+    r.l1_deg = mae;
+  } else {
+    r.rms_deg = INFINITY;
+    r.l1_deg = INFINITY;
   }
 }
 
@@ -1573,20 +1619,28 @@ cudaError_t launch_refine(int dim, const DevSac* sacs, const float* traces, cons
                           int n, int K, float lnlo, float lnhi, float delta, float lambda0, int lcap, float* scratch,
                           opmm_fit_result* out, unsigned* err, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const size_t smem = 2 * (size_t)lcap * sizeof(float);
+  // the trajectory rows go to shared memory when they fit in 96 KB (windows up
+  // to about 600 samples with 18 coordinates), leaving room for two blocks
+  const size_t rows_bytes = (2 * (size_t)dim + 2) * (size_t)lcap * sizeof(float);
+  const int in_smem = rows_bytes <= (size_t)96 * 1024 ? 1 : 0;
+  const size_t smem = 2 * (size_t)lcap * sizeof(float) + (size_t)kQSlotFloats * kRefineThreads * sizeof(float) +
+                      (in_smem ? rows_bytes : 0);
   if (dim == 9) {
     cudaError_t e = cudaFuncSetAttribute(k_refine<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_refine<9><<<n, kRefineThreads, smem, st>>>(sacs, traces, pcs, start, K, lnlo, lnhi, delta, lambda0, lcap,
-                                                 scratch, out, err);
+                                                 scratch, in_smem, out, err);
   } else if (dim == kNumParams) {
     cudaError_t e = cudaFuncSetAttribute(k_refine<kNumParams>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_refine<kNumParams><<<n, kRefineThreads, smem, st>>>(sacs, traces, pcs, start, K, lnlo, lnhi, delta, lambda0,
-                                                          lcap, scratch, out, err);
+                                                          lcap, scratch, in_smem, out, err);
   } else {
     return cudaErrorInvalidValue;
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_refine_check<<<(n + 3) / 4, 4, 0, st>>>(sacs, traces, n, out);
   return cudaGetLastError();
 }
 
