@@ -369,7 +369,7 @@ typedef struct {
  * to *n_events.  Errors: OPMM_EINVAL for bad arguments (n_samples < 2,
  * non-positive rate or threshold, negative filters, windows or max_events,
  * valid_min_deg > valid_max_deg); OPMM_ENOMEM when the stream has more than
- * 2^24 runs of fast steps (a threshold below the noise) or scratch allocation
+ * 2^26 runs of fast steps (a threshold below the noise) or scratch allocation
  * fails; OPMM_ECUDA for CUDA errors. */
 int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int64_t n_samples, float sample_rate_hz,
                          const opmm_ivt_opts* opts, opmm_ivt_event* out, int32_t max_events, int32_t* n_events);

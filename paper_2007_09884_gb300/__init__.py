@@ -289,6 +289,7 @@ def opmm_create(device: int = 0):
 
 
 def opmm_destroy(ctx):
+    _IVT_OUT.pop(_ctx_key(ctx), None)
     load_library().opmm_destroy(ctx)
 
 
@@ -405,6 +406,13 @@ IVT_EVENT_DTYPE = np.dtype([("onset", "<i8"), ("end", "<i8"), ("window_start", "
                             ("reserved", "<i4")])
 
 
+_IVT_OUT = {}
+
+
+def _ctx_key(ctx) -> int:
+    return ctypes.cast(ctx, ctypes.c_void_p).value or 0
+
+
 def opmm_detect_saccades(ctx, stream, sample_rate_hz, threshold_dps=30.0, min_duration_ms=6.0,
                          min_amplitude_deg=4.0, valid_min_deg=-90.0, valid_max_deg=90.0, pre_samples=10,
                          post_samples=40, max_events=None) -> np.ndarray:
@@ -419,7 +427,12 @@ def opmm_detect_saccades(ctx, stream, sample_rate_hz, threshold_dps=30.0, min_du
     ptr, keep = _ptr(stream)
     n = int(stream.numel()) if _is_torch(stream) else int(keep.size)
     cap = int(max_events) if max_events is not None else max(16, n // 64)
-    out = np.zeros(cap, dtype=IVT_EVENT_DTYPE)
+    # the event array is kept per context and reused (its pages are touched
+    # once); the caller gets a copy of the events found
+    out = _IVT_OUT.get(_ctx_key(ctx))
+    if out is None or out.size < cap:
+        out = np.zeros(cap, dtype=IVT_EVENT_DTYPE)
+        _IVT_OUT[_ctx_key(ctx)] = out
     found = ctypes.c_int32()
     _check(ctx, lib.opmm_detect_saccades(ctx, ptr, ctypes.c_int64(n), ctypes.c_float(sample_rate_hz),
                                          ctypes.byref(o), out.ctypes.data, cap, ctypes.byref(found)))

@@ -7,10 +7,14 @@
 // Step k (samples k - 1, k) is fast when both samples are valid (finite, in
 // [valid_min, valid_max]) and |x_k - x_(k-1)| * fs > threshold, in FP32.  A
 // saccade is a maximal run of fast steps [a, b): onset sample s = a - 1, end
-// sample e = b - 1.  Run starts are compacted in stream order in two HBM
-// passes over tiles of kTile steps (count per tile, scan of the counts, write
-// at the tile's offset by warp scans), four steps per thread from one 16-byte
-// load; then one warp per run walks the run and checks its window.
+// sample e = b - 1.  Run starts are compacted in stream order over tiles of
+// kTile steps, four steps per thread from one 16-byte load: one HBM pass
+// counts each tile's starts and records up to kIvtRec of them (tile-local, in
+// any order), a scan of the counts gives the tile offsets, one warp per
+// sparse tile ranks its recorded starts into stream order, and only tiles
+// with more starts than that (a threshold near the noise) are read a second
+// time, writing in order by warp scans; then one warp per run walks the run
+// and checks its window.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -87,22 +91,51 @@ __device__ __forceinline__ long long ivt_group(int it) {
   return (long long)blockIdx.x * (kIvtThreads * kIvtIters) + (long long)it * kIvtThreads + threadIdx.x;
 }
 
-// Pass 1a: run starts per tile.
+constexpr int kIvtRec = 64;   // run starts a tile records during the count pass
+
+// Pass 1a: run starts per tile; the first kIvtRec found are recorded as
+// tile-local step indices (step - first step of the tile, < kTile), in the
+// order the warps happen to claim slots.  The loop over the stream only
+// loads and tests (each thread's eight 4-bit start masks packed in one
+// word); the records collect in shared memory afterwards and go out at the
+// end.
 template <bool VEC>
-__global__ void __launch_bounds__(kIvtThreads) k_ivt_count(IvtDev P, int* tile_count) {
-  int c = 0;
+__global__ void __launch_bounds__(kIvtThreads) k_ivt_count(IvtDev P, int* tile_count, unsigned short* rec) {
+  static_assert(kIvtIters * kVec <= 32, "start masks packed in one word");
+  __shared__ int n_found;
+  __shared__ unsigned short found[kIvtRec];
+  if (threadIdx.x == 0) n_found = 0;
+  unsigned packed = 0;
 #pragma unroll 4
-  for (int it = 0; it < kIvtIters; ++it) c += __popc(ivt_group_starts<VEC>(P, ivt_group(it)));
-  __shared__ int warp_sum[kIvtThreads / 32];
-#pragma unroll
-  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+  for (int it = 0; it < kIvtIters; ++it) packed |= ivt_group_starts<VEC>(P, ivt_group(it)) << (kVec * it);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int sum = 0;
-    for (int w = 0; w < kIvtThreads / 32; ++w) sum += warp_sum[w];
-    tile_count[blockIdx.x] = sum;
+  const int lane = threadIdx.x & 31;
+  if (__syncthreads_or(packed != 0u)) {             // block-uniform: most tiles of a fixation start nothing
+    for (int it = 0; it < kIvtIters; ++it) {
+      const unsigned bits = packed >> (kVec * it) & 15u;
+      if (!__ballot_sync(0xffffffffu, bits != 0u)) continue;   // warp-uniform
+      const int c = __popc(bits);
+      int inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      int base = 0;
+      if (lane == 31) base = atomicAdd(&n_found, inc);
+      int slot = __shfl_sync(0xffffffffu, base, 31) + inc - c;
+      const int local = 4 * (it * kIvtThreads + (int)threadIdx.x);
+      for (int i = 0; i < kVec; ++i)
+        if (bits >> i & 1u) {
+          if (slot < kIvtRec) found[slot] = (unsigned short)(local + i);
+          ++slot;
+        }
+    }
+    __syncthreads();
   }
+  const int c = n_found;
+  if ((int)threadIdx.x < min(c, kIvtRec)) rec[(size_t)blockIdx.x * kIvtRec + threadIdx.x] = found[threadIdx.x];
+  if (threadIdx.x == 0) tile_count[blockIdx.x] = c;
 }
 
 // Exclusive scan of the tile counts (one block of 1024 threads, each taking
@@ -141,10 +174,39 @@ __global__ void __launch_bounds__(1024) k_ivt_scan(const int* tile_count, int nt
   }
 }
 
-// Pass 1b: write each tile's run starts at its offset, in stream order
-// (iteration, warp, lane, step).
+// Pass 1b, sparse tiles (at most kIvtRec starts): one warp per tile ranks
+// the recorded starts (distinct indices: the rank is the number smaller) and
+// writes them at the tile's offset in stream order.
+__global__ void k_ivt_place(const int* tile_count, const unsigned short* rec, const long long* tile_off, int ntiles,
+                            long long* starts) {
+  const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= ntiles) return;                       // warp-uniform
+  const int c = tile_count[t];
+  if (c == 0 || c > kIvtRec) return;             // warp-uniform
+  const unsigned short* r = rec + (size_t)t * kIvtRec;
+  const int v0 = lane < c ? (int)r[lane] : 0x10000;             // padding ranks after every index
+  const int v1 = lane + 32 < c ? (int)r[lane + 32] : 0x10000;
+  int r0 = 0, r1 = 0;
+#pragma unroll 8
+  for (int j = 0; j < 32; ++j) {
+    const int a = __shfl_sync(0xffffffffu, v0, j), b = __shfl_sync(0xffffffffu, v1, j);
+    r0 += (a < v0) + (b < v0);
+    r1 += (a < v1) + (b < v1);
+  }
+  const long long first = (long long)t * kTile + 1;   // step of local index 0
+  const long long off = tile_off[t];
+  if (lane < c) starts[off + r0] = first + v0;
+  if (lane + 32 < c) starts[off + r1] = first + v1;
+}
+
+// Pass 1b, dense tiles (more than kIvtRec starts): read the tile again and
+// write its run starts at its offset in stream order (iteration, warp, lane,
+// step).  Every other block returns at once.
 template <bool VEC>
-__global__ void __launch_bounds__(kIvtThreads) k_ivt_write(IvtDev P, const long long* tile_off, long long* starts) {
+__global__ void __launch_bounds__(kIvtThreads) k_ivt_write(IvtDev P, const int* tile_count, const long long* tile_off,
+                                                           long long* starts) {
+  if (tile_count[blockIdx.x] <= kIvtRec) return;   // block-uniform
   __shared__ int warp_cnt[kIvtThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long run = tile_off[blockIdx.x];
@@ -183,13 +245,14 @@ __global__ void k_ivt_events(IvtDev P, const long long* starts, int m, opmm_ivt_
   const long long a = starts[i];
   long long b = a;
   float peak = 0.0f;
-  for (long long k0 = a;; k0 += 32) {
-    const float sp = ivt_speed(P, k0 + lane);
-    const bool fast = sp > P.thr;
-    const unsigned slow = __ballot_sync(0xffffffffu, !fast);
-    const int stop = slow ? __ffs(slow) - 1 : 32;      // lanes before it are the run's
-    if (lane < stop) peak = fmaxf(peak, sp);
-    if (slow) {
+  for (long long k0 = a;; k0 += 64) {                  // 64 steps per pass: both loads in flight together
+    const float sp0 = ivt_speed(P, k0 + lane), sp1 = ivt_speed(P, k0 + 32 + lane);
+    const unsigned slow0 = __ballot_sync(0xffffffffu, !(sp0 > P.thr));
+    const unsigned slow1 = __ballot_sync(0xffffffffu, !(sp1 > P.thr));
+    const int stop = slow0 ? __ffs(slow0) - 1 : (slow1 ? 32 + __ffs(slow1) - 1 : 64);   // steps before it are the run's
+    if (lane < stop) peak = fmaxf(peak, sp0);
+    if (32 + lane < stop) peak = fmaxf(peak, sp1);
+    if (stop < 64) {
       b = k0 + stop;
       break;
     }
@@ -204,7 +267,8 @@ __global__ void k_ivt_events(IvtDev P, const long long* starts, int m, opmm_ivt_
   bool ok = dur >= P.min_dur && amp >= P.min_amp && ws >= 0 && we <= P.n - 1;
   if (ok) {
     bool good = true;
-    for (long long k = ws + lane; k <= we; k += 32) good = good && ivt_valid(P.x[k], P);
+#pragma unroll 4
+    for (long long k = ws + lane; k <= we; k += 32) good &= ivt_valid(P.x[k], P);   // loads independent of one another
     ok = __all_sync(0xffffffffu, good);
   }
   if (lane == 0) {
@@ -259,6 +323,7 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
   DevBuf& b_keep = ctx->scratch[14];
   DevBuf& b_count = ctx->scratch[15];
   DevBuf& b_off = ctx->scratch[10];
+  DevBuf& b_rec = ctx->scratch[9];
   if (!is_device_ptr(stream_deg)) {
     s = b_x.ensure(sizeof(float) * (size_t)n_samples);
     if (s.ok())
@@ -277,9 +342,12 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
   if (s.ok()) s = b_off.ensure(sizeof(long long) * ((size_t)ntiles + 1));
   if (!s.ok()) return ivt_fail(s);
   long long* d_off = b_off.as<long long>();
+  s = b_rec.ensure(sizeof(unsigned short) * kIvtRec * (size_t)ntiles);
+  if (!s.ok()) return ivt_fail(s);
+  unsigned short* d_rec = b_rec.as<unsigned short>();
   const bool vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;   // 16-byte loads need an aligned stream
-  if (vec) k_ivt_count<true><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>());
-  else k_ivt_count<false><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>());
+  if (vec) k_ivt_count<true><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>(), d_rec);
+  else k_ivt_count<false><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>(), d_rec);
   k_ivt_scan<<<1, 1024, 0, st>>>(b_count.as<int>(), ntiles, d_off, d_off + ntiles);
   s = cuda_status(cudaGetLastError(), "launch I-VT count");
   long long total = 0;
@@ -299,9 +367,11 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
     if (s.ok()) s = h_ev.ensure(sizeof(opmm_ivt_event) * (size_t)m);
     if (s.ok()) s = h_keep.ensure(sizeof(int) * (size_t)m);
     if (!s.ok()) return ivt_fail(s);
-    if (vec) k_ivt_write<true><<<ntiles, kIvtThreads, 0, st>>>(P, d_off, b_starts.as<long long>());
-    else k_ivt_write<false><<<ntiles, kIvtThreads, 0, st>>>(P, d_off, b_starts.as<long long>());
     const long long warps_per_block = 4;
+    k_ivt_place<<<(unsigned)((ntiles + warps_per_block - 1) / warps_per_block), 32 * warps_per_block, 0, st>>>(
+        b_count.as<int>(), d_rec, d_off, ntiles, b_starts.as<long long>());
+    if (vec) k_ivt_write<true><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>(), d_off, b_starts.as<long long>());
+    else k_ivt_write<false><<<ntiles, kIvtThreads, 0, st>>>(P, b_count.as<int>(), d_off, b_starts.as<long long>());
     k_ivt_events<<<(unsigned)((m + warps_per_block - 1) / warps_per_block), 32 * warps_per_block, 0, st>>>(
         P, b_starts.as<long long>(), m, b_ev.as<opmm_ivt_event>(), b_keep.as<int>());
     s = cuda_status(cudaGetLastError(), "launch I-VT events");

@@ -63,6 +63,30 @@ def test_synthetic_stream_matches_the_definition(ctx, fs):
     _same(got, want)
 
 
+def test_tiles_of_many_runs(ctx):
+    """Tiles of 8,192 steps holding 64 run starts (the most the count pass
+    records; ranked into order from those records), 65 and a noisy stretch
+    with hundreds (read again and written in stream order), beside sparse
+    tiles: every run is kept (filters off) and the events are the same as
+    the definition's."""
+    tile = 8192
+    n = 5 * tile + 1000
+    dx = np.zeros(n, np.float64)
+    sign = 1.0
+    for first, count, spacing in ((100, 64, 100), (tile + 50, 65, 120), (2 * tile + 7, 63, 128), (4 * tile + 300, 3, 2000)):
+        for j in range(count):
+            dx[first + j * spacing] = sign      # one fast step: x rises or falls by 1 deg between samples k-1, k
+            sign = -sign
+    x = np.cumsum(dx).astype(np.float32)
+    x[3 * tile:4 * tile] += np.random.default_rng(2).normal(0.0, 0.01, tile).astype(np.float32)
+    kw = {"min_duration_ms": 0.0, "min_amplitude_deg": 0.0}
+    want = ivt(x, 1000.0, **kw)
+    starts = np.array([int(w["onset"]) + 1 for w in want])
+    per_tile = np.bincount((starts - 1) // tile, minlength=5)
+    assert per_tile[0] == 64 and per_tile[1] == 65 and per_tile[2] == 63 and per_tile[3] > 64, per_tile
+    _same(G.opmm_detect_saccades(ctx, x, 1000.0, **kw), want)
+
+
 def test_device_stream_window_options_and_truncation(ctx):
     torch = pytest.importorskip("torch")
     x, _ = W.raw_stream(200_000, seed=11)
