@@ -171,7 +171,8 @@ int opmm_search_variant_info(int32_t variant, int32_t* simplices_per_block, int3
  *   sac_index:  nullable host [n]
  *   out_offset: host [n] element offsets into out_deg
  *   out_deg:    host or device, caller-owned
- * Synchronous with respect to the host. */
+ * n = 0 does nothing and returns OPMM_OK.  Synchronous with respect to the
+ * host. */
 int opmm_simulate(opmm_ctx* ctx, const float* opc, int32_t n, const opmm_saccade* sacs,
                   int32_t n_sacs, const int32_t* sac_index, const int64_t* out_offset,
                   float* out_deg);
@@ -179,13 +180,14 @@ int opmm_simulate(opmm_ctx* ctx, const float* opc, int32_t n, const opmm_saccade
 /* Objective of m candidate OPC vectors against one recorded saccade: mean
  * squared error (deg^2) accumulated in FP32 with compensated summation,
  * +inf for candidates outside RK4's stable step range.  opc: [m][18] host or
- * device; out_f: [m] host or device. */
+ * device; out_f: [m] host or device.  m = 0 does nothing (the descriptor is
+ * still checked). */
 int opmm_score(opmm_ctx* ctx, const float* opc, int32_t m, const opmm_saccade* sac,
                float* out_f);
 
 /* Box centres the estimator would use: the caller's init_opc if given, else
  * Table 1 with W = duration - 6 ms and the agonist pulse chosen by
- * pulse_init.  out_opc: host [n][18]. */
+ * pulse_init.  out_opc: host [n][18].  n = 0 does nothing. */
 int opmm_nominal_opc(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, int32_t pulse_init,
                      float* out_opc);
 
@@ -193,7 +195,8 @@ int opmm_nominal_opc(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, int32_t
 
 /* Fit every saccade of the batch (Algorithm 1: one optimisation task per
  * saccade, all on the device at once).  sacs: host array; traces host or
- * device.  out: host [n], caller-owned.  Synchronous. */
+ * device.  out: host [n], caller-owned.  Synchronous.  n >= 1: an empty
+ * batch is OPMM_EINVAL. */
 int opmm_fit_batch(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts* opts,
                    opmm_fit_result* out);
 

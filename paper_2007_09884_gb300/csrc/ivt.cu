@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cfloat>
 #include <cmath>
 #include <vector>
 
@@ -33,13 +34,15 @@ namespace {
 struct IvtDev {
   const float* x;
   long long n;
-  float fs, thr, vmin, vmax, min_dur, min_amp;
+  float fs, thr;
+  float vmin, vmax;   // valid range clamped to [-FLT_MAX, FLT_MAX] on the host
+  float min_dur, min_amp;
   int pre, post;
 };
 
-__device__ __forceinline__ bool ivt_valid(float v, const IvtDev& P) {
-  return isfinite(v) && v >= P.vmin && v <= P.vmax;
-}
+// Finite and inside [valid_min, valid_max]: with the bounds clamped to the
+// finite range, the two comparisons alone decide it (NaN and +-inf fail one).
+__device__ __forceinline__ bool ivt_valid(float v, const IvtDev& P) { return v >= P.vmin && v <= P.vmax; }
 
 // |x_k - x_(k-1)| * fs, or -1 when the step is not between two valid samples.
 __device__ __forceinline__ float ivt_speed(const IvtDev& P, long long k) {
@@ -54,38 +57,49 @@ constexpr int kIvtIters = 8;
 constexpr int kVec = 4;                                                     // steps per thread and iteration
 constexpr long long kTile = (long long)kIvtThreads * kIvtIters * kVec;     // steps per tile (one block)
 
-__device__ __forceinline__ bool ivt_fast(float a, float b, const IvtDev& P) {
-  return ivt_valid(a, P) && ivt_valid(b, P) && fabsf(b - a) * P.fs > P.thr;
-}
-
 // Run starts among steps 4m+1 .. 4m+4 (bit i for step 4m+1+i).  Group m's
 // samples 4m .. 4m+3 come in one 16-byte load when the stream is aligned;
 // sample 4m-1 (for step 4m) and sample 4m+4 from the neighbouring lanes.
 // Every lane of the warp calls it, with consecutive m on consecutive lanes.
-template <bool VEC>
+// FULL: every sample the group touches, 4m-1 .. 4m+4, lies in the stream
+// (sample -1 of the first group aside), so no load needs a bounds check.
+template <bool VEC, bool FULL>
 __device__ __forceinline__ unsigned ivt_group_starts(const IvtDev& P, long long m) {
   const float nan = __int_as_float(0x7fc00000);
   const long long b = 4 * m;
+  const float* xb = P.x + b;
   float x0, x1, x2, x3;
-  if (VEC && b + 3 < P.n) {
-    const float4 v = *reinterpret_cast<const float4*>(P.x + b);
+  if (VEC && (FULL || b + 3 < P.n)) {
+    const float4 v = *reinterpret_cast<const float4*>(xb);
     x0 = v.x; x1 = v.y; x2 = v.z; x3 = v.w;
+  } else if (FULL) {
+    x0 = xb[0]; x1 = xb[1]; x2 = xb[2]; x3 = xb[3];
   } else {
-    x0 = b < P.n ? P.x[b] : nan;
-    x1 = b + 1 < P.n ? P.x[b + 1] : nan;
-    x2 = b + 2 < P.n ? P.x[b + 2] : nan;
-    x3 = b + 3 < P.n ? P.x[b + 3] : nan;
+    x0 = b < P.n ? xb[0] : nan;
+    x1 = b + 1 < P.n ? xb[1] : nan;
+    x2 = b + 2 < P.n ? xb[2] : nan;
+    x3 = b + 3 < P.n ? xb[3] : nan;
   }
   const int lane = threadIdx.x & 31;
   float xm = __shfl_up_sync(0xffffffffu, x3, 1);
   float x4 = __shfl_down_sync(0xffffffffu, x0, 1);
-  if (lane == 0) xm = (b >= 1 && b - 1 < P.n) ? P.x[b - 1] : nan;
-  if (lane == 31) x4 = b + 4 < P.n ? P.x[b + 4] : nan;
-  // fast steps 4m .. 4m+4 (step 0 does not exist: sample -1 reads as NaN)
-  const bool f0 = ivt_fast(xm, x0, P), f1 = ivt_fast(x0, x1, P), f2 = ivt_fast(x1, x2, P);
-  const bool f3 = ivt_fast(x2, x3, P), f4 = ivt_fast(x3, x4, P);
+  if (lane == 0) xm = (b >= 1 && (FULL || b - 1 < P.n)) ? xb[-1] : nan;
+  if (lane == 31) x4 = (FULL || b + 4 < P.n) ? xb[4] : nan;
+  // per sample validity once, then fast steps 4m .. 4m+4 (step 0 does not
+  // exist: sample -1 reads as NaN, which is not valid)
+  const bool vm = ivt_valid(xm, P), v0 = ivt_valid(x0, P), v1 = ivt_valid(x1, P), v2 = ivt_valid(x2, P);
+  const bool v3 = ivt_valid(x3, P), v4 = ivt_valid(x4, P);
+  const bool f0 = vm && v0 && fabsf(x0 - xm) * P.fs > P.thr;
+  const bool f1 = v0 && v1 && fabsf(x1 - x0) * P.fs > P.thr;
+  const bool f2 = v1 && v2 && fabsf(x2 - x1) * P.fs > P.thr;
+  const bool f3 = v2 && v3 && fabsf(x3 - x2) * P.fs > P.thr;
+  const bool f4 = v3 && v4 && fabsf(x4 - x3) * P.fs > P.thr;
   return (f1 && !f0 ? 1u : 0u) | (f2 && !f1 ? 2u : 0u) | (f3 && !f2 ? 4u : 0u) | (f4 && !f3 ? 8u : 0u);
 }
+
+// A tile whose every group touches only samples inside the stream: its last
+// group reads sample 4m+4 = (t + 1) kTile.
+__device__ __forceinline__ bool ivt_tile_full(const IvtDev& P) { return ((long long)blockIdx.x + 1) * kTile < P.n; }
 
 __device__ __forceinline__ long long ivt_group(int it) {
   return (long long)blockIdx.x * (kIvtThreads * kIvtIters) + (long long)it * kIvtThreads + threadIdx.x;
@@ -106,8 +120,13 @@ __global__ void __launch_bounds__(kIvtThreads) k_ivt_count(IvtDev P, int* tile_c
   __shared__ unsigned short found[kIvtRec];
   if (threadIdx.x == 0) n_found = 0;
   unsigned packed = 0;
+  if (ivt_tile_full(P)) {   // block-uniform
 #pragma unroll 4
-  for (int it = 0; it < kIvtIters; ++it) packed |= ivt_group_starts<VEC>(P, ivt_group(it)) << (kVec * it);
+    for (int it = 0; it < kIvtIters; ++it) packed |= ivt_group_starts<VEC, true>(P, ivt_group(it)) << (kVec * it);
+  } else {
+#pragma unroll 4
+    for (int it = 0; it < kIvtIters; ++it) packed |= ivt_group_starts<VEC, false>(P, ivt_group(it)) << (kVec * it);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   if (__syncthreads_or(packed != 0u)) {             // block-uniform: most tiles of a fixation start nothing
@@ -212,7 +231,7 @@ __global__ void __launch_bounds__(kIvtThreads) k_ivt_write(IvtDev P, const int* 
   long long run = tile_off[blockIdx.x];
   for (int it = 0; it < kIvtIters; ++it) {
     const long long m = ivt_group(it);
-    const unsigned bits = ivt_group_starts<VEC>(P, m);
+    const unsigned bits = ivt_group_starts<VEC, false>(P, m);
     const int c = __popc(bits);
     int inc = c;
 #pragma unroll
@@ -332,7 +351,8 @@ extern "C" int opmm_detect_saccades(opmm_ctx* ctx, const float* stream_deg, int6
     if (!s.ok()) return ivt_fail(s);
     x = b_x.as<float>();
   }
-  IvtDev P{x, (long long)n_samples, sample_rate_hz, opts->threshold_dps, opts->valid_min_deg, opts->valid_max_deg,
+  IvtDev P{x, (long long)n_samples, sample_rate_hz, opts->threshold_dps, std::max(opts->valid_min_deg, -FLT_MAX),
+           std::min(opts->valid_max_deg, FLT_MAX),
            opts->min_duration_ms, opts->min_amplitude_deg, opts->pre_samples, opts->post_samples};
   // run starts in stream order: count per tile, scan, write
   const long long ntiles_ll = (n_samples - 1 + kTile - 1) / kTile;

@@ -87,6 +87,26 @@ def test_tiles_of_many_runs(ctx):
     _same(G.opmm_detect_saccades(ctx, x, 1000.0, **kw), want)
 
 
+def test_degenerate_streams(ctx):
+    """A stream of track loss only, the shortest streams (two and three
+    samples, one step), with and without filters and margins."""
+    streams = (np.full(1000, np.nan, np.float32), np.array([0.0, 10.0], np.float32), np.zeros(2, np.float32),
+               np.array([0.0, 10.0, 10.0], np.float32))
+    for x in streams:
+        for kw in ({}, {"min_duration_ms": 0.0, "min_amplitude_deg": 0.0, "pre_samples": 0, "post_samples": 0}):
+            _same(G.opmm_detect_saccades(ctx, x, 1000.0, **kw), ivt(x, 1000.0, **kw))
+    # infinite samples are never valid, even with an unbounded valid range
+    ramp = np.concatenate([np.zeros(100), np.linspace(0.0, 12.0, 13), np.full(287, 12.0)]).astype(np.float32)
+    inf_in, inf_out = ramp.copy(), ramp.copy()
+    inf_in[105] = np.inf
+    inf_out[300] = -np.inf
+    kw = {"valid_min_deg": -np.inf, "valid_max_deg": np.inf, "min_duration_ms": 0.0, "min_amplitude_deg": 0.0}
+    for x, kept in ((ramp, 1), (inf_in, 0), (inf_out, 1)):
+        want = ivt(x, 1000.0, **kw)
+        assert len(want) == kept
+        _same(G.opmm_detect_saccades(ctx, x, 1000.0, **kw), want)
+
+
 def test_device_stream_window_options_and_truncation(ctx):
     torch = pytest.importorskip("torch")
     x, _ = W.raw_stream(200_000, seed=11)

@@ -305,6 +305,21 @@ def test_invalid_arguments_are_rejected(ctx, bad):
     assert e.value.code == G.OPMM_EINVAL
 
 
+def test_empty_calls(ctx):
+    """An empty batch to fit is OPMM_EINVAL; zero trajectories to simulate,
+    candidates to score or centres to compute are no-ops that succeed."""
+    import ctypes
+    lib = G.load_library()
+    o, _ = G.fit_opts(candidates=44, iterations=2)
+    res = (G.opmm_fit_result * 1)()
+    assert lib.opmm_fit_batch(ctx, None, 0, ctypes.byref(o), res) == G.OPMM_EINVAL
+    batch = G.make_batch([np.zeros(50, np.float32)], [1000.0], [5], [0.0], [5.0], [30.0])
+    descs, keep = batch.descriptors()
+    assert lib.opmm_simulate(ctx, None, 0, descs, 1, None, None, None) == G.OPMM_OK
+    assert lib.opmm_score(ctx, None, 0, descs, None) == G.OPMM_OK
+    assert lib.opmm_nominal_opc(ctx, None, 0, G.OPMM_PULSE_CALIBRATED, None) == G.OPMM_OK
+
+
 def test_every_search_variant_matches_oracle(ctx):
     """All launch-shape variants of the search kernel (simplices per block,
     register budget, register-lean schedule) run the same estimator; 70
