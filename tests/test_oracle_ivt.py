@@ -72,3 +72,23 @@ def test_velocity_scales_with_the_rate():
     ev = ivt(x, 250.0)                 # 250 deg/s at 250 Hz, 48 ms
     assert len(ev) == 1 and ev[0]["duration_ms"] == np.float32(48.0)
     assert ivt(x, 20.0) == []          # 20 deg/s: below threshold
+
+
+def test_infinite_samples_are_invalid_even_in_an_unbounded_range():
+    """Valid means finite as well as in range: with the range opened to
+    (-inf, inf) an infinite sample still breaks its steps and spoils any
+    window that holds it, as NaN does."""
+    x = _ramp(400, 100, 12, 12.0)
+    wide = {"valid_min_deg": -np.inf, "valid_max_deg": np.inf}
+    assert len(ivt(x, 1000.0, **wide)) == 1
+    for bad in (np.inf, -np.inf, np.nan):
+        y = x.copy()
+        y[140] = bad                   # inside the post window
+        assert ivt(y, 1000.0, **wide) == []
+        z = x.copy()
+        z[300] = bad                   # outside every window
+        assert len(ivt(z, 1000.0, **wide)) == 1
+        r = x.copy()
+        r[106] = bad                   # inside the run: steps 106 and 107 are not fast
+        runs = ivt(r, 1000.0, min_duration_ms=0.0, min_amplitude_deg=0.0, pre_samples=0, post_samples=0, **wide)
+        assert [(e["onset"], e["end"]) for e in runs] == [(100, 105), (107, 112)]
