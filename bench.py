@@ -258,12 +258,26 @@ def profile_traffic(kernel_src_hash: str):
     return None
 
 
-def kernel_hash():
+def source_code_digest(texts):
+    """sha256 of source texts with their // comments, trailing blanks and
+    blank lines removed: a comment edit leaves it unchanged, any code edit
+    changes it."""
     h = hashlib.sha256()
-    for f in ("kernels.cu", "plant.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2007_09884_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for t in texts:
+        lines = (ln.split("//", 1)[0].rstrip() for ln in t.splitlines())
+        h.update("\n".join(ln for ln in lines if ln).encode())
+        h.update(b"\0")
     return h.hexdigest()
+
+
+def kernel_hash():
+    """Digest of the search kernel's sources (the key of the committed DRAM
+    traffic record)."""
+    texts = []
+    for f in ("kernels.cu", "plant.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2007_09884_gb300", "csrc", f), encoding="utf-8") as fh:
+            texts.append(fh.read())
+    return source_code_digest(texts)
 
 
 def run_ours(args, ws, rank, local):

@@ -6,6 +6,9 @@
 //   k_score       objective of many OPC vectors against one saccade
 //   k_search      persistent multi-start parallel Nelder-Mead (Algorithm 1)
 //   k_finalize    per-saccade winner and FP64 re-computation of its error
+//   k_refine      Levenberg-Marquardt refinement of search results
+//   k_refine_check  FP64 error of the refined vectors
+//   k_admit, k_advance  request loop: slot admission and iteration progress
 //
 // The hot loop is k_search's candidate evaluation: one thread integrates one
 // trial OPC vector's plant in registers (plant.cuh), scoring each sample against
@@ -13,8 +16,9 @@
 // compensated FP32 sum.  Per block, two groups of G simplices of one saccade
 // advance in turn: all 22 trial points of every simplex of a group are
 // evaluated in one wave (Sec. 3.3: all simplex transformations are computed at
-// once), while the block's controller warp takes the Lagarias decisions of
-// the other group and orders its next wave.
+// once), ordered by pulse-end time by the evaluation warps, while the block's
+// controller warp takes the Lagarias decisions of the other group and sets up
+// that group's next wave.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>

@@ -110,3 +110,14 @@ def test_pulse_end_interval_count():
     # states and the final combination (168 per substep)
     assert 4 * (a + 2) + 3 * 6 * 2 + 6 * 4 * 2 == 168
     assert bench.rk4_stage_flops_per_sim(11, 10) == 168 * 10 * 10
+
+
+def test_traffic_record_key_ignores_comments_only():
+    """The DRAM traffic record is keyed by a digest of the kernel sources
+    that a comment edit leaves alone and a code edit changes."""
+    src = ["int f(int a) {  // add one\n  return a + 1;\n}\n", "// header\n#pragma once\n"]
+    same = ["int f(int a) {  // add one to a\n\n  return a + 1;   \n}\n", "// header, reworded\n#pragma once\n"]
+    code = ["int f(int a) {  // add one\n  return a + 2;\n}\n", "// header\n#pragma once\n"]
+    assert bench.source_code_digest(src) == bench.source_code_digest(same)
+    assert bench.source_code_digest(src) != bench.source_code_digest(code)
+    assert len(bench.kernel_hash()) == 64
