@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (written here, from the FP32 arithmetic of each quantity):
   * trajectories: 1e-4 deg max abs per sample;
   * objective f (mean squared error): the trajectory bound d gives
     |f_gpu - f_ref| <= 2 sqrt(f) d + d^2, plus FP32 summation noise;
