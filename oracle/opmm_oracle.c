@@ -31,7 +31,13 @@
  *   - a multi-start batch of such simplices per saccade (Algorithm 1 spawns
  *     one task per saccade; the candidate budget per iteration is spread over
  *     independent simplices);
- *   - Philox4x32-10 (Salmon et al., SC'11) for the random simplex centres.
+ *   - Philox4x32-10 (Salmon et al., SC'11) for the random simplex centres;
+ *   - the 9-parameter model (Sec. 2.2.2, Table 2) as a map from its nine
+ *     search coordinates to the 18 OPC entries, the neural control signal
+ *     held at the box centre;
+ *   - a Levenberg-Marquardt refinement of a fitted vector (the gradient
+ *     methods Sec. 5 proposes), with a central-difference Jacobian through
+ *     the same RK4 plant.
  *
  * Parity status: the plant equations are a reading of a paper that prints
  * none; agreement with the authors' own (unpublished) implementation is
