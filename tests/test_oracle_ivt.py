@@ -92,3 +92,32 @@ def test_infinite_samples_are_invalid_even_in_an_unbounded_range():
         r[106] = bad                   # inside the run: steps 106 and 107 are not fast
         runs = ivt(r, 1000.0, min_duration_ms=0.0, min_amplitude_deg=0.0, pre_samples=0, post_samples=0, **wide)
         assert [(e["onset"], e["end"]) for e in runs] == [(100, 105), (107, 112)]
+
+
+def test_planted_saccades_of_a_synthetic_stream_are_recovered():
+    """On the seeded raw stream (fixations with 0.005 deg noise, raised-cosine
+    saccades of 1-30 deg, blinks of NaN), every kept event lies on a planted
+    saccade, and the planted saccades of at least 4.5 deg whose windows are
+    free of blinks are found with their amplitude (the raised cosine crosses
+    the 30 deg/s threshold within its first and last few percent of
+    amplitude, so a planted 4.04 deg saccade may measure just under the 4 deg
+    filter)."""
+    import workloads as W
+    x, planted = W.raw_stream(400_000, seed=3)
+    ev = ivt(x, 1000.0)
+    assert len(ev) > 100
+    starts = np.array([p[0] for p in planted])
+    for e in ev:
+        i = int(np.searchsorted(starts, e["onset"] + 1, side="right")) - 1
+        k0, k1, amp = planted[i]
+        assert k0 - 1 <= e["onset"] < e["end"] <= k1, (e, planted[i])
+    found = {int(np.searchsorted(starts, e["onset"] + 1, side="right")) - 1: e for e in ev}
+    eligible = 0
+    for i, (k0, k1, amp) in enumerate(planted):
+        lo, hi = k0 - 10 - 5, k1 + 40 + 5
+        if amp < 4.5 or lo < 0 or hi >= len(x) or not np.all(np.isfinite(x[lo:hi])):
+            continue
+        eligible += 1
+        assert i in found, (k0, k1, amp)
+        assert abs(found[i]["amplitude"] - amp) <= 0.03 * amp + 0.02
+    assert eligible > 100
