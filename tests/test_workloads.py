@@ -69,3 +69,28 @@ def test_poisson_arrivals():
         assert np.all(np.diff(t) > 0) and t[-1] < 2.0
         n = len(t)
         assert abs(n - 2.0 * rate) < 4.0 * math.sqrt(2.0 * rate)
+
+
+def test_raw_stream_recipe():
+    n, fs = 600_000, 1000.0
+    x, planted = W.raw_stream(n, fs=fs, seed=11)
+    assert x.dtype == np.float32 and len(x) == n
+    amps = np.array([p[2] for p in planted])
+    assert amps.min() >= 1.0 and amps.max() <= 30.0
+    # saccade lengths follow the main-sequence duration; fixations between
+    # them last 150-1200 ms
+    for (k0, k1, a) in planted[:-1]:
+        assert k1 - k0 == int(round(float(W.duration_ms(a)) * fs / 1000.0))
+    gaps = np.array([planted[i + 1][0] - planted[i][1] for i in range(len(planted) - 1)])
+    assert gaps.min() >= 150 and gaps.max() <= 1200
+    finite = x[np.isfinite(x)]
+    assert np.abs(finite).max() < 20.0 + 0.05
+    # blinks: runs of NaN of 80-200 ms at about 0.2 per second
+    nan = ~np.isfinite(x)
+    starts = np.flatnonzero(nan[1:] & ~nan[:-1]) + 1
+    assert 0.1 * n / fs < len(starts) < 0.3 * n / fs
+    # fixation noise: 0.005 deg about the fixation position
+    k0 = planted[0][1]
+    seg = x[k0 + 5:planted[1][0] - 5].astype(np.float64)
+    seg = seg[np.isfinite(seg)]
+    assert abs(seg.std() - 0.005) < 0.002
