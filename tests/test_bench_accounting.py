@@ -1,6 +1,8 @@
-"""The algorithmic FLOP counts behind the search kernel's roofline figure
-(bench.py: flops_per_sim, pow_products, pulse_end_flops), checked against
-counts derived independently from the structure of the propagators.
+"""Host-side accounting of the benchmark: the algorithmic FLOP counts behind
+the search kernel's roofline figure (bench.py: flops_per_sim, pow_products,
+pulse_end_flops), checked against counts derived independently from the
+structure of the propagators; the key of the DRAM traffic record; and the
+summary of the clock samples taken during the timed region.
 
 Within one input phase the plant's one-sample RK4 propagator has the block
 structure of the state (theta, omega, x, y | F_a, F_n): the mechanical rows
@@ -121,3 +123,18 @@ def test_traffic_record_key_ignores_comments_only():
     assert bench.source_code_digest(src) == bench.source_code_digest(same)
     assert bench.source_code_digest(src) != bench.source_code_digest(code)
     assert len(bench.kernel_hash()) == 64
+
+
+def test_clock_samples_summary():
+    """nvidia-smi samples during the timed region: the median SM clock and
+    every throttle reason seen active; malformed lines are skipped."""
+    lines = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1400.1, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 0, 0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    d = bench.parse_clock_samples(lines)
+    assert d == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    assert bench.parse_clock_samples([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
