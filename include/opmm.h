@@ -431,11 +431,12 @@ int opmm_surrogate_load(opmm_ctx* ctx, const char* path);
  *   cuda_stream: cudaStream_t to run on (NULL = legacy default stream)
  * Limits: n_samples <= 4096 and candidates <= 65536; larger sizes, a host
  * trace or result pointer, or any malformed argument return OPMM_EINVAL
- * before anything runs.  The working memory is one fixed ~37 KB __device__
- * array inside the library, held by every GPU that loads the library until the
- * process exits.  The first call on a device (with that device current) looks
- * up that array's address and sets kernel attributes; make it before any
- * stream capture.  Calls share the array: calls that overlap on the GPU race,
+ * before anything runs.  The working memory is one fixed 27,648-byte
+ * __device__ array inside the library, held by every GPU that loads the
+ * library until the process exits.  Every call (with the device current) looks
+ * up that array's address and the search kernel's occupancy for this trace;
+ * the first call on a device also loads the library's kernels there, so make
+ * it before any stream capture.  Calls share the array: calls that overlap on the GPU race,
  * so run them one at a time (the call returns only after the fit finished).
  * Returns OPMM_ETIMEDOUT if a kernel's bounded wait expired, OPMM_ECUDA on a
  * CUDA error. */

@@ -382,7 +382,7 @@ extern "C" int opmm_nominal_opc(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t
 // Search coordinates of a model: 18 (the OPC entries) or 9 (Table 2).
 static int model_dim(int32_t model) { return model == OPMM_MODEL_9 ? 9 : OPMM_NPARAM; }
 
-static Status check_opts(const opmm_fit_opts& o) {
+Status opmm::check_opts(const opmm_fit_opts& o) {
   if (o.model != OPMM_MODEL_18 && o.model != OPMM_MODEL_9)
     return Status(OPMM_EINVAL, "model must be OPMM_MODEL_18 or OPMM_MODEL_9");
   if (o.model == OPMM_MODEL_9 && o.use_surrogate)

@@ -1619,6 +1619,25 @@ __global__ void k_refine_check(const DevSac* sacs, const float* traces, int n, o
   }
 }
 
+// Allow kernel k the largest dynamic shared memory the device gives one of its
+// blocks (the opt-in maximum less its static shared memory), after checking
+// that `smem` fits.  The attribute belongs to the kernel for the whole process,
+// so it is only ever raised to that fixed maximum: a call for a smaller size
+// never lowers the limit under a launch that another plan, a request loop or a
+// captured graph makes with a larger one.
+template <class K>
+static cudaError_t allow_dynamic_smem(K k, size_t smem) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if ((size_t)optin < fa.sharedSizeBytes || smem > (size_t)optin - fa.sharedSizeBytes) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t launch_refine(int dim, const DevSac* sacs, const float* traces, const float* pcs, const float* start,
                           int n, int K, float lnlo, float lnhi, float delta, float lambda0, int lcap, float* scratch,
                           opmm_fit_result* out, unsigned* err, cudaStream_t st) {
@@ -1630,12 +1649,12 @@ cudaError_t launch_refine(int dim, const DevSac* sacs, const float* traces, cons
   const size_t smem = 2 * (size_t)lcap * sizeof(float) + (size_t)kQSlotFloats * kRefineThreads * sizeof(float) +
                       (in_smem ? rows_bytes : 0);
   if (dim == 9) {
-    cudaError_t e = cudaFuncSetAttribute(k_refine<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(k_refine<9>, smem);
     if (e != cudaSuccess) return e;
     k_refine<9><<<n, kRefineThreads, smem, st>>>(sacs, traces, pcs, start, K, lnlo, lnhi, delta, lambda0, lcap,
                                                  scratch, in_smem, out, err);
   } else if (dim == kNumParams) {
-    cudaError_t e = cudaFuncSetAttribute(k_refine<kNumParams>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(k_refine<kNumParams>, smem);
     if (e != cudaSuccess) return e;
     k_refine<kNumParams><<<n, kRefineThreads, smem, st>>>(sacs, traces, pcs, start, K, lnlo, lnhi, delta, lambda0,
                                                           lcap, scratch, in_smem, out, err);
@@ -1720,7 +1739,7 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
   if (blocks > 4 * num_sms) blocks = 4 * num_sms;
   const size_t smem = 2 * (size_t)((L + 3) & ~3) * sizeof(float);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(k_score, smem);
     if (e != cudaSuccess) return e;
   }
   k_score<<<blocks, threads, smem, st>>>(opc, m, sac, traces, f, err);
@@ -1752,14 +1771,14 @@ int search_variant_for(int unit, int dim) {
 template <int G, int N, int MINB, bool LEAN>
 static cudaError_t occ_v(int lcap, int* bps) {
   const size_t smem = search_smem_bytes<G, N>(lcap);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_search<G, N, MINB, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem(k_search<G, N, MINB, LEAN>, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, N, MINB, LEAN>, search_threads<G, N>(), smem);
 }
 
-// The dynamic shared-memory attribute is set by search_occupancy_v(), which the
-// host calls for the same variant and lcap before any launch or graph capture.
+// The dynamic shared-memory attribute is raised to its maximum by
+// search_occupancy_v(), which the host calls for the same variant before any
+// launch or graph capture.
 template <int G, int N, int MINB, bool LEAN>
 static cudaError_t launch_v(const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
   const size_t smem = search_smem_bytes<G, N>(P.lcap);

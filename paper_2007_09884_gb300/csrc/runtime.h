@@ -32,6 +32,7 @@ bool is_device_ptr(const void* p);
 int nsub_for(float fs);
 Status check_saccade(const opmm_saccade& s, int i, bool need_duration);
 Status check_opc(const float* opc);
+Status check_opts(const opmm_fit_opts& o);   // the fit options every fit entry point accepts
 DevSac make_devsac(const opmm_saccade& s);
 
 // Grow-only device buffer.

@@ -11,10 +11,11 @@
 // kStaticScratchBytes) and, like any __device__ variable, is held by every GPU
 // that loads the library until the process exits.
 //
-// Set-up: the first call on a device, with that device current, looks up the
-// array's device address with cudaGetSymbolAddress and sets the search
-// kernel's shared-memory attribute; later calls on that device reuse the
-// cached address.  Make that first call before any stream capture.
+// Set-up: every call, with the device current, looks up the array's device
+// address with cudaGetSymbolAddress (cheap, and never stale after a device
+// reset) and makes sure the search kernel may use the shared memory this trace
+// needs.  The first call on a device also loads the library's kernels there;
+// make it before any stream capture.
 //
 // All calls share the one array, so calls whose work overlaps on the GPU
 // (different streams or threads at the same time) race; the call is
@@ -24,7 +25,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "../../include/opmm.h"
 #include "common.cuh"
@@ -52,6 +52,8 @@ constexpr size_t kOffUnits = 1280;                                      // int2[
 constexpr size_t kOffBest = align256(kOffUnits + sizeof(int2) * kStaticMaxUnits);
 constexpr size_t kOffTrace = align256(kOffBest + sizeof(float) * kUnitRecFloats * kStaticMaxUnits);
 constexpr size_t kStaticScratchBytes = align256(kOffTrace + sizeof(float) * kStaticMaxSamples);
+// 27,648 bytes: the size the header and the design notes state.
+static_assert(kStaticScratchBytes == 27648, "update the documented scratch size");
 
 static __device__ __align__(256) unsigned char g_opmm_static_scratch[kStaticScratchBytes];
 
@@ -76,33 +78,24 @@ __global__ void k_static_setup(unsigned char* base, DevSac d, Centre c, int has_
   for (int g = t; g < ngroups; g += blockDim.x) reinterpret_cast<int2*>(base + kOffUnits)[g] = make_int2(0, g);
 }
 
+// Per-call set-up on the current device: the scratch array's device address,
+// the SM count and how many search blocks of this trace capacity fit on an SM.
 struct DeviceSetup {
   unsigned char* scratch = nullptr;
   int num_sms = 0;
   int blocks_per_sm = 0;
-  bool done = false;
 };
 
-std::mutex g_setup_mutex;
-DeviceSetup g_setup[64];
-
-Status device_setup(int dev, DeviceSetup** out) {
-  if (dev < 0 || dev >= 64) return Status(OPMM_EINVAL, "device ordinal above 63");
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  DeviceSetup& s = g_setup[dev];
-  if (!s.done) {
-    void* p = nullptr;
-    Status r = cuda_status(cudaGetSymbolAddress(&p, g_opmm_static_scratch), "cudaGetSymbolAddress");
-    if (!r.ok()) return r;
-    r = cuda_status(cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    if (!r.ok()) return r;
-    r = cuda_status(search_occupancy(kStaticG, kStaticMaxSamples, &s.blocks_per_sm), "search occupancy");
-    if (!r.ok()) return r;
-    if (s.blocks_per_sm < 1) return Status(OPMM_ECUDA, "search kernel does not fit on this device");
-    s.scratch = static_cast<unsigned char*>(p);
-    s.done = true;
-  }
-  *out = &s;
+Status device_setup(int dev, int lcap, DeviceSetup* s) {
+  void* p = nullptr;
+  Status r = cuda_status(cudaGetSymbolAddress(&p, g_opmm_static_scratch), "cudaGetSymbolAddress");
+  if (!r.ok()) return r;
+  r = cuda_status(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  if (!r.ok()) return r;
+  r = cuda_status(search_occupancy(kStaticG, lcap, &s->blocks_per_sm), "search occupancy");
+  if (!r.ok()) return r;
+  if (s->blocks_per_sm < 1) return Status(OPMM_ECUDA, "search kernel does not fit on this device");
+  s->scratch = static_cast<unsigned char*>(p);
   return Status();
 }
 
@@ -115,16 +108,13 @@ using namespace opmm;
 extern "C" int opmm_fit_saccade_static(const opmm_saccade* sac, const opmm_fit_opts* opts,
                                        opmm_fit_result* out_device, void* cuda_stream) {
   if (!sac || !opts || !out_device || !sac->trace_deg) return OPMM_EINVAL;
+  // the options every fit accepts, then this entry point's own limits
+  if (!check_opts(*opts).ok()) return OPMM_EINVAL;
+  if (opts->model != OPMM_MODEL_18 || opts->use_surrogate) return OPMM_EINVAL;
+  if (opts->candidates > kStaticMaxCandidates) return OPMM_EINVAL;
   const bool need_duration = opts->init_opc == nullptr;
   if (!check_saccade(*sac, 0, need_duration).ok()) return OPMM_EINVAL;
   if (sac->n_samples > kStaticMaxSamples) return OPMM_EINVAL;
-  if (opts->model != OPMM_MODEL_18 || opts->use_surrogate) return OPMM_EINVAL;
-  if (opts->candidates < 22 || opts->candidates > kStaticMaxCandidates) return OPMM_EINVAL;
-  if (opts->iterations < 0 || opts->iterations > 1000000) return OPMM_EINVAL;
-  if (!(opts->box_lo > 0.0f) || !(opts->box_lo <= 1.0f) || !(opts->box_hi >= 1.0f) || !std::isfinite(opts->box_hi))
-    return OPMM_EINVAL;
-  if (!(opts->init_step > 0.0f) || !(opts->tol_x >= 0.0f) || !(opts->tol_f >= 0.0f)) return OPMM_EINVAL;
-  if (opts->pulse_init != OPMM_PULSE_TABLE1 && opts->pulse_init != OPMM_PULSE_CALIBRATED) return OPMM_EINVAL;
   if (opts->init_opc && !check_opc(opts->init_opc).ok()) return OPMM_EINVAL;
   if (!is_device_ptr(sac->trace_deg) || !is_device_ptr(out_device)) return OPMM_EINVAL;
 
@@ -133,9 +123,14 @@ extern "C" int opmm_fit_saccade_static(const opmm_saccade* sac, const opmm_fit_o
     cudaGetLastError();
     return OPMM_ECUDA;
   }
-  DeviceSetup* ds = nullptr;
-  Status s = device_setup(dev, &ds);
-  if (!s.ok()) return s.code;
+  const int lcap = (sac->n_samples + 3) & ~3;
+  DeviceSetup setup;
+  Status s = device_setup(dev, lcap, &setup);
+  if (!s.ok()) {
+    cudaGetLastError();
+    return s.code;
+  }
+  DeviceSetup* ds = &setup;
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   unsigned char* base = ds->scratch;
@@ -165,7 +160,7 @@ extern "C" int opmm_fit_saccade_static(const opmm_saccade* sac, const opmm_fit_o
   P.ngroups = ngroups;
   P.S = S;
   P.T = opts->iterations;
-  P.lcap = (d.L + 3) & ~3;
+  P.lcap = lcap;
   P.lnlo = (float)std::log((double)opts->box_lo);
   P.lnhi = (float)std::log((double)opts->box_hi);
   P.step = opts->init_step;
