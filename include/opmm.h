@@ -391,6 +391,15 @@ int opmm_surrogate_set_params(opmm_ctx* ctx, const float* in /* host [n] */);
  * (nullable) receives the network outputs [m][18].  All host memory. */
 int opmm_surrogate_grad(opmm_ctx* ctx, const float* x, const float* t, int32_t m, float* loss, float* grad,
                         float* y_out);
+/* One AdamW step with a caller-given gradient grad (host [n_params], the flat
+ * layout above), as opmm_surrogate_train takes after each batch: step count
+ * t += 1; m = 0.9 m + 0.1 g, v = 0.999 v + 0.001 g^2; weight matrices (not
+ * biases) w -= lr * weight_decay * w; then every entry
+ * w -= lr * (m / (1 - 0.9^t)) / (sqrt(v / (1 - 0.999^t)) + 1e-8), in FP32,
+ * and the BF16 working copies are refreshed.  For gradients accumulated
+ * outside the library (several batches, another loss).  Errors: OPMM_EINVAL
+ * without a surrogate, with a null gradient, lr <= 0 or weight_decay < 0. */
+int opmm_surrogate_apply_grad(opmm_ctx* ctx, const float* grad, float lr, float weight_decay);
 /* `steps` AdamW steps (betas 0.9, 0.999, eps 1e-8, decoupled weight decay on
  * weight matrices) on fresh batches of `batch` saccades (multiple of 128)
  * generated on the device by the plant itself: rates 250/500/1000 Hz, windows

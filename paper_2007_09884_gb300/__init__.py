@@ -44,7 +44,7 @@ EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", 
            "opmm_plan_execute", "opmm_plan_info", "opmm_plan_tuning", "opmm_plan_last_search_ms",
            "opmm_plan_destroy",
            "opmm_fit_saccade_static", "opmm_surrogate_init", "opmm_surrogate_num_params",
-           "opmm_surrogate_get_params", "opmm_surrogate_set_params", "opmm_surrogate_grad",
+           "opmm_surrogate_get_params", "opmm_surrogate_set_params", "opmm_surrogate_grad", "opmm_surrogate_apply_grad",
            "opmm_surrogate_train", "opmm_surrogate_predict", "opmm_surrogate_save", "opmm_surrogate_load", "opmm_featurize",
            "opmm_gemm_bf16", "opmm_serve_start", "opmm_serve_submit", "opmm_serve_poll",
            "opmm_serve_stats_get", "opmm_serve_stop"]
@@ -142,6 +142,7 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_surrogate_get_params.argtypes = [vp, vp]
     lib.opmm_surrogate_set_params.argtypes = [vp, vp]
     lib.opmm_surrogate_grad.argtypes = [vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp, vp]
+    lib.opmm_surrogate_apply_grad.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float]
     lib.opmm_surrogate_train.argtypes = [vp, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
                                          ctypes.c_int64, vp]
     lib.opmm_surrogate_predict.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
@@ -589,6 +590,14 @@ def opmm_surrogate_grad(ctx, x, t):
     loss = ctypes.c_float()
     _check(ctx, load_library().opmm_surrogate_grad(ctx, _vp(x), _vp(t), m, ctypes.byref(loss), _vp(g), _vp(y)))
     return float(loss.value), g, y
+
+
+def opmm_surrogate_apply_grad(ctx, grad, lr, weight_decay=0.0):
+    """One AdamW step of the surrogate's parameters with gradient grad [n_params]."""
+    g = np.ascontiguousarray(grad, dtype=np.float32)
+    if g.shape != (opmm_surrogate_num_params(),):
+        raise ValueError("gradient must have one entry per parameter")
+    _check(ctx, load_library().opmm_surrogate_apply_grad(ctx, _vp(g), float(lr), float(weight_decay)))
 
 
 def opmm_surrogate_train(ctx, steps, batch=4096, lr=1e-3, weight_decay=1e-4, data_seed=1, sample_base=0):

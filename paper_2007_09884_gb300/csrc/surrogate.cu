@@ -337,6 +337,22 @@ extern "C" int opmm_surrogate_grad(opmm_ctx* ctx, const float* x, const float* t
   return OPMM_OK;
 }
 
+extern "C" int opmm_surrogate_apply_grad(opmm_ctx* ctx, const float* grad, float lr, float weight_decay) {
+  if (!ctx) return OPMM_EINVAL;
+  if (!grad || !(lr > 0.0f) || !std::isfinite(lr) || !(weight_decay >= 0.0f) || !std::isfinite(weight_decay))
+    return sfail(ctx, Status(OPMM_EINVAL, "apply_grad: gradient required, lr > 0, weight_decay >= 0"));
+  if (!ctx->surrogate || !ctx->surrogate->ready) return sfail(ctx, Status(OPMM_EINVAL, "no surrogate"));
+  STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
+  SurrogateState& S = *ctx->surrogate;
+  cudaStream_t st = ctx->stream;
+  STRY(cuda_status(cudaMemcpyAsync(S.g.ptr, grad, (size_t)kNumParams * 4, cudaMemcpyHostToDevice, st), "H2D grad"));
+  S.step += 1;
+  STRY(cuda_status(adamw(f32(S.w), f32(S.g), f32(S.m1), f32(S.m2), (int)kNumParams, lr, 0.9f, 0.999f, 1e-8f,
+                         weight_decay, S.step, AdamLayout{}, bf(S.wb), bf(S.wt), st), "AdamW"));
+  STRY(cuda_status(cudaStreamSynchronize(st), "apply_grad"));
+  return OPMM_OK;
+}
+
 extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch, float lr, float weight_decay,
                                     uint64_t data_seed, int64_t sample_base, float* losses) {
   if (!ctx) return OPMM_EINVAL;
