@@ -10,10 +10,18 @@ each (the plain batched-search configuration).
   python bench.py --workload serve       # Poisson arrivals, p50/p99 latency, plain vs seeded
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
-At N=1 the default line also carries `surrogate`: the learned network trained
-on 10 M generated saccades, then saccades fitted/s at <= 0.1 deg RMS on the
-10,000-saccade uneven workload for the plain search and for the seeded search
-with plain fallback.
+At N=1 the default line also carries:
+  uneven10k  the 10,000-saccade uneven workload (250/500/1000 Hz, 16,384 x 30)
+             through an autotuned graph-captured plan: candidate sims/s, the
+             search kernel's FP32 roofline fraction, the autotuner's choice;
+  surrogate  the learned network trained on 10 M generated saccades, then
+             saccades fitted/s at <= 0.1 deg RMS on the uneven workload for
+             the plain search and for the seeded search with plain fallback;
+  serve      the request loop under 1 s of Poisson arrivals at 1k, 10k and
+             50k/s, plain and seeded: p50/p99 latency, throughput, refusals;
+  single10   the single 10 deg saccade (4,096 x 20) fitted on the GPU and,
+             in the CPU-baseline leg, by the oracle: seconds and RMS;
+  refine, ivt  the refinement after the search and the I-VT front end.
 
 Prints one JSON line (rank 0).  value = candidate OPC simulations per second
 over the whole job (all ranks), inputs resident in HBM; e2e = the same metric
@@ -289,6 +297,85 @@ def kernel_hash():
     return source_code_digest(texts)
 
 
+def search_flops(w, r):
+    """Algorithmic FLOPs of one search over workload w with results r (the
+    per-saccade evaluation and pulse-end counts), and the same work counted
+    as stage-by-stage RK4."""
+    flops = 0.0
+    rk4_eq = 0.0
+    for i in range(w.B):
+        nsub = nsub_for(float(w.fs[i]))
+        e = float(r["evaluations"][i])
+        flops += e * flops_per_sim(int(w.L[i]), int(w.onset[i]), nsub)
+        flops += float(r["pulse_end_evals"][i]) * pulse_end_flops(nsub)
+        rk4_eq += e * rk4_stage_flops_per_sim(int(w.L[i]), nsub)
+    return flops, rk4_eq
+
+
+def fp32_peak_tflops(local, clk=None):
+    import torch
+    props = torch.cuda.get_device_properties(local)
+    mp = measured_peaks()
+    sm_max = (mp or {}).get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * float(sm_max) * 1e6 / 1e12
+    return peak, f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (of nominal max clock)"
+
+
+def uneven_measure(G, ctx, local, quick=False, steps=2):
+    """The uneven workload (10,000 saccades at 250/500/1000 Hz, both
+    directions, 1-40 deg, 40-400 samples, 16,384 candidates x 30 iterations):
+    one autotuned, graph-captured plan over device-resident traces, one
+    warm-up execute, then `steps` timed executes with L2 flushed before each.
+    Candidate simulations per second over the whole execute, and the search
+    kernel's FLOP rate (same accounting as the default line) against the FP32
+    peak."""
+    import torch
+    w = W.uneven10k(B=512 if quick else 10000)
+    traces, pulse = gpu_inputs(G, ctx, w)
+    buf, offs = packed(traces)
+    dev = torch.from_numpy(buf).cuda()
+    batch = G.make_batch(dev, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms, n_samples=w.L, offsets=offs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = G.Plan(ctx, batch, candidates=w.candidates, iterations=w.iterations, seed=w.seed, pulse_init=pulse)
+    plan_s = time.perf_counter() - t0
+    plan.execute_raw()
+    flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    step_ms, search_ms = [], []
+    res = None
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = plan.execute_raw()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        search_ms.append(plan.last_search_ms())
+    r = G.results_to_numpy(res)
+    info, probes = plan.info(), plan.tuning()
+    plan.destroy()
+    evals = float(np.sum(r["evaluations"].astype(np.float64)))
+    flops, _ = search_flops(w, r)
+    mean_step, mean_search = statistics.mean(step_ms), statistics.mean(search_ms)
+    peak, basis = fp32_peak_tflops(local)
+    achieved = flops / (mean_search * 1e-3) / 1e12
+    ok = (r["rms_deg"] <= 0.1) & (r["status"] == 0)
+    return {"workload": w.name, "saccades": int(w.B), "candidates_per_iteration": int(w.candidates),
+            "iterations": int(w.iterations), "sample_rates_hz": sorted({float(x) for x in w.fs}),
+            "window_samples": [int(w.L.min()), int(w.L.max())], "timed_steps": steps,
+            "candidate_sims_per_s": evals / (mean_step * 1e-3), "step_ms": mean_step, "search_ms": mean_search,
+            "saccades_fitted_per_s_at_0p1deg": float(ok.sum()) / (mean_step * 1e-3),
+            "fraction_fitted_at_0p1deg": float(ok.mean()), "median_rms_deg": float(np.median(r["rms_deg"])),
+            "roofline": {"bound": "alu", "kernel": "k_search", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "peak_basis": basis},
+            "launch_shape": info, "autotuner_probes": probes, "plan_build_s": plan_s,
+            "l2": "L2 flushed (256 MB write) before every timed execute"}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2007_09884_gb300 as G
@@ -342,22 +429,12 @@ def run_ours(args, ws, rank, local):
     value = evals_all / (t_max * 1e-3)
 
     # algorithmic FLOPs of this rank's search launch
-    flops = 0.0
-    rk4_eq = 0.0
-    for i in range(w.B):
-        nsub = nsub_for(float(w.fs[i]))
-        e = float(r["evaluations"][i])
-        flops += e * flops_per_sim(int(w.L[i]), int(w.onset[i]), nsub)
-        flops += float(r["pulse_end_evals"][i]) * pulse_end_flops(nsub)
-        rk4_eq += e * rk4_stage_flops_per_sim(int(w.L[i]), nsub)
+    flops, rk4_eq = search_flops(w, r)
     mean_search_ms = statistics.mean(search_ms)
     if not mean_search_ms > 0.0:
         raise SystemExit("search kernel events returned no time")
     achieved = flops / (mean_search_ms * 1e-3) / 1e12
-    props = torch.cuda.get_device_properties(local)
-    mp = measured_peaks()
-    sm_max = (mp or {}).get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * float(sm_max) * 1e6 / 1e12
+    peak, peak_basis = fp32_peak_tflops(local, clk)
     prof = profile_traffic(kernel_hash())
 
     # end to end through the C ABI with host buffers
@@ -402,7 +479,7 @@ def run_ours(args, ws, rank, local):
         "roofline": {"bound": "alu", "kernel": "k_search (persistent Nelder-Mead + plant)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (of nominal max clock)",
+                     "peak_basis": peak_basis,
                      "traffic": (prof["dram_bytes_per_launch"] if prof else None),
                      "traffic_basis": (prof.get("basis") if prof else "no ncu capture of the current kernel")},
         "e2e": {"value": e2e_value, "unit": "candidate sims/s", "h2d_bytes_per_step": h2d,
@@ -416,10 +493,20 @@ def run_ours(args, ws, rank, local):
         out["refine"] = refine_after_search(G, ctx, batch_dev, r, args, pulse, w)
     if rank == 0 and ws == 1 and not args.no_ivt:
         out["ivt"] = ivt_measure(G, ctx, 1 << (22 if args.quick else 26), with_oracle=not args.no_cpu_baseline)
-    if rank == 0 and ws == 1 and not args.no_surrogate and args.workload == "batch1024" and args.model == 18:
+    headline = rank == 0 and ws == 1 and args.workload == "batch1024" and args.model == 18
+    if headline and not args.no_uneven:
+        out["uneven10k"] = uneven_measure(G, ctx, local, args.quick)
+    if headline and not args.no_surrogate:
         out["surrogate"] = surrogate_compare(G, ctx, args.quick)
+    if headline and not args.no_serve:
+        out["serve"] = serve_measure(G, ctx, args.rates, seconds=args.serve_seconds_line,
+                                     trained=not args.no_surrogate, quick=args.quick)
+    if headline:
+        out["single10"] = single10_measure(G, ctx)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget, model=args.model)
+        if "single10" in out:
+            out["single10"]["oracle"] = cpu_baseline_single10(out["single10"])
     G.opmm_destroy(ctx)
     return out
 
@@ -764,7 +851,15 @@ def surrogate_compare(G, ctx, quick=False):
         return np.array([math.sqrt(np.mean((traj[offs[i]:offs[i] + len(htr[i])] - htr[i]) ** 2))
                          for i in range(h.B)])
 
+    # share of the log-OPC target variance the network explains (targets
+    # y = ln(hidden / nominal) / 0.2, estimate ln(pred / nominal) / 0.2)
+    yt = np.log(hidden / nominal.astype(np.float64))
+    ye = np.log(pred.astype(np.float64) / nominal.astype(np.float64))
+    ss_res = np.sum((yt - ye) ** 2, axis=0)
+    ss_tot = np.sum((yt - yt.mean(axis=0)) ** 2, axis=0)
     held = {"saccades": int(h.B), "predict_seconds": tpred,
+            "explained_variance_log_opc": float(1.0 - ss_res.sum() / ss_tot.sum()),
+            "explained_variance_per_parameter": [float(x) for x in 1.0 - ss_res / ss_tot],
             "median_abs_log_error_nominal": float(np.median(np.abs(np.log(nominal / hidden)))),
             "median_abs_log_error_surrogate": float(np.median(np.abs(np.log(pred / hidden)))),
             "median_trace_rms_deg_nominal": float(np.median(traj_rms(nominal))),
@@ -774,6 +869,71 @@ def surrogate_compare(G, ctx, quick=False):
             "fitted_per_s_ratio": seeded_row["fitted_per_s_at_0p1deg"] / plain_row["fitted_per_s_at_0p1deg"],
             "variants": variants,
             "training": training, "held_out": held}
+
+
+def serve_measure(G, ctx, rates, seconds=1.0, trained=True, quick=False):
+    """The request loop for about `seconds` of Poisson arrivals per rate,
+    plain search (16,384 x 30) and surrogate-seeded search (1,024 x 20 in
+    +-5%) on the same saccades (uneven distribution): p50/p99 latency from
+    submit to result, throughput, refusals, share fitted to <= 0.1 deg.  The
+    queue holds a quarter second of arrivals, so an overloaded plain search
+    refuses the rest instead of building minutes of backlog."""
+    if not trained:
+        train_surrogate(G, ctx, quick)
+    w = W.uneven10k(B=2048, config_index=4)
+    traces, pulse = gpu_inputs(G, ctx, w)
+    batch = G.make_batch(traces, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms)
+    plain = dict(candidates=16384, iterations=30, seed=0, pulse_init=pulse)
+    seeded = dict(SEEDED_FIT, seed=0, pulse_init=pulse, use_surrogate=True)
+    rows = []
+    for rate in rates:
+        arr = W.poisson_arrivals(rate, seconds, seed=int(rate))
+        for name, fit, ri in (("plain", plain, 10), ("surrogate", seeded, 5)):
+            cfg = G.serve_opts(max_slots=4096, max_queue=max(1000, int(rate * 0.25)), max_samples=400,
+                               round_iters=ri, max_admit_per_round=4096)
+            r = serve_run(G, ctx, batch, arr, fit, cfg)
+            r.update({"rate_per_s": rate, "search": name})
+            rows.append(r)
+    return {"workload": "serve (Poisson arrivals of single saccades, uneven distribution)",
+            "seconds_of_arrivals_per_rate": seconds, "plain": plain,
+            "surrogate": {k: v for k, v in seeded.items()}, "rows": rows}
+
+
+_SINGLE10 = {}
+
+
+def single10_measure(G, ctx):
+    """The single 10 deg saccade (1 kHz, 150 samples, Table 1's 55 g pulse),
+    4,096 candidates x 20 iterations: the GPU fit through opmm_fit_batch with
+    host buffers, wall time after one warm-up call (plan, autotune)."""
+    w = W.single10()
+    traces, pulse = gpu_inputs(G, ctx, w)
+    batch = G.make_batch(traces, w.fs, w.onset, w.theta0, w.thetaf, w.dur_ms)
+    opts = dict(candidates=w.candidates, iterations=w.iterations, seed=w.seed, pulse_init=pulse)
+    G.opmm_fit_batch(ctx, batch, **opts)
+    t0 = time.perf_counter()
+    r = G.opmm_fit_batch(ctx, batch, **opts)
+    dt = time.perf_counter() - t0
+    _SINGLE10.update(w=w, y=traces[0])
+    return {"workload": w.name, "candidates_per_iteration": int(w.candidates), "iterations": int(w.iterations),
+            "simplices": int(w.candidates // 22), "gpu_seconds": dt, "gpu_rms_deg": float(r["rms_deg"][0]),
+            "gpu_evaluations": int(r["evaluations"][0]), "gpu_status": int(r["status"][0])}
+
+
+def cpu_baseline_single10(g):
+    """The oracle's full fit of the same saccade (same trace, same budget,
+    same seed) on the host cores: seconds and RMS beside the GPU's."""
+    import oracle as O
+    w, y = _SINGLE10["w"], _SINGLE10["y"]
+    A, D = float(w.amplitude[0]), float(w.dur_ms[0])
+    pn = np.float32(O.nominal_opc(A, D, calibrated=w.calibrated_pulse)).astype(np.float64)
+    nthreads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ro = O.fit(pn, int(w.L[0]), float(w.fs[0]), int(w.onset[0]), float(w.theta0[0]), float(w.thetaf[0]),
+               np.asarray(y, np.float64), w.candidates // 22, w.iterations, seed=w.seed, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "rms_deg": ro["rms"], "cores": nthreads, "kind": "oracle (FP64)",
+            "abs_rms_difference_deg": abs(ro["rms"] - g["gpu_rms_deg"]), "speedup_gpu": dt / g["gpu_seconds"]}
 
 
 def run_surrogate(args):
@@ -896,6 +1056,10 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="leave the surrogate comparison out of the line")
     ap.add_argument("--rates", type=float, nargs="+", default=[1000.0, 10000.0, 50000.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-seconds-line", type=float, default=1.0,
+                    help="seconds of arrivals per rate for the serve object of the default line")
+    ap.add_argument("--no-serve", action="store_true", help="leave the request-loop measurement out of the line")
+    ap.add_argument("--no-uneven", action="store_true", help="leave the uneven 10,000-saccade search out of the line")
     ap.add_argument("--serve-slots", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="small batch (smoke of the bench itself)")
     ap.add_argument("--model", type=int, default=18, choices=[18, 9],
