@@ -14,11 +14,12 @@
 // trial OPC vector's plant in registers (plant.cuh), scoring each sample against
 // the trace staged once per block in shared memory by a TMA bulk copy, with a
 // compensated FP32 sum.  Per block, two groups of G simplices of one saccade
-// advance in turn: all 22 trial points of every simplex of a group are
+// advance side by side: all 22 trial points of every simplex of a group are
 // evaluated in one wave (Sec. 3.3: all simplex transformations are computed at
-// once), ordered by pulse-end time by the evaluation warps, while the block's
-// controller warp takes the Lagarias decisions of the other group and sets up
-// that group's next wave.
+// once), ordered by pulse-end time and taken in 32-candidate chunks by all of
+// the block's warps; the warp that completes a group's wave takes that group's
+// Lagarias decisions and publishes its next wave while the other warps
+// evaluate the other group's.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -86,11 +87,12 @@ struct PeakSink {
 // Objective of one OPC vector: mean squared error over the window; the
 // samples up to onset (the plant at rest) are folded into (sum0, c0).
 // pe (optional): set to 1 when the pulse ends inside the window.
+template <bool SYNC = false>
 __device__ __forceinline__ float objective(const float* p, const SacConst& sc, const float* z,
                                            float sum0, float c0, float* qs = nullptr, int qstride = 0,
-                                           int* pe = nullptr) {
+                                           int* pe = nullptr, unsigned mask = 0xffffffffu) {
   KahanSink s{z, sum0, c0, 0.0f};
-  if (walk(p, sc, s, qs, qstride, true, pe) < 0) return INFINITY;
+  if (walk<KahanSink, SYNC>(p, sc, s, qs, qstride, true, pe, mask) < 0) return INFINITY;
   s.block_end();
   const float f = (s.sum - s.c) / (float)sc.L;
   return isfinite(f) ? f : INFINITY;
@@ -108,7 +110,7 @@ struct PtrSrc {
 
 // Candidate in ln-parameter space, from two rows in shared memory: a vertex
 // (u = a), or the search's trial-point form u = a + (b - a) / 2 (a = b for the
-// controller's four trial points, best vertex and vertex q - 3 for a shrink
+// deciding warp's four trial points, best vertex and vertex q - 3 for a shrink
 // point).
 struct ULinSrc {
   const float* a;   // first row
@@ -328,27 +330,24 @@ constexpr int kHistPer = kSortBins / 32;              // bins per lane of the sc
 constexpr int kHistLen = kSortBins + 32;                // bin b stored at b + b / kHistPer
 
 // One block runs G simplices in each of two groups (a unit of 2G simplices of
-// one saccade).  NE evaluation threads (22 per simplex of a group rounded to
-// warps, at most 11 warps) evaluate the pending wave of one group while the
-// block's last warp, the controller, takes the Nelder-Mead decisions of the
-// other group's last wave and sets up its next wave; the two swap at the
-// single block barrier that ends each step.  Eleven evaluation warps and the
-// controller at 168 registers per thread fill the SM's register file (3 warps
-// per SM sub-partition); a wave larger than NE (G = 32: 704 candidates) is
-// taken in chunks of 32 candidates that the evaluation warps pull in turn, so
-// that warps sharing a sub-partition with fewer others take more chunks.
-constexpr int kMaxEvalThreads = 352;
+// one saccade) with twelve warps, all of which evaluate: a group's wave (its
+// 22 trial points per simplex, or its initial vertices) is published in
+// chunks of 32 candidates that the warps claim in turn; the warp that
+// completes a wave's last chunk takes that group's Nelder-Mead decisions,
+// orders and publishes its next wave, while the other warps work on the other
+// group's wave.  There is no block barrier between steps.  Twelve warps at 168
+// registers per thread fill the SM's register file (3 warps per SM
+// sub-partition).
+constexpr int kSearchWarps = 12;
+// Longest a search warp waits with nothing to claim (SM clock cycles, about
+// four seconds): far above one chunk's evaluation plus one group's decisions;
+// past it the warp raises kErrWaitTimeout and the block leaves the kernel.
+constexpr long long kMaxIdleCycles = 8000000000LL;
 template <int G, int N>
-__host__ __device__ constexpr int search_eval_threads() {
-  return ((G * trials<N>() + 31) / 32) * 32 < kMaxEvalThreads ? ((G * trials<N>() + 31) / 32) * 32 : kMaxEvalThreads;
-}
+__host__ __device__ constexpr int search_threads() { return 32 * kSearchWarps; }
+// candidates per lane when one warp orders a wave
 template <int G, int N>
-__host__ __device__ constexpr int search_threads() { return search_eval_threads<G, N>() + 32; }
-// candidates per evaluation thread in one wave (ordering)
-template <int G, int N>
-__host__ __device__ constexpr int wave_per_thread() {
-  return (G * trials<N>() + search_eval_threads<G, N>() - 1) / search_eval_threads<G, N>();
-}
+__host__ __device__ constexpr int wave_per_lane() { return (G * trials<N>() + 31) / 32; }
 
 // State of one group of G simplices over N coordinates.
 template <int G, int N>
@@ -362,44 +361,52 @@ struct GroupSmem {
   float FT[G][kNT];              // trial values
   int hist[kHistLen];            // counting sort of the pending wave by pulse-end time (padded)
   unsigned short perm[G * kNT];  // candidate ids of the pending wave in key order
+  int kr[G * kNT];               // ordering scratch: key << 16 | rank within the key's bin, or -1
   unsigned char ord[G][kNV + 1]; // ord[r] = slot of rank r
   int active[G];
   int iters[G];
-  int okf[G];   // controller scratch: value spread within tol_f
-  int okx[G];   // controller scratch: vertex spread within tol_x
-  int shr[G];   // controller scratch: the simplex shrinks this step
+  int okf[G];   // decision scratch: value spread within tol_f
+  int okx[G];   // decision scratch: vertex spread within tol_x
+  int shr[G];   // decision scratch: the simplex shrinks this step
   int nsim;     // simplices of this group (0: empty group)
   int nvalid;   // candidates of the pending wave
   int kind;     // pending wave: 0 initial vertices, 1 trial points
-  int state;    // kPending (a wave is ordered) or kDone; written by the controller only
+  int state;    // kPending (a wave is ordered) or kDone; written by the deciding warp only
   int it;       // trial waves evaluated in this launch
   int evals;    // candidate evaluations of this group
   int pe;       // of those, candidates whose pulse ends inside the window
-  int chunk;    // next chunk of 32 candidates (in key order) of the pending wave
+  int pub;      // published wave: sequence number << 16 | chunks (0 chunks: nothing to take)
+  int claim;    // sequence number << 16 | next chunk of 32 candidates (in key order) to claim
+  int done;     // chunks of the published wave evaluated
 };
 
 enum : int { kPending = 0, kDone = 2 };
 
-template <int G, int N>
-struct SearchSmem {
-  GroupSmem<G, N> grp[2];
+// The staged saccade of a search block.
+struct SacStage {
   float pc[kNumParams];          // box centre of the current saccade
   SacConst sc;
   TraceStage st;
+};
+
+template <int G, int N, int NG>
+struct SearchSmem {
+  GroupSmem<G, N> grp[NG];
+  SacStage sv;
   int cur_b;
   int unit;
-  int finished[2];               // by step parity: both groups done
+  int abort;                     // a warp's bounded wait gave up: the block leaves
   uint64_t bar;
 };
 
 constexpr int kQSlotFloats = (int)(sizeof(Prop2) / sizeof(float));
 
 // Dynamic shared memory: the block state, the raw and shifted traces (lcap
-// floats each) and one single-substep propagator slot per evaluation thread.
-template <int G, int N>
+// floats each) and one single-substep propagator slot per thread.
+template <int G, int N, int NG>
 size_t search_smem_bytes(int lcap) {
-  return ((sizeof(SearchSmem<G, N>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float) +
-         (size_t)kQSlotFloats * search_eval_threads<G, N>() * sizeof(float);
+  return ((sizeof(SearchSmem<G, N, NG>) + 127) / 128) * 128 + 2 * (size_t)lcap * sizeof(float) +
+         (size_t)kQSlotFloats * search_threads<G, N>() * sizeof(float);
 }
 
 // Trial point coordinate (Lagarias et al. coefficients rho 1, chi 2, gamma 1/2).
@@ -440,13 +447,15 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
   return isfinite(f) ? f : INFINITY;
 }
 
+// Objective of search point u; the lanes in `mask` call it together and
+// reconverge inside the walk.
 template <int N>
 __device__ __forceinline__ float eval_u(const float (&u)[N], const float* pc, float lnlo,
                                         float lnhi, const SacConst& sc, const float* z, float sum0,
-                                        float c0, float* qs, int qstride, int* pe) {
+                                        float c0, float* qs, int qstride, int* pe, unsigned mask) {
   float p[kNumParams];
   u_to_p<N>(u, pc, lnlo, lnhi, p);
-  return objective(p, sc, z, sum0, c0, qs, qstride, pe);
+  return objective<true>(p, sc, z, sum0, c0, qs, qstride, pe, mask);
 }
 
 // Sort key of a candidate: its pulse-end time, binned over the window (the
@@ -464,7 +473,7 @@ __device__ __forceinline__ int switch_key(float u_pw, float pc_pw, float lnlo, f
 __device__ __forceinline__ int hist_slot(int b) { return b + b / kHistPer; }
 
 // Rows of trial point q of simplex gi, as u = a + (b - a) / 2 coordinate by
-// coordinate: a = b = the controller's XT row for q < 4 (so u = a exactly),
+// coordinate: a = b = the deciding warp's XT row for q < 4 (so u = a exactly),
 // the best vertex and vertex q - 3 for the shrink points.  One form for every
 // lane, so a warp holding both kinds does not diverge.
 template <int G, int N>
@@ -474,88 +483,9 @@ __device__ __forceinline__ void trial_rows(const GroupSmem<G, N>& g, int gi, int
   b = q < 4 ? g.XT[gi][q] : g.U[gi][o[q - 3]];
 }
 
-// Barrier of the evaluation threads only (the controller warp runs on).
-template <int NE>
-__device__ __forceinline__ void eval_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(NE) : "memory");
-}
-
-// Counting sort of a group's due wave by pulse-end time, by the evaluation
-// threads at the start of the step that evaluates it: thread t keys
-// candidates t, t + NE, ..., one warp scans the histogram (cleared by the
-// controller when it set the wave up), and afterwards g.perm[0 .. g.nvalid)
-// lists the candidates in key order.
-template <int G, int N>
-__device__ __forceinline__ void order_wave(GroupSmem<G, N>& g, const SearchSmem<G, N>& S, const SearchParams& P, int tid) {
-  constexpr int NE = search_eval_threads<G, N>();
-  constexpr int R = wave_per_thread<G, N>();
-  static_assert(G * trials<N>() <= NE * R, "every candidate keyed");
-  constexpr int kPwCoord = search_coord<N>(kPw);   // -1: pulse width held at the centre
-  const int ncand = (g.kind == 0 ? verts<N>() : trials<N>()) * g.nsim;
-  int key[R], slot[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int c = tid + r * NE;
-    key[r] = -1;
-    slot[r] = 0;
-    if (c < ncand) {
-      if (g.kind == 0) {
-        const int gi = c / verts<N>(), v = c - gi * verts<N>();
-        key[r] = switch_key(kPwCoord < 0 ? 0.0f : g.U[gi][v][kPwCoord < 0 ? 0 : kPwCoord], S.pc[kPw], P.lnlo,
-                            P.lnhi, S.sc);
-      } else {
-        const int gi = c / trials<N>(), q = c - gi * trials<N>();
-        if (g.active[gi]) {
-          const float* a;
-          const float* bb;
-          trial_rows(g, gi, q, a, bb);
-          const int jp = kPwCoord < 0 ? 0 : kPwCoord;
-          key[r] = switch_key(kPwCoord < 0 ? 0.0f : shrink_coord(a[jp], bb[jp]), S.pc[kPw], P.lnlo, P.lnhi, S.sc);
-        }
-      }
-      if (key[r] >= 0) slot[r] = atomicAdd(&g.hist[hist_slot(key[r])], 1);
-    }
-  }
-  eval_sync<NE>();
-  if (tid < 32) {
-    // lane l owns bins [per l, per l + per), stored at hist_slot(per l + i) =
-    // (per + 1) l + i: one padding word per lane keeps the lanes on distinct
-    // banks; the counts are read once into registers
-    const int lane = tid;
-    constexpr int per = kHistPer;
-    static_assert(per * 32 == kSortBins && (per + 1) * 31 + per <= kHistLen, "histogram layout");
-    int* h = g.hist + lane * (per + 1);
-    int v[per];
-    int s = 0;
-#pragma unroll
-    for (int i = 0; i < per; ++i) {
-      v[i] = h[i];
-      s += v[i];
-    }
-    int incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int x = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += x;
-    }
-    int run = incl - s;
-#pragma unroll
-    for (int i = 0; i < per; ++i) {
-      h[i] = run;
-      run += v[i];
-    }
-    if (lane == 31) g.nvalid = incl;
-  }
-  eval_sync<NE>();
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (key[r] >= 0) g.perm[g.hist[hist_slot(key[r])] + slot[r]] = (unsigned short)(tid + r * NE);
-  eval_sync<NE>();
-}
-
 // Centroid of the best n vertices and the vertex-spread half of the exit test
 // (Sec. 3.3: every vertex within tol_x of the best in max-norm), spread over
-// the controller warp's lanes by (simplex, coordinate); `sel` picks the
+// the deciding warp's lanes by (simplex, coordinate); `sel` picks the
 // simplices to process.  g.okx[gi] must be 1 on entry and is cleared by any
 // coordinate that fails.
 template <int G, int N, class Sel>
@@ -729,22 +659,19 @@ __device__ __forceinline__ void decide_group(GroupSmem<G, N>& g, int lane, float
   __syncwarp();
 }
 
-// Set up a group's next wave (controller warp): the initial vertices (kind 0)
-// or the 22 trial points of every active simplex, ordered by the evaluation
-// threads when they take it; a group with nothing left to evaluate, or at its
-// iteration cap, is done.  The controller writes the four trial points
-// (reflection, expansion, both contractions) to XT; the 18 shrink points are
-// formed by the evaluation threads from the vertices.
+// Set up a group's next wave (one warp): the initial vertices (kind 0) or the
+// 22 trial points of every active simplex; a group with nothing left to
+// evaluate, or at its iteration cap, is done.  The warp writes the four trial
+// points (reflection, expansion, both contractions) to XT; the 18 shrink
+// points are formed by the evaluating threads from the vertices.
 template <int G, int N>
 __device__ __forceinline__ void next_wave(GroupSmem<G, N>& g, int kind, int t_run, int lane) {
   int nact = 0;
   if (kind == 1) {
     for (int gi = 0; gi < g.nsim; ++gi) nact += g.active[gi];
     if (g.it >= t_run || nact == 0) {
-      if (lane == 0) {
-        g.state = kDone;
-        g.nvalid = 0;
-      }
+      if (lane == 0) g.state = kDone;
+      if (lane == 0) g.nvalid = 0;
       __syncwarp();
       return;
     }
@@ -757,13 +684,155 @@ __device__ __forceinline__ void next_wave(GroupSmem<G, N>& g, int kind, int t_ru
       if (g.active[gi]) g.XT[gi][q][j] = trial_coord(q, g.XB[gi][j], g.U[gi][g.ord[gi][N]][j]);
     }
   }
-  if (lane == 0) {
-    g.kind = kind;
-    g.chunk = 0;
-    g.state = kPending;
-    if (kind == 1) g.evals += trials<N>() * nact;
+  if (lane == 0) g.kind = kind;
+  if (lane == 0) g.state = kPending;
+  if (lane == 0 && kind == 1) g.evals += trials<N>() * nact;
+  __syncwarp();
+}
+
+// Counting sort of a group's freshly set-up wave by pulse-end time, by the
+// warp that set it up: lane l keys candidates l, l + 32, ..., the histogram
+// (cleared by next_wave) is scanned by the same warp, and afterwards
+// g.perm[0 .. g.nvalid) lists the candidates in key order.
+template <int G, int N>
+__device__ __forceinline__ void order_wave(GroupSmem<G, N>& g, const SacStage& V, const SearchParams& P, int lane) {
+  constexpr int R = wave_per_lane<G, N>();
+  static_assert(G * trials<N>() <= 32 * R, "every candidate keyed");
+  static_assert(G * trials<N>() < (1 << 16), "bin rank in 16 bits");
+  constexpr int kPwCoord = search_coord<N>(kPw);   // -1: pulse width held at the centre
+  const int ncand = (g.kind == 0 ? verts<N>() : trials<N>()) * g.nsim;
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) {
+    const int c = lane + 32 * r;
+    int key = -1;
+    if (c < ncand) {
+      if (g.kind == 0) {
+        const int gi = c / verts<N>(), v = c - gi * verts<N>();
+        key = switch_key(kPwCoord < 0 ? 0.0f : g.U[gi][v][kPwCoord < 0 ? 0 : kPwCoord], V.pc[kPw], P.lnlo,
+                         P.lnhi, V.sc);
+      } else {
+        const int gi = c / trials<N>(), q = c - gi * trials<N>();
+        if (g.active[gi]) {
+          const float* a;
+          const float* bb;
+          trial_rows(g, gi, q, a, bb);
+          const int jp = kPwCoord < 0 ? 0 : kPwCoord;
+          key = switch_key(kPwCoord < 0 ? 0.0f : shrink_coord(a[jp], bb[jp]), V.pc[kPw], P.lnlo, P.lnhi, V.sc);
+        }
+      }
+    }
+    if (c < G * trials<N>()) g.kr[c] = key >= 0 ? (key << 16) | atomicAdd(&g.hist[hist_slot(key)], 1) : -1;
   }
   __syncwarp();
+  {
+    // lane l owns bins [per l, per l + per), stored at hist_slot(per l + i) =
+    // (per + 1) l + i: one padding word per lane keeps the lanes on distinct
+    // banks; the counts are read once into registers
+    constexpr int per = kHistPer;
+    static_assert(per * 32 == kSortBins && (per + 1) * 31 + per <= kHistLen, "histogram layout");
+    int* h = g.hist + lane * (per + 1);
+    int v[per];
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+      v[i] = h[i];
+      sum += v[i];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += x;
+    }
+    int run = incl - sum;
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+      h[i] = run;
+      run += v[i];
+    }
+    if (lane == 31) g.nvalid = incl;
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int c = lane; c < ncand; c += 32) {
+    const int kr = g.kr[c];
+    if (kr >= 0) g.perm[g.hist[hist_slot(kr >> 16)] + (kr & 0xffff)] = (unsigned short)c;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ int vload(const int& x) { return *reinterpret_cast<const volatile int*>(&x); }
+
+// Make a group's set-up wave (or its end) visible to the block's warps.  The
+// wave's data is written before; then the done count and the claim word are
+// reset for the next sequence number, then the published word (sequence,
+// chunks) is written, with block-scope fences between, so a warp that claims a
+// chunk of this sequence sees the wave.  A finished group publishes 0 chunks.
+template <int G, int N>
+__device__ __forceinline__ void publish_wave(GroupSmem<G, N>& g, int lane) {
+  __syncwarp();
+  __threadfence_block();
+  // every lane computes the words; lane 0 alone stores them (single
+  // predicated stores, so the warp never splits around them)
+  const int seq = ((vload(g.pub) >> 16) + 1) & 0x7fff;
+  const int n = g.state == kDone ? 0 : (g.nvalid + 31) >> 5;
+  if (lane == 0) atomicExch(&g.done, 0);
+  if (lane == 0) atomicExch(&g.claim, seq << 16);
+  __threadfence_block();
+  if (lane == 0) atomicExch(&g.pub, (seq << 16) | n);
+  __syncwarp();
+}
+
+// Claim the next chunk of a group's published wave, by the whole warp with
+// uniform control flow: lane 0 alone reads the words and attempts the
+// compare-and-swap (single predicated instructions) and every value is
+// broadcast, so the warp stays converged.  Returns the chunk index and its
+// wave's chunk count, or -1 when the wave has no chunk left, the claim word
+// belongs to another sequence (a wave being published), or other warps kept
+// winning the race (the caller tries again).
+template <int G, int N>
+__device__ __forceinline__ int try_claim(GroupSmem<G, N>& g, int lane, int& nchunks) {
+  int pub = 0, old = 0;
+  if (lane == 0) pub = vload(g.pub);
+  pub = __shfl_sync(0xffffffffu, pub, 0);
+  const int n = pub & 0xffff;
+  if (n == 0) return -1;
+  const int want = pub & ~0xffff;
+  if (lane == 0) old = vload(g.claim);
+  old = __shfl_sync(0xffffffffu, old, 0);
+#pragma unroll 1
+  for (int t = 0; t < 64; ++t) {
+    if ((old & ~0xffff) != want || (old & 0xffff) >= n) return -1;
+    int prev = 0;
+    if (lane == 0) prev = atomicCAS(&g.claim, old, old + 1);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev == old) {
+      __threadfence_block();
+      nchunks = n;
+      return old & 0xffff;
+    }
+    old = prev;
+  }
+  return -1;
+}
+
+// The warp that completed a group's wave: Nelder-Mead decisions on the values
+// just computed (ranking of the initial simplices, or the Lagarias step of
+// every active simplex), then the group's next wave, its ordering and its
+// publication.
+template <int G, int N>
+__device__ __forceinline__ void advance_group(GroupSmem<G, N>& g, const SacStage& V, const SearchParams& P, int lane,
+                                              int t_run) {
+  if (g.kind == 0) {
+    init_rank<G, N>(g, lane, P.tolx, P.tolf);
+  } else {
+    decide_group<G, N>(g, lane, P.tolx, P.tolf);
+    if (lane == 0) g.it += 1;
+    __syncwarp();
+  }
+  next_wave<G, N>(g, 1, t_run, lane);
+  if (g.state == kPending) order_wave<G, N>(g, V, P, lane);
+  publish_wave<G, N>(g, lane);
 }
 
 // Evaluate the candidate at position pos (key order) of a group's pending
@@ -771,60 +840,74 @@ __device__ __forceinline__ void next_wave(GroupSmem<G, N>& g, int kind, int t_ru
 // candidate's pulse ends inside the window (its pulse-end sample was
 // integrated substep by substep), else 0 (also for pos past the wave).
 template <int G, int N, bool LEAN>
-__device__ __forceinline__ int eval_candidate(GroupSmem<G, N>& g, const SearchSmem<G, N>& S, const SearchParams& P,
+__device__ __forceinline__ int eval_candidate(GroupSmem<G, N>& g, const SacStage& S, const SearchParams& P,
                                               const float* z, float* qs, int pos) {
-  constexpr int NE = search_eval_threads<G, N>();
+  constexpr int NT = search_threads<G, N>();
+  const unsigned live = __ballot_sync(0xffffffffu, pos < g.nvalid);   // the lanes that walk
   if (pos >= g.nvalid) return 0;
   int pe = 0;
   const SacConst& sc = S.sc;
   const float sum0 = S.st.sum0, c0 = S.st.c0;
   const int c = g.perm[pos];
   static_assert(!LEAN || N == N, "register-lean walk: 18 coordinates only");
-  if (g.kind == 0) {
-    const int gi = c / verts<N>(), v = c - gi * verts<N>();
-    if constexpr (LEAN) {
-      const ULinSrc src{g.U[gi][v], g.U[gi][v], false, S.pc, P.lnlo, P.lnhi};
-      g.F[gi][v] = objective_lean(src, sc, z, sum0, c0, &pe);
-    } else {
-      float u[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) u[j] = g.U[gi][v][j];
-      g.F[gi][v] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE, &pe);
-    }
-    return pe;
-  }
-  const int gi = c / trials<N>(), q = c - gi * trials<N>();
+  // both kinds of wave through one walk: a vertex is the row pair (v, v), for
+  // which a + (a - a) / 2 = a exactly
   const float* a;
   const float* bb;
-  trial_rows(g, gi, q, a, bb);
+  float* out;
+  if (g.kind == 0) {
+    const int gi = c / verts<N>(), v = c - gi * verts<N>();
+    a = bb = g.U[gi][v];
+    out = &g.F[gi][v];
+  } else {
+    const int gi = c / trials<N>(), q = c - gi * trials<N>();
+    trial_rows(g, gi, q, a, bb);
+    out = &g.FT[gi][q];
+  }
   if constexpr (LEAN) {
     const ULinSrc src{a, bb, true, S.pc, P.lnlo, P.lnhi};
-    g.FT[gi][q] = objective_lean(src, sc, z, sum0, c0, &pe);
+    *out = objective_lean(src, sc, z, sum0, c0, &pe);
   } else {
     float u[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) u[j] = shrink_coord(a[j], bb[j]);
-    g.FT[gi][q] = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NE, &pe);
+    *out = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NT, &pe, live);
   }
   return pe;
 }
 
-template <int G, int N, int MINB, bool LEAN>
+// Group of a unit's simplex sg and its index in that group: group h holds the
+// unit's simplices [group_start(h), group_start(h + 1)).
+template <int G, int NG>
+__device__ __forceinline__ int group_start(int h, int nunit, bool balanced) {
+  return balanced ? (nunit * h) / NG : min(nunit, h * G);
+}
+template <int G, int NG>
+__device__ __forceinline__ int group_of(int sg, int nunit, bool balanced, int& gi) {
+  int h = 0;
+#pragma unroll
+  for (int t = 1; t < NG; ++t)
+    if (sg >= group_start<G, NG>(t, nunit, balanced)) h = t;
+  gi = sg - group_start<G, NG>(h, nunit, balanced);
+  return h;
+}
+
+template <int G, int N, int NG, int MINB, bool LEAN>
 __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchParams P) {
   constexpr int NT = search_threads<G, N>();
-  constexpr int NE = search_eval_threads<G, N>();
+  static_assert(NG >= 2 && NG <= kSearchWarps, "one warp sets up each group's first wave");
   extern __shared__ __align__(128) unsigned char smraw[];
-  SearchSmem<G, N>& S = *reinterpret_cast<SearchSmem<G, N>*>(smraw);
-  float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G, N>) + 127) / 128) * 128);
+  SearchSmem<G, N, NG>& S = *reinterpret_cast<SearchSmem<G, N, NG>*>(smraw);
+  float* yraw = reinterpret_cast<float*>(smraw + ((sizeof(SearchSmem<G, N, NG>) + 127) / 128) * 128);
   float* z = yraw + P.lcap;
   float* qslot = z + P.lcap;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const bool ctrl = tid >= NE;   // the controller warp
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
     mbar_init(&S.bar, 1);
     fence_mbar_init();
     S.cur_b = -1;
+    S.abort = 0;
   }
   __syncthreads();
   uint32_t phase = 0;
@@ -838,50 +921,52 @@ __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchP
     const int b = un.x, g0 = un.y;
     if (b != S.cur_b) {
       const DevSac d = P.sacs[b];
-      if (!stage_trace(d, P.traces, yraw, z, &S.bar, phase, &S.st)) {
+      if (!stage_trace(d, P.traces, yraw, z, &S.bar, phase, &S.sv.st)) {
         if (tid == 0) raise_error(P.err, kErrWaitTimeout);
         return;
       }
-      if (tid < kNumParams) S.pc[tid] = P.pc[(size_t)b * kNumParams + tid];
+      if (tid < kNumParams) S.sv.pc[tid] = P.pc[(size_t)b * kNumParams + tid];
       if (tid == 0) {
-        S.sc = sac_const(d);
+        S.sv.sc = sac_const(d);
         S.cur_b = b;
       }
       __syncthreads();
     }
-    // this unit's simplices: units of 2 G (the last takes the rest), or, with
+    // this unit's simplices: units of NG G (the last takes the rest), or, with
     // P.balanced, the saccade's S simplices split evenly over its P.ngroups
-    // units; group 0 holds the unit's first nA
-    int s0, nunit, nA;
-    if (P.balanced) {
+    // units; within the unit, groups of G in order, or an even split
+    int s0, nunit;
+    const bool bal = P.balanced != 0;
+    if (bal) {
       s0 = (int)(((long long)g0 * P.S) / P.ngroups);
-      nunit = (int)(((long long)(g0 + 1) * P.S) / P.ngroups) - s0;   // <= 2 G
-      nA = (nunit + 1) / 2;
+      nunit = (int)(((long long)(g0 + 1) * P.S) / P.ngroups) - s0;   // <= NG G
     } else {
-      s0 = g0 * 2 * G;
-      nunit = min(2 * G, P.S - s0);
-      nA = min(G, nunit);
+      s0 = g0 * NG * G;
+      nunit = min(NG * G, P.S - s0);
     }
     // resumable mode (serving): iterations already done by this saccade and
     // this launch's share; the simplex state lives in HBM between launches
     const int it0 = P.state ? P.progress[b] : 0;
     const int t_run = P.state ? min(P.round_iters, P.T - it0) : P.T;
-    if (tid < 2) {
+    if (tid < NG) {
       GroupSmem<G, N>& g = S.grp[tid];
-      g.nsim = tid == 0 ? nA : nunit - nA;
+      g.nsim = group_start<G, NG>(tid + 1, nunit, bal) - group_start<G, NG>(tid, nunit, bal);
       g.it = 0;
       g.evals = 0;
       g.pe = 0;
       g.nvalid = 0;
       g.state = g.nsim > 0 ? kPending : kDone;
+      g.pub = 0;
+      g.claim = 0;
+      g.done = 0;
     }
     if (it0 > 0) {
       // restore the simplices: vertices, values, centroid, order, flags
       const float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * state_floats<N>();
       for (int idx = tid; idx < nunit * state_floats<N>(); idx += NT) {
         const int sg = idx / state_floats<N>(), r = idx - sg * state_floats<N>();
-        GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
-        const int gi = sg < nA ? sg : sg - nA;
+        int gi;
+        GroupSmem<G, N>& g = S.grp[group_of<G, NG>(sg, nunit, bal, gi)];
         const float v = gstate[idx];
         if (r < verts<N>() * N) (&g.U[gi][0][0])[r] = v;
         else if (r < verts<N>() * N + verts<N>()) g.F[gi][r - verts<N>() * N] = v;
@@ -895,8 +980,8 @@ __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchP
       constexpr int kBlk = (N + 3) / 4;   // Philox blocks of 4 coordinates
       for (int t5 = tid; t5 < kBlk * nunit; t5 += NT) {
         const int sg = t5 / kBlk, blk = t5 - sg * kBlk;
-        GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
-        const int gi = sg < nA ? sg : sg - nA;
+        int gi;
+        GroupSmem<G, N>& g = S.grp[group_of<G, NG>(sg, nunit, bal, gi)];
         const int s = s0 + sg;
         uint32_t r[4] = {0u, 0u, 0u, 0u};
         if (s != 0) philox4x32_10((uint32_t)P.sac_index[b], (uint32_t)s, (uint32_t)blk, 0u, P.seed_lo, P.seed_hi, r);
@@ -910,8 +995,8 @@ __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchP
       __syncthreads();
       for (int idx = tid; idx < nunit * N * N; idx += NT) {
         const int sg = idx / (N * N);
-        GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
-        const int gi = sg < nA ? sg : sg - nA;
+        int gi;
+        GroupSmem<G, N>& g = S.grp[group_of<G, NG>(sg, nunit, bal, gi)];
         const int rem = idx - sg * N * N;
         const int v = rem / N + 1, j = rem - (v - 1) * N;
         float x = g.U[gi][0][j];
@@ -920,73 +1005,93 @@ __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchP
       }
     }
     __syncthreads();
-    // the controller sets up both groups' first waves
-    if (ctrl) {
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        GroupSmem<G, N>& g = S.grp[h];
-        if (g.nsim == 0) continue;
+    // warp h < NG sets up, orders and publishes group h's first wave
+    if (warp < NG) {
+      GroupSmem<G, N>& g = S.grp[warp];
+      if (g.nsim > 0) {
         if (it0 == 0 && lane == 0) g.evals = verts<N>() * g.nsim;
         __syncwarp();
         next_wave<G, N>(g, it0 > 0 ? 1 : 0, t_run, lane);
+        if (g.state == kPending) order_wave<G, N>(g, S.sv, P, lane);
+        publish_wave<G, N>(g, lane);
       }
     }
     __syncthreads();
 
-    // ---- steps: the evaluation warps order and evaluate group cur's pending
-    // wave while the controller decides group 1 - cur (evaluated in the
-    // previous step) and sets up its next wave.  Only the controller writes group states, so
-    // one block barrier per step suffices; the finished flag alternates
-    // between two words so that a late reader never sees the next step's.
-    int cur = 0;
-    bool decide_next = false;   // controller: the group evaluated this step is decided in the next
+    // ---- steps, with no block barrier: each warp claims 32-candidate chunks
+    // of any group's published wave (the group it worked on last first, then
+    // the following ones in turn), evaluates them and counts them done; the
+    // warp that completes a wave takes that group's decisions and publishes
+    // its next wave while the other warps work on the other groups' waves.
+    // All warps start on group 0, so the groups' waves complete one after
+    // another and each group's decisions overlap the evaluation of the
+    // others'.  Every decision to leave the loop is taken on lane 0 and
+    // broadcast; a warp that finds nothing to claim waits, for at most
+    // kMaxIdleCycles, until a wave is published or every group is done.
+    int pref = 0;
+    long long idle_since = -1;
 #pragma unroll 1
-    for (int k = 0;; ++k) {
-      GroupSmem<G, N>& ge = S.grp[cur];
-      GroupSmem<G, N>& gd = S.grp[cur ^ 1];
-      if (!ctrl) {
-        if (ge.state == kPending) {
-          order_wave<G, N>(ge, S, P, tid);
-          // pull chunks of 32 candidates in key order until the wave is taken
-          int npe = 0;
+    for (;;) {
+      int gsel = -1, ch = -1, nch = 0;
 #pragma unroll 1
-          for (;;) {
-            int ch = 0;
-            if (lane == 0) ch = atomicAdd(&ge.chunk, 1);
-            ch = __shfl_sync(0xffffffffu, ch, 0);
-            if (ch * 32 >= ge.nvalid) break;
-            npe += __popc(__ballot_sync(0xffffffffu,
-                                        eval_candidate<G, N, LEAN>(ge, S, P, z, qslot + tid, ch * 32 + lane)));
-          }
-          if (lane == 0 && npe) atomicAdd(&ge.pe, npe);
-        }
-      } else {
-        const bool ge_evaluated = ge.state == kPending;
-        if (decide_next) {
-          if (gd.kind == 0) {
-            init_rank<G, N>(gd, lane, P.tolx, P.tolf);
-          } else {
-            decide_group<G, N>(gd, lane, P.tolx, P.tolf);
-            if (lane == 0) gd.it += 1;
-            __syncwarp();
-          }
-          next_wave<G, N>(gd, 1, t_run, lane);
-        }
-        if (lane == 0) S.finished[k & 1] = (!ge_evaluated && gd.state == kDone) ? 1 : 0;
-        decide_next = ge_evaluated;
+      for (int t = 0; t < NG && ch < 0; ++t) {
+        const int h = pref + t < NG ? pref + t : pref + t - NG;
+        ch = try_claim<G, N>(S.grp[h], lane, nch);
+        if (ch >= 0) gsel = h;
       }
-      __syncthreads();
-      if (S.finished[k & 1]) break;
-      cur ^= 1;
+      if (ch >= 0) {
+        __syncwarp();   // orders lane 0's acquire of the wave before every lane's reads
+        GroupSmem<G, N>& g = S.grp[gsel];
+        const int npe = __popc(__ballot_sync(0xffffffffu,
+                                             eval_candidate<G, N, LEAN>(g, S.sv, P, z, qslot + tid, ch * 32 + lane)));
+        __syncwarp();
+        __threadfence_block();   // the chunk's values before its done count
+        if (lane == 0 && npe) atomicAdd(&g.pe, npe);
+        int done_before = 0;
+        if (lane == 0) done_before = atomicAdd(&g.done, 1);
+        done_before = __shfl_sync(0xffffffffu, done_before, 0);
+        const bool last = done_before == nch - 1;
+        if (last) __threadfence_block();
+        __syncwarp();
+        if (last) {
+          advance_group<G, N>(g, S.sv, P, lane, t_run);
+          pref = gsel + 1 < NG ? gsel + 1 : 0;
+        } else {
+          pref = gsel;
+        }
+        idle_since = -1;
+        continue;
+      }
+      // nothing to claim: 1 = every group done or the block aborts, 2 = waited
+      // too long; lane 0's view of the words and the clock decides for the warp
+      int fin = 0;
+      {
+        const long long now = clock64();
+        if (idle_since < 0) idle_since = now;
+        bool all_done = true;
+#pragma unroll
+        for (int h = 0; h < NG; ++h) all_done = all_done && vload(S.grp[h].state) == kDone;
+        fin = (vload(S.abort) || all_done) ? 1 : (now - idle_since > kMaxIdleCycles ? 2 : 0);
+      }
+      fin = __shfl_sync(0xffffffffu, fin, 0);
+      if (fin == 2) {
+        if (lane == 0) raise_error(P.err, kErrWaitTimeout);
+        if (lane == 0) atomicExch(&S.abort, 1);
+        break;
+      }
+      if (fin) break;
+      __nanosleep(128);
     }
+    __syncthreads();
+    if (S.abort) return;
 
     if (P.state) {
       // save the simplices for the next launch
       float* gstate = P.state + ((size_t)b * P.S + (size_t)s0) * state_floats<N>();
       for (int idx = tid; idx < nunit * state_floats<N>(); idx += NT) {
         const int sg = idx / state_floats<N>(), r = idx - sg * state_floats<N>();
-        const GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
-        const int gi = sg < nA ? sg : sg - nA;
+        int gi;
+        const GroupSmem<G, N>& g = S.grp[group_of<G, NG>(sg, nunit, bal, gi)];
         float v;
         if (r < verts<N>() * N) v = (&g.U[gi][0][0])[r];
         else if (r < verts<N>() * N + verts<N>()) v = g.F[gi][r - verts<N>() * N];
@@ -1005,8 +1110,8 @@ __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchP
       float f = INFINITY;
       int best = 0x7fffffff;
       for (int sg = lane; sg < nunit; sg += 32) {
-        const GroupSmem<G, N>& g = S.grp[sg < nA ? 0 : 1];
-        const int gi = sg < nA ? sg : sg - nA;
+        int gi;
+        const GroupSmem<G, N>& g = S.grp[group_of<G, NG>(sg, nunit, bal, gi)];
         const float fv = g.F[gi][g.ord[gi][0]];
         if (fv < f || (fv == f && sg < best)) { f = fv; best = sg; }
       }
@@ -1018,17 +1123,22 @@ __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchP
       }
       const int evals_prev = it0 > 0 ? __float_as_int(rec[3]) : 0;
       const int pe_prev = it0 > 0 ? __float_as_int(rec[22]) : 0;
+      int evals = 0, pes = 0;
+      for (int h = 0; h < NG; ++h) {
+        evals += S.grp[h].evals;
+        pes += S.grp[h].pe;
+      }
       __syncwarp();
       if (best < nunit) {
-        const GroupSmem<G, N>& g = S.grp[best < nA ? 0 : 1];
-        const int gi = best < nA ? best : best - nA;
+        int gi;
+        const GroupSmem<G, N>& g = S.grp[group_of<G, NG>(best, nunit, bal, gi)];
         if (lane < N) rec[4 + lane] = g.U[gi][g.ord[gi][0]][lane];
         if (lane == 0) {
           rec[0] = f;
           rec[1] = __int_as_float(s0 + best);
           rec[2] = __int_as_float(g.iters[gi]);
-          rec[3] = __int_as_float(evals_prev + S.grp[0].evals + S.grp[1].evals);
-          rec[22] = __int_as_float(pe_prev + S.grp[0].pe + S.grp[1].pe);
+          rec[3] = __int_as_float(evals_prev + evals);
+          rec[22] = __int_as_float(pe_prev + pes);
         }
       }
     }
@@ -1746,83 +1856,90 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
   return cudaGetLastError();
 }
 
-// Launch-shape variants of the search kernel: simplices per group G (a block
-// runs a unit of 2 G simplices), the search coordinates N (18, or 9 for the
-// 9-parameter model), the minimum resident blocks per SM the register
-// allocation is bounded for, and the register-lean walk.  The host sees the
-// unit size (simplices per block) and N.
-struct SearchVariantDesc { int G, N, minb, lean; };
+// Launch-shape variants of the search kernel: simplices per group G, groups
+// per block NG (a block runs a unit of NG G simplices), the search
+// coordinates N (18, or 9 for the 9-parameter model), the minimum resident
+// blocks per SM the register allocation is bounded for, and the
+// register-lean walk.  The host sees the unit size (simplices per block) and
+// N.  More groups per block keep more waves open, so that the warps always
+// find chunks to claim while a group's decisions are taken.
+struct SearchVariantDesc { int G, N, NG, minb, lean; };
 static const SearchVariantDesc kVariants[] = {
-    {16, 18, 1, 0}, {16, 18, 1, 1}, {8, 18, 1, 0}, {32, 18, 1, 0}, {27, 9, 1, 0}};
+    {16, 18, 2, 1, 0}, {16, 18, 2, 1, 1}, {8, 18, 2, 1, 0}, {32, 18, 2, 1, 0}, {27, 9, 2, 1, 0},
+    {16, 18, 4, 1, 0}, {8, 18, 4, 1, 0},  {27, 9, 4, 1, 0}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 static bool variant_ok(int v) { return v >= 0 && v < kNumVariants; }
 int search_variant_count() { return kNumVariants; }
-int search_variant_g(int v) { return variant_ok(v) ? 2 * kVariants[v].G : 0; }
+int search_variant_g(int v) { return variant_ok(v) ? kVariants[v].NG * kVariants[v].G : 0; }
 int search_variant_dim(int v) { return variant_ok(v) ? kVariants[v].N : 0; }
 int search_variant_minb(int v) { return variant_ok(v) ? kVariants[v].minb : 0; }
 int search_variant_lean(int v) { return variant_ok(v) ? kVariants[v].lean : 0; }
 int search_variant_for(int unit, int dim) {
   for (int v = 0; v < kNumVariants; ++v)
-    if (2 * kVariants[v].G == unit && kVariants[v].N == dim) return v;
+    if (kVariants[v].NG * kVariants[v].G == unit && kVariants[v].N == dim) return v;
   return -1;
 }
 
-template <int G, int N, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN>
 static cudaError_t occ_v(int lcap, int* bps) {
-  const size_t smem = search_smem_bytes<G, N>(lcap);
-  cudaError_t e = allow_dynamic_smem(k_search<G, N, MINB, LEAN>, smem);
+  const size_t smem = search_smem_bytes<G, N, NG>(lcap);
+  cudaError_t e = allow_dynamic_smem(k_search<G, N, NG, MINB, LEAN>, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, N, MINB, LEAN>, search_threads<G, N>(), smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, N, NG, MINB, LEAN>, search_threads<G, N>(),
+                                                       smem);
 }
 
 // The dynamic shared-memory attribute is raised to its maximum by
 // search_occupancy_v(), which the host calls for the same variant before any
 // launch or graph capture.
-template <int G, int N, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN>
 static cudaError_t launch_v(const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
-  const size_t smem = search_smem_bytes<G, N>(P.lcap);
-  k_search<G, N, MINB, LEAN><<<blocks_per_sm * num_sms, search_threads<G, N>(), smem, st>>>(P);
+  const size_t smem = search_smem_bytes<G, N, NG>(P.lcap);
+  k_search<G, N, NG, MINB, LEAN><<<blocks_per_sm * num_sms, search_threads<G, N>(), smem, st>>>(P);
   return cudaGetLastError();
 }
 
-template <int G, int N, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN>
 static int threads_v() { return search_threads<G, N>(); }
 
-template <int G, int N, int MINB, bool LEAN>
-static size_t smem_v(int lcap) { return search_smem_bytes<G, N>(lcap); }
+template <int G, int N, int NG, int MINB, bool LEAN>
+static size_t smem_v(int lcap) { return search_smem_bytes<G, N, NG>(lcap); }
 
-#define OPMM_VARIANT_SWITCH(v, CALL, BAD)   \
-  switch (v) {                              \
-    case 0: return CALL(16, 18, 1, false);  \
-    case 1: return CALL(16, 18, 1, true);   \
-    case 2: return CALL(8, 18, 1, false);   \
-    case 3: return CALL(32, 18, 1, false);  \
-    case 4: return CALL(27, 9, 1, false);   \
-    default: return BAD;                    \
+#define OPMM_VARIANT_SWITCH(v, CALL, BAD)      \
+  switch (v) {                                 \
+    case 0: return CALL(16, 18, 2, 1, false);  \
+    case 1: return CALL(16, 18, 2, 1, true);   \
+    case 2: return CALL(8, 18, 2, 1, false);   \
+    case 3: return CALL(32, 18, 2, 1, false);  \
+    case 4: return CALL(27, 9, 2, 1, false);   \
+    case 5: return CALL(16, 18, 4, 1, false);  \
+    case 6: return CALL(8, 18, 4, 1, false);   \
+    case 7: return CALL(27, 9, 4, 1, false);   \
+    default: return BAD;                       \
   }
 
 cudaError_t search_occupancy_v(int v, int lcap, int* blocks_per_sm) {
-#define OCC_CALL(G, N, M, L) occ_v<G, N, M, L>(lcap, blocks_per_sm)
+#define OCC_CALL(G, N, NG, M, L) occ_v<G, N, NG, M, L>(lcap, blocks_per_sm)
   OPMM_VARIANT_SWITCH(v, OCC_CALL, cudaErrorInvalidValue)
 #undef OCC_CALL
 }
 
 cudaError_t launch_search_v(int v, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
-#define LAUNCH_CALL(G, N, M, L) launch_v<G, N, M, L>(P, blocks_per_sm, num_sms, st)
+#define LAUNCH_CALL(G, N, NG, M, L) launch_v<G, N, NG, M, L>(P, blocks_per_sm, num_sms, st)
   OPMM_VARIANT_SWITCH(v, LAUNCH_CALL, cudaErrorInvalidValue)
 #undef LAUNCH_CALL
 }
 
 // Threads and dynamic shared memory of a block of variant v.
 int search_variant_threads(int v) {
-#define THREADS_CALL(G, N, M, L) threads_v<G, N, M, L>()
+#define THREADS_CALL(G, N, NG, M, L) threads_v<G, N, NG, M, L>()
   OPMM_VARIANT_SWITCH(v, THREADS_CALL, 0)
 #undef THREADS_CALL
 }
 
 size_t search_variant_smem(int v, int lcap) {
-#define SMEM_CALL(G, N, M, L) smem_v<G, N, M, L>(lcap)
+#define SMEM_CALL(G, N, NG, M, L) smem_v<G, N, NG, M, L>(lcap)
   OPMM_VARIANT_SWITCH(v, SMEM_CALL, (size_t)0)
 #undef SMEM_CALL
 }

@@ -595,6 +595,14 @@ __device__ __forceinline__ void prop_load(Prop2& q, const float* qs, int stride)
   for (int i = 0; i < (int)(sizeof(Prop2) / sizeof(float)); ++i) f[i] = qs[i * stride];
 }
 
+// Bring the lanes of `mask` together before a loop whose trip count n varies
+// by lane: a warp-wide maximum of n, which every lane of the mask must take
+// part in (kept alive by an empty asm so that it is not removed).
+__device__ __forceinline__ void converge_on(unsigned mask, int n) {
+  const unsigned m = __reduce_max_sync(mask, (unsigned)n);
+  asm volatile("" ::"r"(m));
+}
+
 // Walk one candidate's trajectory from the first sample after onset to the
 // end of the window.  The sink receives, for each sample k > onset, the value
 // dth = theta_k - thf (positive frame), and block_end() after blocks of
@@ -605,12 +613,20 @@ __device__ __forceinline__ void prop_load(Prop2& q, const float* qs, int stride)
 // propagator from the set-up to the pulse-end interval instead of rebuilding it.
 // pulse_end (optional): set to 1 when the pulse ends inside the window (the
 // pulse-end sample was integrated substep by substep), else 0.
-template <class Sink>
+// SYNC: the lanes in `mask` (all of which call walk together) reconverge
+// before each phase's sample loop, by a warp reduction over the loop's trip
+// count, so that a warp runs each sample loop once for all of its lanes
+// instead of once per group of lanes that reached it together (a plain
+// __syncwarp did not keep them together); lanes that return early leave the
+// mask first.
+template <class Sink, bool SYNC = false>
 __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& sink, float* qs = nullptr,
-                                    int qstride = 0, bool guard = false, int* pulse_end = nullptr) {
+                                    int qstride = 0, bool guard = false, int* pulse_end = nullptr,
+                                    unsigned mask = 0xffffffffu) {
   Coef k;
   make_coef(p, k);
   const int rs = refine_shift(k, sc0.h);
+  if (SYNC) mask = __ballot_sync(mask, !(guard && rs < 0));
   if (guard && rs < 0) return -1;
   const int sh = rs < 0 ? kMaxRefine : rs;
   const int nsub = sc0.nsub << sh;            // substeps per sample, refined
@@ -652,8 +668,10 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
     prop_pow(q, nsub, phi);
   }
   int kk = sc.onset + 1;
+  if (SYNC) converge_on(mask, n1);
   run_samples<1>(phi, e, off1, kk, n1, sink);
   if (pulse_end) *pulse_end = sw ? 1 : 0;
+  if (SYNC) mask = __ballot_sync(mask, sw);
   if (sw) {
     // pulse-end interval: jsw whole substeps of the pulse phase, the split
     // substep (two RK4 steps around the switch), the rest of the step phase
@@ -669,6 +687,7 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
     for (int s = jsw + 1; s < nsub; ++s) prop_apply<2>(q, e);
     sink.emit(kk++, e[0]);
     const int n2 = ntot - n1 - 1;
+    if (SYNC) converge_on(mask, n2);
     run_samples<2>(phi, e, 0.0f, kk, n2, sink);
   }
   return ntot;
