@@ -509,10 +509,13 @@ __device__ __forceinline__ void centroids(GroupSmem<G, N>& g, int lane, float to
 }
 
 // Stable ranking of 19 values by one thread: rank[r] = #{s : v_s < v_r or
-// (v_s == v_r and s < r)}; the slots are written to ord in rank order.
+// (v_s == v_r and s < r)}; the slots are written to ord in rank order.  The
+// outer loop is kept rolled: this runs on the decision path, and its fully
+// unrolled form (19 x 19 compares) crowds the instruction cache that the
+// evaluating warps share.
 template <int G, int N>
 __device__ __forceinline__ void rank_simplex(GroupSmem<G, N>& g, int gi, const int (&sl)[verts<N>()], const float (&fv)[verts<N>()]) {
-#pragma unroll
+#pragma unroll 1
   for (int r = 0; r < verts<N>(); ++r) {
     int rank = 0;
 #pragma unroll
@@ -666,9 +669,10 @@ __device__ __forceinline__ void decide_group(GroupSmem<G, N>& g, int lane, float
 // points are formed by the evaluating threads from the vertices.
 template <int G, int N>
 __device__ __forceinline__ void next_wave(GroupSmem<G, N>& g, int kind, int t_run, int lane) {
+  static_assert(G <= 32, "one lane per simplex counts the active ones");
   int nact = 0;
   if (kind == 1) {
-    for (int gi = 0; gi < g.nsim; ++gi) nact += g.active[gi];
+    nact = (int)__reduce_add_sync(0xffffffffu, lane < g.nsim ? (unsigned)g.active[lane] : 0u);
     if (g.it >= t_run || nact == 0) {
       if (lane == 0) g.state = kDone;
       if (lane == 0) g.nvalid = 0;
@@ -678,10 +682,14 @@ __device__ __forceinline__ void next_wave(GroupSmem<G, N>& g, int kind, int t_ru
   }
   for (int i = lane; i < kHistLen; i += 32) g.hist[i] = 0;
   if (kind == 1) {
-    for (int e = lane; e < g.nsim * 4 * N; e += 32) {
-      const int gi = e / (4 * N), r = e - gi * 4 * N;
-      const int q = r / N, j = r - q * N;
-      if (g.active[gi]) g.XT[gi][q][j] = trial_coord(q, g.XB[gi][j], g.U[gi][g.ord[gi][N]][j]);
+#pragma unroll 2
+    for (int e = lane; e < g.nsim * N; e += 32) {
+      const int gi = e / N, j = e - gi * N;
+      if (g.active[gi]) {
+        const float xb = g.XB[gi][j], w = g.U[gi][g.ord[gi][N]][j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g.XT[gi][q][j] = trial_coord(q, xb, w);
+      }
     }
   }
   if (lane == 0) g.kind = kind;
@@ -701,7 +709,7 @@ __device__ __forceinline__ void order_wave(GroupSmem<G, N>& g, const SacStage& V
   static_assert(G * trials<N>() < (1 << 16), "bin rank in 16 bits");
   constexpr int kPwCoord = search_coord<N>(kPw);   // -1: pulse width held at the centre
   const int ncand = (g.kind == 0 ? verts<N>() : trials<N>()) * g.nsim;
-#pragma unroll 1
+#pragma unroll 4
   for (int r = 0; r < R; ++r) {
     const int c = lane + 32 * r;
     int key = -1;
@@ -753,7 +761,7 @@ __device__ __forceinline__ void order_wave(GroupSmem<G, N>& g, const SacStage& V
     if (lane == 31) g.nvalid = incl;
   }
   __syncwarp();
-#pragma unroll 1
+#pragma unroll 4
   for (int c = lane; c < ncand; c += 32) {
     const int kr = g.kr[c];
     if (kr >= 0) g.perm[g.hist[hist_slot(kr >> 16)] + (kr & 0xffff)] = (unsigned short)c;
@@ -1866,7 +1874,7 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
 struct SearchVariantDesc { int G, N, NG, minb, lean; };
 static const SearchVariantDesc kVariants[] = {
     {16, 18, 2, 1, 0}, {16, 18, 2, 1, 1}, {8, 18, 2, 1, 0}, {32, 18, 2, 1, 0}, {27, 9, 2, 1, 0},
-    {16, 18, 4, 1, 0}, {8, 18, 4, 1, 0},  {27, 9, 4, 1, 0}};
+    {16, 18, 4, 1, 0}, {8, 18, 4, 1, 0},  {27, 9, 4, 1, 0}, {24, 18, 3, 1, 0}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 static bool variant_ok(int v) { return v >= 0 && v < kNumVariants; }
@@ -1916,6 +1924,7 @@ static size_t smem_v(int lcap) { return search_smem_bytes<G, N, NG>(lcap); }
     case 5: return CALL(16, 18, 4, 1, false);  \
     case 6: return CALL(8, 18, 4, 1, false);   \
     case 7: return CALL(27, 9, 4, 1, false);   \
+    case 8: return CALL(24, 18, 3, 1, false);  \
     default: return BAD;                       \
   }
 
