@@ -158,6 +158,15 @@ int opmm_search_variants(int32_t* count);
  * applies to fits of that model only).  Either output may be NULL.
  * OPMM_EINVAL for a variant out of range. */
 int opmm_search_variant_info(int32_t variant, int32_t* simplices_per_block, int32_t* model);
+/* How search variant `variant` integrates a candidate (the autotuner's
+ * integrator axis): OPMM_WALK_SCALAR (one FMA per matrix element of the
+ * one-sample update), OPMM_WALK_PACKED (the same update with two rows per
+ * packed FP32 FMA instruction: identical arithmetic, fewer instructions) or
+ * OPMM_WALK_LEAN (one phase's propagator live at a time, parameters
+ * re-derived when needed).  OPMM_EINVAL for a variant out of range or a NULL
+ * output. */
+enum { OPMM_WALK_SCALAR = 0, OPMM_WALK_PACKED = 1, OPMM_WALK_LEAN = 2 };
+int opmm_search_variant_walk(int32_t variant, int32_t* walk);
 
 /* ------------------------------------------------------------ plant */
 
@@ -214,6 +223,9 @@ int opmm_plan_execute(opmm_plan* plan, opmm_fit_result* out);
  * blocks per SM; and the number of kernels one execute launches. */
 int opmm_plan_info(const opmm_plan* plan, int32_t* simplices_per_block, int32_t* threads,
                    int32_t* blocks_per_sm, int32_t* kernels_per_execute);
+/* The search variant the plan runs (see opmm_search_variant_info and
+ * opmm_search_variant_walk). */
+int opmm_plan_variant(const opmm_plan* plan, int32_t* variant);
 /* The autotuner's probes for this plan: for each launch-shape variant tried,
  * its id, simplices per block, register bound (minimum resident blocks), the
  * blocks per SM launched, and the probe's device time in ms (iteration cap 2).

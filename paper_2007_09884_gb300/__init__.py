@@ -33,15 +33,17 @@ OPMM_SOURCE_REFINED = 3
 OPMM_PULSE_TABLE1 = 0
 OPMM_SOURCE_PLAIN, OPMM_SOURCE_SEEDED, OPMM_SOURCE_FALLBACK = 0, 1, 2
 OPMM_PULSE_CALIBRATED = 1
+OPMM_WALK_SCALAR, OPMM_WALK_PACKED, OPMM_WALK_LEAN = 0, 1, 2
+WALK_NAMES = {OPMM_WALK_SCALAR: "scalar", OPMM_WALK_PACKED: "packed", OPMM_WALK_LEAN: "lean"}
 
 PARAM_NAMES = ["SE_ag", "SE_ant", "LT_ag", "LT_ant", "PE_ag", "PE_ant", "Vis", "FV_ag", "FV_ant",
                "Inert", "Act_ag", "Act_ant", "Deact_ag", "Deact_ant", "Step", "H_ag", "H_ant", "W"]
 
 # Every symbol include/opmm.h declares.
 EXPORTS = ["opmm_create", "opmm_destroy", "opmm_last_error", "opmm_set_stream", "opmm_set_search_variant",
-           "opmm_search_variants", "opmm_simulate",
+           "opmm_search_variants", "opmm_search_variant_walk", "opmm_simulate",
            "opmm_score", "opmm_nominal_opc", "opmm_fit_batch", "opmm_plan_create",
-           "opmm_plan_execute", "opmm_plan_info", "opmm_plan_tuning", "opmm_plan_last_search_ms",
+           "opmm_plan_execute", "opmm_plan_info", "opmm_plan_variant", "opmm_plan_tuning", "opmm_plan_last_search_ms",
            "opmm_plan_destroy",
            "opmm_fit_saccade_static", "opmm_surrogate_init", "opmm_surrogate_num_params",
            "opmm_surrogate_get_params", "opmm_surrogate_set_params", "opmm_surrogate_grad", "opmm_surrogate_apply_grad",
@@ -115,6 +117,7 @@ def load_library(path: str = LIB_PATH):
     lib.opmm_set_search_variant.argtypes = [vp, i32]
     lib.opmm_search_variants.argtypes = [ctypes.POINTER(i32)]
     lib.opmm_search_variant_info.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.opmm_search_variant_walk.argtypes = [i32, ctypes.POINTER(i32)]
     lib.opmm_simulate.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), i32, vp, i64p, vp]
     lib.opmm_score.argtypes = [vp, vp, i32, ctypes.POINTER(opmm_saccade), vp]
     lib.opmm_nominal_opc.argtypes = [vp, ctypes.POINTER(opmm_saccade), i32, i32, vp]
@@ -131,6 +134,7 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(opmm_fit_opts), ctypes.POINTER(vp)]
     lib.opmm_plan_execute.argtypes = [vp, ctypes.POINTER(opmm_fit_result)]
     lib.opmm_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
+    lib.opmm_plan_variant.argtypes = [vp, ctypes.POINTER(i32)]
     lib.opmm_plan_last_search_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.opmm_plan_tuning.argtypes = [vp] + [vp] * 5 + [i32, ctypes.POINTER(i32)]
     lib.opmm_plan_destroy.argtypes = [vp]
@@ -321,6 +325,15 @@ def opmm_search_variant_info(variant: int):
     return int(g.value), int(m.value)
 
 
+def opmm_search_variant_walk(variant: int) -> int:
+    """How a search variant integrates a candidate (OPMM_WALK_*)."""
+    w = ctypes.c_int32()
+    rc = load_library().opmm_search_variant_walk(int(variant), ctypes.byref(w))
+    if rc != OPMM_OK:
+        raise OpmmError(rc, "search variant out of range")
+    return int(w.value)
+
+
 def opmm_simulate(ctx, opc, batch: SaccadeBatch, sac_index=None, out=None):
     """Trajectories [n][L_i] packed; returns (out, offsets)."""
     lib = load_library()
@@ -492,7 +505,10 @@ class Plan:
     def info(self) -> dict:
         v = [ctypes.c_int32() for _ in range(4)]
         _check(self.ctx, self.lib.opmm_plan_info(self.h, *[ctypes.byref(x) for x in v]))
-        return {"simplices_per_block": v[0].value, "threads": v[1].value,
+        var = ctypes.c_int32()
+        _check(self.ctx, self.lib.opmm_plan_variant(self.h, ctypes.byref(var)))
+        return {"variant": var.value, "walk": WALK_NAMES[opmm_search_variant_walk(var.value)],
+                "simplices_per_block": v[0].value, "threads": v[1].value,
                 "blocks_per_sm": v[2].value, "kernels_per_execute": v[3].value}
 
     def tuning(self) -> list:
@@ -504,6 +520,7 @@ class Plan:
                                                    ms.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(cnt)))
         n = min(cnt.value, cap)
         return [{"variant": int(arrs[0][i]), "simplices_per_block": int(arrs[1][i]),
+                 "walk": WALK_NAMES[opmm_search_variant_walk(int(arrs[0][i]))],
                  "min_blocks": int(arrs[2][i]), "blocks_per_sm": int(arrs[3][i]),
                  "probe_ms": float(ms[i])} for i in range(n)]
 

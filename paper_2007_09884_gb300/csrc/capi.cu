@@ -236,6 +236,13 @@ extern "C" int opmm_search_variant_info(int32_t variant, int32_t* simplices_per_
   return OPMM_OK;
 }
 
+extern "C" int opmm_search_variant_walk(int32_t variant, int32_t* walk) {
+  if (variant < 0 || variant >= search_variant_count() || !walk) return OPMM_EINVAL;
+  *walk = search_variant_lean(variant) ? OPMM_WALK_LEAN
+                                       : (search_variant_pack(variant) ? OPMM_WALK_PACKED : OPMM_WALK_SCALAR);
+  return OPMM_OK;
+}
+
 extern "C" int opmm_set_stream(opmm_ctx* ctx, void* stream) {
   if (!ctx) return OPMM_EINVAL;
   ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
@@ -814,6 +821,12 @@ extern "C" int opmm_plan_info(const opmm_plan* plan, int32_t* g, int32_t* thread
   if (threads) *threads = plan->threads;
   if (bps) *bps = plan->blocks_per_sm;
   if (kernels) *kernels = (plan->traces_on_device ? 1 : 0) + (plan->centres_given ? 0 : 1) + plan->pre_search_kernels + 2;
+  return OPMM_OK;
+}
+
+extern "C" int opmm_plan_variant(const opmm_plan* plan, int32_t* variant) {
+  if (!plan || !variant) return OPMM_EINVAL;
+  *variant = plan->variant;
   return OPMM_OK;
 }
 

@@ -87,12 +87,12 @@ struct PeakSink {
 // Objective of one OPC vector: mean squared error over the window; the
 // samples up to onset (the plant at rest) are folded into (sum0, c0).
 // pe (optional): set to 1 when the pulse ends inside the window.
-template <bool SYNC = false>
+template <bool SYNC = false, bool PACK = false>
 __device__ __forceinline__ float objective(const float* p, const SacConst& sc, const float* z,
                                            float sum0, float c0, float* qs = nullptr, int qstride = 0,
                                            int* pe = nullptr, unsigned mask = 0xffffffffu) {
   KahanSink s{z, sum0, c0, 0.0f};
-  if (walk<KahanSink, SYNC>(p, sc, s, qs, qstride, true, pe, mask) < 0) return INFINITY;
+  if (walk<KahanSink, SYNC, PACK>(p, sc, s, qs, qstride, true, pe, mask) < 0) return INFINITY;
   s.block_end();
   const float f = (s.sum - s.c) / (float)sc.L;
   return isfinite(f) ? f : INFINITY;
@@ -448,14 +448,14 @@ __device__ __forceinline__ float objective_lean(const ULinSrc& src, const SacCon
 }
 
 // Objective of search point u; the lanes in `mask` call it together and
-// reconverge inside the walk.
-template <int N>
+// reconverge inside the walk; PACK picks the packed sample update.
+template <int N, bool PACK>
 __device__ __forceinline__ float eval_u(const float (&u)[N], const float* pc, float lnlo,
                                         float lnhi, const SacConst& sc, const float* z, float sum0,
                                         float c0, float* qs, int qstride, int* pe, unsigned mask) {
   float p[kNumParams];
   u_to_p<N>(u, pc, lnlo, lnhi, p);
-  return objective<true>(p, sc, z, sum0, c0, qs, qstride, pe, mask);
+  return objective<true, PACK>(p, sc, z, sum0, c0, qs, qstride, pe, mask);
 }
 
 // Sort key of a candidate: its pulse-end time, binned over the window (the
@@ -847,7 +847,7 @@ __device__ __forceinline__ void advance_group(GroupSmem<G, N>& g, const SacStage
 // wave; qs is the calling thread's propagator slot.  Returns 1 when that
 // candidate's pulse ends inside the window (its pulse-end sample was
 // integrated substep by substep), else 0 (also for pos past the wave).
-template <int G, int N, bool LEAN>
+template <int G, int N, bool LEAN, bool PACK>
 __device__ __forceinline__ int eval_candidate(GroupSmem<G, N>& g, const SacStage& S, const SearchParams& P,
                                               const float* z, float* qs, int pos) {
   constexpr int NT = search_threads<G, N>();
@@ -879,7 +879,7 @@ __device__ __forceinline__ int eval_candidate(GroupSmem<G, N>& g, const SacStage
     float u[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) u[j] = shrink_coord(a[j], bb[j]);
-    *out = eval_u(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NT, &pe, live);
+    *out = eval_u<N, PACK>(u, S.pc, P.lnlo, P.lnhi, sc, z, sum0, c0, qs, NT, &pe, live);
   }
   return pe;
 }
@@ -900,7 +900,7 @@ __device__ __forceinline__ int group_of(int sg, int nunit, bool balanced, int& g
   return h;
 }
 
-template <int G, int N, int NG, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN, bool PACK>
 __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchParams P) {
   constexpr int NT = search_threads<G, N>();
   static_assert(NG >= 2 && NG <= kSearchWarps, "one warp sets up each group's first wave");
@@ -1051,7 +1051,7 @@ __global__ void __launch_bounds__(search_threads<G, N>(), MINB) k_search(SearchP
         __syncwarp();   // orders lane 0's acquire of the wave before every lane's reads
         GroupSmem<G, N>& g = S.grp[gsel];
         const int npe = __popc(__ballot_sync(0xffffffffu,
-                                             eval_candidate<G, N, LEAN>(g, S.sv, P, z, qslot + tid, ch * 32 + lane)));
+                                             eval_candidate<G, N, LEAN, PACK>(g, S.sv, P, z, qslot + tid, ch * 32 + lane)));
         __syncwarp();
         __threadfence_block();   // the chunk's values before its done count
         if (lane == 0 && npe) atomicAdd(&g.pe, npe);
@@ -1867,14 +1867,17 @@ cudaError_t launch_score(const float* opc, int m, const DevSac* sac, int L, cons
 // Launch-shape variants of the search kernel: simplices per group G, groups
 // per block NG (a block runs a unit of NG G simplices), the search
 // coordinates N (18, or 9 for the 9-parameter model), the minimum resident
-// blocks per SM the register allocation is bounded for, and the
-// register-lean walk.  The host sees the unit size (simplices per block) and
-// N.  More groups per block keep more waves open, so that the warps always
-// find chunks to claim while a group's decisions are taken.
-struct SearchVariantDesc { int G, N, NG, minb, lean; };
+// blocks per SM the register allocation is bounded for, and the walk: the
+// register-lean walk, or the packed sample update (two row FMAs per packed
+// FP32 instruction, the same arithmetic), or neither.  The host sees the unit
+// size (simplices per block), N and the walk.  More groups per block keep
+// more waves open, so that the warps always find chunks to claim while a
+// group's decisions are taken.
+struct SearchVariantDesc { int G, N, NG, minb, lean, pack; };
 static const SearchVariantDesc kVariants[] = {
-    {16, 18, 2, 1, 0}, {16, 18, 2, 1, 1}, {8, 18, 2, 1, 0}, {32, 18, 2, 1, 0}, {27, 9, 2, 1, 0},
-    {16, 18, 4, 1, 0}, {8, 18, 4, 1, 0},  {27, 9, 4, 1, 0}, {24, 18, 3, 1, 0}};
+    {16, 18, 2, 1, 0, 0}, {16, 18, 2, 1, 1, 0}, {8, 18, 2, 1, 0, 0}, {32, 18, 2, 1, 0, 0}, {27, 9, 2, 1, 0, 0},
+    {16, 18, 4, 1, 0, 0}, {27, 9, 4, 1, 0, 0},  {24, 18, 3, 1, 0, 0}, {16, 18, 2, 1, 0, 1}, {32, 18, 2, 1, 0, 1},
+    {16, 18, 4, 1, 0, 1}, {24, 18, 3, 1, 0, 1}, {27, 9, 4, 1, 0, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 static bool variant_ok(int v) { return v >= 0 && v < kNumVariants; }
@@ -1883,72 +1886,77 @@ int search_variant_g(int v) { return variant_ok(v) ? kVariants[v].NG * kVariants
 int search_variant_dim(int v) { return variant_ok(v) ? kVariants[v].N : 0; }
 int search_variant_minb(int v) { return variant_ok(v) ? kVariants[v].minb : 0; }
 int search_variant_lean(int v) { return variant_ok(v) ? kVariants[v].lean : 0; }
+int search_variant_pack(int v) { return variant_ok(v) ? kVariants[v].pack : 0; }
 int search_variant_for(int unit, int dim) {
   for (int v = 0; v < kNumVariants; ++v)
     if (kVariants[v].NG * kVariants[v].G == unit && kVariants[v].N == dim) return v;
   return -1;
 }
 
-template <int G, int N, int NG, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN, bool PACK>
 static cudaError_t occ_v(int lcap, int* bps) {
   const size_t smem = search_smem_bytes<G, N, NG>(lcap);
-  cudaError_t e = allow_dynamic_smem(k_search<G, N, NG, MINB, LEAN>, smem);
+  cudaError_t e = allow_dynamic_smem(k_search<G, N, NG, MINB, LEAN, PACK>, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, N, NG, MINB, LEAN>, search_threads<G, N>(),
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_search<G, N, NG, MINB, LEAN, PACK>, search_threads<G, N>(),
                                                        smem);
 }
 
 // The dynamic shared-memory attribute is raised to its maximum by
 // search_occupancy_v(), which the host calls for the same variant before any
 // launch or graph capture.
-template <int G, int N, int NG, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN, bool PACK>
 static cudaError_t launch_v(const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
   const size_t smem = search_smem_bytes<G, N, NG>(P.lcap);
-  k_search<G, N, NG, MINB, LEAN><<<blocks_per_sm * num_sms, search_threads<G, N>(), smem, st>>>(P);
+  k_search<G, N, NG, MINB, LEAN, PACK><<<blocks_per_sm * num_sms, search_threads<G, N>(), smem, st>>>(P);
   return cudaGetLastError();
 }
 
-template <int G, int N, int NG, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN, bool PACK>
 static int threads_v() { return search_threads<G, N>(); }
 
-template <int G, int N, int NG, int MINB, bool LEAN>
+template <int G, int N, int NG, int MINB, bool LEAN, bool PACK>
 static size_t smem_v(int lcap) { return search_smem_bytes<G, N, NG>(lcap); }
 
-#define OPMM_VARIANT_SWITCH(v, CALL, BAD)      \
-  switch (v) {                                 \
-    case 0: return CALL(16, 18, 2, 1, false);  \
-    case 1: return CALL(16, 18, 2, 1, true);   \
-    case 2: return CALL(8, 18, 2, 1, false);   \
-    case 3: return CALL(32, 18, 2, 1, false);  \
-    case 4: return CALL(27, 9, 2, 1, false);   \
-    case 5: return CALL(16, 18, 4, 1, false);  \
-    case 6: return CALL(8, 18, 4, 1, false);   \
-    case 7: return CALL(27, 9, 4, 1, false);   \
-    case 8: return CALL(24, 18, 3, 1, false);  \
-    default: return BAD;                       \
+#define OPMM_VARIANT_SWITCH(v, CALL, BAD)             \
+  switch (v) {                                        \
+    case 0: return CALL(16, 18, 2, 1, false, false);  \
+    case 1: return CALL(16, 18, 2, 1, true, false);   \
+    case 2: return CALL(8, 18, 2, 1, false, false);   \
+    case 3: return CALL(32, 18, 2, 1, false, false);  \
+    case 4: return CALL(27, 9, 2, 1, false, false);   \
+    case 5: return CALL(16, 18, 4, 1, false, false);  \
+    case 6: return CALL(27, 9, 4, 1, false, false);   \
+    case 7: return CALL(24, 18, 3, 1, false, false);  \
+    case 8: return CALL(16, 18, 2, 1, false, true);   \
+    case 9: return CALL(32, 18, 2, 1, false, true);   \
+    case 10: return CALL(16, 18, 4, 1, false, true);  \
+    case 11: return CALL(24, 18, 3, 1, false, true);  \
+    case 12: return CALL(27, 9, 4, 1, false, true);   \
+    default: return BAD;                              \
   }
 
 cudaError_t search_occupancy_v(int v, int lcap, int* blocks_per_sm) {
-#define OCC_CALL(G, N, NG, M, L) occ_v<G, N, NG, M, L>(lcap, blocks_per_sm)
+#define OCC_CALL(G, N, NG, M, L, K) occ_v<G, N, NG, M, L, K>(lcap, blocks_per_sm)
   OPMM_VARIANT_SWITCH(v, OCC_CALL, cudaErrorInvalidValue)
 #undef OCC_CALL
 }
 
 cudaError_t launch_search_v(int v, const SearchParams& P, int blocks_per_sm, int num_sms, cudaStream_t st) {
-#define LAUNCH_CALL(G, N, NG, M, L) launch_v<G, N, NG, M, L>(P, blocks_per_sm, num_sms, st)
+#define LAUNCH_CALL(G, N, NG, M, L, K) launch_v<G, N, NG, M, L, K>(P, blocks_per_sm, num_sms, st)
   OPMM_VARIANT_SWITCH(v, LAUNCH_CALL, cudaErrorInvalidValue)
 #undef LAUNCH_CALL
 }
 
 // Threads and dynamic shared memory of a block of variant v.
 int search_variant_threads(int v) {
-#define THREADS_CALL(G, N, NG, M, L) threads_v<G, N, NG, M, L>()
+#define THREADS_CALL(G, N, NG, M, L, K) threads_v<G, N, NG, M, L, K>()
   OPMM_VARIANT_SWITCH(v, THREADS_CALL, 0)
 #undef THREADS_CALL
 }
 
 size_t search_variant_smem(int v, int lcap) {
-#define SMEM_CALL(G, N, NG, M, L) smem_v<G, N, NG, M, L>(lcap)
+#define SMEM_CALL(G, N, NG, M, L, K) smem_v<G, N, NG, M, L, K>(lcap)
   OPMM_VARIANT_SWITCH(v, SMEM_CALL, (size_t)0)
 #undef SMEM_CALL
 }

@@ -57,6 +57,7 @@ int search_variant_g(int v);
 int search_variant_dim(int v);
 int search_variant_minb(int v);
 int search_variant_lean(int v);
+int search_variant_pack(int v);
 int search_variant_for(int unit, int dim);
 int search_variant_threads(int v);
 size_t search_variant_smem(int v, int lcap);

@@ -516,6 +516,74 @@ __device__ __forceinline__ void run_samples(const Prop2& phi, float (&e)[6], flo
   }
 }
 
+// One phase's one-sample propagator with its rows paired for packed FP32
+// (two single-precision FMAs per instruction): column j of rows 0-1 and of
+// rows 2-3, and the activation diagonal.
+struct PropX2 {
+  float2 r01[6], r23[6];
+  float2 d;
+};
+
+template <int PH>
+__device__ __forceinline__ void pack_phase(const Prop2& q, PropX2& x) {
+  const float (&c)[4][2] = PH == 1 ? q.c1 : q.c2;
+  const float (&d)[2] = PH == 1 ? q.d1 : q.d2;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    x.r01[j] = make_float2(j < 4 ? q.m[0][j] : c[0][j - 4], j < 4 ? q.m[1][j] : c[1][j - 4]);
+    x.r23[j] = make_float2(j < 4 ? q.m[2][j] : c[2][j - 4], j < 4 ? q.m[3][j] : c[3][j - 4]);
+  }
+  x.d = make_float2(d[0], d[1]);
+}
+
+// The same update as prop_apply with the rows taken two at a time: each
+// packed FMA performs the two row FMAs that prop_apply issues one after the
+// other, with the same operands in the same order, so the result is the same
+// bit for bit.
+__device__ __forceinline__ void prop_apply_x2(const PropX2& x, float (&e)[6]) {
+  float2 a01 = make_float2(e[0], e[1]), a23 = make_float2(e[2], e[3]);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float2 ej = make_float2(e[j], e[j]);
+    a01 = __ffma2_rn(x.r01[j], ej, a01);
+    a23 = __ffma2_rn(x.r23[j], ej, a23);
+  }
+  const float2 f = make_float2(e[4], e[5]);
+  const float2 nf = __ffma2_rn(x.d, f, f);
+  e[0] = a01.x;
+  e[1] = a01.y;
+  e[2] = a23.x;
+  e[3] = a23.y;
+  e[4] = nf.x;
+  e[5] = nf.y;
+}
+
+// run_samples with the packed update (PACK) or the scalar one.
+template <int PH, bool PACK, class Sink>
+__device__ __forceinline__ void run_samples_v(const Prop2& phi, float (&e)[6], float off, int& kk, int n,
+                                              Sink& sink) {
+  if constexpr (!PACK) {
+    run_samples<PH>(phi, e, off, kk, n, sink);
+  } else {
+    PropX2 x;
+    pack_phase<PH>(phi, x);
+    int i = 0;
+#pragma unroll 1
+    for (; i + 4 <= n; i += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        prop_apply_x2(x, e);
+        sink.emit(kk++, PH == 2 ? e[0] : e[0] + off);
+      }
+      sink.block_end();
+    }
+    for (; i < n; ++i) {
+      prop_apply_x2(x, e);
+      sink.emit(kk++, PH == 2 ? e[0] : e[0] + off);
+    }
+  }
+}
+
 // x <- x + y + x y (increment form of (I + x)(I + y)) in place, one block at
 // a time so that only one block of y is live: the coupling blocks first (they
 // read the old mechanical block of x), then the activation diagonals, then the
@@ -619,7 +687,9 @@ __device__ __forceinline__ void converge_on(unsigned mask, int n) {
 // instead of once per group of lanes that reached it together (a plain
 // __syncwarp did not keep them together); lanes that return early leave the
 // mask first.
-template <class Sink, bool SYNC = false>
+// PACK: the sample loops use the packed update (prop_apply_x2: the same
+// arithmetic, two row FMAs per instruction).
+template <class Sink, bool SYNC = false, bool PACK = false>
 __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& sink, float* qs = nullptr,
                                     int qstride = 0, bool guard = false, int* pulse_end = nullptr,
                                     unsigned mask = 0xffffffffu) {
@@ -669,7 +739,7 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
   }
   int kk = sc.onset + 1;
   if (SYNC) converge_on(mask, n1);
-  run_samples<1>(phi, e, off1, kk, n1, sink);
+  run_samples_v<1, PACK>(phi, e, off1, kk, n1, sink);
   if (pulse_end) *pulse_end = sw ? 1 : 0;
   if (SYNC) mask = __ballot_sync(mask, sw);
   if (sw) {
@@ -688,7 +758,7 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
     sink.emit(kk++, e[0]);
     const int n2 = ntot - n1 - 1;
     if (SYNC) converge_on(mask, n2);
-    run_samples<2>(phi, e, 0.0f, kk, n2, sink);
+    run_samples_v<2, PACK>(phi, e, 0.0f, kk, n2, sink);
   }
   return ntot;
 }
