@@ -640,13 +640,73 @@ __device__ __forceinline__ void prop_mul_inplace(Prop2& x, const float* qs, int 
   }
 }
 
+// prop_mul_inplace with two columns per packed FP32 instruction: every entry
+// gets the same operations in the same order (its own add, then the FMAs over
+// k = 0..3), so the result is the same bit for bit.
+template <bool SQUARE>
+__device__ __forceinline__ void prop_mul_inplace_x2(Prop2& x, const float* qs, int stride) {
+#pragma unroll
+  for (int ph = 0; ph < 2; ++ph) {
+    float (&c)[4][2] = ph == 0 ? x.c1 : x.c2;
+    float (&d)[2] = ph == 0 ? x.d1 : x.d2;
+    const int oc = ph == 0 ? 16 : 24, od = ph == 0 ? 32 : 34;
+    float2 yc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      yc[i] = SQUARE ? make_float2(c[i][0], c[i][1])
+                     : make_float2(qs[(oc + 2 * i) * stride], qs[(oc + 2 * i + 1) * stride]);
+    const float2 yd = SQUARE ? make_float2(d[0], d[1]) : make_float2(qs[od * stride], qs[(od + 1) * stride]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 ci = make_float2(c[i][0], c[i][1]);
+      float2 acc = __ffma2_rn(ci, yd, __fadd2_rn(ci, yc[i]));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc = __ffma2_rn(make_float2(x.m[i][kk], x.m[i][kk]), yc[kk], acc);
+      c[i][0] = acc.x;
+      c[i][1] = acc.y;
+    }
+    const float2 dd = make_float2(d[0], d[1]);
+    const float2 nd = __ffma2_rn(dd, yd, __fadd2_rn(dd, yd));
+    d[0] = nd.x;
+    d[1] = nd.y;
+  }
+  float2 ym[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 2; ++jp)
+      ym[i][jp] = SQUARE ? make_float2(x.m[i][2 * jp], x.m[i][2 * jp + 1])
+                         : make_float2(qs[(4 * i + 2 * jp) * stride], qs[(4 * i + 2 * jp + 1) * stride]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float a[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) a[kk] = x.m[i][kk];
+#pragma unroll
+    for (int jp = 0; jp < 2; ++jp) {
+      float2 acc = __fadd2_rn(make_float2(a[2 * jp], a[2 * jp + 1]), ym[i][jp]);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc = __ffma2_rn(make_float2(a[kk], a[kk]), ym[kk][jp], acc);
+      x.m[i][2 * jp] = acc.x;
+      x.m[i][2 * jp + 1] = acc.y;
+    }
+  }
+}
+
 // x = (I + q)^n - I for n >= 1, x holding q on entry and q stored in the slot:
-// left-to-right binary powering with at most one propagator live.
+// left-to-right binary powering with at most one propagator live (PACK: the
+// packed products).
+template <bool PACK = false>
 __device__ __forceinline__ void prop_pow_slot(Prop2& x, const float* qs, int stride, int n) {
   const int msb = 31 - __clz(n);
   for (int b = msb - 1; b >= 0; --b) {
-    prop_mul_inplace<true>(x, qs, stride);
-    if ((n >> b) & 1) prop_mul_inplace<false>(x, qs, stride);
+    if constexpr (PACK) {
+      prop_mul_inplace_x2<true>(x, qs, stride);
+      if ((n >> b) & 1) prop_mul_inplace_x2<false>(x, qs, stride);
+    } else {
+      prop_mul_inplace<true>(x, qs, stride);
+      if ((n >> b) & 1) prop_mul_inplace<false>(x, qs, stride);
+    }
   }
 }
 
@@ -661,6 +721,21 @@ __device__ __forceinline__ void prop_load(Prop2& q, const float* qs, int stride)
   float* f = reinterpret_cast<float*>(&q);
 #pragma unroll
   for (int i = 0; i < (int)(sizeof(Prop2) / sizeof(float)); ++i) f[i] = qs[i * stride];
+}
+
+// One phase of a slot's propagator (Prop2 element order: m row-major, c1,
+// c2, d1, d2), read straight into the row-paired form of pack_phase.
+template <int PH>
+__device__ __forceinline__ void slot_load_x2(PropX2& x, const float* qs, int stride) {
+  constexpr int oc = PH == 1 ? 16 : 24, od = PH == 1 ? 32 : 34;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int e0 = j < 4 ? 0 * 4 + j : oc + 0 * 2 + (j - 4), e1 = j < 4 ? 1 * 4 + j : oc + 1 * 2 + (j - 4);
+    const int e2 = j < 4 ? 2 * 4 + j : oc + 2 * 2 + (j - 4), e3 = j < 4 ? 3 * 4 + j : oc + 3 * 2 + (j - 4);
+    x.r01[j] = make_float2(qs[e0 * stride], qs[e1 * stride]);
+    x.r23[j] = make_float2(qs[e2 * stride], qs[e3 * stride]);
+  }
+  x.d = make_float2(qs[od * stride], qs[(od + 1) * stride]);
 }
 
 // Bring the lanes of `mask` together before a loop whose trip count n varies
@@ -731,7 +806,7 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
   if (qs) {
     step_increment(k, h, phi);
     prop_store(phi, qs, qstride);
-    prop_pow_slot(phi, qs, qstride, nsub);
+    prop_pow_slot<PACK>(phi, qs, qstride, nsub);
   } else {
     Prop2 q;
     step_increment(k, h, q);
@@ -745,16 +820,29 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
   if (sw) {
     // pulse-end interval: jsw whole substeps of the pulse phase, the split
     // substep (two RK4 steps around the switch), the rest of the step phase
-    Prop2 q;
-    if (qs) prop_load(q, qs, qstride);
-    else step_increment(k, h, q);
-    for (int s = 0; s < jsw; ++s) prop_apply<1>(q, e);
     const float h1 = frac * h;
-    rk4_vec(k, k.da1, k.dn1, h1, e);
+    if constexpr (PACK) {
+      // the single-substep matrix of each phase straight from the slot, rows paired
+      PropX2 x;
+      slot_load_x2<1>(x, qs, qstride);
+      for (int s = 0; s < jsw; ++s) prop_apply_x2(x, e);
+      rk4_vec(k, k.da1, k.dn1, h1, e);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) e[i] += dl[i];
-    rk4_vec(k, k.da2, k.dn2, h - h1, e);
-    for (int s = jsw + 1; s < nsub; ++s) prop_apply<2>(q, e);
+      for (int i = 0; i < 6; ++i) e[i] += dl[i];
+      rk4_vec(k, k.da2, k.dn2, h - h1, e);
+      slot_load_x2<2>(x, qs, qstride);
+      for (int s = jsw + 1; s < nsub; ++s) prop_apply_x2(x, e);
+    } else {
+      Prop2 q;
+      if (qs) prop_load(q, qs, qstride);
+      else step_increment(k, h, q);
+      for (int s = 0; s < jsw; ++s) prop_apply<1>(q, e);
+      rk4_vec(k, k.da1, k.dn1, h1, e);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) e[i] += dl[i];
+      rk4_vec(k, k.da2, k.dn2, h - h1, e);
+      for (int s = jsw + 1; s < nsub; ++s) prop_apply<2>(q, e);
+    }
     sink.emit(kk++, e[0]);
     const int n2 = ntot - n1 - 1;
     if (SYNC) converge_on(mask, n2);
