@@ -204,6 +204,8 @@ __device__ __forceinline__ void zm_mul(const ZMech& z, const float (&w)[4][NC], 
 
 // Single-substep increment propagator Q = T4(hA) - I of both phases by Horner:
 // W3 = I + Z/4, W2 = I + Z W3 / 3, W1 = I + Z W2 / 2, Q = Z W1, block by block.
+// Every sum of a product is written as an explicit single-rounding FMA (or
+// an explicit product), so step_increment_x2 can reproduce it bit for bit.
 __device__ __forceinline__ void step_increment(const Coef& k, float h, Prop2& q) {
   ZMech z;
   z.h = h;
@@ -227,7 +229,7 @@ __device__ __forceinline__ void step_increment(const Coef& k, float h, Prop2& q)
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) w[i][j] = (i == j ? 1.0f : 0.0f) + t[i][j] * (1.0f / 3.0f);
+    for (int j = 0; j < 4; ++j) w[i][j] = __fmaf_rn(t[i][j], 1.0f / 3.0f, i == j ? 1.0f : 0.0f);
   // W1 = I + Zm W2 / 2
   zm_mul<4>(z, w, t);
 #pragma unroll
@@ -251,16 +253,16 @@ __device__ __forceinline__ void step_increment(const Coef& k, float h, Prop2& q)
     tc[3][1] = fmaf(zcy, wdn, tc[3][1]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) { wc[i][0] = tc[i][0] * (1.0f / 3.0f); wc[i][1] = tc[i][1] * (1.0f / 3.0f); }
-    wda = 1.0f + zda * wda * (1.0f / 3.0f);
-    wdn = 1.0f + zdn * wdn * (1.0f / 3.0f);
+    wda = __fmaf_rn(__fmul_rn(zda, wda), 1.0f / 3.0f, 1.0f);
+    wdn = __fmaf_rn(__fmul_rn(zdn, wdn), 1.0f / 3.0f, 1.0f);
     // level 1: Wc1 = (Zm Wc2 + Zc Wd2) / 2, Wd1 = 1 + Zd Wd2 / 2
     zm_mul<2>(z, wc, tc);
     tc[2][0] = fmaf(zcx, wda, tc[2][0]);
     tc[3][1] = fmaf(zcy, wdn, tc[3][1]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) { wc[i][0] = 0.5f * tc[i][0]; wc[i][1] = 0.5f * tc[i][1]; }
-    wda = 1.0f + 0.5f * zda * wda;
-    wdn = 1.0f + 0.5f * zdn * wdn;
+    wda = __fmaf_rn(0.5f * zda, wda, 1.0f);
+    wdn = __fmaf_rn(0.5f * zdn, wdn, 1.0f);
     // Q: Qc = Zm Wc1 + Zc Wd1, Qd = Zd Wd1
     zm_mul<2>(z, wc, tc);
     tc[2][0] = fmaf(zcx, wda, tc[2][0]);
@@ -274,6 +276,89 @@ __device__ __forceinline__ void step_increment(const Coef& k, float h, Prop2& q)
       for (int i = 0; i < 4; ++i) { q.c2[i][0] = tc[i][0]; q.c2[i][1] = tc[i][1]; }
       q.d2[0] = zda * wda; q.d2[1] = zdn * wdn;
     }
+  }
+}
+
+// step_increment with two columns per packed FP32 instruction: the
+// mechanical block by column pairs, the coupling block's two columns as one
+// pair.  Every entry gets the operations step_increment gives it, in the same
+// order and with the same single roundings, so the result is the same bit
+// for bit.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+
+// o = Zm w for one column pair (w, o: four rows of pairs)
+__device__ __forceinline__ void zm_mul_x2(const float2 (&Z)[9], const float2 (&w)[4], float2 (&o)[4]) {
+  // Z: h, m10, m11, m12, m13, m20, m22, m30, m33 broadcast
+  o[0] = __fmul2_rn(Z[0], w[1]);
+  o[1] = __ffma2_rn(Z[4], w[3], __ffma2_rn(Z[3], w[2], __ffma2_rn(Z[2], w[1], __fmul2_rn(Z[1], w[0]))));
+  o[2] = __ffma2_rn(Z[6], w[2], __fmul2_rn(Z[5], w[0]));
+  o[3] = __ffma2_rn(Z[8], w[3], __fmul2_rn(Z[7], w[0]));
+}
+
+__device__ __forceinline__ void step_increment_x2(const Coef& k, float h, Prop2& q) {
+  const float2 Z[9] = {bc(h), bc(h * k.m10), bc(h * k.m11), bc(h * k.m12), bc(h * k.m13),
+                       bc(h * k.m20), bc(h * k.m22), bc(h * k.m30), bc(h * k.m33)};
+  const float zcx = h * k.cx, zcy = h * k.cy;
+  // mechanical block, column pairs jp = 0 (columns 0, 1) and 1 (columns 2, 3)
+#pragma unroll
+  for (int jp = 0; jp < 2; ++jp) {
+    float2 id[4], w[4], t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      id[i] = f2(i == 2 * jp ? 1.0f : 0.0f, i == 2 * jp + 1 ? 1.0f : 0.0f);
+      w[i] = id[i];
+    }
+    zm_mul_x2(Z, w, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = __fadd2_rn(id[i], __fmul2_rn(bc(0.25f), t[i]));
+    zm_mul_x2(Z, w, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = __ffma2_rn(t[i], bc(1.0f / 3.0f), id[i]);
+    zm_mul_x2(Z, w, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = __fadd2_rn(id[i], __fmul2_rn(bc(0.5f), t[i]));
+    zm_mul_x2(Z, w, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      q.m[i][2 * jp] = t[i].x;
+      q.m[i][2 * jp + 1] = t[i].y;
+    }
+  }
+  // coupling and activation blocks, per phase; the pair is (column Fa, column Fn)
+#pragma unroll
+  for (int ph = 0; ph < 2; ++ph) {
+    const float zda = h * (ph == 0 ? k.da1 : k.da2);
+    const float zdn = h * (ph == 0 ? k.dn1 : k.dn2);
+    float2 wc[4] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.25f * zcx, 0.f), f2(0.f, 0.25f * zcy)};
+    float wda = 1.0f + 0.25f * zda, wdn = 1.0f + 0.25f * zdn;
+    float2 tc[4];
+    zm_mul_x2(Z, wc, tc);
+    tc[2].x = fmaf(zcx, wda, tc[2].x);
+    tc[3].y = fmaf(zcy, wdn, tc[3].y);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) wc[i] = __fmul2_rn(tc[i], bc(1.0f / 3.0f));
+    wda = __fmaf_rn(__fmul_rn(zda, wda), 1.0f / 3.0f, 1.0f);
+    wdn = __fmaf_rn(__fmul_rn(zdn, wdn), 1.0f / 3.0f, 1.0f);
+    zm_mul_x2(Z, wc, tc);
+    tc[2].x = fmaf(zcx, wda, tc[2].x);
+    tc[3].y = fmaf(zcy, wdn, tc[3].y);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) wc[i] = __fmul2_rn(bc(0.5f), tc[i]);
+    wda = __fmaf_rn(0.5f * zda, wda, 1.0f);
+    wdn = __fmaf_rn(0.5f * zdn, wdn, 1.0f);
+    zm_mul_x2(Z, wc, tc);
+    tc[2].x = fmaf(zcx, wda, tc[2].x);
+    tc[3].y = fmaf(zcy, wdn, tc[3].y);
+    float (&c)[4][2] = ph == 0 ? q.c1 : q.c2;
+    float (&d)[2] = ph == 0 ? q.d1 : q.d2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c[i][0] = tc[i].x;
+      c[i][1] = tc[i].y;
+    }
+    d[0] = zda * wda;
+    d[1] = zdn * wdn;
   }
 }
 
@@ -804,7 +889,8 @@ __device__ __forceinline__ int walk(const float* p, const SacConst& sc0, Sink& s
   const float off1 = s1[0] - sc.thf;
   Prop2 phi;
   if (qs) {
-    step_increment(k, h, phi);
+    if constexpr (PACK) step_increment_x2(k, h, phi);
+    else step_increment(k, h, phi);
     prop_store(phi, qs, qstride);
     prop_pow_slot<PACK>(phi, qs, qstride, nsub);
   } else {
