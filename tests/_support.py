@@ -72,3 +72,18 @@ def oracle_inputs_parallel(w, procs=None):
     with mp.get_context("spawn").Pool(procs) as pool:
         parts = pool.map(_oracle_chunk, [(w.subset(c), c) for c in chunks])
     return [it for part in parts for it in part]
+
+
+def pulse_equilibrium_distance(p, th0, thf):
+    """|theta_eq - theta_0| in the saccade's positive frame, where theta_eq is
+    the plant's steady state under the pulse heights held (the closed form
+    pinned by the oracle tests: (a_g F_a - a_n F_n) / (K_P + a_g K_LT_AG +
+    a_n K_LT_ANT), a = K_SE / (K_SE + K_LT), K_P = N_C_AG + N_C_ANT).  The
+    FP32 path keeps the pulse-phase state as its deviation from that steady
+    state, so this is the scale its rounding acts on."""
+    p = np.asarray(p, dtype=np.float64)
+    ag = p[0] / (p[0] + p[2])
+    an = p[1] / (p[1] + p[3])
+    th_eq = (ag * p[15] - an * p[16]) / (p[4] + p[5] + ag * p[2] + an * p[3])
+    sign = -1.0 if thf < th0 else 1.0
+    return abs(th_eq - sign * th0)

@@ -19,7 +19,7 @@ import pytest
 import oracle as O
 import paper_2007_09884_gb300 as G
 import workloads as W
-from _support import centres, f32, oracle_inputs, oracle_inputs_parallel, to_batch
+from _support import centres, f32, oracle_inputs, oracle_inputs_parallel, pulse_equilibrium_distance, to_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -410,14 +410,15 @@ def test_full_candidate_budget_initial_vertices_match_oracle(ctx):
 
 # In the wide box the plant's modes spread over up to five decades and its
 # trajectories over three (a strong pulse against weak tension slopes can
-# carry a candidate past 1,000 deg).  FP32 rounding in the one-sample
-# propagator and in the sample updates then costs a few millionths of the
-# trajectory's own scale (measured: 3e-6 to 7e-6 of max |theta| for the worst
-# random candidates; an FP32 emulation of the pipeline with either stage in
-# FP64 halves the error, with both it vanishes): the bound is 1e-4 deg plus
-# 2e-5 of the largest |theta| of the reference trajectory.
-def wide_traj_tol(ref):
-    return TRAJ_TOL + 2e-5 * float(np.max(np.abs(ref)))
+# carry a candidate past 1,000 deg).  The FP32 path keeps the pulse-phase
+# state as its deviation from the steady state the pulse heights would hold,
+# which there can lie a hundred times beyond the trajectory, and its sample
+# updates round at that scale: the bound is 1e-4 deg plus 2e-5 of the larger
+# of the reference trajectory's largest |theta| and that distance
+# (tests/test_gpu_wide_box.py checks it over 12,288 random candidates).
+def wide_traj_tol(ref, p, it):
+    scale = max(float(np.max(np.abs(ref))), pulse_equilibrium_distance(p, it["th0"], it["thf"]))
+    return TRAJ_TOL + 2e-5 * scale
 
 
 def test_wide_box_simulation_and_fit_match_oracle(ctx):
@@ -444,7 +445,7 @@ def test_wide_box_simulation_and_fit_match_oracle(ctx):
             refined += O.substeps(p, it["fs"]) > O.nsub(it["fs"])
             ref = O.simulate_rk4(p, it["L"], it["fs"], it["onset"], it["th0"], it["thf"])
             got = traj[offs[i]:offs[i] + it["L"]]
-            assert np.max(np.abs(got - ref)) <= wide_traj_tol(ref), (i, np.max(np.abs(got - ref)),
+            assert np.max(np.abs(got - ref)) <= wide_traj_tol(ref, p, it), (i, np.max(np.abs(got - ref)),
                                                                      np.max(np.abs(ref)))
         assert refined >= 1
     res, refs = _fit_both(ctx, items[:3], 6, 6, box_lo=0.1, box_hi=10.0)

@@ -155,15 +155,14 @@ def test_adamw_matches_oracle_element_by_element(ctx):
 def test_training_reduces_loss_and_weights_round_trip(ctx, tmp_path):
     # targets ln(U(0.8, 1.2)) / 0.2 have variance ~0.333 per output: an untrained
     # network starts there; 600 steps of 2,048 generated saccades must cut it.
-    # The mean of the last 50 losses is known to about 0.2% (batch noise), but
-    # where 600 steps land varies from run to run of the same schedule: seeds
-    # (3, 11), (3, 12), (4, 11) ended at 0.913-0.948 of the first losses, so the
-    # bound is 0.96.
+    # Over 12 (initialisation, data) seed pairs the last-50 / first-5 loss
+    # ratio measured 0.910-0.938 (mean 0.922, standard deviation 0.007); the
+    # bound is the mean plus four standard deviations.
     G.opmm_surrogate_init(ctx, 3)
     losses = G.opmm_surrogate_train(ctx, 600, batch=2048, lr=2e-3, data_seed=11)
     assert np.all(np.isfinite(losses))
     assert 0.30 < losses[:5].mean() < 0.37
-    assert losses[-50:].mean() < 0.96 * losses[:5].mean(), (losses[:5], losses[-50:])
+    assert losses[-50:].mean() < 0.95 * losses[:5].mean(), (losses[:5], losses[-50:])
     path = str(tmp_path / "w.bin")
     G.opmm_surrogate_save(ctx, path)
     p1 = G.opmm_surrogate_get_params(ctx)
@@ -221,8 +220,11 @@ def test_trained_surrogate_gains_over_plain_search(ctx):
                          for j, it in enumerate(items)])
 
     # held-out medians over 100,000 saccades are 0.075 deg (network) against
-    # 0.17 deg (nominal); over these 400 the ratio scatters around 0.45
-    assert np.median(rms_of(pred)) < 0.7 * np.median(rms_of(nominal))
+    # 0.17 deg (nominal).  Over 10 held-out sets of 400 (config indices 3-12)
+    # and two training seeds the ratio of the medians measured 0.402-0.495
+    # (mean 0.44); this set (index 3) is the highest at 0.490, and the bound
+    # leaves a tenth above the largest value seen.
+    assert np.median(rms_of(pred)) < 0.55 * np.median(rms_of(nominal))
 
     small = dict(candidates=1024, iterations=20, seed=0)
     seeded = dict(small, box_lo=0.95, box_hi=1.05, init_step=0.025)
