@@ -203,11 +203,11 @@ def barrier(ws: int):
 
 
 # ------------------------------------------------------------------ workloads
-def make_workload(name: str, rank: int, quick: bool):
+def make_workload(name: str, rank: int, quick: bool, saccades: int = 0):
     if name == "batch1024":
-        w = W.batch1024(B=64 if quick else 1024)
+        w = W.batch1024(B=saccades or (64 if quick else 1024))
     elif name == "uneven10k":
-        w = W.uneven10k(B=256 if quick else 10000)
+        w = W.uneven10k(B=saccades or (256 if quick else 10000))
     elif name == "single10":
         w = W.single10()
     else:
@@ -381,7 +381,7 @@ def run_ours(args, ws, rank, local):
     import paper_2007_09884_gb300 as G
 
     torch.cuda.set_device(local)
-    w = make_workload(args.workload, rank, args.quick)
+    w = make_workload(args.workload, rank, args.quick, args.saccades)
     ctx = G.opmm_create(local)
     stream = torch.cuda.current_stream()
     G.opmm_set_stream(ctx, stream.cuda_stream)
@@ -1062,6 +1062,8 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="leave the uneven 10,000-saccade search out of the line")
     ap.add_argument("--serve-slots", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="small batch (smoke of the bench itself)")
+    ap.add_argument("--saccades", type=int, default=0,
+                    help="batch size of the batch1024 / uneven10k workload (profiling runs; 0 = the workload's own)")
     ap.add_argument("--model", type=int, default=18, choices=[18, 9],
                     help="search coordinates: the 18-parameter OPMM or the 9-parameter model (Sec. 2.2.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
