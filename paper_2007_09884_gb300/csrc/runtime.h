@@ -124,7 +124,7 @@ struct opmm_plan {
 
 namespace opmm {
 
-Status build_units(opmm_plan* p, int G);
+Status build_units(opmm_plan* p, int G, int probe_stride = 1);
 Status plan_stage(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o, opmm_plan* p);
 Status plan_build(opmm_ctx* ctx, const opmm_saccade* sacs, int32_t n, const opmm_fit_opts& o, bool capture,
                   bool tune, opmm_plan* p);
