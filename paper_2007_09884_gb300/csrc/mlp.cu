@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/opmm.h"
 #include "common.cuh"
@@ -110,21 +111,60 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 // ------------------------------------------------------------------ GEMM
-__global__ void __launch_bounds__(kGemmThreads, 2)
-    k_gemm_tn(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, GemmArgs g) {
+// Tensor maps of a grouped launch: A and B of each problem.
+struct GemmMaps {
+  CUtensorMap a[kMaxGroup];
+  CUtensorMap b[kMaxGroup];
+};
+
+// The launch's shape and the problems' outputs, as the kernel sees them.
+struct GemmArgs {
+  int N, nkb, ksplit, ldo, ldt;        // nkb: 64-wide K blocks per slice
+  long long zstride;
+  unsigned* err;
+  GemmProblem p[kMaxGroup];
+};
+
+// Barrier of the eight epilogue warps (named barrier 1).
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// D tile (tm, tn) of problem blockIdx.z / ksplit over K slice blockIdx.z %
+// ksplit.  Warp 8 lane 0 streams the A and B tiles of each 64-wide K block
+// into the ring (TMA, 128-byte swizzle); warp 9 lane 0 issues four
+// tcgen05.mma (K = 16 each) per stage into a 128 x 128 FP32 accumulator in
+// tensor memory and frees the stage with tcgen05.commit.  Warps 0-7 are the
+// epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its tile rows) and
+// columns 64 (w / 4) .. + 63, 16 at a time, applies the epilogue EPI and
+// stages the tile in the ring, which every MMA has finished reading by then;
+// the eight warps then write the tile out in whole rows (16-byte stores,
+// consecutive threads on consecutive addresses).  Eight warps rather than
+// four: the epilogue's per-element math (GELU, GELU') is latency bound with
+// one warp per scheduler.  Staging: Sf [128][128] FP32 at 0 and Sbf [128][128]
+// BF16 at 64 KB, their 16-byte chunks permuted by XOR with (row & 7) so that
+// 32 rows writing the same logical chunk hit distinct banks; St [128][128]
+// BF16 at 96 KB, the transpose (32 rows of one column are 64 contiguous
+// bytes).  Every wait is bounded; a wait that expires raises the error word
+// and the tile's output is not written.
+template <int STAGES, int EPI>
+__global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
+    k_gemm_tn(const __grid_constant__ GemmMaps maps, const __grid_constant__ GemmArgs g) {
+  static_assert(STAGES * kStageBytes >= (EPI == kEpiF32 ? 65536 : EPI == kEpiGeluBwd ? 131072 : 131072),
+                "the epilogue stages its tile in the ring");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kStages * kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + STAGES * kStageBytes);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   int* bail = reinterpret_cast<int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tn = blockIdx.x, tm = blockIdx.y;
-  const int nk = g.K / kBK;
+  const int prob = blockIdx.z / g.ksplit, slice = blockIdx.z - prob * g.ksplit;
+  const int kb0 = slice * g.nkb;
+  const int nk = g.nkb;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -132,36 +172,38 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
     *bail = 0;
     fence_mbar_init();
   }
-  if (warp == 5) tc_alloc(tmem_slot, kBN);
+  if (warp == kGemmMmaWarp) tc_alloc(tmem_slot, kBN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == kGemmTmaWarp) {
     if (lane == 0) {
       // TMA producer
+      const CUtensorMap* ma = &maps.a[prob];
+      const CUtensorMap* mb = &maps.b[prob];
       for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % kStages;
-        const uint32_t use = (uint32_t)(kb / kStages);
-        if (kb >= kStages && !mbar_wait(&empty[s], (use & 1u) ^ 1u, kMaxWaitTries)) {
+        const int s = kb % STAGES;
+        const uint32_t use = (uint32_t)(kb / STAGES);
+        if (kb >= STAGES && !mbar_wait(&empty[s], (use & 1u) ^ 1u, kMaxWaitTries)) {
           raise_error(g.err, kErrWaitTimeout);
           atomicExch(bail, 1);
           break;
         }
         unsigned char* st = sm + s * kStageBytes;
         mbar_arrive_expect_tx(&full[s], kStageBytes);
-        tma_load_2d(st, &ta, kb * kBK, tm * kBM, &full[s]);
-        tma_load_2d(st + kTileABytes, &tb, kb * kBK, tn * kBN, &full[s]);
+        tma_load_2d(st, ma, (kb0 + kb) * kBK, tm * kBM, &full[s]);
+        tma_load_2d(st + kTileABytes, mb, (kb0 + kb) * kBK, tn * kBN, &full[s]);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == kGemmMmaWarp) {
     if (lane == 0) {
       // MMA issuer
       constexpr uint32_t idesc = f16_idesc(kBM, kBN);
       for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % kStages;
-        const uint32_t use = (uint32_t)(kb / kStages);
+        const int s = kb % STAGES;
+        const uint32_t use = (uint32_t)(kb / STAGES);
         if (!mbar_wait(&full[s], use & 1u, kMaxWaitTries)) {
           raise_error(g.err, kErrWaitTimeout);
           atomicExch(bail, 1);
@@ -178,105 +220,130 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
       tc_commit(done);
     }
   } else {
-    // epilogue warpgroup: warp w owns TMEM lanes [32 w, 32 w + 32) = rows of the tile
+    // epilogue
     const bool ok = mbar_wait(done, 0u, kMaxWaitTries);
-    if (!ok) raise_error(g.err, kErrWaitTimeout);
+    if (!ok) {
+      raise_error(g.err, kErrWaitTimeout);
+      atomicExch(bail, 1);
+    }
     tc_fence_after();
-    const int row = tm * kBM + warp * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < kBN && ok; c0 += 16) {
-      float v[16];
-      tc_ld16(tbase + (uint32_t)c0, v);
-      const int col = tn * kBN + c0;
-      if (g.epi == kEpiF32) {
-        float4* o = reinterpret_cast<float4*>(g.out_f32 + (size_t)row * g.ldo + col);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    epi_bar();
+    const bool go = *reinterpret_cast<volatile int*>(bail) == 0;
+    const GemmProblem& P = g.p[prob];
+    const int tid = threadIdx.x;                 // 0..255
+    const int q = warp & 3;                      // TMEM lane quarter
+    const int r = q * 32 + lane;                 // tile row
+    const int row = tm * kBM + r;
+    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
+    unsigned char* Sf = sm;                      // [128][128] FP32, chunks ^ (row & 7)
+    unsigned char* Sbf = sm + 65536;             // [128][128] BF16, chunks ^ (row & 7)
+    __nv_bfloat16* St = reinterpret_cast<__nv_bfloat16*>(sm + 98304);   // [128][128] BF16, transposed
+    const bool want_f32 = EPI == kEpiF32 || (EPI == kEpiBiasGelu && P.out_f32 != nullptr);
+    const bool want_t = EPI != kEpiF32 && P.out_t != nullptr;
+    if (go) {
+#pragma unroll 1
+      for (int c = 0; c < 64; c += 16) {
+        const int col0 = (warp >> 2) * 64 + c;   // column within the tile
+        const int col = tn * kBN + col0;         // column of D
+        float v[16];
+        tc_ld16(tbase + (uint32_t)col0, v);
+        if constexpr (EPI == kEpiGeluBwd) {
+          const float4* zp = reinterpret_cast<const float4*>(P.zin + (size_t)row * g.ldo + col);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-      } else {
-        if (g.bias) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += g.bias[col + i];
-        }
-        if (g.epi == kEpiBiasGelu) {
-          if (g.out_f32) {
-            float4* o = reinterpret_cast<float4*>(g.out_f32 + (size_t)row * g.ldo + col);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          for (int i = 0; i < 4; ++i) {
+            const float4 z = zp[i];
+            v[4 * i] *= gelu_grad(z.x);
+            v[4 * i + 1] *= gelu_grad(z.y);
+            v[4 * i + 2] *= gelu_grad(z.z);
+            v[4 * i + 3] *= gelu_grad(z.w);
           }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
         }
-        __nv_bfloat162 h[8];
+        if constexpr (EPI == kEpiBiasGelu) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        uint4* o = reinterpret_cast<uint4*>(g.out_bf16 + (size_t)row * g.ldo + col);
-        o[0] = *reinterpret_cast<uint4*>(&h[0]);
-        o[1] = *reinterpret_cast<uint4*>(&h[4]);
-        if (g.out_t) {
-          // transposed copy: for each column the warp writes 32 consecutive rows
+          for (int i = 0; i < 16; ++i) v[i] += P.bias[col + i];
+        }
+        if (want_f32) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            g.out_t[(size_t)(col + i) * g.ldt + row] = __float2bfloat16_rn(v[i]);
+          for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4*>(Sf + r * 512 + ((((col0 >> 2) + j) ^ (r & 7)) << 4)) =
+                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+        if constexpr (EPI != kEpiF32) {
+          if constexpr (EPI == kEpiBiasGelu) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+          }
+          __nv_bfloat162 h[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+            *reinterpret_cast<uint4*>(Sbf + r * 256 + ((((col0 >> 3) + j) ^ (r & 7)) << 4)) =
+                *reinterpret_cast<const uint4*>(&h[4 * j]);
+          if (want_t) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              St[(col0 + 2 * i) * 128 + r] = h[i].x;
+              St[(col0 + 2 * i + 1) * 128 + r] = h[i].y;
+            }
+          }
+        }
+      }
+    }
+    epi_bar();
+    if (go) {
+      const size_t r0 = (size_t)tm * kBM;
+      const int c0 = tn * kBN;
+      if (want_f32) {
+        float* out = EPI == kEpiF32 ? P.out_f32 + (size_t)slice * (size_t)g.zstride : P.out_f32;
+        for (int qq = tid; qq < 128 * 32; qq += 256) {
+          const int rr = qq >> 5, ch = qq & 31;
+          const uint4 x = *reinterpret_cast<const uint4*>(Sf + rr * 512 + ((ch ^ (rr & 7)) << 4));
+          *reinterpret_cast<uint4*>(out + (r0 + rr) * g.ldo + c0 + ch * 4) = x;
+        }
+      }
+      if constexpr (EPI != kEpiF32) {
+        for (int qq = tid; qq < 128 * 16; qq += 256) {
+          const int rr = qq >> 4, ch = qq & 15;
+          const uint4 x = *reinterpret_cast<const uint4*>(Sbf + rr * 256 + ((ch ^ (rr & 7)) << 4));
+          *reinterpret_cast<uint4*>(P.out_bf16 + (r0 + rr) * g.ldo + c0 + ch * 8) = x;
+        }
+        if (want_t) {
+          for (int qq = tid; qq < 128 * 16; qq += 256) {
+            const int cc = qq >> 4, ch = qq & 15;
+            const uint4 x = *reinterpret_cast<const uint4*>(St + cc * 128 + ch * 8);
+            *reinterpret_cast<uint4*>(P.out_t + (size_t)(c0 + cc) * g.ldt + r0 + ch * 8) = x;
+          }
+        }
+      }
+      if constexpr (EPI == kEpiGeluBwd) {
+        if (tid < 128) {
+          // column sum of the rounded errors over the tile's rows, in row order
+          float s = 0.0f;
+          for (int rr = 0; rr < 128; ++rr)
+            s += __bfloat162float(
+                *reinterpret_cast<const __nv_bfloat16*>(Sbf + rr * 256 + ((((tid >> 3) ^ (rr & 7))) << 4) + (tid & 7) * 2));
+          P.colpart[(size_t)tm * g.N + c0 + tid] = s;
         }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) tc_dealloc(tmem, kBN);
+  if (warp == kGemmMmaWarp) tc_dealloc(tmem, kBN);
 }
 
 // ------------------------------------------------------------------ elementwise / reductions
-// 32x32 tiled transpose of a BF16 matrix [R][C] -> [C][R].
-__global__ void k_transpose_bf16(const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C) {
-  __shared__ __nv_bfloat16 t[32][33];
+// Transposes of the hidden weight matrices: wt_l = wb_l^T for the four
+// 512 x 512 BF16 matrices (blockIdx.z = layer), through a 32 x 32 tile.
+__global__ void k_transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt) {
+  __shared__ __nv_bfloat16 t[32][34];
+  const size_t lo = (size_t)blockIdx.z * kHidden * kHidden;
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int r = r0 + i, c = c0 + threadIdx.x;
-    if (r < R && c < C) t[i][threadIdx.x] = in[(size_t)r * C + c];
-  }
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) t[i][threadIdx.x] = wb[lo + (size_t)(r0 + i) * kHidden + c0 + threadIdx.x];
   __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int c = c0 + i, r = r0 + threadIdx.x;
-    if (r < R && c < C) out[(size_t)c * R + r] = t[threadIdx.x][i];
-  }
-}
-
-// dZ = dH * GELU'(Z) for a [M][N] layer: writes dZ (BF16, row-major and
-// transposed) and per-32-row partial column sums (bias gradient, reduced
-// deterministically by k_colsum).
-__global__ void k_gelu_bwd(const float* dH, const float* Z, int M, int N, __nv_bfloat16* dZ, __nv_bfloat16* dZt,
-                           float* colpart) {
-  __shared__ float t[32][33];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  const int tx = threadIdx.x;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int r = r0 + i, c = c0 + tx;
-    const size_t idx = (size_t)r * N + c;
-    const float d = dH[idx] * gelu_grad(Z[idx]);
-    const __nv_bfloat16 b = __float2bfloat16_rn(d);
-    dZ[idx] = b;
-    t[i][tx] = __bfloat162float(b);
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int c = c0 + i, r = r0 + tx;
-    dZt[(size_t)c * M + r] = __float2bfloat16_rn(t[tx][i]);
-  }
-  if (threadIdx.y == 0) {
-    float s = 0.0f;
-    for (int i = 0; i < 32; ++i) s += t[i][tx];
-    colpart[(size_t)blockIdx.y * N + c0 + tx] = s;
-  }
-}
-
-// out[n] = sum over row blocks of part[rb][n] (fixed order).
-__global__ void k_colsum(const float* part, int rblocks, int N, float* out) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  float s = 0.0f;
-  for (int rb = 0; rb < rblocks; ++rb) s += part[(size_t)rb * N + n];
-  out[n] = s;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) wt[lo + (size_t)(c0 + i) * kHidden + r0 + threadIdx.x] = t[threadIdx.x][i];
 }
 
 // Output layer and loss: Y[m][o] = H[m] . W5[o] + b5[o] (o < 18, CUDA cores);
@@ -313,50 +380,134 @@ __global__ void k_head_fwd_loss(const __nv_bfloat16* H, const __nv_bfloat16* W5,
   if (lane == 0 && row_loss) row_loss[m] = l / (float)(M * kOut);
 }
 
-// Backward of the output layer: dH[m][k] = sum_o dY[m][o] W5[o][k] (FP32);
-// partial sums over 32-row blocks of dW5[o][k] = sum_m dY[m][o] H[m][k] and
-// db5[o] = sum_m dY[m][o].  Block: 32 rows x 512 columns, 256 threads.
-__global__ void k_head_bwd(const float* dY, const __nv_bfloat16* H, const __nv_bfloat16* W5, int M, float* dH,
-                           float* dWpart, float* dbpart) {
-  __shared__ float sdy[32][kOut];
-  const int r0 = blockIdx.x * 32;
-  for (int i = threadIdx.x; i < 32 * kOut; i += blockDim.x) sdy[i / kOut][i % kOut] = dY[(size_t)(r0 + i / kOut) * kOut + i % kOut];
+// Output layer, loss and the first steps of the backward pass for 32 rows
+// per block (training; 512 threads): y = H3 . W5^T + b5, the rows' loss terms
+// and dY = 2 (y - t) / (M 18); then per column k (one thread each): the
+// block's partial sums of dW5[o][k] = sum_m dY[m][o] H3[m][k] (and of db5 =
+// sum_m dY), dH3 = dY . W5 and the rounded layer-3 error dZ3 = BF16(dH3 *
+// GELU'(Z3)), written row-major and transposed (through shared memory, in
+// whole rows) with its column sums over the block's rows.  W5, the block's
+// H3 and Z3 rows are staged in shared memory first.  Every sum runs in a
+// fixed order.
+constexpr int kHeadRows = 32;
+constexpr int kHeadThreads = 512;
+static_assert(kHeadThreads == kHidden && kHeadRows == 2 * (kHeadThreads / 32), "one thread per column, two rows per warp");
+constexpr int kSdzPitch = kHidden + 2;     // BF16 elements: rows one bank apart
+constexpr size_t kHeadSmem = (size_t)kOut * kHidden * 2 + (size_t)kHeadRows * kHidden * 2 +
+                             (size_t)kHeadRows * kHidden * 4 + (size_t)kHeadRows * kSdzPitch * 2 +
+                             (size_t)kHeadRows * kOut * 4;
+
+__global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5,
+                                                             const float* b5, const float* T, const float* Z, int M,
+                                                             float* Y, float* dY, float* row_loss, __nv_bfloat16* dZ,
+                                                             __nv_bfloat16* dZt, float* colpart, float* dWpart,
+                                                             float* dbpart) {
+  extern __shared__ __align__(16) unsigned char hsm[];
+  __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(hsm);                     // [18][512]
+  __nv_bfloat16* sh = sw + kOut * kHidden;                                      // [32][512]
+  float* sz = reinterpret_cast<float*>(sh + kHeadRows * kHidden);               // [32][512]
+  __nv_bfloat16* sdz = reinterpret_cast<__nv_bfloat16*>(sz + kHeadRows * kHidden);   // [32][kSdzPitch]
+  float* sdy = reinterpret_cast<float*>(sdz + kHeadRows * kSdzPitch);           // [32][18]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = blockIdx.x * kHeadRows;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(W5);
+    uint4* dst = reinterpret_cast<uint4*>(sw);
+    for (int i = tid; i < kOut * kHidden / 8; i += kHeadThreads) dst[i] = src[i];
+    const uint4* hs = reinterpret_cast<const uint4*>(H + (size_t)r0 * kHidden);
+    uint4* hd = reinterpret_cast<uint4*>(sh);
+    for (int i = tid; i < kHeadRows * kHidden / 8; i += kHeadThreads) hd[i] = hs[i];
+    const uint4* zs = reinterpret_cast<const uint4*>(Z + (size_t)r0 * kHidden);
+    uint4* zd = reinterpret_cast<uint4*>(sz);
+    for (int i = tid; i < kHeadRows * kHidden / 4; i += kHeadThreads) zd[i] = zs[i];
+  }
   __syncthreads();
-  for (int k = threadIdx.x; k < kHidden; k += blockDim.x) {
-    float w[kOut];
+  // forward and loss: warp w takes rows 2 w, 2 w + 1
+  for (int i = 2 * warp; i < 2 * warp + 2; ++i) {
+    const int m = r0 + i;
+    float acc[kOut];
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) w[o] = __bfloat162float(W5[(size_t)o * kHidden + k]);
-    float gw[kOut];
+    for (int o = 0; o < kOut; ++o) acc[o] = 0.0f;
+    for (int k = lane; k < kHidden; k += 32) {
+      const float h = __bfloat162float(sh[i * kHidden + k]);
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) gw[o] = 0.0f;
-    for (int i = 0; i < 32; ++i) {
-      const int m = r0 + i;
-      const float h = __bfloat162float(H[(size_t)m * kHidden + k]);
+      for (int o = 0; o < kOut; ++o) acc[o] = fmaf(h, __bfloat162float(sw[o * kHidden + k]), acc[o]);
+    }
+    float l = 0.0f;
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) {
+      float v = acc[o];
+#pragma unroll
+      for (int s = 16; s; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+      v += b5[o];
+      const float d = v - T[(size_t)m * kOut + o];
+      l += d * d;
+      const float g = 2.0f * d / (float)(M * kOut);
+      if (lane == 0) {
+        Y[(size_t)m * kOut + o] = v;
+        dY[(size_t)m * kOut + o] = g;
+        sdy[i * kOut + o] = g;
+      }
+    }
+    if (lane == 0) row_loss[m] = l / (float)(M * kOut);
+  }
+  __syncthreads();
+  // per column: output-layer gradient partials, dH3, GELU backward
+  {
+    const int k = tid;
+    float w[kOut], gw[kOut];
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) {
+      w[o] = __bfloat162float(sw[o * kHidden + k]);
+      gw[o] = 0.0f;
+    }
+    for (int i = 0; i < kHeadRows; ++i) {
+      const float h = __bfloat162float(sh[i * kHidden + k]);
       float s = 0.0f;
 #pragma unroll
       for (int o = 0; o < kOut; ++o) {
-        s = fmaf(sdy[i][o], w[o], s);
-        gw[o] = fmaf(sdy[i][o], h, gw[o]);
+        s = fmaf(sdy[i * kOut + o], w[o], s);
+        gw[o] = fmaf(sdy[i * kOut + o], h, gw[o]);
       }
-      dH[(size_t)m * kHidden + k] = s;
+      const float d = s * gelu_grad(sz[i * kHidden + k]);
+      sdz[i * kSdzPitch + k] = __float2bfloat16_rn(d);
     }
 #pragma unroll
     for (int o = 0; o < kOut; ++o) dWpart[((size_t)blockIdx.x * kOut + o) * kHidden + k] = gw[o];
   }
-  if (threadIdx.x < kOut) {
+  if (tid < kOut) {
     float s = 0.0f;
-    for (int i = 0; i < 32; ++i) s += sdy[i][threadIdx.x];
-    dbpart[(size_t)blockIdx.x * kOut + threadIdx.x] = s;
+    for (int i = 0; i < kHeadRows; ++i) s += sdy[i * kOut + tid];
+    dbpart[(size_t)blockIdx.x * kOut + tid] = s;
+  }
+  __syncthreads();
+  // dZ3 row-major (pairs of columns per thread), its transpose (8 rows of one
+  // column per 16-byte store) and the column sums
+  for (int q = tid; q < kHeadRows * kHidden / 2; q += kHeadThreads) {
+    const int i = q / (kHidden / 2), c2 = q - i * (kHidden / 2);
+    *reinterpret_cast<__nv_bfloat162*>(dZ + (size_t)(r0 + i) * kHidden + 2 * c2) =
+        *reinterpret_cast<const __nv_bfloat162*>(sdz + i * kSdzPitch + 2 * c2);
+  }
+  for (int q = tid; q < kHidden * (kHeadRows / 8); q += kHeadThreads) {
+    const int k = q / (kHeadRows / 8), part = q - k * (kHeadRows / 8);
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sdz[(part * 8 + e) * kSdzPitch + k];
+    *reinterpret_cast<uint4*>(dZt + (size_t)k * M + r0 + part * 8) = *reinterpret_cast<const uint4*>(v);
+  }
+  {
+    const int k = tid;
+    float s = 0.0f;
+    for (int i = 0; i < kHeadRows; ++i) s += __bfloat162float(sdz[i * kSdzPitch + k]);
+    colpart[(size_t)blockIdx.x * kHidden + k] = s;
   }
 }
 
-// AdamW on the flat FP32 parameter vector; refreshes the BF16 working copies
-// (weights [out][in] and, for the hidden layers, their transposes [in][out]).
-__global__ void k_adamw(float* w, const float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
-                        float wd, float bc1, float bc2, const AdamLayout L, __nv_bfloat16* wb, __nv_bfloat16* wt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float gi = g[i];
+// One AdamW step of entry i with gradient gi (decoupled weight decay on
+// weight matrices only), refreshing its row-major BF16 working copy.
+__device__ __forceinline__ void adamw_update(long long i, float gi, float* w, float* m1, float* m2, float lr, float b1,
+                                             float b2, float eps, float wd, float bc1, float bc2, const AdamLayout& L,
+                                             __nv_bfloat16* wb) {
   const float a = b1 * m1[i] + (1.0f - b1) * gi;
   const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
   m1[i] = a;
@@ -366,14 +517,99 @@ __global__ void k_adamw(float* w, const float* g, float* m1, float* m2, int n, f
   if (decay) wi -= lr * wd * wi;
   wi -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
   w[i] = wi;
-  L.scatter(i, wi, wb, wt);
+  L.store_bf16(i, wi, wb);
 }
 
-// Refresh the BF16 working copies from the FP32 master parameters.
-__global__ void k_pack_params(const float* w, int n, const AdamLayout L, __nv_bfloat16* wb, __nv_bfloat16* wt) {
+// AdamW on the flat FP32 parameter vector with a given gradient; refreshes
+// the row-major BF16 working copies (their transposes follow from
+// k_transpose_layers).
+__global__ void k_adamw(float* w, const float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
+                        float wd, float bc1, float bc2, const AdamLayout L, __nv_bfloat16* wb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  L.scatter(i, w[i], wb, wt);
+  adamw_update(i, g[i], w, m1, m2, lr, b1, b2, eps, wd, bc1, bc2, L, wb);
+}
+
+// Refresh the row-major BF16 working copies from the FP32 master parameters.
+__global__ void k_pack_params(const float* w, int n, const AdamLayout L, __nv_bfloat16* wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  L.store_bf16(i, w[i], wb);
+}
+
+// Gradient assembly and, when a.adam is set, the AdamW step (see FinishArgs).
+// Blocks [0, kFinishWBlocks): one thread per hidden weight entry, summing the
+// K-slice partials in slice order.  The next kFinishRBlocks blocks: one warp
+// per bias or output-layer entry, lane j summing partials j, j + 32, ... in
+// order, then a fixed butterfly across the lanes.  The last block: the batch
+// loss (strided per thread, then a tree over the block).
+constexpr int kFinishW = kLayers * kHidden * kHidden;                     // hidden weight entries
+constexpr int kFinishR = kLayers * kHidden + kOut * kHidden + kOut;       // reduced entries
+constexpr int kFinishWBlocks = kFinishW / 256;
+constexpr int kFinishRBlocks = (kFinishR + 7) / 8;
+
+__global__ void __launch_bounds__(256) k_grad_finish(const __grid_constant__ FinishArgs a) {
+  const int tid = threadIdx.x;
+  if (blockIdx.x == kFinishWBlocks + kFinishRBlocks) {
+    if (!a.loss) return;
+    __shared__ float s[256];
+    float acc = 0.0f;
+    for (int i = tid; i < a.M; i += blockDim.x) acc += a.row_loss[i];
+    s[tid] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (tid < w) s[tid] += s[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) *a.loss = s[0];
+    return;
+  }
+  constexpr long long kW = (long long)kHidden * kHidden;
+  if (blockIdx.x < kFinishWBlocks) {
+    const int e = blockIdx.x * 256 + tid;
+    const int l = e / (int)kW;
+    const long long r = e - (long long)l * kW;
+    const float* p = a.wpart + (size_t)l * a.ksplit * kW + r;
+    float v = 0.0f;
+    for (int s = 0; s < a.ksplit; ++s) v += p[(size_t)s * kW];
+    const long long i = (long long)l * kLayerParams + r;
+    a.g[i] = v;
+    if (a.adam) adamw_update(i, v, a.w, a.m1, a.m2, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, AdamLayout{}, a.wb);
+    return;
+  }
+  const int e = (blockIdx.x - kFinishWBlocks) * 8 + (tid >> 5);
+  const int lane = tid & 31;
+  if (e >= kFinishR) return;
+  const float* p;
+  int n, stride;
+  long long i;
+  if (e < kLayers * kHidden) {
+    const int l = e / kHidden, c = e - l * kHidden;
+    p = a.colpart[l] + c;
+    n = a.ntiles[l];
+    stride = kHidden;
+    i = (long long)l * kLayerParams + kW + c;
+  } else if (e < kLayers * kHidden + kOut * kHidden) {
+    const int c = e - kLayers * kHidden;
+    p = a.dWpart + c;
+    n = a.nblk;
+    stride = kOut * kHidden;
+    i = kHeadW + c;
+  } else {
+    const int c = e - kLayers * kHidden - kOut * kHidden;
+    p = a.dbpart + c;
+    n = a.nblk;
+    stride = kOut;
+    i = kHeadB + c;
+  }
+  float v = 0.0f;
+  for (int t = lane; t < n; t += 32) v += p[(size_t)t * stride];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    a.g[i] = v;
+    if (a.adam) adamw_update(i, v, a.w, a.m1, a.m2, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, AdamLayout{}, a.wb);
+  }
 }
 
 // ------------------------------------------------------------------ data
@@ -381,46 +617,70 @@ __global__ void k_pack_params(const float* w, int n, const AdamLayout L, __nv_bf
 // interpolation, held after the window end) in the positive frame, position
 // normalised by the amplitude (start fixation = 0, end fixation = 1) and
 // velocity as 10 x the per-millisecond difference.  Output BF16 [n][512]
-// and its transpose [512][n_pad].
-__global__ void k_featurize(const DevSac* sacs, const float* traces, int n, __nv_bfloat16* X, __nv_bfloat16* Xt,
-                            int ldt) {
-  const int lane = threadIdx.x & 31;
-  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (b >= n) return;
-  const DevSac d = sacs[b];
-  const float* y = traces + d.off;
-  const float amp = fmaxf(d.thf - d.th0, 0.5f);
-  const float inv = 1.0f / amp;
-  float pos[kFeatPoints / 32 + 1];
+// and, optionally, its transpose [512][ldt].  A block of 4 warps takes 32
+// saccades (a warp per saccade at a time) and stages their features in shared
+// memory, then writes whole rows of X and, for each feature, the 32
+// saccades' values as 64 contiguous bytes of Xt.
+constexpr int kFeatRows = 32;
+constexpr int kSxPitch = kIn + 2;          // BF16 elements: rows one bank apart
+
+__global__ void __launch_bounds__(128) k_featurize(const DevSac* sacs, const float* traces, int n, __nv_bfloat16* X,
+                                                   __nv_bfloat16* Xt, int ldt) {
+  __shared__ __align__(16) __nv_bfloat16 sx[kFeatRows * kSxPitch];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b0 = blockIdx.x * kFeatRows;
+  for (int rb = warp; rb < kFeatRows; rb += 4) {
+    const int b = b0 + rb;
+    if (b >= n) break;
+    const DevSac d = sacs[b];
+    const float* y = traces + d.off;
+    const float amp = fmaxf(d.thf - d.th0, 0.5f);
+    const float inv = 1.0f / amp;
+    float pos[kFeatPoints / 32 + 1];
 #pragma unroll
-  for (int j = 0; j <= kFeatPoints / 32; ++j) {
-    const int i = lane + 32 * j;
-    float v = 0.0f;
-    if (i <= kFeatPoints) {
-      float s = (float)d.onset + (float)i * d.fs * 1e-3f;
-      s = fminf(s, (float)(d.L - 1));
-      const int k0 = (int)floorf(s);
-      const int k1 = min(k0 + 1, d.L - 1);
-      const float w = s - (float)k0;
-      const float yy = (1.0f - w) * y[k0] + w * y[k1];
-      v = (d.sign * yy - d.th0) * inv;
+    for (int j = 0; j <= kFeatPoints / 32; ++j) {
+      const int i = lane + 32 * j;
+      float v = 0.0f;
+      if (i <= kFeatPoints) {
+        float s = (float)d.onset + (float)i * d.fs * 1e-3f;
+        s = fminf(s, (float)(d.L - 1));
+        const int k0 = (int)floorf(s);
+        const int k1 = min(k0 + 1, d.L - 1);
+        const float w = s - (float)k0;
+        const float yy = (1.0f - w) * y[k0] + w * y[k1];
+        v = (d.sign * yy - d.th0) * inv;
+      }
+      pos[j] = v;
     }
-    pos[j] = v;
-  }
 #pragma unroll
-  for (int j = 0; j < kFeatPoints / 32; ++j) {
-    const int i = lane + 32 * j;
-    const float nxt = __shfl_down_sync(0xffffffffu, pos[j], 1);
-    const float nxt2 = __shfl_sync(0xffffffffu, pos[j + 1], 0);
-    const float p1 = lane == 31 ? nxt2 : nxt;
-    const float vel = (i == kFeatPoints - 1) ? 0.0f : 10.0f * (p1 - pos[j]);
-    const __nv_bfloat16 bp = __float2bfloat16_rn(pos[j]);
-    const __nv_bfloat16 bv = __float2bfloat16_rn(vel);
-    X[(size_t)b * kIn + i] = bp;
-    X[(size_t)b * kIn + kFeatPoints + i] = bv;
-    if (Xt) {
-      Xt[(size_t)i * ldt + b] = bp;
-      Xt[(size_t)(kFeatPoints + i) * ldt + b] = bv;
+    for (int j = 0; j < kFeatPoints / 32; ++j) {
+      const int i = lane + 32 * j;
+      const float nxt = __shfl_down_sync(0xffffffffu, pos[j], 1);
+      const float nxt2 = __shfl_sync(0xffffffffu, pos[j + 1], 0);
+      const float p1 = lane == 31 ? nxt2 : nxt;
+      const float vel = (i == kFeatPoints - 1) ? 0.0f : 10.0f * (p1 - pos[j]);
+      sx[rb * kSxPitch + i] = __float2bfloat16_rn(pos[j]);
+      sx[rb * kSxPitch + kFeatPoints + i] = __float2bfloat16_rn(vel);
+    }
+  }
+  __syncthreads();
+  const int nr = min(kFeatRows, n - b0);
+  for (int q = tid; q < nr * (kIn / 2); q += 128) {
+    const int i = q / (kIn / 2), c2 = q - i * (kIn / 2);
+    *reinterpret_cast<__nv_bfloat162*>(X + (size_t)(b0 + i) * kIn + 2 * c2) =
+        *reinterpret_cast<const __nv_bfloat162*>(sx + i * kSxPitch + 2 * c2);
+  }
+  if (Xt) {
+    for (int q = tid; q < kIn * (kFeatRows / 8); q += 128) {
+      const int k = q / (kFeatRows / 8), part = q - k * (kFeatRows / 8);
+      if (part * 8 + 8 <= nr) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = sx[(part * 8 + e) * kSxPitch + k];
+        *reinterpret_cast<uint4*>(Xt + (size_t)k * ldt + b0 + part * 8) = *reinterpret_cast<const uint4*>(v);
+      } else {
+        for (int e = 0; part * 8 + e < nr; ++e) Xt[(size_t)k * ldt + b0 + part * 8 + e] = sx[(part * 8 + e) * kSxPitch + k];
+      }
     }
   }
 }
@@ -517,20 +777,6 @@ __global__ void k_add_noise(uint64_t seed, long long base, const DevSac* sacs, i
   }
 }
 
-// Sum of n floats by one block in a fixed order (deterministic).
-__global__ void k_sum(const float* x, int n, float* out) {
-  __shared__ float s[256];
-  float a = 0.0f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
-  s[threadIdx.x] = a;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = s[0];
-}
-
 // ------------------------------------------------------------------ host launchers
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -560,36 +806,57 @@ static bool make_map(CUtensorMap* map, const void* base, int rows, int cols) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int S, int E>
+static cudaError_t gemm_attr() {
+  return cudaFuncSetAttribute(k_gemm_tn<S, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(S));
+}
+
 cudaError_t gemm_prepare() {
-  return cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+  cudaError_t e = gemm_attr<3, kEpiF32>();
+  if (e == cudaSuccess) e = gemm_attr<6, kEpiF32>();
+  if (e == cudaSuccess) e = gemm_attr<6, kEpiBiasGelu>();
+  if (e == cudaSuccess) e = gemm_attr<6, kEpiGeluBwd>();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_head_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeadSmem);
+  return e;
 }
 
-cudaError_t gemm_tn(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, const GemmArgs& args,
-                    cudaStream_t st) {
-  if (M % kBM || N % kBN || K % kBK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) return cudaErrorInvalidValue;
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, A, M, K) || !make_map(&tb, B, N, K)) return cudaErrorInvalidValue;
-  GemmArgs g = args;
-  g.M = M;
-  g.N = N;
-  g.K = K;
-  dim3 grid(N / kBN, M / kBM);
-  k_gemm_tn<<<grid, kGemmThreads, kGemmSmem, st>>>(ta, tb, g);
-  return cudaGetLastError();
-}
-
-cudaError_t transpose_bf16(const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C, cudaStream_t st) {
-  dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
-  k_transpose_bf16<<<grid, block, 0, st>>>(in, out, R, C);
-  return cudaGetLastError();
-}
-
-cudaError_t gelu_bwd(const float* dH, const float* Z, int M, int N, __nv_bfloat16* dZ, __nv_bfloat16* dZt,
-                     float* colpart, float* db, cudaStream_t st) {
-  dim3 grid(N / 32, M / 32), block(32, 8);
-  k_gelu_bwd<<<grid, block, 0, st>>>(dH, Z, M, N, dZ, dZt, colpart);
-  k_colsum<<<(N + 127) / 128, 128, 0, st>>>(colpart, M / 32, N, db);
+cudaError_t gemm(const GemmLaunch& L, cudaStream_t st) {
+  if (L.np < 1 || L.np > kMaxGroup || L.ksplit < 1 || L.M <= 0 || L.N <= 0 || L.K <= 0) return cudaErrorInvalidValue;
+  if (L.M % kBM || L.N % kBN || L.K % (L.ksplit * kBK)) return cudaErrorInvalidValue;
+  // launchable (stages, epilogue) pairs: the epilogue's staging must fit the ring
+  if (!((L.stages == 3 && L.epi == kEpiF32) || (L.stages == 6 && (L.epi == kEpiF32 || L.epi == kEpiBiasGelu ||
+                                                                   L.epi == kEpiGeluBwd))))
+    return cudaErrorInvalidValue;
+  if (L.ldo % 8 || (L.epi != kEpiF32 && L.ldt % 8)) return cudaErrorInvalidValue;
+  if (L.ksplit > 1 && L.epi != kEpiF32) return cudaErrorInvalidValue;
+  GemmMaps maps;
+  memset(&maps, 0, sizeof maps);
+  GemmArgs g{};
+  for (int i = 0; i < L.np; ++i) {
+    const GemmProblem& p = L.p[i];
+    auto mis = [](const void* x) { return (reinterpret_cast<uintptr_t>(x) & 15u) != 0; };
+    if (mis(p.A) || mis(p.B)) return cudaErrorInvalidValue;
+    const bool f32 = L.epi == kEpiF32 || (L.epi == kEpiBiasGelu && p.out_f32);
+    if (f32 && (!p.out_f32 || mis(p.out_f32))) return cudaErrorInvalidValue;
+    if (L.epi != kEpiF32 && (!p.out_bf16 || mis(p.out_bf16))) return cudaErrorInvalidValue;
+    if (p.out_t && mis(p.out_t)) return cudaErrorInvalidValue;
+    if (L.epi == kEpiBiasGelu && !p.bias) return cudaErrorInvalidValue;
+    if (L.epi == kEpiGeluBwd && (!p.zin || !p.colpart || mis(p.zin))) return cudaErrorInvalidValue;
+    if (!make_map(&maps.a[i], p.A, L.M, L.K) || !make_map(&maps.b[i], p.B, L.N, L.K)) return cudaErrorInvalidValue;
+    g.p[i] = p;
+  }
+  g.N = L.N;
+  g.nkb = L.K / L.ksplit / kBK;
+  g.ksplit = L.ksplit;
+  g.ldo = L.ldo;
+  g.ldt = L.ldt;
+  g.zstride = L.zstride;
+  g.err = L.err;
+  dim3 grid(L.N / kBN, L.M / kBM, L.np * L.ksplit);
+  if (L.stages == 3) k_gemm_tn<3, kEpiF32><<<grid, kGemmThreads, gemm_smem(3), st>>>(maps, g);
+  else if (L.epi == kEpiF32) k_gemm_tn<6, kEpiF32><<<grid, kGemmThreads, gemm_smem(6), st>>>(maps, g);
+  else if (L.epi == kEpiBiasGelu) k_gemm_tn<6, kEpiBiasGelu><<<grid, kGemmThreads, gemm_smem(6), st>>>(maps, g);
+  else k_gemm_tn<6, kEpiGeluBwd><<<grid, kGemmThreads, gemm_smem(6), st>>>(maps, g);
   return cudaGetLastError();
 }
 
@@ -599,34 +866,57 @@ cudaError_t head_fwd_loss(const __nv_bfloat16* H, const __nv_bfloat16* W5, const
   return cudaGetLastError();
 }
 
-cudaError_t head_bwd(const float* dY, const __nv_bfloat16* H, const __nv_bfloat16* W5, int M, float* dH, float* dWpart,
-                     float* dbpart, float* dW, float* db, cudaStream_t st) {
-  k_head_bwd<<<M / 32, 256, 0, st>>>(dY, H, W5, M, dH, dWpart, dbpart);
-  k_colsum<<<(kOut * kHidden + 127) / 128, 128, 0, st>>>(dWpart, M / 32, kOut * kHidden, dW);
-  k_colsum<<<1, 32, 0, st>>>(dbpart, M / 32, kOut, db);
+cudaError_t head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5, const float* b5, const float* T, const float* Z,
+                       int M, float* Y, float* dY, float* row_loss, __nv_bfloat16* dZ, __nv_bfloat16* dZt, float* colpart,
+                       float* dWpart, float* dbpart, cudaStream_t st) {
+  if (M % kHeadRows) return cudaErrorInvalidValue;
+  k_head_train<<<M / kHeadRows, kHeadThreads, kHeadSmem, st>>>(H, W5, b5, T, Z, M, Y, dY, row_loss, dZ, dZt, colpart, dWpart,
+                                                     dbpart);
+  return cudaGetLastError();
+}
+
+cudaError_t grad_finish(const FinishArgs& a, cudaStream_t st) {
+  static_assert(kFinishW % 256 == 0 && (long long)kFinishW + kFinishR == kNumParams, "every entry once");
+  k_grad_finish<<<kFinishWBlocks + kFinishRBlocks + 1, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && a.adam) e = transpose_layers(a.wb, a.wt, st);
+  return e;
+}
+
+cudaError_t adam_corrections(float b1, float b2, int step, float* bc1, float* bc2) {
+  // bias corrections 1 - beta^t of the FP32 betas the kernels use, formed in
+  // double: in FP32 the cancellation in 1 - 0.999^t would cost up to 2^-24 /
+  // (1 - 0.999^t) of relative precision (1.5e-5 at t = 2)
+  *bc1 = (float)(1.0 - pow((double)b1, (double)step));
+  *bc2 = (float)(1.0 - pow((double)b2, (double)step));
+  return cudaSuccess;
+}
+
+cudaError_t transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st) {
+  k_transpose_layers<<<dim3(kHidden / 32, kHidden / 32, kLayers), dim3(32, 8), 0, st>>>(wb, wt);
   return cudaGetLastError();
 }
 
 cudaError_t adamw(float* w, const float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
                   float wd, int step, const AdamLayout& L, __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st) {
-  // bias corrections 1 - beta^t of the FP32 betas the kernel uses, formed in
-  // double: in FP32 the cancellation in 1 - 0.999^t would cost up to 2^-24 /
-  // (1 - 0.999^t) of relative precision (1.5e-5 at t = 2)
-  const float bc1 = (float)(1.0 - pow((double)b1, (double)step));
-  const float bc2 = (float)(1.0 - pow((double)b2, (double)step));
-  k_adamw<<<(n + 255) / 256, 256, 0, st>>>(w, g, m1, m2, n, lr, b1, b2, eps, wd, bc1, bc2, L, wb, wt);
-  return cudaGetLastError();
+  float bc1, bc2;
+  adam_corrections(b1, b2, step, &bc1, &bc2);
+  k_adamw<<<(n + 255) / 256, 256, 0, st>>>(w, g, m1, m2, n, lr, b1, b2, eps, wd, bc1, bc2, L, wb);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? transpose_layers(wb, wt, st) : e;
 }
 
 cudaError_t pack_params(const float* w, int n, const AdamLayout& L, __nv_bfloat16* wb, __nv_bfloat16* wt,
                         cudaStream_t st) {
-  k_pack_params<<<(n + 255) / 256, 256, 0, st>>>(w, n, L, wb, wt);
-  return cudaGetLastError();
+  k_pack_params<<<(n + 255) / 256, 256, 0, st>>>(w, n, L, wb);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? transpose_layers(wb, wt, st) : e;
 }
 
 cudaError_t featurize(const DevSac* sacs, const float* traces, int n, __nv_bfloat16* X, __nv_bfloat16* Xt, int ldt,
                       cudaStream_t st) {
-  k_featurize<<<(n * 32 + 127) / 128, 128, 0, st>>>(sacs, traces, n, X, Xt, ldt);
+  if (Xt && ldt % 8) return cudaErrorInvalidValue;
+  k_featurize<<<(n + kFeatRows - 1) / kFeatRows, 128, 0, st>>>(sacs, traces, n, X, Xt, ldt);
   return cudaGetLastError();
 }
 
@@ -644,11 +934,6 @@ cudaError_t gen_desc(uint64_t seed, long long base, int n, const float* cal_amp,
 cudaError_t add_noise(uint64_t seed, long long base, const DevSac* sacs, int n, float* traces, float sigma,
                       cudaStream_t st) {
   k_add_noise<<<n, 128, 0, st>>>(seed, base, sacs, n, traces, sigma);
-  return cudaGetLastError();
-}
-
-cudaError_t sum_array(const float* x, int n, float* out, cudaStream_t st) {
-  k_sum<<<1, 256, 0, st>>>(x, n, out);
   return cudaGetLastError();
 }
 

@@ -17,27 +17,53 @@ constexpr int kLayers = 4;                // hidden layers (tensor-core GEMMs)
 constexpr int kOut = 18;                  // OPC vector in log units
 constexpr float kTargetScale = 0.2f;      // output y = ln(p / centre) / 0.2
 
-// GEMM tiling: 128 x 128 output tile, 64-wide K slices, 3-stage ring (99 KB of
-// shared memory, so two CTAs share an SM and one's epilogue overlaps the
-// other's main loop).
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3;
+// GEMM tiling: 128 x 128 output tile, 64-wide K slices in a ring of
+// shared-memory stages: 3 stages (97 KB, two CTAs per SM, so one CTA's
+// epilogue overlaps the other's main loop: large GEMMs) or 6 stages (193 KB,
+// one CTA per SM, a deeper prefetch: the network's one-wave GEMMs).  The
+// epilogue stages its output tile in the ring (free once every MMA has read
+// it) and writes it out in whole rows.
+constexpr int kBM = 128, kBN = 128, kBK = 64;
 constexpr int kTileABytes = kBM * kBK * 2;
 constexpr int kTileBBytes = kBN * kBK * 2;
 constexpr int kStageBytes = kTileABytes + kTileBBytes;
-constexpr int kGemmThreads = 192;         // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
-constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + 1024 + 256;
+constexpr int kGemmThreads = 320;         // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
+constexpr int kGemmTmaWarp = 8, kGemmMmaWarp = 9;
+constexpr size_t gemm_smem(int stages) { return (size_t)stages * kStageBytes + 1024 + 256; }
+constexpr int kMaxGroup = 4;              // GEMM problems of one launch
 
-enum : int { kEpiBiasGelu = 0, kEpiF32 = 1, kEpiBias = 2 };
+// Epilogues: kEpiBiasGelu  z = acc + bias -> out_f32 (z, optional), out_bf16
+//                          = GELU(z), out_t = its transpose (optional);
+//            kEpiF32       out_f32 = acc (K slice s at out_f32 + s * zstride);
+//            kEpiGeluBwd   d = BF16(acc * GELU'(zin)) -> out_bf16, out_t (its
+//                          transpose), colpart[row tile][col] = column sums
+//                          of d over the tile's 128 rows (FP32, in row order).
+// The FP32 epilogue runs with either ring; the others stage 128 KB and take
+// the 6-stage ring.
+enum : int { kEpiBiasGelu = 0, kEpiF32 = 1, kEpiGeluBwd = 3 };
 
-struct GemmArgs {
-  int M, N, K;
-  int epi;                     // kEpi*
-  const float* bias;           // [N] or nullptr
-  __nv_bfloat16* out_bf16;     // [M][ldo] (kEpiBiasGelu, kEpiBias)
-  float* out_f32;              // [M][ldo]: result (kEpiF32) or pre-activation (kEpiBiasGelu, optional)
-  __nv_bfloat16* out_t;        // optional transposed BF16 copy [N][ldt]
-  int ldo, ldt;
-  unsigned* err;
+// Operands and outputs of one problem of a grouped launch: D = A . B^T with
+// A [M][K] and B [N][K] row-major BF16.
+struct GemmProblem {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  const float* bias;           // [N] (kEpiBiasGelu)
+  __nv_bfloat16* out_bf16;     // [M][ldo]
+  float* out_f32;              // [M][ldo]
+  __nv_bfloat16* out_t;        // [N][ldt] or nullptr
+  const float* zin;            // [M][ldo] pre-activations (kEpiGeluBwd)
+  float* colpart;              // [M / 128][N] (kEpiGeluBwd)
+};
+
+// One launch: np problems of the same shape, each split into ksplit slices
+// of K (K / ksplit a multiple of 64).
+struct GemmLaunch {
+  int np = 1, M = 0, N = 0, K = 0, ksplit = 1, epi = kEpiF32;
+  int ldo = 0, ldt = 0;
+  long long zstride = 0;       // elements between the outputs of consecutive K slices
+  int stages = 3;              // 3 or 6
+  unsigned* err = nullptr;
+  GemmProblem p[kMaxGroup] = {};
 };
 
 // Flat FP32 parameter vector: for l < 4, W_l [512 out][in] then b_l [512]
@@ -56,7 +82,8 @@ struct AdamLayout {
     if (i >= kHeadW) return true;
     return (i % kLayerParams) < (long long)kHidden * kHidden;
   }
-  __device__ __forceinline__ void scatter(long long i, float w, __nv_bfloat16* wb, __nv_bfloat16* wt) const {
+  // the row-major BF16 working copy of a weight entry (biases have none)
+  __device__ __forceinline__ void store_bf16(long long i, float w, __nv_bfloat16* wb) const {
     if (i >= kHeadB) return;
     if (i >= kHeadW) {
       wb[(long long)kLayers * kHidden * kHidden + (i - kHeadW)] = __float2bfloat16_rn(w);
@@ -64,23 +91,53 @@ struct AdamLayout {
     }
     const long long l = i / kLayerParams, r = i % kLayerParams;
     if (r >= (long long)kHidden * kHidden) return;
-    const long long o = r / kHidden, c = r % kHidden;
-    const __nv_bfloat16 b = __float2bfloat16_rn(w);
-    wb[l * kHidden * kHidden + r] = b;
-    wt[l * kHidden * kHidden + c * kHidden + o] = b;
+    wb[l * kHidden * kHidden + r] = __float2bfloat16_rn(w);
   }
 };
 
+// Gradient assembly, every sum in a fixed order: hidden weight matrices from
+// the K-slice partials of the weight-gradient GEMM (slice order), hidden
+// biases from the per-row-tile column sums of the rounded errors, the output
+// layer from the head kernel's per-block partials (partials j, j + 32, ...
+// per lane, then a fixed butterfly).  The batch loss (sum of the rows' terms)
+// into *loss when given.  With adam set, each entry's AdamW step follows
+// from its assembled gradient (as k_adamw), and the transposed BF16 copies
+// are refreshed after.
+struct FinishArgs {
+  const float* wpart;          // [4][ksplit][512][512]
+  int ksplit;
+  const float* colpart[kLayers];
+  int ntiles[kLayers];         // partials summed per hidden bias
+  const float* dWpart;         // [nblk][18][512]
+  const float* dbpart;         // [nblk][18]
+  int nblk;
+  const float* row_loss;
+  int M;
+  float* loss;
+  float* g;
+  int adam;
+  float lr, b1, b2, eps, wd, bc1, bc2;
+  float* w;
+  float* m1;
+  float* m2;
+  __nv_bfloat16* wb;
+  __nv_bfloat16* wt;
+};
+
+
 cudaError_t gemm_prepare();
-cudaError_t gemm_tn(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, const GemmArgs& args,
-                    cudaStream_t st);
-cudaError_t transpose_bf16(const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C, cudaStream_t st);
-cudaError_t gelu_bwd(const float* dH, const float* Z, int M, int N, __nv_bfloat16* dZ, __nv_bfloat16* dZt,
-                     float* colpart, float* db, cudaStream_t st);
+cudaError_t gemm(const GemmLaunch& L, cudaStream_t st);
 cudaError_t head_fwd_loss(const __nv_bfloat16* H, const __nv_bfloat16* W5, const float* b5, const float* T, int M,
                           float* Y, float* dY, float* row_loss, cudaStream_t st);
-cudaError_t head_bwd(const float* dY, const __nv_bfloat16* H, const __nv_bfloat16* W5, int M, float* dH, float* dWpart,
-                     float* dbpart, float* dW, float* db, cudaStream_t st);
+// Training head: output layer, loss terms, dY, the layer-3 error dZ3 (and
+// its transpose and per-32-row column sums), output-layer gradient partials
+// per 32-row block.  M a multiple of 32.
+cudaError_t head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5, const float* b5, const float* T, const float* Z,
+                       int M, float* Y, float* dY, float* row_loss, __nv_bfloat16* dZ, __nv_bfloat16* dZt, float* colpart,
+                       float* dWpart, float* dbpart, cudaStream_t st);
+cudaError_t grad_finish(const FinishArgs& a, cudaStream_t st);
+cudaError_t adam_corrections(float b1, float b2, int step, float* bc1, float* bc2);
+cudaError_t transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st);
 cudaError_t adamw(float* w, const float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
                   float wd, int step, const AdamLayout& L, __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st);
 cudaError_t pack_params(const float* w, int n, const AdamLayout& L, __nv_bfloat16* wb, __nv_bfloat16* wt,
@@ -92,7 +149,6 @@ cudaError_t gen_desc(uint64_t seed, long long base, int n, const float* cal_amp,
                      DevSac* sacs, float* hidden, float* target, int lcap, cudaStream_t st);
 cudaError_t add_noise(uint64_t seed, long long base, const DevSac* sacs, int n, float* traces, float sigma,
                       cudaStream_t st);
-cudaError_t sum_array(const float* x, int n, float* out, cudaStream_t st);
 
 }  // namespace mlp
 }  // namespace opmm

@@ -28,9 +28,11 @@ constexpr int kTrainLcap = 400;         // longest training window
 }  // namespace
 
 // Activations and gradients of one batch of M rows (M a multiple of 128).
+constexpr int kWgradSplit = 2;          // K slices of the weight-gradient GEMM
 struct MlpBuffers {
   int M = 0;
-  DevBuf X, Xt, H[kLayers], Ht[kLayers], Z[kLayers], Y, dY, rowloss, dH, dZ, dZt, colpart, dWpart, dbpart;
+  DevBuf X, Xt, H[kLayers], Ht[kLayers], Z[kLayers], Y, dY, rowloss, dZ[kLayers], dZt[kLayers], colpart[kLayers],
+      wpart, dWpart, dbpart;
   Status ensure(int m) {
     if (m <= M) return Status();
     Status s;
@@ -41,14 +43,15 @@ struct MlpBuffers {
       s = H[l].ensure(act * 2);
       if (s.ok()) s = Ht[l].ensure(act * 2);
       if (s.ok()) s = Z[l].ensure(act * 4);
+      if (s.ok()) s = dZ[l].ensure(act * 2);
+      if (s.ok()) s = dZt[l].ensure(act * 2);
+      // column sums per 128-row tile (GEMM epilogue) or per 32-row block (head)
+      if (s.ok()) s = colpart[l].ensure((size_t)(m / (l == kLayers - 1 ? 32 : kBM)) * kHidden * 4);
     }
     if (s.ok()) s = Y.ensure((size_t)m * kOut * 4);
     if (s.ok()) s = dY.ensure((size_t)m * kOut * 4);
     if (s.ok()) s = rowloss.ensure((size_t)m * 4);
-    if (s.ok()) s = dH.ensure(act * 4);
-    if (s.ok()) s = dZ.ensure(act * 2);
-    if (s.ok()) s = dZt.ensure(act * 2);
-    if (s.ok()) s = colpart.ensure((size_t)(m / 32) * kHidden * 4);
+    if (s.ok()) s = wpart.ensure((size_t)kLayers * kWgradSplit * kHidden * kHidden * 4);
     if (s.ok()) s = dWpart.ensure((size_t)(m / 32) * kOut * kHidden * 4);
     if (s.ok()) s = dbpart.ensure((size_t)(m / 32) * kOut * 4);
     if (s.ok()) M = m;
@@ -122,58 +125,134 @@ static Status refresh_copies(opmm_ctx* ctx) {
   return cuda_status(pack_params(f32(S.w), (int)kNumParams, AdamLayout{}, bf(S.wb), bf(S.wt), ctx->stream), "pack");
 }
 
-// Forward pass of M rows from B.X (and B.Xt): hidden layers on the tensor
-// cores, output layer (and, with T, loss and its gradient) on CUDA cores.
-static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, const float* T, bool keep_transposes, cudaStream_t st) {
+// Hidden layers of M rows from B.X on the tensor cores: Z (pre-activation,
+// FP32), H = GELU(Z) (BF16) and, for training, H's transpose.
+static Status forward_hidden(opmm_ctx* ctx, MlpBuffers& B, int M, bool keep_transposes, cudaStream_t st) {
   SurrogateState& S = *ctx->surrogate;
   for (int l = 0; l < kLayers; ++l) {
-    GemmArgs a{};
-    a.epi = kEpiBiasGelu;
-    a.bias = f32(S.w, (size_t)l * kLayerParams + (size_t)kHidden * kHidden);
-    a.out_bf16 = bf(B.H[l]);
-    a.out_f32 = f32(B.Z[l]);
-    a.out_t = keep_transposes ? bf(B.Ht[l]) : nullptr;
-    a.ldo = kHidden;
-    a.ldt = M;
-    a.err = ctx->d_err.as<unsigned>();
-    const __nv_bfloat16* in = l == 0 ? bf(B.X) : bf(B.H[l - 1]);
-    Status s = cuda_status(gemm_tn(in, bf(S.wb, (size_t)l * kHidden * kHidden), M, kHidden, kHidden, a, st), "GEMM fwd");
+    GemmLaunch L;
+    L.M = M;
+    L.N = kHidden;
+    L.K = kHidden;
+    L.epi = kEpiBiasGelu;
+    L.ldo = kHidden;
+    L.ldt = M;
+    L.stages = 6;
+    L.err = ctx->d_err.as<unsigned>();
+    GemmProblem& p = L.p[0];
+    p.A = l == 0 ? bf(B.X) : bf(B.H[l - 1]);
+    p.B = bf(S.wb, (size_t)l * kHidden * kHidden);
+    p.bias = f32(S.w, (size_t)l * kLayerParams + (size_t)kHidden * kHidden);
+    p.out_bf16 = bf(B.H[l]);
+    p.out_f32 = f32(B.Z[l]);
+    p.out_t = keep_transposes ? bf(B.Ht[l]) : nullptr;
+    Status s = cuda_status(gemm(L, st), "GEMM fwd");
     if (!s.ok()) return s;
   }
+  return Status();
+}
+
+// Inference: hidden layers, then the output layer on CUDA cores into B.Y.
+static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, cudaStream_t st) {
+  SurrogateState& S = *ctx->surrogate;
+  Status s = forward_hidden(ctx, B, M, false, st);
+  if (!s.ok()) return s;
   return cuda_status(head_fwd_loss(bf(B.H[kLayers - 1]), bf(S.wb, (size_t)kLayers * kHidden * kHidden),
-                                   f32(S.w, kHeadB), T, M, f32(B.Y), f32(B.dY), T ? f32(B.rowloss) : nullptr, st),
+                                   f32(S.w, kHeadB), nullptr, M, f32(B.Y), f32(B.dY), nullptr, st),
                      "head");
 }
 
-// Backward pass into S.g (after forward with T and transposes kept).
-static Status backward(opmm_ctx* ctx, MlpBuffers& B, int M) {
+// One training pass of M rows against targets T into S.g (and the batch
+// loss into *loss when given): hidden layers; the head kernel (output layer,
+// loss terms, output-layer gradient partials, the layer-3 error); the error
+// of layers 2, 1, 0 by GEMMs whose epilogue applies GELU' and rounds
+// (dZ_{l-1} = BF16((dZ_l . W_l) * GELU'(Z_{l-1}))); all four weight gradients
+// dW_l = dZ_l^T . H_{l-1} in one grouped launch over two K slices; the
+// gradient assembly, with the AdamW step of every entry when `adam` is given.
+struct AdamStep {
+  float lr, wd;
+  int step;   // t >= 1
+};
+static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const float* T, float* loss, const AdamStep* adam,
+                         cudaStream_t st) {
   SurrogateState& S = *ctx->surrogate;
-  cudaStream_t st = ctx->stream;
-  Status s = cuda_status(head_bwd(f32(B.dY), bf(B.H[kLayers - 1]), bf(S.wb, (size_t)kLayers * kHidden * kHidden), M,
-                                  f32(B.dH), f32(B.dWpart), f32(B.dbpart), f32(S.g, kHeadW), f32(S.g, kHeadB), st),
-                         "head backward");
-  for (int l = kLayers - 1; l >= 0 && s.ok(); --l) {
-    const size_t wo = (size_t)l * kLayerParams;
-    s = cuda_status(gelu_bwd(f32(B.dH), f32(B.Z[l]), M, kHidden, bf(B.dZ), bf(B.dZt), f32(B.colpart),
-                             f32(S.g, wo + (size_t)kHidden * kHidden), st),
-                    "GELU backward");
-    if (!s.ok()) break;
-    // dW[n][k] = sum_m dZ[m][n] H_{l-1}[m][k]
-    GemmArgs a{};
-    a.epi = kEpiF32;
-    a.out_f32 = f32(S.g, wo);
-    a.ldo = kHidden;
-    a.err = ctx->d_err.as<unsigned>();
-    const __nv_bfloat16* ht = l == 0 ? bf(B.Xt) : bf(B.Ht[l - 1]);
-    s = cuda_status(gemm_tn(bf(B.dZt), ht, kHidden, kHidden, M, a, st), "GEMM wgrad");
-    if (!s.ok() || l == 0) break;
-    // dH_{l-1}[m][k] = sum_n dZ[m][n] W_l[n][k]
-    GemmArgs d{};
-    d.epi = kEpiF32;
-    d.out_f32 = f32(B.dH);
-    d.ldo = kHidden;
-    d.err = ctx->d_err.as<unsigned>();
-    s = cuda_status(gemm_tn(bf(B.dZ), bf(S.wt, (size_t)l * kHidden * kHidden), M, kHidden, kHidden, d, st), "GEMM dgrad");
+  Status s = forward_hidden(ctx, B, M, true, st);
+  if (!s.ok()) return s;
+  s = cuda_status(head_train(bf(B.H[kLayers - 1]), bf(S.wb, (size_t)kLayers * kHidden * kHidden), f32(S.w, kHeadB), T,
+                             f32(B.Z[kLayers - 1]), M, f32(B.Y), f32(B.dY), f32(B.rowloss), bf(B.dZ[kLayers - 1]),
+                             bf(B.dZt[kLayers - 1]), f32(B.colpart[kLayers - 1]), f32(B.dWpart), f32(B.dbpart), st),
+                  "head");
+  for (int l = kLayers - 1; l >= 1 && s.ok(); --l) {
+    // dZ_{l-1} from dH_{l-1}[m][k] = sum_n dZ_l[m][n] W_l[n][k]
+    GemmLaunch L;
+    L.M = M;
+    L.N = kHidden;
+    L.K = kHidden;
+    L.epi = kEpiGeluBwd;
+    L.ldo = kHidden;
+    L.ldt = M;
+    L.stages = 6;
+    L.err = ctx->d_err.as<unsigned>();
+    GemmProblem& p = L.p[0];
+    p.A = bf(B.dZ[l]);
+    p.B = bf(S.wt, (size_t)l * kHidden * kHidden);
+    p.zin = f32(B.Z[l - 1]);
+    p.out_bf16 = bf(B.dZ[l - 1]);
+    p.out_t = bf(B.dZt[l - 1]);
+    p.colpart = f32(B.colpart[l - 1]);
+    s = cuda_status(gemm(L, st), "GEMM dgrad");
+  }
+  if (s.ok()) {
+    // dW_l[n][k] = sum_m dZ_l[m][n] H_{l-1}[m][k], K = M split in slices
+    GemmLaunch L;
+    L.np = kLayers;
+    L.M = kHidden;
+    L.N = kHidden;
+    L.K = M;
+    L.ksplit = M >= 2 * kBM ? kWgradSplit : 1;
+    L.epi = kEpiF32;
+    L.ldo = kHidden;
+    L.zstride = (long long)kHidden * kHidden;
+    L.stages = 6;
+    L.err = ctx->d_err.as<unsigned>();
+    for (int l = 0; l < kLayers; ++l) {
+      GemmProblem& p = L.p[l];
+      p.A = bf(B.dZt[l]);
+      p.B = l == 0 ? bf(B.Xt) : bf(B.Ht[l - 1]);
+      p.out_f32 = f32(B.wpart, (size_t)l * L.ksplit * kHidden * kHidden);
+    }
+    s = cuda_status(gemm(L, st), "GEMM wgrad");
+    if (s.ok()) {
+      FinishArgs a{};
+      a.wpart = f32(B.wpart);
+      a.ksplit = L.ksplit;
+      for (int l = 0; l < kLayers; ++l) {
+        a.colpart[l] = f32(B.colpart[l]);
+        a.ntiles[l] = l == kLayers - 1 ? M / 32 : M / kBM;
+      }
+      a.dWpart = f32(B.dWpart);
+      a.dbpart = f32(B.dbpart);
+      a.nblk = M / 32;
+      a.row_loss = f32(B.rowloss);
+      a.M = M;
+      a.loss = loss;
+      a.g = f32(S.g);
+      if (adam) {
+        a.adam = 1;
+        a.lr = adam->lr;
+        a.wd = adam->wd;
+        a.b1 = 0.9f;
+        a.b2 = 0.999f;
+        a.eps = 1e-8f;
+        adam_corrections(a.b1, a.b2, adam->step, &a.bc1, &a.bc2);
+        a.w = f32(S.w);
+        a.m1 = f32(S.m1);
+        a.m2 = f32(S.m2);
+        a.wb = bf(S.wb);
+        a.wt = bf(S.wt);
+      }
+      s = cuda_status(grad_finish(a, st), adam ? "gradient assembly and AdamW" : "gradient assembly");
+    }
   }
   return s;
 }
@@ -190,7 +269,7 @@ Status surrogate_centres(opmm_ctx* ctx, const DevSac* sacs, const float* traces,
     if (!s.ok()) return s;
   }
   Status s = cuda_status(featurize(sacs, traces, n, bf(B.X), nullptr, M, st), "featurize");
-  if (s.ok()) s = forward(ctx, B, M, nullptr, false, st);
+  if (s.ok()) s = forward(ctx, B, M, st);
   if (s.ok()) s = cuda_status(apply_centres(f32(B.Y), n, pc, st), "centres");
   return s;
 }
@@ -225,7 +304,7 @@ Status surrogate_prepare_plan(opmm_ctx* ctx, opmm_plan* p, const opmm_saccade*, 
     (void)saved;
     Status r = cuda_status(featurize(pl->d_sacs.as<DevSac>(), pl->d_traces.as<float>(), pl->n, bf(keep->X), nullptr, M, st),
                            "featurize");
-    if (r.ok()) r = forward(c, *keep, M, nullptr, false, st);
+    if (r.ok()) r = forward(c, *keep, M, st);
     if (r.ok()) r = cuda_status(apply_centres(f32(keep->Y), pl->n, pl->d_pc.as<float>(), st), "centres");
     return r;
   };
@@ -321,8 +400,7 @@ extern "C" int opmm_surrogate_grad(opmm_ctx* ctx, const float* x, const float* t
   STRY(cuda_status(cudaMemcpyAsync(B.Xt.ptr, xt.data(), xt.size() * 2, cudaMemcpyHostToDevice, st), "H2D Xt"));
   STRY(cuda_status(cudaMemcpyAsync(dt.ptr, t, (size_t)m * kOut * 4, cudaMemcpyHostToDevice, st), "H2D T"));
   STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, st), "clear error"));
-  STRY(forward(ctx, B, m, f32(dt), true, st));
-  STRY(backward(ctx, B, m));
+  STRY(train_pass(ctx, B, m, f32(dt), nullptr, nullptr, st));
   std::vector<float> rl((size_t)m);
   STRY(cuda_status(cudaMemcpyAsync(rl.data(), B.rowloss.ptr, (size_t)m * 4, cudaMemcpyDeviceToHost, st), "D2H loss"));
   STRY(cuda_status(cudaMemcpyAsync(grad, S.g.ptr, (size_t)kNumParams * 4, cudaMemcpyDeviceToHost, st), "D2H grad"));
@@ -385,13 +463,9 @@ extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch,
                                      f32(S.traces), st), "simulate"));
     STRY(cuda_status(add_noise(data_seed, base, S.sacs.as<DevSac>(), batch, f32(S.traces), 0.05f, st), "noise"));
     STRY(cuda_status(featurize(S.sacs.as<DevSac>(), f32(S.traces), batch, bf(B.X), bf(B.Xt), batch, st), "featurize"));
-    STRY(forward(ctx, B, batch, f32(S.target), true, st));
-    STRY(backward(ctx, B, batch));
+    const AdamStep step{lr, weight_decay, S.step + 1};
+    STRY(train_pass(ctx, B, batch, f32(S.target), f32(S.losses, (size_t)it), &step, st));
     S.step += 1;
-    STRY(cuda_status(adamw(f32(S.w), f32(S.g), f32(S.m1), f32(S.m2), (int)kNumParams, lr, 0.9f, 0.999f, 1e-8f,
-                           weight_decay, S.step, AdamLayout{}, bf(S.wb), bf(S.wt), st), "AdamW"));
-    // batch loss (sum of per-row contributions, fixed order)
-    STRY(cuda_status(sum_array(f32(B.rowloss), batch, f32(S.losses, (size_t)it), st), "loss"));
   }
   if (losses && steps > 0)
     STRY(cuda_status(cudaMemcpyAsync(losses, S.losses.ptr, (size_t)steps * 4, cudaMemcpyDeviceToHost, st), "D2H losses"));
@@ -496,14 +570,19 @@ extern "C" int opmm_gemm_bf16(opmm_ctx* ctx, const void* A, const void* B, int32
     return sfail(ctx, Status(OPMM_EINVAL, "gemm: device pointers required"));
   STRY(cuda_status(cudaSetDevice(ctx->device), "cudaSetDevice"));
   STRY(cuda_status(gemm_prepare(), "GEMM attributes"));
-  GemmArgs a{};
-  a.epi = kEpiF32;
-  a.out_f32 = D;
-  a.ldo = N;
-  a.err = ctx->d_err.as<unsigned>();
+  GemmLaunch L;
+  L.M = M;
+  L.N = N;
+  L.K = K;
+  L.epi = kEpiF32;
+  L.ldo = N;
+  L.stages = 3;
+  L.err = ctx->d_err.as<unsigned>();
+  L.p[0].A = static_cast<const __nv_bfloat16*>(A);
+  L.p[0].B = static_cast<const __nv_bfloat16*>(B);
+  L.p[0].out_f32 = D;
   STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, ctx->stream), "clear error"));
-  STRY(cuda_status(gemm_tn(static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), M, N, K, a,
-                           ctx->stream), "GEMM"));
+  STRY(cuda_status(gemm(L, ctx->stream), "GEMM"));
   unsigned e = 0;
   STRY(cuda_status(cudaMemcpyAsync(&e, ctx->d_err.ptr, 4, cudaMemcpyDeviceToHost, ctx->stream), "D2H error"));
   STRY(cuda_status(cudaStreamSynchronize(ctx->stream), "gemm"));
