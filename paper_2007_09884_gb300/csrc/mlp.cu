@@ -83,6 +83,21 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 64 consecutive FP32 accumulator columns of this thread's TMEM lane, with
+// the wait for the load in the same statement (the registers are not valid
+// before it).
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzling:
 // rows of 64 BF16 (128 B), 8-row core groups 1024 B apart (stride byte
 // offset), leading byte offset unused by this layout, descriptor version 1,
@@ -220,7 +235,31 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
       tc_commit(done);
     }
   } else {
-    // epilogue
+    // epilogue.  Before the accumulator is ready (overlapping the main loop):
+    // the tile's bias in shared memory (kEpiBiasGelu) or GELU' of this
+    // thread's 64 pre-activations (kEpiGeluBwd).
+    const GemmProblem& P = g.p[prob];
+    const int tid = threadIdx.x;                 // 0..255
+    const int q = warp & 3;                      // TMEM lane quarter
+    const int r = q * 32 + lane;                 // tile row
+    const int row = tm * kBM + r;
+    const int cb = (warp >> 2) * 64;             // first tile column of this warp
+    float* sbias = reinterpret_cast<float*>(sm + STAGES * kStageBytes + 256);   // [128], after the barriers
+    float gz[EPI == kEpiGeluBwd ? 64 : 1];
+    if constexpr (EPI == kEpiBiasGelu) {
+      if (tid < kBN) sbias[tid] = P.bias[tn * kBN + tid];
+    }
+    if constexpr (EPI == kEpiGeluBwd) {
+      const float4* zp = reinterpret_cast<const float4*>(P.zin + (size_t)row * g.ldo + tn * kBN + cb);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float4 z = zp[i];
+        gz[4 * i] = gelu_grad(z.x);
+        gz[4 * i + 1] = gelu_grad(z.y);
+        gz[4 * i + 2] = gelu_grad(z.z);
+        gz[4 * i + 3] = gelu_grad(z.w);
+      }
+    }
     const bool ok = mbar_wait(done, 0u, kMaxWaitTries);
     if (!ok) {
       raise_error(g.err, kErrWaitTimeout);
@@ -230,11 +269,6 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     epi_bar();
     const bool go = *reinterpret_cast<volatile int*>(bail) == 0;
-    const GemmProblem& P = g.p[prob];
-    const int tid = threadIdx.x;                 // 0..255
-    const int q = warp & 3;                      // TMEM lane quarter
-    const int r = q * 32 + lane;                 // tile row
-    const int row = tm * kBM + r;
     const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
     unsigned char* Sf = sm;                      // [128][128] FP32, chunks ^ (row & 7)
     unsigned char* Sbf = sm + 65536;             // [128][128] BF16, chunks ^ (row & 7)
@@ -242,41 +276,33 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
     const bool want_f32 = EPI == kEpiF32 || (EPI == kEpiBiasGelu && P.out_f32 != nullptr);
     const bool want_t = EPI != kEpiF32 && P.out_t != nullptr;
     if (go) {
-#pragma unroll 1
-      for (int c = 0; c < 64; c += 16) {
-        const int col0 = (warp >> 2) * 64 + c;   // column within the tile
-        const int col = tn * kBN + col0;         // column of D
-        float v[16];
-        tc_ld16(tbase + (uint32_t)col0, v);
-        if constexpr (EPI == kEpiGeluBwd) {
-          const float4* zp = reinterpret_cast<const float4*>(P.zin + (size_t)row * g.ldo + col);
+      float v[64];
+      tc_ld64(tbase + (uint32_t)cb, v);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float4 z = zp[i];
-            v[4 * i] *= gelu_grad(z.x);
-            v[4 * i + 1] *= gelu_grad(z.y);
-            v[4 * i + 2] *= gelu_grad(z.z);
-            v[4 * i + 3] *= gelu_grad(z.w);
-          }
+      for (int c = 0; c < 64; c += 16) {
+        const int col0 = cb + c;                 // column within the tile
+        if constexpr (EPI == kEpiGeluBwd) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[c + i] *= gz[c + i];
         }
         if constexpr (EPI == kEpiBiasGelu) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += P.bias[col + i];
+          for (int i = 0; i < 16; ++i) v[c + i] += sbias[col0 + i];
         }
         if (want_f32) {
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             *reinterpret_cast<float4*>(Sf + r * 512 + ((((col0 >> 2) + j) ^ (r & 7)) << 4)) =
-                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                make_float4(v[c + 4 * j], v[c + 4 * j + 1], v[c + 4 * j + 2], v[c + 4 * j + 3]);
         }
         if constexpr (EPI != kEpiF32) {
           if constexpr (EPI == kEpiBiasGelu) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+            for (int i = 0; i < 16; ++i) v[c + i] = gelu(v[c + i]);
           }
           __nv_bfloat162 h[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[c + 2 * i], v[c + 2 * i + 1]);
 #pragma unroll
           for (int j = 0; j < 2; ++j)
             *reinterpret_cast<uint4*>(Sbf + r * 256 + ((((col0 >> 3) + j) ^ (r & 7)) << 4)) =
@@ -386,16 +412,16 @@ __global__ void k_head_fwd_loss(const __nv_bfloat16* H, const __nv_bfloat16* W5,
 // block's partial sums of dW5[o][k] = sum_m dY[m][o] H3[m][k] (and of db5 =
 // sum_m dY), dH3 = dY . W5 and the rounded layer-3 error dZ3 = BF16(dH3 *
 // GELU'(Z3)), written row-major and transposed (through shared memory, in
-// whole rows) with its column sums over the block's rows.  W5, the block's
-// H3 and Z3 rows are staged in shared memory first.  Every sum runs in a
-// fixed order.
+// whole rows) with its column sums over the block's rows.  W5 (as FP32) and
+// the block's H3 rows are staged in shared memory; each thread's 32 Z3
+// values are loaded at the start, so their latency overlaps the forward
+// part.  Every sum runs in a fixed order.
 constexpr int kHeadRows = 32;
 constexpr int kHeadThreads = 512;
 static_assert(kHeadThreads == kHidden && kHeadRows == 2 * (kHeadThreads / 32), "one thread per column, two rows per warp");
 constexpr int kSdzPitch = kHidden + 2;     // BF16 elements: rows one bank apart
-constexpr size_t kHeadSmem = (size_t)kOut * kHidden * 2 + (size_t)kHeadRows * kHidden * 2 +
-                             (size_t)kHeadRows * kHidden * 4 + (size_t)kHeadRows * kSdzPitch * 2 +
-                             (size_t)kHeadRows * kOut * 4;
+constexpr size_t kHeadSmem = (size_t)kOut * kHidden * 4 + (size_t)kHeadRows * kHidden * 2 +
+                             (size_t)kHeadRows * kSdzPitch * 2 + (size_t)kHeadRows * kOut * 4;
 
 __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5,
                                                              const float* b5, const float* T, const float* Z, int M,
@@ -403,35 +429,40 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
                                                              __nv_bfloat16* dZt, float* colpart, float* dWpart,
                                                              float* dbpart) {
   extern __shared__ __align__(16) unsigned char hsm[];
-  __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(hsm);                     // [18][512]
-  __nv_bfloat16* sh = sw + kOut * kHidden;                                      // [32][512]
-  float* sz = reinterpret_cast<float*>(sh + kHeadRows * kHidden);               // [32][512]
-  __nv_bfloat16* sdz = reinterpret_cast<__nv_bfloat16*>(sz + kHeadRows * kHidden);   // [32][kSdzPitch]
+  float* sw = reinterpret_cast<float*>(hsm);                                    // [18][512]
+  __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sw + kOut * kHidden);   // [32][512]
+  __nv_bfloat16* sdz = sh + kHeadRows * kHidden;                                // [32][kSdzPitch]
   float* sdy = reinterpret_cast<float*>(sdz + kHeadRows * kSdzPitch);           // [32][18]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = blockIdx.x * kHeadRows;
+  float z[kHeadRows];
+#pragma unroll
+  for (int i = 0; i < kHeadRows; ++i) z[i] = Z[(size_t)(r0 + i) * kHidden + tid];
+  for (int i = tid; i < kOut * kHidden / 2; i += kHeadThreads) {
+    const float2 w = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(W5)[i]);
+    reinterpret_cast<float2*>(sw)[i] = w;
+  }
   {
-    const uint4* src = reinterpret_cast<const uint4*>(W5);
-    uint4* dst = reinterpret_cast<uint4*>(sw);
-    for (int i = tid; i < kOut * kHidden / 8; i += kHeadThreads) dst[i] = src[i];
     const uint4* hs = reinterpret_cast<const uint4*>(H + (size_t)r0 * kHidden);
     uint4* hd = reinterpret_cast<uint4*>(sh);
     for (int i = tid; i < kHeadRows * kHidden / 8; i += kHeadThreads) hd[i] = hs[i];
-    const uint4* zs = reinterpret_cast<const uint4*>(Z + (size_t)r0 * kHidden);
-    uint4* zd = reinterpret_cast<uint4*>(sz);
-    for (int i = tid; i < kHeadRows * kHidden / 4; i += kHeadThreads) zd[i] = zs[i];
   }
   __syncthreads();
-  // forward and loss: warp w takes rows 2 w, 2 w + 1
+  // forward and loss: warp w takes rows 2 w, 2 w + 1; lane l the column
+  // pairs 2 l + 64 j
   for (int i = 2 * warp; i < 2 * warp + 2; ++i) {
     const int m = r0 + i;
     float acc[kOut];
 #pragma unroll
     for (int o = 0; o < kOut; ++o) acc[o] = 0.0f;
-    for (int k = lane; k < kHidden; k += 32) {
-      const float h = __bfloat162float(sh[i * kHidden + k]);
+#pragma unroll 2
+    for (int k = 2 * lane; k < kHidden; k += 64) {
+      const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(sh + i * kHidden + k));
 #pragma unroll
-      for (int o = 0; o < kOut; ++o) acc[o] = fmaf(h, __bfloat162float(sw[o * kHidden + k]), acc[o]);
+      for (int o = 0; o < kOut; ++o) {
+        const float2 w = *reinterpret_cast<const float2*>(sw + o * kHidden + k);
+        acc[o] = fmaf(h.y, w.y, fmaf(h.x, w.x, acc[o]));
+      }
     }
     float l = 0.0f;
 #pragma unroll
@@ -458,18 +489,26 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
     float w[kOut], gw[kOut];
 #pragma unroll
     for (int o = 0; o < kOut; ++o) {
-      w[o] = __bfloat162float(sw[o * kHidden + k]);
+      w[o] = sw[o * kHidden + k];
       gw[o] = 0.0f;
     }
+#pragma unroll
     for (int i = 0; i < kHeadRows; ++i) {
       const float h = __bfloat162float(sh[i * kHidden + k]);
+      float dy[kOut];
+#pragma unroll
+      for (int o = 0; o < kOut; o += 2) {
+        const float2 t = *reinterpret_cast<const float2*>(sdy + i * kOut + o);
+        dy[o] = t.x;
+        dy[o + 1] = t.y;
+      }
       float s = 0.0f;
 #pragma unroll
       for (int o = 0; o < kOut; ++o) {
-        s = fmaf(sdy[i * kOut + o], w[o], s);
-        gw[o] = fmaf(sdy[i * kOut + o], h, gw[o]);
+        s = fmaf(dy[o], w[o], s);
+        gw[o] = fmaf(dy[o], h, gw[o]);
       }
-      const float d = s * gelu_grad(sz[i * kHidden + k]);
+      const float d = s * gelu_grad(z[i]);
       sdz[i * kSdzPitch + k] = __float2bfloat16_rn(d);
     }
 #pragma unroll
@@ -503,19 +542,28 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
   }
 }
 
-// One AdamW step of entry i with gradient gi (decoupled weight decay on
-// weight matrices only), refreshing its row-major BF16 working copy.
+// One AdamW step on one entry with gradient gi: moments m1, m2, then
+// decoupled weight decay (weight matrices only) and the bias-corrected step.
+__device__ __forceinline__ void adamw_math(float gi, float& m1, float& m2, float& w, bool decay, float lr, float b1,
+                                           float b2, float eps, float wd, float bc1, float bc2) {
+  const float a = b1 * m1 + (1.0f - b1) * gi;
+  const float b = b2 * m2 + (1.0f - b2) * gi * gi;
+  m1 = a;
+  m2 = b;
+  float wi = w;
+  if (decay) wi -= lr * wd * wi;
+  wi -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
+  w = wi;
+}
+
+// The AdamW step of flat entry i, refreshing its row-major BF16 working copy.
 __device__ __forceinline__ void adamw_update(long long i, float gi, float* w, float* m1, float* m2, float lr, float b1,
                                              float b2, float eps, float wd, float bc1, float bc2, const AdamLayout& L,
                                              __nv_bfloat16* wb) {
-  const float a = b1 * m1[i] + (1.0f - b1) * gi;
-  const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+  float a = m1[i], b = m2[i], wi = w[i];
+  adamw_math(gi, a, b, wi, L.is_weight(i), lr, b1, b2, eps, wd, bc1, bc2);
   m1[i] = a;
   m2[i] = b;
-  const bool decay = L.is_weight(i);
-  float wi = w[i];
-  if (decay) wi -= lr * wd * wi;
-  wi -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
   w[i] = wi;
   L.store_bf16(i, wi, wb);
 }
@@ -538,14 +586,15 @@ __global__ void k_pack_params(const float* w, int n, const AdamLayout L, __nv_bf
 }
 
 // Gradient assembly and, when a.adam is set, the AdamW step (see FinishArgs).
-// Blocks [0, kFinishWBlocks): one thread per hidden weight entry, summing the
-// K-slice partials in slice order.  The next kFinishRBlocks blocks: one warp
+// Blocks [0, kFinishWBlocks): four consecutive hidden weight entries per
+// thread (16-byte loads and stores), each summing its K-slice partials in
+// slice order.  The next kFinishRBlocks blocks: one warp
 // per bias or output-layer entry, lane j summing partials j, j + 32, ... in
 // order, then a fixed butterfly across the lanes.  The last block: the batch
 // loss (strided per thread, then a tree over the block).
 constexpr int kFinishW = kLayers * kHidden * kHidden;                     // hidden weight entries
 constexpr int kFinishR = kLayers * kHidden + kOut * kHidden + kOut;       // reduced entries
-constexpr int kFinishWBlocks = kFinishW / 256;
+constexpr int kFinishWBlocks = kFinishW / 1024;
 constexpr int kFinishRBlocks = (kFinishR + 7) / 8;
 
 __global__ void __launch_bounds__(256) k_grad_finish(const __grid_constant__ FinishArgs a) {
@@ -566,15 +615,34 @@ __global__ void __launch_bounds__(256) k_grad_finish(const __grid_constant__ Fin
   }
   constexpr long long kW = (long long)kHidden * kHidden;
   if (blockIdx.x < kFinishWBlocks) {
-    const int e = blockIdx.x * 256 + tid;
+    static_assert(kW % 4 == 0 && kLayerParams % 4 == 0, "16-byte groups stay within a matrix");
+    const int e = (blockIdx.x * 256 + tid) * 4;
     const int l = e / (int)kW;
     const long long r = e - (long long)l * kW;
     const float* p = a.wpart + (size_t)l * a.ksplit * kW + r;
-    float v = 0.0f;
-    for (int s = 0; s < a.ksplit; ++s) v += p[(size_t)s * kW];
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int s = 0; s < a.ksplit; ++s) {
+      const float4 x = *reinterpret_cast<const float4*>(p + (size_t)s * kW);
+      v[0] += x.x;
+      v[1] += x.y;
+      v[2] += x.z;
+      v[3] += x.w;
+    }
     const long long i = (long long)l * kLayerParams + r;
-    a.g[i] = v;
-    if (a.adam) adamw_update(i, v, a.w, a.m1, a.m2, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, AdamLayout{}, a.wb);
+    *reinterpret_cast<float4*>(a.g + i) = make_float4(v[0], v[1], v[2], v[3]);
+    if (a.adam) {
+      const float4 m1 = *reinterpret_cast<const float4*>(a.m1 + i);
+      const float4 m2 = *reinterpret_cast<const float4*>(a.m2 + i);
+      const float4 w = *reinterpret_cast<const float4*>(a.w + i);
+      float am[4] = {m1.x, m1.y, m1.z, m1.w}, av[4] = {m2.x, m2.y, m2.z, m2.w}, aw[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) adamw_math(v[j], am[j], av[j], aw[j], true, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2);
+      *reinterpret_cast<float4*>(a.m1 + i) = make_float4(am[0], am[1], am[2], am[3]);
+      *reinterpret_cast<float4*>(a.m2 + i) = make_float4(av[0], av[1], av[2], av[3]);
+      *reinterpret_cast<float4*>(a.w + i) = make_float4(aw[0], aw[1], aw[2], aw[3]);
+      __nv_bfloat162 b[2] = {__floats2bfloat162_rn(aw[0], aw[1]), __floats2bfloat162_rn(aw[2], aw[3])};
+      *reinterpret_cast<uint2*>(a.wb + (size_t)l * kW + r) = *reinterpret_cast<const uint2*>(b);
+    }
     return;
   }
   const int e = (blockIdx.x - kFinishWBlocks) * 8 + (tid >> 5);
@@ -876,7 +944,7 @@ cudaError_t head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5, const fl
 }
 
 cudaError_t grad_finish(const FinishArgs& a, cudaStream_t st) {
-  static_assert(kFinishW % 256 == 0 && (long long)kFinishW + kFinishR == kNumParams, "every entry once");
+  static_assert(kFinishW % 1024 == 0 && (long long)kFinishW + kFinishR == kNumParams, "every entry once");
   k_grad_finish<<<kFinishWBlocks + kFinishRBlocks + 1, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && a.adam) e = transpose_layers(a.wb, a.wt, st);

@@ -29,7 +29,9 @@ constexpr int kTileBBytes = kBN * kBK * 2;
 constexpr int kStageBytes = kTileABytes + kTileBBytes;
 constexpr int kGemmThreads = 320;         // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
 constexpr int kGemmTmaWarp = 8, kGemmMmaWarp = 9;
-constexpr size_t gemm_smem(int stages) { return (size_t)stages * kStageBytes + 1024 + 256; }
+// ring, then 256 bytes of barriers and the tile's bias (512 bytes), plus the
+// 1024-byte alignment of the ring
+constexpr size_t gemm_smem(int stages) { return (size_t)stages * kStageBytes + 1024 + 256 + 512; }
 constexpr int kMaxGroup = 4;              // GEMM problems of one launch
 
 // Epilogues: kEpiBiasGelu  z = acc + bias -> out_f32 (z, optional), out_bf16

@@ -64,8 +64,12 @@ struct SurrogateState {
   DevBuf cal_amp, cal_pulse;             // agonist pulse by amplitude (calibrated nominal)
   MlpBuffers buf;
   MlpBuffers infer;                      // admission-time inference of the request loop
-  // training data of one batch
-  DevBuf sacs, traces, hidden, target, outoff, losses;
+  // training data: two slots, so that one batch is generated (on a side
+  // stream) while the network trains on the other
+  struct DataSlot {
+    DevBuf sacs, traces, hidden, target, X, Xt;
+  } slot[2];
+  DevBuf outoff, losses;
   int train_M = 0;
   int step = 0;
   bool ready = false;
@@ -127,7 +131,8 @@ static Status refresh_copies(opmm_ctx* ctx) {
 
 // Hidden layers of M rows from B.X on the tensor cores: Z (pre-activation,
 // FP32), H = GELU(Z) (BF16) and, for training, H's transpose.
-static Status forward_hidden(opmm_ctx* ctx, MlpBuffers& B, int M, bool keep_transposes, cudaStream_t st) {
+static Status forward_hidden(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfloat16* X, bool keep_transposes,
+                             cudaStream_t st) {
   SurrogateState& S = *ctx->surrogate;
   for (int l = 0; l < kLayers; ++l) {
     GemmLaunch L;
@@ -140,7 +145,7 @@ static Status forward_hidden(opmm_ctx* ctx, MlpBuffers& B, int M, bool keep_tran
     L.stages = 6;
     L.err = ctx->d_err.as<unsigned>();
     GemmProblem& p = L.p[0];
-    p.A = l == 0 ? bf(B.X) : bf(B.H[l - 1]);
+    p.A = l == 0 ? X : bf(B.H[l - 1]);
     p.B = bf(S.wb, (size_t)l * kHidden * kHidden);
     p.bias = f32(S.w, (size_t)l * kLayerParams + (size_t)kHidden * kHidden);
     p.out_bf16 = bf(B.H[l]);
@@ -155,7 +160,7 @@ static Status forward_hidden(opmm_ctx* ctx, MlpBuffers& B, int M, bool keep_tran
 // Inference: hidden layers, then the output layer on CUDA cores into B.Y.
 static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, cudaStream_t st) {
   SurrogateState& S = *ctx->surrogate;
-  Status s = forward_hidden(ctx, B, M, false, st);
+  Status s = forward_hidden(ctx, B, M, bf(B.X), false, st);
   if (!s.ok()) return s;
   return cuda_status(head_fwd_loss(bf(B.H[kLayers - 1]), bf(S.wb, (size_t)kLayers * kHidden * kHidden),
                                    f32(S.w, kHeadB), nullptr, M, f32(B.Y), f32(B.dY), nullptr, st),
@@ -173,10 +178,10 @@ struct AdamStep {
   float lr, wd;
   int step;   // t >= 1
 };
-static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const float* T, float* loss, const AdamStep* adam,
-                         cudaStream_t st) {
+static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfloat16* X, const __nv_bfloat16* Xt,
+                         const float* T, float* loss, const AdamStep* adam, cudaStream_t st) {
   SurrogateState& S = *ctx->surrogate;
-  Status s = forward_hidden(ctx, B, M, true, st);
+  Status s = forward_hidden(ctx, B, M, X, true, st);
   if (!s.ok()) return s;
   s = cuda_status(head_train(bf(B.H[kLayers - 1]), bf(S.wb, (size_t)kLayers * kHidden * kHidden), f32(S.w, kHeadB), T,
                              f32(B.Z[kLayers - 1]), M, f32(B.Y), f32(B.dY), f32(B.rowloss), bf(B.dZ[kLayers - 1]),
@@ -218,7 +223,7 @@ static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const float* T, fl
     for (int l = 0; l < kLayers; ++l) {
       GemmProblem& p = L.p[l];
       p.A = bf(B.dZt[l]);
-      p.B = l == 0 ? bf(B.Xt) : bf(B.Ht[l - 1]);
+      p.B = l == 0 ? Xt : bf(B.Ht[l - 1]);
       p.out_f32 = f32(B.wpart, (size_t)l * L.ksplit * kHidden * kHidden);
     }
     s = cuda_status(gemm(L, st), "GEMM wgrad");
@@ -300,8 +305,6 @@ Status surrogate_prepare_plan(opmm_ctx* ctx, opmm_plan* p, const opmm_saccade*, 
   p->pre_search_kernels = 1 + kLayers + 2;
   p->pre_search = [keep, M](opmm_plan* pl, cudaStream_t st) -> Status {
     opmm_ctx* c = pl->ctx;
-    cudaStream_t saved = c->stream;
-    (void)saved;
     Status r = cuda_status(featurize(pl->d_sacs.as<DevSac>(), pl->d_traces.as<float>(), pl->n, bf(keep->X), nullptr, M, st),
                            "featurize");
     if (r.ok()) r = forward(c, *keep, M, st);
@@ -400,7 +403,7 @@ extern "C" int opmm_surrogate_grad(opmm_ctx* ctx, const float* x, const float* t
   STRY(cuda_status(cudaMemcpyAsync(B.Xt.ptr, xt.data(), xt.size() * 2, cudaMemcpyHostToDevice, st), "H2D Xt"));
   STRY(cuda_status(cudaMemcpyAsync(dt.ptr, t, (size_t)m * kOut * 4, cudaMemcpyHostToDevice, st), "H2D T"));
   STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, st), "clear error"));
-  STRY(train_pass(ctx, B, m, f32(dt), nullptr, nullptr, st));
+  STRY(train_pass(ctx, B, m, bf(B.X), bf(B.Xt), f32(dt), nullptr, nullptr, st));
   std::vector<float> rl((size_t)m);
   STRY(cuda_status(cudaMemcpyAsync(rl.data(), B.rowloss.ptr, (size_t)m * 4, cudaMemcpyDeviceToHost, st), "D2H loss"));
   STRY(cuda_status(cudaMemcpyAsync(grad, S.g.ptr, (size_t)kNumParams * 4, cudaMemcpyDeviceToHost, st), "D2H grad"));
@@ -442,10 +445,14 @@ extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch,
   MlpBuffers& B = S.buf;
   STRY(B.ensure(batch));
   if (S.train_M < batch) {
-    STRY(S.sacs.ensure(sizeof(DevSac) * (size_t)batch));
-    STRY(S.traces.ensure(sizeof(float) * (size_t)batch * kTrainLcap));
-    STRY(S.hidden.ensure(sizeof(float) * (size_t)batch * kOut));
-    STRY(S.target.ensure(sizeof(float) * (size_t)batch * kOut));
+    for (auto& D : S.slot) {
+      STRY(D.sacs.ensure(sizeof(DevSac) * (size_t)batch));
+      STRY(D.traces.ensure(sizeof(float) * (size_t)batch * kTrainLcap));
+      STRY(D.hidden.ensure(sizeof(float) * (size_t)batch * kOut));
+      STRY(D.target.ensure(sizeof(float) * (size_t)batch * kOut));
+      STRY(D.X.ensure((size_t)batch * kIn * 2));
+      STRY(D.Xt.ensure((size_t)batch * kIn * 2));
+    }
     STRY(S.outoff.ensure(sizeof(long long) * (size_t)batch));
     std::vector<long long> off((size_t)batch);
     for (int i = 0; i < batch; ++i) off[(size_t)i] = (long long)i * kTrainLcap;
@@ -455,18 +462,59 @@ extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch,
   STRY(S.losses.ensure(sizeof(float) * (size_t)(steps > 0 ? steps : 1)));
   cudaStream_t st = ctx->stream;
   STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, st), "clear error"));
-  for (int it = 0; it < steps; ++it) {
+  // Batch it + 1 is generated on a side stream while the network trains on
+  // batch it (slots alternate; a slot is refilled only after the step that
+  // read it); the side stream starts after the work already queued on the
+  // main stream, and the main stream waits for its last batch at the end.
+  struct Side {
+    cudaStream_t s = nullptr;
+    cudaEvent_t start = nullptr, data[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr}, end = nullptr;
+    ~Side() {
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+      for (cudaEvent_t e : {start, data[0], data[1], used[0], used[1], end})
+        if (e) cudaEventDestroy(e);
+      cudaGetLastError();
+    }
+  } side;
+  STRY(cuda_status(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking), "side stream"));
+  for (cudaEvent_t* e : {&side.start, &side.data[0], &side.data[1], &side.used[0], &side.used[1], &side.end})
+    STRY(cuda_status(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event"));
+  auto gen = [&](int it, int b) -> Status {
     const long long base = (long long)sample_base + (long long)it * batch;
-    STRY(cuda_status(gen_desc(data_seed, base, batch, f32(S.cal_amp), f32(S.cal_pulse), kCal, S.sacs.as<DevSac>(),
-                              f32(S.hidden), f32(S.target), kTrainLcap, st), "generate"));
-    STRY(cuda_status(launch_simulate(f32(S.hidden), batch, S.sacs.as<DevSac>(), nullptr, S.outoff.as<long long>(),
-                                     f32(S.traces), st), "simulate"));
-    STRY(cuda_status(add_noise(data_seed, base, S.sacs.as<DevSac>(), batch, f32(S.traces), 0.05f, st), "noise"));
-    STRY(cuda_status(featurize(S.sacs.as<DevSac>(), f32(S.traces), batch, bf(B.X), bf(B.Xt), batch, st), "featurize"));
+    SurrogateState::DataSlot& D = S.slot[b];
+    cudaStream_t s2 = side.s;
+    Status r = cuda_status(gen_desc(data_seed, base, batch, f32(S.cal_amp), f32(S.cal_pulse), kCal, D.sacs.as<DevSac>(),
+                                    f32(D.hidden), f32(D.target), kTrainLcap, s2), "generate");
+    if (r.ok())
+      r = cuda_status(launch_simulate(f32(D.hidden), batch, D.sacs.as<DevSac>(), nullptr, S.outoff.as<long long>(),
+                                      f32(D.traces), s2), "simulate");
+    if (r.ok()) r = cuda_status(add_noise(data_seed, base, D.sacs.as<DevSac>(), batch, f32(D.traces), 0.05f, s2), "noise");
+    if (r.ok())
+      r = cuda_status(featurize(D.sacs.as<DevSac>(), f32(D.traces), batch, bf(D.X), bf(D.Xt), batch, s2), "featurize");
+    if (r.ok()) r = cuda_status(cudaEventRecord(side.data[b], s2), "record");
+    return r;
+  };
+  STRY(cuda_status(cudaEventRecord(side.start, st), "record"));
+  STRY(cuda_status(cudaStreamWaitEvent(side.s, side.start, 0), "wait"));
+  if (steps > 0) STRY(gen(0, 0));
+  for (int it = 0; it < steps; ++it) {
+    const int b = it & 1;
+    if (it + 1 < steps) {
+      if (it >= 1) STRY(cuda_status(cudaStreamWaitEvent(side.s, side.used[b ^ 1], 0), "wait"));
+      STRY(gen(it + 1, b ^ 1));
+    }
+    STRY(cuda_status(cudaStreamWaitEvent(st, side.data[b], 0), "wait"));
     const AdamStep step{lr, weight_decay, S.step + 1};
-    STRY(train_pass(ctx, B, batch, f32(S.target), f32(S.losses, (size_t)it), &step, st));
+    SurrogateState::DataSlot& D = S.slot[b];
+    STRY(train_pass(ctx, B, batch, bf(D.X), bf(D.Xt), f32(D.target), f32(S.losses, (size_t)it), &step, st));
+    STRY(cuda_status(cudaEventRecord(side.used[b], st), "record"));
     S.step += 1;
   }
+  STRY(cuda_status(cudaEventRecord(side.end, side.s), "record"));
+  STRY(cuda_status(cudaStreamWaitEvent(st, side.end, 0), "wait"));
   if (losses && steps > 0)
     STRY(cuda_status(cudaMemcpyAsync(losses, S.losses.ptr, (size_t)steps * 4, cudaMemcpyDeviceToHost, st), "D2H losses"));
   unsigned e = 0;
