@@ -42,6 +42,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Bulk tensor store of a shared-memory box to global memory (tile mode,
+// bulk-group completion), and the wait until this thread's bulk groups have
+// read their shared-memory sources.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+               "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
                : "memory");
@@ -98,6 +109,26 @@ __device__ __forceinline__ void tc_ld64(uint32_t taddr, float (&v)[64]) {
   for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (load
+// and wait in one statement).
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_ld(uint32_t taddr, float (&v)[32]) { tc_ld32(taddr, v); }
+__device__ __forceinline__ void tc_ld(uint32_t taddr, float (&v)[64]) { tc_ld64(taddr, v); }
+
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzling:
 // rows of 64 BF16 (128 B), 8-row core groups 1024 B apart (stride byte
 // offset), leading byte offset unused by this layout, descriptor version 1,
@@ -118,52 +149,87 @@ __host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// The Gaussian CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2 with erf from
+// Abramowitz and Stegun, Handbook of Mathematical Functions, formula 7.1.26:
+// for x >= 0, erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) e^(-x^2)
+// with t = 1 / (1 + p x), absolute error at most 1.5e-7.  Written as
+// Phi = 1 - q (z >= 0) or q (z < 0) with q = poly(t) e^(-z^2 / 2) / 2, so
+// the negative side has no cancellation; e = e^(-z^2 / 2) also gives the
+// density phi(z) = e / sqrt(2 pi) that GELU' needs.  GELU(z) = z Phi(z),
+// GELU'(z) = Phi(z) + z phi(z).
+// A&S 7.1.26: p 0.3275911 a1 0.254829592 a2 -0.284496736 a3 1.421413741 a4 -1.453152027 a5 1.061405429
+__device__ __forceinline__ float gauss_cdf(float z, float& e) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  e = __expf(-0.5f * z * z);
+  const float q = 0.5f * poly * e;
+  return z >= 0.0f ? 1.0f - q : q;
+}
+__device__ __forceinline__ float gelu(float z) {
+  float e;
+  return z * gauss_cdf(z, e);
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-  const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
-  const float pdf = 0.39894228040143268f * __expf(-0.5f * z * z);
-  return cdf + z * pdf;
+  float e;
+  const float cdf = gauss_cdf(z, e);
+  return fmaf(z, 0.39894228040143268f * e, cdf);
 }
 
 // ------------------------------------------------------------------ GEMM
-// Tensor maps of a grouped launch: A and B of each problem.
+// Tensor maps of a grouped launch: A and B of each problem, and its outputs
+// (FP32 in 32-column boxes, BF16 row-major and transposed in 64-column
+// boxes, all 128 rows high with the 128-byte swizzle).
 struct GemmMaps {
   CUtensorMap a[kMaxGroup];
   CUtensorMap b[kMaxGroup];
+  CUtensorMap of[kMaxGroup];
+  CUtensorMap ob[kMaxGroup];
+  CUtensorMap ot[kMaxGroup];
 };
 
 // The launch's shape and the problems' outputs, as the kernel sees them.
 struct GemmArgs {
-  int N, nkb, ksplit, ldo, ldt;        // nkb: 64-wide K blocks per slice
+  int M, N, nkb, ksplit, ldo, ldt;     // nkb: 64-wide K blocks per slice
   long long zstride;
   unsigned* err;
   GemmProblem p[kMaxGroup];
 };
 
-// Barrier of the eight epilogue warps (named barrier 1).
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Barrier of the NT epilogue threads (named barrier 1).
+template <int NT>
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
 
 // D tile (tm, tn) of problem blockIdx.z / ksplit over K slice blockIdx.z %
 // ksplit.  Warp 8 lane 0 streams the A and B tiles of each 64-wide K block
 // into the ring (TMA, 128-byte swizzle); warp 9 lane 0 issues four
 // tcgen05.mma (K = 16 each) per stage into a 128 x 128 FP32 accumulator in
-// tensor memory and frees the stage with tcgen05.commit.  Warps 0-7 are the
-// epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its tile rows) and
-// columns 64 (w / 4) .. + 63, 16 at a time, applies the epilogue EPI and
-// stages the tile in the ring, which every MMA has finished reading by then;
-// the eight warps then write the tile out in whole rows (16-byte stores,
-// consecutive threads on consecutive addresses).  Eight warps rather than
-// four: the epilogue's per-element math (GELU, GELU') is latency bound with
-// one warp per scheduler.  Staging: Sf [128][128] FP32 at 0 and Sbf [128][128]
-// BF16 at 64 KB, their 16-byte chunks permuted by XOR with (row & 7) so that
-// 32 rows writing the same logical chunk hit distinct banks; St [128][128]
-// BF16 at 96 KB, the transpose (32 rows of one column are 64 contiguous
-// bytes).  Every wait is bounded; a wait that expires raises the error word
-// and the tile's output is not written.
-template <int STAGES, int EPI>
-__global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
+// tensor memory and frees the stage with tcgen05.commit.  Warps 0 .. EW - 1
+// are the epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its tile
+// rows) and NC = 512 / EW columns from NC (w / 4), applies the epilogue EPI
+// and stages the tile in the ring, which every MMA has finished reading by
+// then, in the boxes of the output tensor maps; one thread then writes the
+// boxes out with bulk tensor stores.  EW = 16 with the 6-stage
+// ring (one CTA per SM; the network's one-wave GEMMs, whose time is the
+// latency of one tile: the per-element math of GELU and GELU' is spread over
+// as many threads as the registers allow) and 8 with the 3-stage ring (two
+// CTAs per SM).  Staging, as the 128-byte swizzle of the tensor maps lays a
+// box out (row q of a box at 128 q bytes, its 16-byte chunk c at position
+// c ^ (q & 7)): Sf, BN / 32 FP32 boxes of [128 rows][32 columns] at 0; Sbf,
+// two BF16 boxes of [128 rows][64 columns] at 64 KB; St, the transpose, two
+// BF16 boxes of [128 columns][64 rows] at 96 KB.  The swizzle also puts the
+// 32 rows of a warp that write one logical chunk on distinct banks.  Every
+// wait is bounded; a wait that expires raises the error word and the tile's
+// output is not written.
+template <int STAGES, int EPI, int BN>
+__global__ void __launch_bounds__(gemm_threads(STAGES), STAGES <= 3 ? 2 : 1)
     k_gemm_tn(const __grid_constant__ GemmMaps maps, const __grid_constant__ GemmArgs g) {
-  static_assert(STAGES * kStageBytes >= (EPI == kEpiF32 ? 65536 : EPI == kEpiGeluBwd ? 131072 : 131072),
+  constexpr int EW = gemm_epi_warps(STAGES), ET = EW * 32, NC = BN * 4 / EW;
+  constexpr int kTmaWarp = EW, kMmaWarp = EW + 1;
+  constexpr int kStageBytes = stage_bytes(BN);
+  static_assert(EPI == kEpiF32 || BN == 128, "the BF16 epilogues take 128-wide tiles");
+  static_assert(STAGES * kStageBytes >= (EPI == kEpiF32 ? kBM * BN * 4 : 131072),
                 "the epilogue stages its tile in the ring");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -187,13 +253,13 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
     *bail = 0;
     fence_mbar_init();
   }
-  if (warp == kGemmMmaWarp) tc_alloc(tmem_slot, kBN);
+  if (warp == kMmaWarp) tc_alloc(tmem_slot, BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == kGemmTmaWarp) {
+  if (warp == kTmaWarp) {
     if (lane == 0) {
       // TMA producer
       const CUtensorMap* ma = &maps.a[prob];
@@ -209,13 +275,13 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
         unsigned char* st = sm + s * kStageBytes;
         mbar_arrive_expect_tx(&full[s], kStageBytes);
         tma_load_2d(st, ma, (kb0 + kb) * kBK, tm * kBM, &full[s]);
-        tma_load_2d(st + kTileABytes, mb, (kb0 + kb) * kBK, tn * kBN, &full[s]);
+        tma_load_2d(st + kTileABytes, mb, (kb0 + kb) * kBK, tn * BN, &full[s]);
       }
     }
-  } else if (warp == kGemmMmaWarp) {
+  } else if (warp == kMmaWarp) {
     if (lane == 0) {
       // MMA issuer
-      constexpr uint32_t idesc = f16_idesc(kBM, kBN);
+      constexpr uint32_t idesc = f16_idesc(kBM, BN);
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % STAGES;
         const uint32_t use = (uint32_t)(kb / STAGES);
@@ -237,22 +303,22 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
   } else {
     // epilogue.  Before the accumulator is ready (overlapping the main loop):
     // the tile's bias in shared memory (kEpiBiasGelu) or GELU' of this
-    // thread's 64 pre-activations (kEpiGeluBwd).
+    // thread's NC pre-activations (kEpiGeluBwd).
     const GemmProblem& P = g.p[prob];
-    const int tid = threadIdx.x;                 // 0..255
+    const int tid = threadIdx.x;                 // 0 .. ET - 1
     const int q = warp & 3;                      // TMEM lane quarter
     const int r = q * 32 + lane;                 // tile row
     const int row = tm * kBM + r;
-    const int cb = (warp >> 2) * 64;             // first tile column of this warp
+    const int cb = (warp >> 2) * NC;             // first tile column of this warp
     float* sbias = reinterpret_cast<float*>(sm + STAGES * kStageBytes + 256);   // [128], after the barriers
-    float gz[EPI == kEpiGeluBwd ? 64 : 1];
+    float gz[EPI == kEpiGeluBwd ? NC : 1];
     if constexpr (EPI == kEpiBiasGelu) {
       if (tid < kBN) sbias[tid] = P.bias[tn * kBN + tid];
     }
     if constexpr (EPI == kEpiGeluBwd) {
-      const float4* zp = reinterpret_cast<const float4*>(P.zin + (size_t)row * g.ldo + tn * kBN + cb);
+      const float4* zp = reinterpret_cast<const float4*>(P.zin + (size_t)row * g.ldo + tn * BN + cb);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < NC / 4; ++i) {
         const float4 z = zp[i];
         gz[4 * i] = gelu_grad(z.x);
         gz[4 * i + 1] = gelu_grad(z.y);
@@ -267,19 +333,20 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
     }
     tc_fence_after();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    epi_bar();
+    epi_bar<ET>();
     const bool go = *reinterpret_cast<volatile int*>(bail) == 0;
     const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
-    unsigned char* Sf = sm;                      // [128][128] FP32, chunks ^ (row & 7)
-    unsigned char* Sbf = sm + 65536;             // [128][128] BF16, chunks ^ (row & 7)
-    __nv_bfloat16* St = reinterpret_cast<__nv_bfloat16*>(sm + 98304);   // [128][128] BF16, transposed
+    unsigned char* Sf = sm;                      // BN / 32 boxes [128][32] FP32
+    unsigned char* Sbf = sm + 65536;             // 2 boxes [128][64] BF16
+    unsigned char* St = sm + 98304;              // 2 boxes [128 columns][64 rows] BF16
     const bool want_f32 = EPI == kEpiF32 || (EPI == kEpiBiasGelu && P.out_f32 != nullptr);
     const bool want_t = EPI != kEpiF32 && P.out_t != nullptr;
+    const int sw = r & 7;
     if (go) {
-      float v[64];
-      tc_ld64(tbase + (uint32_t)cb, v);
+      float v[NC];
+      tc_ld(tbase + (uint32_t)cb, v);
 #pragma unroll
-      for (int c = 0; c < 64; c += 16) {
+      for (int c = 0; c < NC; c += 16) {
         const int col0 = cb + c;                 // column within the tile
         if constexpr (EPI == kEpiGeluBwd) {
 #pragma unroll
@@ -291,9 +358,11 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
         }
         if (want_f32) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            *reinterpret_cast<float4*>(Sf + r * 512 + ((((col0 >> 2) + j) ^ (r & 7)) << 4)) =
+          for (int j = 0; j < 4; ++j) {
+            const int cc = col0 + 4 * j;         // box cc / 32, chunk (cc % 32) / 4
+            *reinterpret_cast<float4*>(Sf + (cc >> 5) * 16384 + r * 128 + ((((cc & 31) >> 2) ^ sw) << 4)) =
                 make_float4(v[c + 4 * j], v[c + 4 * j + 1], v[c + 4 * j + 2], v[c + 4 * j + 3]);
+          }
         }
         if constexpr (EPI != kEpiF32) {
           if constexpr (EPI == kEpiBiasGelu) {
@@ -304,60 +373,63 @@ __global__ void __launch_bounds__(kGemmThreads, STAGES <= 3 ? 2 : 1)
 #pragma unroll
           for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[c + 2 * i], v[c + 2 * i + 1]);
 #pragma unroll
-          for (int j = 0; j < 2; ++j)
-            *reinterpret_cast<uint4*>(Sbf + r * 256 + ((((col0 >> 3) + j) ^ (r & 7)) << 4)) =
+          for (int j = 0; j < 2; ++j) {
+            const int cc = col0 + 8 * j;         // box cc / 64, chunk (cc % 64) / 8
+            *reinterpret_cast<uint4*>(Sbf + (cc >> 6) * 16384 + r * 128 + ((((cc & 63) >> 3) ^ sw) << 4)) =
                 *reinterpret_cast<const uint4*>(&h[4 * j]);
+          }
           if (want_t) {
+            // element (row r, column cc): box r / 64, box row cc, chunk (r % 64) / 8
+            unsigned char* tb = St + (r >> 6) * 16384 + (r & 7) * 2;
+            const int rc = (r & 63) >> 3;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              St[(col0 + 2 * i) * 128 + r] = h[i].x;
-              St[(col0 + 2 * i + 1) * 128 + r] = h[i].y;
+              const int c0 = col0 + 2 * i, c1 = c0 + 1;
+              *reinterpret_cast<__nv_bfloat16*>(tb + c0 * 128 + ((rc ^ (c0 & 7)) << 4)) = h[i].x;
+              *reinterpret_cast<__nv_bfloat16*>(tb + c1 * 128 + ((rc ^ (c1 & 7)) << 4)) = h[i].y;
             }
           }
         }
       }
     }
-    epi_bar();
+    // the staged boxes become visible to the bulk copies (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    epi_bar<ET>();
     if (go) {
-      const size_t r0 = (size_t)tm * kBM;
-      const int c0 = tn * kBN;
-      if (want_f32) {
-        float* out = EPI == kEpiF32 ? P.out_f32 + (size_t)slice * (size_t)g.zstride : P.out_f32;
-        for (int qq = tid; qq < 128 * 32; qq += 256) {
-          const int rr = qq >> 5, ch = qq & 31;
-          const uint4 x = *reinterpret_cast<const uint4*>(Sf + rr * 512 + ((ch ^ (rr & 7)) << 4));
-          *reinterpret_cast<uint4*>(out + (r0 + rr) * g.ldo + c0 + ch * 4) = x;
+      const int y0 = tm * kBM;
+      const int x0 = tn * BN;
+      if (tid == 0) {
+        if (want_f32) {
+          const int yf = EPI == kEpiF32 ? y0 + slice * g.M : y0;   // K slices stacked by rows
+#pragma unroll 1
+          for (int bx = 0; bx < BN / 32; ++bx) tma_store_2d(&maps.of[prob], x0 + 32 * bx, yf, Sf + bx * 16384);
         }
-      }
-      if constexpr (EPI != kEpiF32) {
-        for (int qq = tid; qq < 128 * 16; qq += 256) {
-          const int rr = qq >> 4, ch = qq & 15;
-          const uint4 x = *reinterpret_cast<const uint4*>(Sbf + rr * 256 + ((ch ^ (rr & 7)) << 4));
-          *reinterpret_cast<uint4*>(P.out_bf16 + (r0 + rr) * g.ldo + c0 + ch * 8) = x;
+        if constexpr (EPI != kEpiF32) {
+          for (int bx = 0; bx < 2; ++bx) tma_store_2d(&maps.ob[prob], x0 + 64 * bx, y0, Sbf + bx * 16384);
+          if (want_t)
+            for (int bx = 0; bx < 2; ++bx) tma_store_2d(&maps.ot[prob], y0 + 64 * bx, x0, St + bx * 16384);
         }
-        if (want_t) {
-          for (int qq = tid; qq < 128 * 16; qq += 256) {
-            const int cc = qq >> 4, ch = qq & 15;
-            const uint4 x = *reinterpret_cast<const uint4*>(St + cc * 128 + ch * 8);
-            *reinterpret_cast<uint4*>(P.out_t + (size_t)(c0 + cc) * g.ldt + r0 + ch * 8) = x;
-          }
-        }
+        bulk_commit();
       }
       if constexpr (EPI == kEpiGeluBwd) {
         if (tid < 128) {
           // column sum of the rounded errors over the tile's rows, in row order
+          const unsigned char* cbp = Sbf + (tid >> 6) * 16384 + (tid & 7) * 2;
+          const int ch = (tid & 63) >> 3;
           float s = 0.0f;
           for (int rr = 0; rr < 128; ++rr)
-            s += __bfloat162float(
-                *reinterpret_cast<const __nv_bfloat16*>(Sbf + rr * 256 + ((((tid >> 3) ^ (rr & 7))) << 4) + (tid & 7) * 2));
-          P.colpart[(size_t)tm * g.N + c0 + tid] = s;
+            s += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(cbp + rr * 128 + ((ch ^ (rr & 7)) << 4)));
+          P.colpart[(size_t)tm * g.N + x0 + tid] = s;
         }
       }
+      // the copies must have read the staging area before the block exits
+      // (their writes are complete when the grid is)
+      if (tid == 0) bulk_wait_read();
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == kGemmMmaWarp) tc_dealloc(tmem, kBN);
+  if (warp == kMmaWarp) tc_dealloc(tmem, BN);
 }
 
 // ------------------------------------------------------------------ elementwise / reductions
@@ -420,8 +492,10 @@ constexpr int kHeadRows = 32;
 constexpr int kHeadThreads = 512;
 static_assert(kHeadThreads == kHidden && kHeadRows == 2 * (kHeadThreads / 32), "one thread per column, two rows per warp");
 constexpr int kSdzPitch = kHidden + 2;     // BF16 elements: rows one bank apart
+constexpr int kSdyPitch = 20;              // FP32 elements per row of dY in shared memory (16-byte rows)
+static_assert(kOut == 18 && kSdyPitch >= kOut && kSdyPitch % 4 == 0, "dY rows read as four float4 and a float2");
 constexpr size_t kHeadSmem = (size_t)kOut * kHidden * 4 + (size_t)kHeadRows * kHidden * 2 +
-                             (size_t)kHeadRows * kSdzPitch * 2 + (size_t)kHeadRows * kOut * 4;
+                             (size_t)kHeadRows * kSdzPitch * 2 + 2 * (size_t)kHeadRows * kSdyPitch * 4;
 
 __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5,
                                                              const float* b5, const float* T, const float* Z, int M,
@@ -432,7 +506,9 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
   float* sw = reinterpret_cast<float*>(hsm);                                    // [18][512]
   __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sw + kOut * kHidden);   // [32][512]
   __nv_bfloat16* sdz = sh + kHeadRows * kHidden;                                // [32][kSdzPitch]
-  float* sdy = reinterpret_cast<float*>(sdz + kHeadRows * kSdzPitch);           // [32][18]
+  float* sdy = reinterpret_cast<float*>(sdz + kHeadRows * kSdzPitch);           // [32][kSdyPitch]
+  float* stg = sdy + kHeadRows * kSdyPitch;                                     // [32][kSdyPitch] targets
+  __shared__ float sb5[kOut];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = blockIdx.x * kHeadRows;
   float z[kHeadRows];
@@ -446,38 +522,48 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
     const uint4* hs = reinterpret_cast<const uint4*>(H + (size_t)r0 * kHidden);
     uint4* hd = reinterpret_cast<uint4*>(sh);
     for (int i = tid; i < kHeadRows * kHidden / 8; i += kHeadThreads) hd[i] = hs[i];
+    // the block's targets, so that the loss below reads none of them from
+    // global memory between its stores
+    for (int i = tid; i < kHeadRows * kOut; i += kHeadThreads) stg[(i / kOut) * kSdyPitch + i % kOut] = T[(size_t)r0 * kOut + i];
+    if (tid < kOut) sb5[tid] = b5[tid];
   }
   __syncthreads();
-  // forward and loss: warp w takes rows 2 w, 2 w + 1; lane l the column
-  // pairs 2 l + 64 j
-  for (int i = 2 * warp; i < 2 * warp + 2; ++i) {
-    const int m = r0 + i;
-    float acc[kOut];
+  // forward and loss: warp w takes rows 2 w and 2 w + 1 together (each W5
+  // pair read from shared memory serves both), lane l the column pairs
+  // 2 l + 64 j
+  float acc2[2][kOut];
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) acc[o] = 0.0f;
+  for (int o = 0; o < kOut; ++o) acc2[0][o] = acc2[1][o] = 0.0f;
 #pragma unroll 2
-    for (int k = 2 * lane; k < kHidden; k += 64) {
-      const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(sh + i * kHidden + k));
+  for (int k = 2 * lane; k < kHidden; k += 64) {
+    const float2 h0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(sh + (2 * warp) * kHidden + k));
+    const float2 h1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(sh + (2 * warp + 1) * kHidden + k));
 #pragma unroll
-      for (int o = 0; o < kOut; ++o) {
-        const float2 w = *reinterpret_cast<const float2*>(sw + o * kHidden + k);
-        acc[o] = fmaf(h.y, w.y, fmaf(h.x, w.x, acc[o]));
-      }
+    for (int o = 0; o < kOut; ++o) {
+      const float2 w = *reinterpret_cast<const float2*>(sw + o * kHidden + k);
+      acc2[0][o] = fmaf(h0.y, w.y, fmaf(h0.x, w.x, acc2[0][o]));
+      acc2[1][o] = fmaf(h1.y, w.y, fmaf(h1.x, w.x, acc2[1][o]));
     }
+  }
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    const int i = 2 * warp + rr;
+    const int m = r0 + i;
+    const float (&acc)[kOut] = acc2[rr];
     float l = 0.0f;
 #pragma unroll
     for (int o = 0; o < kOut; ++o) {
       float v = acc[o];
 #pragma unroll
       for (int s = 16; s; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-      v += b5[o];
-      const float d = v - T[(size_t)m * kOut + o];
+      v += sb5[o];
+      const float d = v - stg[i * kSdyPitch + o];
       l += d * d;
       const float g = 2.0f * d / (float)(M * kOut);
       if (lane == 0) {
         Y[(size_t)m * kOut + o] = v;
         dY[(size_t)m * kOut + o] = g;
-        sdy[i * kOut + o] = g;
+        sdy[i * kSdyPitch + o] = g;
       }
     }
     if (lane == 0) row_loss[m] = l / (float)(M * kOut);
@@ -497,10 +583,17 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
       const float h = __bfloat162float(sh[i * kHidden + k]);
       float dy[kOut];
 #pragma unroll
-      for (int o = 0; o < kOut; o += 2) {
-        const float2 t = *reinterpret_cast<const float2*>(sdy + i * kOut + o);
+      for (int o = 0; o < 16; o += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(sdy + i * kSdyPitch + o);
         dy[o] = t.x;
         dy[o + 1] = t.y;
+        dy[o + 2] = t.z;
+        dy[o + 3] = t.w;
+      }
+      {
+        const float2 t = *reinterpret_cast<const float2*>(sdy + i * kSdyPitch + 16);
+        dy[16] = t.x;
+        dy[17] = t.y;
       }
       float s = 0.0f;
 #pragma unroll
@@ -516,7 +609,7 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
   }
   if (tid < kOut) {
     float s = 0.0f;
-    for (int i = 0; i < kHeadRows; ++i) s += sdy[i * kOut + tid];
+    for (int i = 0; i < kHeadRows; ++i) s += sdy[i * kSdyPitch + tid];
     dbpart[(size_t)blockIdx.x * kOut + tid] = s;
   }
   __syncthreads();
@@ -588,17 +681,22 @@ __global__ void k_pack_params(const float* w, int n, const AdamLayout L, __nv_bf
 // Gradient assembly and, when a.adam is set, the AdamW step (see FinishArgs).
 // Blocks [0, kFinishWBlocks): four consecutive hidden weight entries per
 // thread (16-byte loads and stores), each summing its K-slice partials in
-// slice order.  The next kFinishRBlocks blocks: one warp
-// per bias or output-layer entry, lane j summing partials j, j + 32, ... in
-// order, then a fixed butterfly across the lanes.  The last block: the batch
+// slice order.  The next kFinishRBlocks blocks: 32 bias or output-layer
+// entries each, eight partial sums per entry (partials j, j + 8, ...) added
+// in order.  The last block: the batch
 // loss (strided per thread, then a tree over the block).
 constexpr int kFinishW = kLayers * kHidden * kHidden;                     // hidden weight entries
 constexpr int kFinishR = kLayers * kHidden + kOut * kHidden + kOut;       // reduced entries
 constexpr int kFinishWBlocks = kFinishW / 1024;
-constexpr int kFinishRBlocks = (kFinishR + 7) / 8;
+constexpr int kFinishBiasGroups = kLayers * kHidden / 32;                // hidden biases, 32 per block
+constexpr int kFinishHeadWGroups = kOut * kHidden / 32;                  // output-layer weights, 32 per block
+constexpr int kFinishRBlocks = kFinishBiasGroups + kFinishHeadWGroups + 1;   // + the output biases
 
 __global__ void __launch_bounds__(256) k_grad_finish(const __grid_constant__ FinishArgs a) {
   const int tid = threadIdx.x;
+  const int t = a.t_idx ? *a.t_idx : 0;            // step within a replayed sequence
+  const float bc1 = a.bc_tab ? a.bc_tab[2 * t] : a.bc1;
+  const float bc2 = a.bc_tab ? a.bc_tab[2 * t + 1] : a.bc2;
   if (blockIdx.x == kFinishWBlocks + kFinishRBlocks) {
     if (!a.loss) return;
     __shared__ float s[256];
@@ -610,7 +708,7 @@ __global__ void __launch_bounds__(256) k_grad_finish(const __grid_constant__ Fin
       if (tid < w) s[tid] += s[tid + w];
       __syncthreads();
     }
-    if (tid == 0) *a.loss = s[0];
+    if (tid == 0) a.loss[t] = s[0];
     return;
   }
   constexpr long long kW = (long long)kHidden * kHidden;
@@ -636,7 +734,7 @@ __global__ void __launch_bounds__(256) k_grad_finish(const __grid_constant__ Fin
       const float4 w = *reinterpret_cast<const float4*>(a.w + i);
       float am[4] = {m1.x, m1.y, m1.z, m1.w}, av[4] = {m2.x, m2.y, m2.z, m2.w}, aw[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) adamw_math(v[j], am[j], av[j], aw[j], true, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2);
+      for (int j = 0; j < 4; ++j) adamw_math(v[j], am[j], av[j], aw[j], true, a.lr, a.b1, a.b2, a.eps, a.wd, bc1, bc2);
       *reinterpret_cast<float4*>(a.m1 + i) = make_float4(am[0], am[1], am[2], am[3]);
       *reinterpret_cast<float4*>(a.m2 + i) = make_float4(av[0], av[1], av[2], av[3]);
       *reinterpret_cast<float4*>(a.w + i) = make_float4(aw[0], aw[1], aw[2], aw[3]);
@@ -645,38 +743,48 @@ __global__ void __launch_bounds__(256) k_grad_finish(const __grid_constant__ Fin
     }
     return;
   }
-  const int e = (blockIdx.x - kFinishWBlocks) * 8 + (tid >> 5);
-  const int lane = tid & 31;
-  if (e >= kFinishR) return;
+  // 32 consecutive entries of one kind per block: thread (j, e) = (tid / 32,
+  // tid % 32) sums partials j, j + 8, ... of entry e (a warp reads 32
+  // consecutive entries of one partial row), then warp 0 adds the eight
+  // group sums in order
+  __shared__ float part[8][32];
+  const int grp = blockIdx.x - kFinishWBlocks, j = tid >> 5, e = tid & 31;
   const float* p;
-  int n, stride;
-  long long i;
-  if (e < kLayers * kHidden) {
-    const int l = e / kHidden, c = e - l * kHidden;
-    p = a.colpart[l] + c;
+  int n, stride, cnt;
+  long long i0;
+  if (grp < kFinishBiasGroups) {
+    const int l = grp / (kHidden / 32), c0 = (grp - l * (kHidden / 32)) * 32;
+    p = a.colpart[l] + c0;
     n = a.ntiles[l];
     stride = kHidden;
-    i = (long long)l * kLayerParams + kW + c;
-  } else if (e < kLayers * kHidden + kOut * kHidden) {
-    const int c = e - kLayers * kHidden;
-    p = a.dWpart + c;
+    i0 = (long long)l * kLayerParams + kW + c0;
+    cnt = 32;
+  } else if (grp < kFinishBiasGroups + kFinishHeadWGroups) {
+    const int c0 = (grp - kFinishBiasGroups) * 32;
+    p = a.dWpart + c0;
     n = a.nblk;
     stride = kOut * kHidden;
-    i = kHeadW + c;
+    i0 = kHeadW + c0;
+    cnt = 32;
   } else {
-    const int c = e - kLayers * kHidden - kOut * kHidden;
-    p = a.dbpart + c;
+    p = a.dbpart;
     n = a.nblk;
     stride = kOut;
-    i = kHeadB + c;
+    i0 = kHeadB;
+    cnt = kOut;
   }
   float v = 0.0f;
-  for (int t = lane; t < n; t += 32) v += p[(size_t)t * stride];
+  if (e < cnt)
+    for (int t = j; t < n; t += 8) v += p[(size_t)t * stride + e];
+  part[j][e] = v;
+  __syncthreads();
+  if (j == 0 && e < cnt) {
+    float sum = 0.0f;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) {
-    a.g[i] = v;
-    if (a.adam) adamw_update(i, v, a.w, a.m1, a.m2, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, AdamLayout{}, a.wb);
+    for (int q = 0; q < 8; ++q) sum += part[q][e];
+    const long long i = i0 + e;
+    a.g[i] = sum;
+    if (a.adam) adamw_update(i, sum, a.w, a.m1, a.m2, a.lr, a.b1, a.b2, a.eps, a.wd, bc1, bc2, AdamLayout{}, a.wb);
   }
 }
 
@@ -753,6 +861,15 @@ __global__ void __launch_bounds__(128) k_featurize(const DevSac* sacs, const flo
   }
 }
 
+// Device-side counters of a replayable training step: *p64 += by64 (the
+// sample base of a data slot), *p32 += 1 (the step index).
+__global__ void k_bump(long long* p64, long long by64, int* p32) {
+  if (threadIdx.x == 0) {
+    if (p64) *p64 += by64;
+    if (p32) *p32 += 1;
+  }
+}
+
 // Box centres from the network's output: centre = nominal * exp(scale * y).
 __global__ void k_apply_centres(const float* Y, int n, float scale, float* pc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -768,11 +885,11 @@ __global__ void k_apply_centres(const float* Y, int n, float scale, float* pc) {
 // hidden OPC is the interpolated nominal centre times the multipliers.
 __device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
-__global__ void k_gen_desc(uint64_t seed, long long base, int n, const float* cal_amp, const float* cal_pulse,
+__global__ void k_gen_desc(uint64_t seed, const long long* base_ptr, int n, const float* cal_amp, const float* cal_pulse,
                            int ncal, DevSac* sacs, float* hidden, float* target, int lcap) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const long long g = base + i;
+  const long long g = *base_ptr + i;
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   uint32_t r[4];
   philox4x32_10((uint32_t)g, (uint32_t)(g >> 32), 0u, 0u, k0, k1, r);
@@ -830,11 +947,12 @@ __global__ void k_gen_desc(uint64_t seed, long long base, int n, const float* ca
 }
 
 // Noisy trace: simulated trajectory plus N(0, 0.05^2) deg noise, in place.
-__global__ void k_add_noise(uint64_t seed, long long base, const DevSac* sacs, int n, float* traces, float sigma) {
+__global__ void k_add_noise(uint64_t seed, const long long* base_ptr, const DevSac* sacs, int n, float* traces,
+                            float sigma) {
   const int b = blockIdx.x;
   if (b >= n) return;
   const DevSac d = sacs[b];
-  const long long g = base + b;
+  const long long g = *base_ptr + b;
   for (int k2 = threadIdx.x * 2; k2 < d.L; k2 += 2 * blockDim.x) {
     uint32_t q[4];
     philox4x32_10((uint32_t)g, (uint32_t)(g >> 32), 3u, (uint32_t)k2, (uint32_t)seed, (uint32_t)(seed >> 32), q);
@@ -860,43 +978,60 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D tensor map of a row-major BF16 matrix [rows][cols], box 64 x 128
+// 2-D tensor map of a row-major matrix [rows][cols] (row stride in bytes),
+// box box_cols x box_rows with 128-byte box rows and the 128-byte swizzle.
+static bool make_map_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int rows, int cols, size_t stride,
+                        int box_cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 2-D tensor map of a row-major BF16 matrix [rows][cols], box 64 x box_rows
 // (128-byte rows, 128-byte swizzle).
-static bool make_map(CUtensorMap* map, const void* base, int rows, int cols) {
+static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int S, int E>
+template <int S, int E, int BN>
 static cudaError_t gemm_attr() {
-  return cudaFuncSetAttribute(k_gemm_tn<S, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(S));
+  return cudaFuncSetAttribute(k_gemm_tn<S, E, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(S, BN));
 }
 
 cudaError_t gemm_prepare() {
-  cudaError_t e = gemm_attr<3, kEpiF32>();
-  if (e == cudaSuccess) e = gemm_attr<6, kEpiF32>();
-  if (e == cudaSuccess) e = gemm_attr<6, kEpiBiasGelu>();
-  if (e == cudaSuccess) e = gemm_attr<6, kEpiGeluBwd>();
+  cudaError_t e = gemm_attr<3, kEpiF32, 128>();
+  if (e == cudaSuccess) e = gemm_attr<6, kEpiBiasGelu, 128>();
+  if (e == cudaSuccess) e = gemm_attr<6, kEpiGeluBwd, 128>();
+  if (e == cudaSuccess) e = gemm_attr<4, kEpiF32, 256>();
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_head_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeadSmem);
   return e;
 }
 
 cudaError_t gemm(const GemmLaunch& L, cudaStream_t st) {
   if (L.np < 1 || L.np > kMaxGroup || L.ksplit < 1 || L.M <= 0 || L.N <= 0 || L.K <= 0) return cudaErrorInvalidValue;
-  if (L.M % kBM || L.N % kBN || L.K % (L.ksplit * kBK)) return cudaErrorInvalidValue;
-  // launchable (stages, epilogue) pairs: the epilogue's staging must fit the ring
-  if (!((L.stages == 3 && L.epi == kEpiF32) || (L.stages == 6 && (L.epi == kEpiF32 || L.epi == kEpiBiasGelu ||
-                                                                   L.epi == kEpiGeluBwd))))
-    return cudaErrorInvalidValue;
+  if (L.M % kBM || L.N % L.bn || L.K % (L.ksplit * kBK)) return cudaErrorInvalidValue;
+  // launchable (stages, epilogue, width): the epilogue's staging must fit the ring
+  const int kind = (L.stages == 3 && L.epi == kEpiF32 && L.bn == 128)        ? 0
+                   : (L.stages == 6 && L.epi == kEpiBiasGelu && L.bn == 128) ? 1
+                   : (L.stages == 6 && L.epi == kEpiGeluBwd && L.bn == 128)  ? 2
+                   : (L.stages == 4 && L.epi == kEpiF32 && L.bn == 256)      ? 3
+                                                                              : -1;
+  if (kind < 0) return cudaErrorInvalidValue;
   if (L.ldo % 8 || (L.epi != kEpiF32 && L.ldt % 8)) return cudaErrorInvalidValue;
-  if (L.ksplit > 1 && L.epi != kEpiF32) return cudaErrorInvalidValue;
+  if (L.ksplit > 1 && (L.epi != kEpiF32 || L.zstride != (long long)L.M * L.ldo)) return cudaErrorInvalidValue;
   GemmMaps maps;
   memset(&maps, 0, sizeof maps);
   GemmArgs g{};
@@ -910,9 +1045,20 @@ cudaError_t gemm(const GemmLaunch& L, cudaStream_t st) {
     if (p.out_t && mis(p.out_t)) return cudaErrorInvalidValue;
     if (L.epi == kEpiBiasGelu && !p.bias) return cudaErrorInvalidValue;
     if (L.epi == kEpiGeluBwd && (!p.zin || !p.colpart || mis(p.zin))) return cudaErrorInvalidValue;
-    if (!make_map(&maps.a[i], p.A, L.M, L.K) || !make_map(&maps.b[i], p.B, L.N, L.K)) return cudaErrorInvalidValue;
+    if (!make_map(&maps.a[i], p.A, L.M, L.K, kBM) || !make_map(&maps.b[i], p.B, L.N, L.K, L.bn)) return cudaErrorInvalidValue;
+    // outputs: FP32 (K slices stacked by rows), BF16 row-major, BF16 transposed
+    if (f32 && !make_map_2d(&maps.of[i], p.out_f32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, L.M * L.ksplit, L.N,
+                            (size_t)L.ldo * 4, 32, kBM))
+      return cudaErrorInvalidValue;
+    if (L.epi != kEpiF32 && !make_map_2d(&maps.ob[i], p.out_bf16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.M, L.N,
+                                         (size_t)L.ldo * 2, 64, kBM))
+      return cudaErrorInvalidValue;
+    if (p.out_t && !make_map_2d(&maps.ot[i], p.out_t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.N, L.M, (size_t)L.ldt * 2, 64,
+                                kBM))
+      return cudaErrorInvalidValue;
     g.p[i] = p;
   }
+  g.M = L.M;
   g.N = L.N;
   g.nkb = L.K / L.ksplit / kBK;
   g.ksplit = L.ksplit;
@@ -920,11 +1066,11 @@ cudaError_t gemm(const GemmLaunch& L, cudaStream_t st) {
   g.ldt = L.ldt;
   g.zstride = L.zstride;
   g.err = L.err;
-  dim3 grid(L.N / kBN, L.M / kBM, L.np * L.ksplit);
-  if (L.stages == 3) k_gemm_tn<3, kEpiF32><<<grid, kGemmThreads, gemm_smem(3), st>>>(maps, g);
-  else if (L.epi == kEpiF32) k_gemm_tn<6, kEpiF32><<<grid, kGemmThreads, gemm_smem(6), st>>>(maps, g);
-  else if (L.epi == kEpiBiasGelu) k_gemm_tn<6, kEpiBiasGelu><<<grid, kGemmThreads, gemm_smem(6), st>>>(maps, g);
-  else k_gemm_tn<6, kEpiGeluBwd><<<grid, kGemmThreads, gemm_smem(6), st>>>(maps, g);
+  dim3 grid(L.N / L.bn, L.M / kBM, L.np * L.ksplit);
+  if (kind == 0) k_gemm_tn<3, kEpiF32, 128><<<grid, gemm_threads(3), gemm_smem(3, 128), st>>>(maps, g);
+  else if (kind == 1) k_gemm_tn<6, kEpiBiasGelu, 128><<<grid, gemm_threads(6), gemm_smem(6, 128), st>>>(maps, g);
+  else if (kind == 2) k_gemm_tn<6, kEpiGeluBwd, 128><<<grid, gemm_threads(6), gemm_smem(6, 128), st>>>(maps, g);
+  else k_gemm_tn<4, kEpiF32, 256><<<grid, gemm_threads(4), gemm_smem(4, 256), st>>>(maps, g);
   return cudaGetLastError();
 }
 
@@ -945,6 +1091,7 @@ cudaError_t head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5, const fl
 
 cudaError_t grad_finish(const FinishArgs& a, cudaStream_t st) {
   static_assert(kFinishW % 1024 == 0 && (long long)kFinishW + kFinishR == kNumParams, "every entry once");
+  static_assert(kFinishBiasGroups * 32 + kFinishHeadWGroups * 32 + kOut == kFinishR, "every reduced entry once");
   k_grad_finish<<<kFinishWBlocks + kFinishRBlocks + 1, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && a.adam) e = transpose_layers(a.wb, a.wt, st);
@@ -988,18 +1135,23 @@ cudaError_t featurize(const DevSac* sacs, const float* traces, int n, __nv_bfloa
   return cudaGetLastError();
 }
 
+cudaError_t bump(long long* p64, long long by64, int* p32, cudaStream_t st) {
+  k_bump<<<1, 32, 0, st>>>(p64, by64, p32);
+  return cudaGetLastError();
+}
+
 cudaError_t apply_centres(const float* Y, int n, float* pc, cudaStream_t st) {
   k_apply_centres<<<(n * kOut + 255) / 256, 256, 0, st>>>(Y, n, kTargetScale, pc);
   return cudaGetLastError();
 }
 
-cudaError_t gen_desc(uint64_t seed, long long base, int n, const float* cal_amp, const float* cal_pulse, int ncal,
+cudaError_t gen_desc(uint64_t seed, const long long* base, int n, const float* cal_amp, const float* cal_pulse, int ncal,
                      DevSac* sacs, float* hidden, float* target, int lcap, cudaStream_t st) {
   k_gen_desc<<<(n + 127) / 128, 128, 0, st>>>(seed, base, n, cal_amp, cal_pulse, ncal, sacs, hidden, target, lcap);
   return cudaGetLastError();
 }
 
-cudaError_t add_noise(uint64_t seed, long long base, const DevSac* sacs, int n, float* traces, float sigma,
+cudaError_t add_noise(uint64_t seed, const long long* base, const DevSac* sacs, int n, float* traces, float sigma,
                       cudaStream_t st) {
   k_add_noise<<<n, 128, 0, st>>>(seed, base, sacs, n, traces, sigma);
   return cudaGetLastError();

@@ -23,15 +23,15 @@ constexpr float kTargetScale = 0.2f;      // output y = ln(p / centre) / 0.2
 // one CTA per SM, a deeper prefetch: the network's one-wave GEMMs).  The
 // epilogue stages its output tile in the ring (free once every MMA has read
 // it) and writes it out in whole rows.
-constexpr int kBM = 128, kBN = 128, kBK = 64;
+constexpr int kBM = 128, kBN = 128, kBK = 64;   // kBN: the usual tile width (256 for the weight gradients)
 constexpr int kTileABytes = kBM * kBK * 2;
-constexpr int kTileBBytes = kBN * kBK * 2;
-constexpr int kStageBytes = kTileABytes + kTileBBytes;
-constexpr int kGemmThreads = 320;         // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
-constexpr int kGemmTmaWarp = 8, kGemmMmaWarp = 9;
+constexpr int stage_bytes(int bn) { return kTileABytes + bn * kBK * 2; }
+// epilogue warps (then one TMA producer warp and one MMA issuer warp)
+constexpr int gemm_epi_warps(int stages) { return stages <= 3 ? 8 : 16; }
+constexpr int gemm_threads(int stages) { return gemm_epi_warps(stages) * 32 + 64; }
 // ring, then 256 bytes of barriers and the tile's bias (512 bytes), plus the
 // 1024-byte alignment of the ring
-constexpr size_t gemm_smem(int stages) { return (size_t)stages * kStageBytes + 1024 + 256 + 512; }
+constexpr size_t gemm_smem(int stages, int bn) { return (size_t)stages * stage_bytes(bn) + 1024 + 256 + 512; }
 constexpr int kMaxGroup = 4;              // GEMM problems of one launch
 
 // Epilogues: kEpiBiasGelu  z = acc + bias -> out_f32 (z, optional), out_bf16
@@ -58,12 +58,15 @@ struct GemmProblem {
 };
 
 // One launch: np problems of the same shape, each split into ksplit slices
-// of K (K / ksplit a multiple of 64).
+// of K (K / ksplit a multiple of 64), in tiles of 128 x bn.  Launchable
+// (stages, epilogue, bn): (3, F32, 128), (6, BiasGelu, 128), (6, GeluBwd,
+// 128), (4, F32, 256); the 256-wide tile runs the tensor cores at twice the
+// rate of the 128-wide one (M = 128, N = 256 per instruction).
 struct GemmLaunch {
-  int np = 1, M = 0, N = 0, K = 0, ksplit = 1, epi = kEpiF32;
+  int np = 1, M = 0, N = 0, K = 0, ksplit = 1, epi = kEpiF32, bn = kBN;
   int ldo = 0, ldt = 0;
   long long zstride = 0;       // elements between the outputs of consecutive K slices
-  int stages = 3;              // 3 or 6
+  int stages = 3;
   unsigned* err = nullptr;
   GemmProblem p[kMaxGroup] = {};
 };
@@ -100,11 +103,13 @@ struct AdamLayout {
 // Gradient assembly, every sum in a fixed order: hidden weight matrices from
 // the K-slice partials of the weight-gradient GEMM (slice order), hidden
 // biases from the per-row-tile column sums of the rounded errors, the output
-// layer from the head kernel's per-block partials (partials j, j + 32, ...
-// per lane, then a fixed butterfly).  The batch loss (sum of the rows' terms)
-// into *loss when given.  With adam set, each entry's AdamW step follows
-// from its assembled gradient (as k_adamw), and the transposed BF16 copies
-// are refreshed after.
+// layer from the head kernel's per-block partials (eight interleaved partial
+// sums per entry, then their sum in order).  The batch loss (the sum of the
+// rows' terms) goes into loss[t] when given.  With adam set, each entry's
+// AdamW step follows from its assembled gradient (as k_adamw), and the
+// transposed BF16 copies are refreshed after.  t = *t_idx when t_idx is
+// given (a step of a replayed sequence), else 0; the bias corrections are
+// bc_tab[2 t], bc_tab[2 t + 1] when bc_tab is given, else bc1, bc2.
 struct FinishArgs {
   const float* wpart;          // [4][ksplit][512][512]
   int ksplit;
@@ -116,6 +121,8 @@ struct FinishArgs {
   const float* row_loss;
   int M;
   float* loss;
+  const int* t_idx;
+  const float* bc_tab;
   float* g;
   int adam;
   float lr, b1, b2, eps, wd, bc1, bc2;
@@ -147,9 +154,10 @@ cudaError_t pack_params(const float* w, int n, const AdamLayout& L, __nv_bfloat1
 cudaError_t featurize(const DevSac* sacs, const float* traces, int n, __nv_bfloat16* X, __nv_bfloat16* Xt, int ldt,
                       cudaStream_t st);
 cudaError_t apply_centres(const float* Y, int n, float* pc, cudaStream_t st);
-cudaError_t gen_desc(uint64_t seed, long long base, int n, const float* cal_amp, const float* cal_pulse, int ncal,
+cudaError_t bump(long long* p64, long long by64, int* p32, cudaStream_t st);
+cudaError_t gen_desc(uint64_t seed, const long long* base, int n, const float* cal_amp, const float* cal_pulse, int ncal,
                      DevSac* sacs, float* hidden, float* target, int lcap, cudaStream_t st);
-cudaError_t add_noise(uint64_t seed, long long base, const DevSac* sacs, int n, float* traces, float sigma,
+cudaError_t add_noise(uint64_t seed, const long long* base, const DevSac* sacs, int n, float* traces, float sigma,
                       cudaStream_t st);
 
 }  // namespace mlp

@@ -28,7 +28,7 @@ constexpr int kTrainLcap = 400;         // longest training window
 }  // namespace
 
 // Activations and gradients of one batch of M rows (M a multiple of 128).
-constexpr int kWgradSplit = 2;          // K slices of the weight-gradient GEMM
+constexpr int kWgradSplit = 4;          // largest number of K slices of the weight-gradient GEMM
 struct MlpBuffers {
   int M = 0;
   DevBuf X, Xt, H[kLayers], Ht[kLayers], Z[kLayers], Y, dY, rowloss, dZ[kLayers], dZt[kLayers], colpart[kLayers],
@@ -70,6 +70,8 @@ struct SurrogateState {
     DevBuf sacs, traces, hidden, target, X, Xt;
   } slot[2];
   DevBuf outoff, losses;
+  DevBuf tstate;                         // device step state: next sample base per slot, step index
+  DevBuf bctab;                          // AdamW bias corrections of the steps of a call
   int train_M = 0;
   int step = 0;
   bool ready = false;
@@ -174,9 +176,13 @@ static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, cudaStream_t st) {
 // (dZ_{l-1} = BF16((dZ_l . W_l) * GELU'(Z_{l-1}))); all four weight gradients
 // dW_l = dZ_l^T . H_{l-1} in one grouped launch over two K slices; the
 // gradient assembly, with the AdamW step of every entry when `adam` is given.
+// AdamW settings of a step of a replayable sequence: the step's index t is
+// read on the device from *t_idx, its bias corrections from bc_tab[2 t],
+// bc_tab[2 t + 1] and its loss goes to loss[t].
 struct AdamStep {
   float lr, wd;
-  int step;   // t >= 1
+  const float* bc_tab;
+  const int* t_idx;
 };
 static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfloat16* X, const __nv_bfloat16* Xt,
                          const float* T, float* loss, const AdamStep* adam, cudaStream_t st) {
@@ -208,17 +214,19 @@ static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfloat1
     s = cuda_status(gemm(L, st), "GEMM dgrad");
   }
   if (s.ok()) {
-    // dW_l[n][k] = sum_m dZ_l[m][n] H_{l-1}[m][k], K = M split in slices
+    // dW_l[n][k] = sum_m dZ_l[m][n] H_{l-1}[m][k] in 128 x 256 tiles, K = M
+    // split in slices so that the four layers fill the GPU (4 x 8 tiles x 4)
     GemmLaunch L;
     L.np = kLayers;
     L.M = kHidden;
     L.N = kHidden;
     L.K = M;
-    L.ksplit = M >= 2 * kBM ? kWgradSplit : 1;
+    L.ksplit = M % (4 * kBK) == 0 && M >= 1024 ? kWgradSplit : M >= 2 * kBM ? 2 : 1;
     L.epi = kEpiF32;
+    L.bn = 256;
     L.ldo = kHidden;
     L.zstride = (long long)kHidden * kHidden;
-    L.stages = 6;
+    L.stages = 4;
     L.err = ctx->d_err.as<unsigned>();
     for (int l = 0; l < kLayers; ++l) {
       GemmProblem& p = L.p[l];
@@ -249,7 +257,8 @@ static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfloat1
         a.b1 = 0.9f;
         a.b2 = 0.999f;
         a.eps = 1e-8f;
-        adam_corrections(a.b1, a.b2, adam->step, &a.bc1, &a.bc2);
+        a.bc_tab = adam->bc_tab;
+        a.t_idx = adam->t_idx;
         a.w = f32(S.w);
         a.m1 = f32(S.m1);
         a.m2 = f32(S.m2);
@@ -462,59 +471,94 @@ extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch,
   STRY(S.losses.ensure(sizeof(float) * (size_t)(steps > 0 ? steps : 1)));
   cudaStream_t st = ctx->stream;
   STRY(cuda_status(cudaMemsetAsync(ctx->d_err.ptr, 0, 4, st), "clear error"));
-  // Batch it + 1 is generated on a side stream while the network trains on
-  // batch it (slots alternate; a slot is refilled only after the step that
-  // read it); the side stream starts after the work already queued on the
-  // main stream, and the main stream waits for its last batch at the end.
+  // Device step state: the sample base of the next batch of each data slot
+  // and the index of the next step; the AdamW bias corrections of every step
+  // of this call (formed in double on the host as for opmm_surrogate_apply_grad).
+  STRY(S.tstate.ensure(32));
+  STRY(S.bctab.ensure(sizeof(float) * 2 * (size_t)(steps > 0 ? steps : 1)));
+  long long* gbase = S.tstate.as<long long>();
+  int* t_idx = reinterpret_cast<int*>(gbase + 2);
+  {
+    std::vector<float> tab(2 * (size_t)(steps > 0 ? steps : 1));
+    for (int t = 0; t < steps; ++t) adam_corrections(0.9f, 0.999f, S.step + 1 + t, &tab[2 * (size_t)t], &tab[2 * (size_t)t + 1]);
+    const long long init[2] = {(long long)sample_base, (long long)sample_base + batch};
+    STRY(cuda_status(cudaMemcpyAsync(gbase, init, sizeof init, cudaMemcpyHostToDevice, st), "H2D step state"));
+    STRY(cuda_status(cudaMemsetAsync(t_idx, 0, sizeof(int), st), "clear step index"));
+    STRY(cuda_status(cudaMemcpyAsync(S.bctab.ptr, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st), "H2D corrections"));
+    STRY(cuda_status(cudaStreamSynchronize(st), "stage step state"));
+  }
+  // Steps run in pairs replayed from one CUDA graph: while the network
+  // trains on slot 0, the side stream generates slot 1; while it trains on
+  // slot 1, slot 0 is refilled for the next pair (after the step that read
+  // it).  Every per-step quantity comes from the device step state, so the
+  // same graph serves every pair.  Before the first pair, slot 0 is filled;
+  // an odd last step runs without the graph.
   struct Side {
-    cudaStream_t s = nullptr;
-    cudaEvent_t start = nullptr, data[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr}, end = nullptr;
+    cudaStream_t main = nullptr, s = nullptr;
+    cudaEvent_t fork = nullptr, data0 = nullptr, data1 = nullptr, used0 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     ~Side() {
+      if (main) cudaStreamSynchronize(main);
       if (s) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
       }
-      for (cudaEvent_t e : {start, data[0], data[1], used[0], used[1], end})
+      for (cudaEvent_t e : {fork, data0, data1, used0})
         if (e) cudaEventDestroy(e);
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
     }
   } side;
+  side.main = st;
   STRY(cuda_status(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking), "side stream"));
-  for (cudaEvent_t* e : {&side.start, &side.data[0], &side.data[1], &side.used[0], &side.used[1], &side.end})
+  for (cudaEvent_t* e : {&side.fork, &side.data0, &side.data1, &side.used0})
     STRY(cuda_status(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event"));
-  auto gen = [&](int it, int b) -> Status {
-    const long long base = (long long)sample_base + (long long)it * batch;
+  const AdamStep adam{lr, weight_decay, f32(S.bctab), t_idx};
+  auto gen = [&](int b, cudaStream_t s2) -> Status {
     SurrogateState::DataSlot& D = S.slot[b];
-    cudaStream_t s2 = side.s;
-    Status r = cuda_status(gen_desc(data_seed, base, batch, f32(S.cal_amp), f32(S.cal_pulse), kCal, D.sacs.as<DevSac>(),
-                                    f32(D.hidden), f32(D.target), kTrainLcap, s2), "generate");
+    Status r = cuda_status(gen_desc(data_seed, gbase + b, batch, f32(S.cal_amp), f32(S.cal_pulse), kCal,
+                                    D.sacs.as<DevSac>(), f32(D.hidden), f32(D.target), kTrainLcap, s2), "generate");
     if (r.ok())
       r = cuda_status(launch_simulate(f32(D.hidden), batch, D.sacs.as<DevSac>(), nullptr, S.outoff.as<long long>(),
                                       f32(D.traces), s2), "simulate");
-    if (r.ok()) r = cuda_status(add_noise(data_seed, base, D.sacs.as<DevSac>(), batch, f32(D.traces), 0.05f, s2), "noise");
+    if (r.ok()) r = cuda_status(add_noise(data_seed, gbase + b, D.sacs.as<DevSac>(), batch, f32(D.traces), 0.05f, s2), "noise");
     if (r.ok())
       r = cuda_status(featurize(D.sacs.as<DevSac>(), f32(D.traces), batch, bf(D.X), bf(D.Xt), batch, s2), "featurize");
-    if (r.ok()) r = cuda_status(cudaEventRecord(side.data[b], s2), "record");
+    if (r.ok()) r = cuda_status(bump(gbase + b, 2LL * batch, nullptr, s2), "advance sample base");
     return r;
   };
-  STRY(cuda_status(cudaEventRecord(side.start, st), "record"));
-  STRY(cuda_status(cudaStreamWaitEvent(side.s, side.start, 0), "wait"));
-  if (steps > 0) STRY(gen(0, 0));
-  for (int it = 0; it < steps; ++it) {
-    const int b = it & 1;
-    if (it + 1 < steps) {
-      if (it >= 1) STRY(cuda_status(cudaStreamWaitEvent(side.s, side.used[b ^ 1], 0), "wait"));
-      STRY(gen(it + 1, b ^ 1));
-    }
-    STRY(cuda_status(cudaStreamWaitEvent(st, side.data[b], 0), "wait"));
-    const AdamStep step{lr, weight_decay, S.step + 1};
+  auto net = [&](int b, cudaStream_t s1) -> Status {
     SurrogateState::DataSlot& D = S.slot[b];
-    STRY(train_pass(ctx, B, batch, bf(D.X), bf(D.Xt), f32(D.target), f32(S.losses, (size_t)it), &step, st));
-    STRY(cuda_status(cudaEventRecord(side.used[b], st), "record"));
-    S.step += 1;
+    Status r = train_pass(ctx, B, batch, bf(D.X), bf(D.Xt), f32(D.target), f32(S.losses), &adam, s1);
+    if (r.ok()) r = cuda_status(bump(nullptr, 0, t_idx, s1), "advance step index");
+    return r;
+  };
+  if (steps > 0) STRY(gen(0, st));
+  const int pairs = steps / 2;
+  if (pairs > 0) {
+    STRY(cuda_status(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"));
+    Status cs = cuda_status(cudaEventRecord(side.fork, st), "record");
+    if (cs.ok()) cs = cuda_status(cudaStreamWaitEvent(side.s, side.fork, 0), "wait");
+    if (cs.ok()) cs = gen(1, side.s);
+    if (cs.ok()) cs = cuda_status(cudaEventRecord(side.data1, side.s), "record");
+    if (cs.ok()) cs = net(0, st);
+    if (cs.ok()) cs = cuda_status(cudaEventRecord(side.used0, st), "record");
+    if (cs.ok()) cs = cuda_status(cudaStreamWaitEvent(side.s, side.used0, 0), "wait");
+    if (cs.ok()) cs = gen(0, side.s);
+    if (cs.ok()) cs = cuda_status(cudaEventRecord(side.data0, side.s), "record");
+    if (cs.ok()) cs = cuda_status(cudaStreamWaitEvent(st, side.data1, 0), "wait");
+    if (cs.ok()) cs = net(1, st);
+    if (cs.ok()) cs = cuda_status(cudaStreamWaitEvent(st, side.data0, 0), "wait");
+    const cudaError_t ce = cudaStreamEndCapture(st, &side.graph);
+    if (!cs.ok()) return sfail(ctx, cs);
+    STRY(cuda_status(ce, "end capture"));
+    STRY(cuda_status(cudaGraphInstantiate(&side.exec, side.graph, 0), "instantiate"));
+    for (int k = 0; k < pairs; ++k) STRY(cuda_status(cudaGraphLaunch(side.exec, st), "graph launch"));
   }
-  STRY(cuda_status(cudaEventRecord(side.end, side.s), "record"));
-  STRY(cuda_status(cudaStreamWaitEvent(st, side.end, 0), "wait"));
+  if (steps & 1) STRY(net(0, st));
+  S.step += steps;
   if (losses && steps > 0)
     STRY(cuda_status(cudaMemcpyAsync(losses, S.losses.ptr, (size_t)steps * 4, cudaMemcpyDeviceToHost, st), "D2H losses"));
   unsigned e = 0;
