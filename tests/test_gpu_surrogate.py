@@ -171,6 +171,24 @@ def test_training_reduces_loss_and_weights_round_trip(ctx, tmp_path):
     np.testing.assert_array_equal(G.opmm_surrogate_get_params(ctx), p1)
 
 
+def test_training_is_deterministic_and_split_calls_continue_it(ctx):
+    # Steps run in graph-replayed pairs plus a direct odd step, with the
+    # sample bases, the step index and the AdamW corrections in device
+    # memory: five steps in one call must equal three then two (sample_base
+    # continued), bit for bit, in the parameters and in every step's loss.
+    B = 512
+    G.opmm_surrogate_init(ctx, 7)
+    la = G.opmm_surrogate_train(ctx, 5, batch=B, lr=1e-3, data_seed=3)
+    pa = G.opmm_surrogate_get_params(ctx)
+    G.opmm_surrogate_init(ctx, 7)
+    l1 = G.opmm_surrogate_train(ctx, 3, batch=B, lr=1e-3, data_seed=3)
+    l2 = G.opmm_surrogate_train(ctx, 2, batch=B, lr=1e-3, data_seed=3, sample_base=3 * B)
+    pb = G.opmm_surrogate_get_params(ctx)
+    np.testing.assert_array_equal(np.concatenate([l1, l2]), la)
+    np.testing.assert_array_equal(pb, pa)
+    assert np.all(np.isfinite(la)) and np.all(np.isfinite(pa))
+
+
 def test_seeded_fit_stays_in_the_narrowed_box(ctx):
     G.opmm_surrogate_init(ctx, 5)
     G.opmm_surrogate_train(ctx, 50, batch=1024, lr=1e-3, data_seed=12)
