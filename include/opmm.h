@@ -418,7 +418,11 @@ int opmm_surrogate_apply_grad(opmm_ctx* ctx, const float* grad, float lr, float 
  * of 40-400 samples, amplitudes log-uniform in 1-40 deg, both directions,
  * hidden OPC = calibrated nominal x U(0.8, 1.2) per entry, N(0, 0.05^2) deg
  * noise; sample i of step s is drawn from Philox4x32-10 (key data_seed,
- * counter sample_base + s * batch + i).  losses (nullable, host [steps]). */
+ * counter sample_base + s * batch + i).  losses (nullable, host [steps]).
+ * Deterministic: the same initialisation, data_seed and samples give the
+ * same parameters and losses bit for bit, in one call or split over several
+ * calls with sample_base continued.  The call returns when every step is
+ * done (it uses a stream of its own for the data besides the context's). */
 int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch, float lr, float weight_decay,
                          uint64_t data_seed, int64_t sample_base, float* losses);
 /* Box centres the surrogate proposes for n saccades (host descriptors, traces

@@ -4,19 +4,23 @@
 // maps a resampled saccade to an OPC estimate.  Its dense layers run on the
 // 5th-generation tensor cores:
 //
-//   k_gemm_tn   D[M,N] = A[M,K] . B[N,K]^T, BF16 operands, FP32 accumulate.
-//               Warp 4 streams 128x64 tiles of A and B into a 3-stage shared
-//               memory ring with TMA (cp.async.bulk.tensor, 128-byte swizzle);
-//               one thread of warp 5 issues tcgen05.mma (M = 128, N = 128,
-//               K = 16 per instruction) into an FP32 accumulator in tensor
-//               memory and releases each stage with tcgen05.commit; warps 0-3
-//               (one warpgroup, one TMEM lane quarter each) read the
-//               accumulator with tcgen05.ld and apply the epilogue (bias,
-//               GELU, BF16 conversion, optional transposed copy).
+//   k_gemm_tn   D = A . B^T for up to four same-shape problems per launch
+//               (each optionally split into K slices), BF16 operands, FP32
+//               accumulate: a producer warp streams 128 x 64 tiles of A and
+//               BN x 64 tiles of B into a shared-memory ring with TMA
+//               (cp.async.bulk.tensor, 128-byte swizzle), one thread of the
+//               MMA warp issues tcgen05.mma (M = 128, N = BN, K = 16) into a
+//               TMEM accumulator and frees each stage with tcgen05.commit,
+//               and 8 or 16 epilogue warps read the accumulator with
+//               tcgen05.ld, apply the epilogue (bias + GELU with Z and H^T;
+//               GELU' with the rounded error, its transpose and bias-gradient
+//               column sums; plain FP32) and stage the tile for bulk tensor
+//               stores.
 //
-// Around it: the output layer (18 wide, CUDA cores), the loss, GELU backward
-// with deterministic column sums, transposes, AdamW, the on-device training
-// data generator and the featurizer.
+// Around it: the training head (output layer, loss, the layer-3 error, the
+// output layer's gradient partials), the gradient assembly fused with AdamW,
+// the transposes of the BF16 weights, the inference head, the on-device
+// training data generator and the featurizer.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
