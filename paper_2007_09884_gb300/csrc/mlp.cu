@@ -549,28 +549,48 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_train(const __nv_bfloat16
       acc2[1][o] = fmaf(h1.y, w.y, fmaf(h1.x, w.x, acc2[1][o]));
     }
   }
+  // Sum the 36 lane partials (2 rows x 18 outputs) over the warp by a
+  // reduce-scatter: the values as v[2 o + rr] (o < 32, zero past 18); at each
+  // of five levels a lane keeps the half its lane bit selects and adds its
+  // partner's copy of that half (62 shuffles in all), after which lane o holds
+  // output o of both rows.
+  {
+    float v[64];
 #pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
-    const int i = 2 * warp + rr;
-    const int m = r0 + i;
-    const float (&acc)[kOut] = acc2[rr];
-    float l = 0.0f;
+    for (int o = 0; o < 32; ++o) {
+      v[2 * o] = o < kOut ? acc2[0][o] : 0.0f;
+      v[2 * o + 1] = o < kOut ? acc2[1][o] : 0.0f;
+    }
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) {
-      float v = acc[o];
+    for (int lev = 0; lev < 5; ++lev) {
+      const int off = 16 >> lev, half = 32 >> lev;
+      const bool up = (lane & off) != 0;
 #pragma unroll
-      for (int s = 16; s; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-      v += sb5[o];
-      const float d = v - stg[i * kSdyPitch + o];
-      l += d * d;
-      const float g = 2.0f * d / (float)(M * kOut);
-      if (lane == 0) {
-        Y[(size_t)m * kOut + o] = v;
+      for (int j = 0; j < half; ++j) {
+        const float send = up ? v[j] : v[j + half];
+        const float keep = up ? v[j + half] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+    const int o = lane;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int i = 2 * warp + rr;
+      const int m = r0 + i;
+      float l = 0.0f;
+      if (o < kOut) {
+        const float y = v[rr] + sb5[o];
+        const float d = y - stg[i * kSdyPitch + o];
+        l = d * d;
+        const float g = 2.0f * d / (float)(M * kOut);
+        Y[(size_t)m * kOut + o] = y;
         dY[(size_t)m * kOut + o] = g;
         sdy[i * kSdyPitch + o] = g;
       }
+#pragma unroll
+      for (int sft = 16; sft; sft >>= 1) l += __shfl_xor_sync(0xffffffffu, l, sft);
+      if (lane == 0) row_loss[m] = l / (float)(M * kOut);
     }
-    if (lane == 0) row_loss[m] = l / (float)(M * kOut);
   }
   __syncthreads();
   // per column: output-layer gradient partials, dH3, GELU backward
