@@ -514,8 +514,10 @@ static std::vector<std::pair<int, int>> shape_candidates(int lcap, int dim) {
 // Results of probe runs are overwritten by the real run.
 static Status autotune(opmm_plan* p) {
   opmm_ctx* ctx = p->ctx;
+  // the probes run the plan's own iteration count (at most 32), so it is part
+  // of the key, with the model's coordinate count
   const auto key = std::make_tuple(p->lcap, p->S, p->n >= 64 ? 64 : p->n,
-                                   (p->opts.iterations > 0 ? 1 : 0) | (p->dim << 1));
+                                   std::min(p->opts.iterations, 32) * 64 + (p->dim << 1));
   auto it = ctx->tune_cache.find(key);
   auto cands = shape_candidates(p->lcap, p->dim);
   if (cands.empty()) return Status(OPMM_ECUDA, "no launchable search shape (shared memory)");
@@ -547,7 +549,7 @@ static Status autotune(opmm_plan* p) {
   float best_ms = 1e30f;
   std::pair<int, int> best = cands[0];
   constexpr long long kProbeSimplices = 160000;
-  constexpr int kProbeIters = 32;
+  constexpr int kProbeIters = 32;   // also in the cache key above
   const long long want = std::max(1LL, (kProbeSimplices + p->S - 1) / std::max(1, p->S));
   const int stride = (int)std::max(1LL, (long long)p->n / want);
   for (auto& c : cands) {

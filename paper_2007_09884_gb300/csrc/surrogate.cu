@@ -131,8 +131,8 @@ static Status refresh_copies(opmm_ctx* ctx) {
   return cuda_status(pack_params(f32(S.w), (int)kNumParams, AdamLayout{}, bf(S.wb), bf(S.wt), ctx->stream), "pack");
 }
 
-// Hidden layers of M rows from B.X on the tensor cores: Z (pre-activation,
-// FP32), H = GELU(Z) (BF16) and, for training, H's transpose.
+// Hidden layers of M rows from X on the tensor cores: H = GELU(Z) (BF16)
+// and, for training, Z (pre-activations, FP32) and H's transpose.
 static Status forward_hidden(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfloat16* X, bool keep_transposes,
                              cudaStream_t st) {
   SurrogateState& S = *ctx->surrogate;
@@ -151,7 +151,7 @@ static Status forward_hidden(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfl
     p.B = bf(S.wb, (size_t)l * kHidden * kHidden);
     p.bias = f32(S.w, (size_t)l * kLayerParams + (size_t)kHidden * kHidden);
     p.out_bf16 = bf(B.H[l]);
-    p.out_f32 = f32(B.Z[l]);
+    p.out_f32 = keep_transposes ? f32(B.Z[l]) : nullptr;   // Z only for the backward pass
     p.out_t = keep_transposes ? bf(B.Ht[l]) : nullptr;
     Status s = cuda_status(gemm(L, st), "GEMM fwd");
     if (!s.ok()) return s;
