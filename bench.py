@@ -756,8 +756,12 @@ SURROGATE_SCHEDULE = [(800, 2e-3), (800, 1e-3), (500, 5e-4), (341, 2.5e-4)]
 SEEDED_FIT = dict(candidates=1024, iterations=20, box_lo=0.95, box_hi=1.05, init_step=0.025)
 # the plain search that re-fits the seeded search's misses (> 0.1 deg)
 FALLBACK_FIT = dict(candidates=4096, iterations=30)
-# forward 2 (4 512x512 + 18x512) FLOP per sample; backward twice that
-MLP_TRAIN_FLOP_PER_SAMPLE = 3 * 2 * (4 * 512 * 512 + 18 * 512)
+# Network arithmetic per training sample, as the training step performs it:
+# forward 2 (4 x 512 x 512 + 18 x 512); backward: the output layer's weight
+# gradient and dH3 (2 x 2 x 18 x 512), the four hidden weight gradients and
+# the three error products of layers 3, 2, 1 (2 x 7 x 512 x 512; no error
+# product is formed for the input layer)
+MLP_TRAIN_FLOP_PER_SAMPLE = 2 * (4 * 512 * 512 + 18 * 512) + 2 * 2 * 18 * 512 + 2 * 7 * 512 * 512
 
 
 def train_surrogate(G, ctx, quick=False):

@@ -138,3 +138,13 @@ def test_clock_samples_summary():
     d = bench.parse_clock_samples(lines)
     assert d == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
     assert bench.parse_clock_samples([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_surrogate_training_flops_count_the_products_formed():
+    # forward: four 512 x 512 layers and the 18-wide output layer; backward:
+    # the output layer's weight gradient and dH3, four hidden weight
+    # gradients, error products for layers 3, 2, 1 only
+    fwd = 4 * 512 * 512 + 18 * 512
+    bwd = 2 * 18 * 512 + 4 * 512 * 512 + 3 * 512 * 512
+    assert bench.MLP_TRAIN_FLOP_PER_SAMPLE == 2 * (fwd + bwd)
+    assert bench.MLP_TRAIN_FLOP_PER_SAMPLE < 3 * 2 * fwd
