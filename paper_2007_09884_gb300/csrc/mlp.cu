@@ -425,7 +425,12 @@ __global__ void __launch_bounds__(gemm_threads(STAGES), STAGES <= 3 ? 2 : 1)
 // ------------------------------------------------------------------ elementwise / reductions
 // Transposes of the hidden weight matrices: wt_l = wb_l^T for the four
 // 512 x 512 BF16 matrices (blockIdx.z = layer), through a 32 x 32 tile.
-__global__ void k_transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt) {
+// When step_idx is given (the step index of a replayed training sequence),
+// one thread advances it: this kernel follows the step's AdamW, the last
+// reader of the index.
+__global__ void k_transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt, int* step_idx) {
+  if (step_idx && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    *step_idx += 1;
   __shared__ __nv_bfloat16 t[32][34];
   const size_t lo = (size_t)blockIdx.z * kHidden * kHidden;
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
@@ -1104,7 +1109,7 @@ cudaError_t grad_finish(const FinishArgs& a, cudaStream_t st) {
   static_assert(kFinishBiasGroups * 32 + kFinishHeadWGroups * 32 + kOut == kFinishR, "every reduced entry once");
   k_grad_finish<<<kFinishWBlocks + kFinishRBlocks + 1, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && a.adam) e = transpose_layers(a.wb, a.wt, st);
+  if (e == cudaSuccess && a.adam) e = transpose_layers(a.wb, a.wt, st, a.t_idx);
   return e;
 }
 
@@ -1117,8 +1122,8 @@ cudaError_t adam_corrections(float b1, float b2, int step, float* bc1, float* bc
   return cudaSuccess;
 }
 
-cudaError_t transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st) {
-  k_transpose_layers<<<dim3(kHidden / 32, kHidden / 32, kLayers), dim3(32, 8), 0, st>>>(wb, wt);
+cudaError_t transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st, int* step_idx) {
+  k_transpose_layers<<<dim3(kHidden / 32, kHidden / 32, kLayers), dim3(32, 8), 0, st>>>(wb, wt, step_idx);
   return cudaGetLastError();
 }
 

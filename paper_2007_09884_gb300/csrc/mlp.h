@@ -108,8 +108,9 @@ struct AdamLayout {
 // rows' terms) goes into loss[t] when given.  With adam set, each entry's
 // AdamW step follows from its assembled gradient (as k_adamw), and the
 // transposed BF16 copies are refreshed after.  t = *t_idx when t_idx is
-// given (a step of a replayed sequence), else 0; the bias corrections are
-// bc_tab[2 t], bc_tab[2 t + 1] when bc_tab is given, else bc1, bc2.
+// given (a step of a replayed sequence; the transposes then advance it by
+// one), else 0; the bias corrections are bc_tab[2 t], bc_tab[2 t + 1] when
+// bc_tab is given, else bc1, bc2.
 struct FinishArgs {
   const float* wpart;          // [4][ksplit][512][512]
   int ksplit;
@@ -121,7 +122,7 @@ struct FinishArgs {
   const float* row_loss;
   int M;
   float* loss;
-  const int* t_idx;
+  int* t_idx;                  // read by every block; advanced after the AdamW step
   const float* bc_tab;
   float* g;
   int adam;
@@ -146,7 +147,7 @@ cudaError_t head_train(const __nv_bfloat16* H, const __nv_bfloat16* W5, const fl
                        float* dWpart, float* dbpart, cudaStream_t st);
 cudaError_t grad_finish(const FinishArgs& a, cudaStream_t st);
 cudaError_t adam_corrections(float b1, float b2, int step, float* bc1, float* bc2);
-cudaError_t transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st);
+cudaError_t transpose_layers(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st, int* step_idx = nullptr);
 cudaError_t adamw(float* w, const float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
                   float wd, int step, const AdamLayout& L, __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st);
 cudaError_t pack_params(const float* w, int n, const AdamLayout& L, __nv_bfloat16* wb, __nv_bfloat16* wt,

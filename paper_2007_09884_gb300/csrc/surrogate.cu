@@ -174,7 +174,7 @@ static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, cudaStream_t st) {
 // loss terms, output-layer gradient partials, the layer-3 error); the error
 // of layers 2, 1, 0 by GEMMs whose epilogue applies GELU' and rounds
 // (dZ_{l-1} = BF16((dZ_l . W_l) * GELU'(Z_{l-1}))); all four weight gradients
-// dW_l = dZ_l^T . H_{l-1} in one grouped launch over two K slices; the
+// dW_l = dZ_l^T . H_{l-1} in one grouped launch over K slices; the
 // gradient assembly, with the AdamW step of every entry when `adam` is given.
 // AdamW settings of a step of a replayable sequence: the step's index t is
 // read on the device from *t_idx, its bias corrections from bc_tab[2 t],
@@ -182,7 +182,7 @@ static Status forward(opmm_ctx* ctx, MlpBuffers& B, int M, cudaStream_t st) {
 struct AdamStep {
   float lr, wd;
   const float* bc_tab;
-  const int* t_idx;
+  int* t_idx;
 };
 static Status train_pass(opmm_ctx* ctx, MlpBuffers& B, int M, const __nv_bfloat16* X, const __nv_bfloat16* Xt,
                          const float* T, float* loss, const AdamStep* adam, cudaStream_t st) {
@@ -531,9 +531,8 @@ extern "C" int opmm_surrogate_train(opmm_ctx* ctx, int32_t steps, int32_t batch,
   };
   auto net = [&](int b, cudaStream_t s1) -> Status {
     SurrogateState::DataSlot& D = S.slot[b];
-    Status r = train_pass(ctx, B, batch, bf(D.X), bf(D.Xt), f32(D.target), f32(S.losses), &adam, s1);
-    if (r.ok()) r = cuda_status(bump(nullptr, 0, t_idx, s1), "advance step index");
-    return r;
+    // the step index advances in the weight transposes that end the step
+    return train_pass(ctx, B, batch, bf(D.X), bf(D.Xt), f32(D.target), f32(S.losses), &adam, s1);
   };
   if (steps > 0) STRY(gen(0, st));
   const int pairs = steps / 2;
